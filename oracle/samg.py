@@ -1,0 +1,630 @@
+"""FP64 CPU oracle of the self-learning AMG method for extremal singular
+triplets and eigenpairs (H. De Sterck, arXiv:1102.0919).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg may import this module.  It shares no code
+with the GPU library and never imports it.
+
+The oracle is a plain restatement of the paper: every step runs in the
+paper's order with scipy/numpy primitives (sparse and dense products, dense
+QR/SVD/eigh) and the sequential loops of ``oracle.c``.  Where the paper is
+silent the readings below are used (numbers as in the design notes):
+
+* R1/R2  minimal relaxation: block Gauss-Seidel, first Kaczmarz over the rows
+  of A for v (Eq. genSVDresid1), then over the rows of A^t for u
+  (Eq. genSVDresid2); SPD kind: one Kaczmarz sweep over the rows of A-lam*B.
+* R3  sweeps in natural row order of the stored matrix.
+* R4  V(mu_b, mu_b) cycles in the additive phase.
+* R5  random test vectors from SplitMix64 (see oracle.c).
+* R6  coarsest level: max(m_l, n_l) <= coarsest_max, or the coarsening keeps
+  more than 90% of the points, or min(m_c, n_c) < 2 n_b, or max_levels.
+* R7  coarsest additive solve: SVD pseudo-inverse of X - sigma_j Y with the
+  single smallest singular value left out.
+* R8  strength sums run over all columns including the diagonal.
+* R9  Ruge-Stueben ties go to the lowest index.
+* R10 coarse points are numbered in increasing fine index.
+* R11 residual rho_j = sqrt(|A v - s u|^2 + |A^t u - s v|^2) / s for unit
+  u, v; SPD kind |A x - lam x| / |lam|.
+* R13 LS weights |RQ| (dominant) or 1/|RQ| (minimal) multiply the squared
+  residuals; |RQ| is floored at 1e-300.
+* R14 minimal kind: the F-point values are first replaced by one weighted
+  Jacobi step on N x = 0 (N = A A^t, A^t A, or A) with weight
+  omega_J * 2 / g, g the Gershgorin bound of D^-1 N (g = 2, weight omega_J,
+  for 5-point operators).
+* R15 C^i is capped to the n_f - 1 strongest members (ties: lowest index).
+* R16 minimal kind: test vectors are scaled to unit B (C) norm after each
+  block of mu_t relaxations.
+* R21 minimal SVD kind with m >= n: the paper's A A^t-based coarsening of the
+  row variables cannot represent the minimal left singular vectors of the
+  gradient operator (F edges lack same-orientation C neighbours), and
+  Kaczmarz on A^t u = 0 drives row test vectors into null(A^t), the |m-n|
+  spurious zero modes of Thm genSVD.  The rows are therefore coarsened
+  "directly from A" (the option Sec. 3.7 leaves open): P_0 = A Q_0, whose
+  range A range(Q_0) holds u = A v / s for v in range(Q_0); below the
+  finest level A_l = B_l is symmetric, so Sec. 5.2's specialization applies
+  (coarsening on A_l, P_l = Q_l).  Row test vectors are A v_t (finest) or
+  v_t (coarser); the coarse boot u is v_b[C] / s (finest) or u_b[C].
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from . import build as _build
+
+_LIB = None
+
+DEFAULTS = dict(n_t=8, theta=0.06, mu_t=8, mu_b=4, mu_tJ=1, mu_bJ=1, omega_J=0.7,
+                n_mult=10, coarsest_max=100, max_levels=30, seed=20110204)
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        L.oracle_random_block.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, P]
+        L.oracle_random_block.restype = None
+        L.oracle_kaczmarz_sweep.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P, P, P, P, P,
+                                            P, P, P]
+        L.oracle_kaczmarz_sweep.restype = None
+        L.oracle_rs_coarsen.argtypes = [ctypes.c_int32, P, P, P]
+        L.oracle_rs_coarsen.restype = ctypes.c_int
+        L.oracle_ls_fit.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
+        L.oracle_ls_fit.restype = ctypes.c_int64
+        _LIB = L
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _csr(a) -> sp.csr_matrix:
+    """Canonical CSR: sorted column indices, int64 pointers, int32 columns."""
+    a = sp.csr_matrix(a)
+    a.sort_indices()
+    return sp.csr_matrix((np.ascontiguousarray(a.data, dtype=np.float64),
+                          np.ascontiguousarray(a.indices, dtype=np.int32),
+                          np.ascontiguousarray(a.indptr, dtype=np.int64)), shape=a.shape)
+
+
+def _arrs(a: sp.csr_matrix):
+    return (np.ascontiguousarray(a.indptr, dtype=np.int64),
+            np.ascontiguousarray(a.indices, dtype=np.int32),
+            np.ascontiguousarray(a.data, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# primitives
+# --------------------------------------------------------------------------
+
+def random_block(seed: int, nrows: int, nvec: int) -> np.ndarray:
+    """Random test vectors in [-1, 1) (R5, SplitMix64 counter generator)."""
+    out = np.empty((nrows, nvec), dtype=np.float64)
+    _lib().oracle_random_block(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), nrows, nvec, _ptr(out))
+    return out
+
+
+def kaczmarz_sweep(R: sp.csr_matrix, X: np.ndarray, rhs: np.ndarray,
+                   B: sp.csr_matrix | None = None, shift: np.ndarray | None = None) -> None:
+    """One Kaczmarz sweep in natural row order over the rows of R - shift_j B
+    (Sec. 5.3), in place on X (ncols x nb); rhs is nrows x nb."""
+    assert X.flags.c_contiguous and X.dtype == np.float64
+    nb = X.shape[1]
+    rp, rc, rv = _arrs(R)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    if B is not None:
+        bp, bc, bv = _arrs(B)
+        sh = np.ascontiguousarray(shift, dtype=np.float64)
+    else:
+        bp = bc = bv = sh = None
+    _lib().oracle_kaczmarz_sweep(R.shape[0], nb, _ptr(rp), _ptr(rc), _ptr(rv), _ptr(bp),
+                                 _ptr(bc), _ptr(bv), _ptr(sh), _ptr(rhs), _ptr(X))
+
+
+def strength(N: sp.csr_matrix, theta: float) -> sp.csr_matrix:
+    """Strong influences (Eq. strength): i is strongly influenced by j != i
+    iff |n_ij| >= theta * sum_k |n_ik| (k over all columns, R8).  Returns S
+    with S[i, j] = |n_ij| for the strong pairs."""
+    N = _csr(N)
+    absN = abs(N)
+    rowsum = np.asarray(absN.sum(axis=1)).ravel()
+    coo = absN.tocoo()
+    keep = (coo.row != coo.col) & (coo.data >= theta * rowsum[coo.row]) & (coo.data > 0)
+    S = sp.csr_matrix((coo.data[keep], (coo.row[keep], coo.col[keep])), shape=N.shape)
+    return _csr(S)
+
+
+def rs_coarsen(S: sp.csr_matrix) -> np.ndarray:
+    """One-pass Ruge-Stueben coarsening (Algorithm "coarsening"); cf[i]=1 for C."""
+    S = _csr(S)
+    sp_, sc, _ = _arrs(S)
+    cf = np.zeros(S.shape[0], dtype=np.int32)
+    rc = _lib().oracle_rs_coarsen(S.shape[0], _ptr(sp_), _ptr(sc), _ptr(cf))
+    if rc != 0:
+        raise MemoryError("rs_coarsen")
+    return cf
+
+
+def interp_sets(S: sp.csr_matrix, cf: np.ndarray, cap: int):
+    """Coarse interpolatory sets C^i = strong C-point influences of F point i
+    (Sec. 3.7), strongest first, capped to `cap` members (R15)."""
+    S = _csr(S)
+    n = S.shape[0]
+    ptr = [0]
+    cols = []
+    for i in range(n):
+        if cf[i]:
+            ptr.append(len(cols))
+            continue
+        lo, hi = S.indptr[i], S.indptr[i + 1]
+        js = S.indices[lo:hi]
+        ws = S.data[lo:hi]
+        sel = cf[js] == 1
+        js, ws = js[sel], ws[sel]
+        order = np.lexsort((js, -ws))[:cap]
+        cols.extend(int(j) for j in js[order])
+        ptr.append(len(cols))
+    return np.asarray(ptr, dtype=np.int64), np.asarray(cols, dtype=np.int32)
+
+
+def fit_interp(S: sp.csr_matrix, cf: np.ndarray, Yf: np.ndarray, Yc: np.ndarray,
+               w: np.ndarray) -> sp.csr_matrix:
+    """Interpolation operator (Secs. 3.7-3.8): C rows carry a single 1 at the
+    coarse index alpha(i); F rows carry the weighted LS weights of Eq. LS on
+    C^i.  Yf = values used on F points, Yc = values used on C points."""
+    n, nf = Yc.shape
+    ci_ptr, ci_col = interp_sets(S, cf, max(nf - 1, 1))
+    pval = np.zeros(ci_col.size, dtype=np.float64)
+    _lib().oracle_ls_fit(n, nf, _ptr(ci_ptr), _ptr(ci_col),
+                         _ptr(np.ascontiguousarray(Yf, dtype=np.float64)),
+                         _ptr(np.ascontiguousarray(Yc, dtype=np.float64)),
+                         _ptr(np.ascontiguousarray(w, dtype=np.float64)), _ptr(pval))
+    alpha = np.cumsum(cf) - 1          # R10: increasing fine index
+    rows = np.repeat(np.arange(n), np.diff(ci_ptr))
+    crow = np.flatnonzero(cf)
+    r = np.concatenate([crow, rows])
+    c = np.concatenate([alpha[crow], alpha[ci_col]])
+    v = np.concatenate([np.ones(crow.size), pval])
+    return _csr(sp.csr_matrix((v, (r, c)), shape=(n, int(cf.sum()))))
+
+
+# --------------------------------------------------------------------------
+# hierarchy
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Level:
+    """Operators of one level: A (m x n), B (m x m), C (n x n), and the
+    interpolation P (m x m_c), Q (n x n_c) to the next coarser level.  The
+    SPD kind uses A, B, P only (Sec. 5.2)."""
+
+    A: sp.csr_matrix
+    B: sp.csr_matrix
+    C: sp.csr_matrix | None = None
+    P: sp.csr_matrix | None = None
+    Q: sp.csr_matrix | None = None
+
+    def __post_init__(self):
+        self.A = _csr(self.A)
+        self.B = _csr(self.B)
+        self.At = _csr(self.A.T)
+        if self.C is not None:
+            self.C = _csr(self.C)
+
+
+@dataclasses.dataclass
+class Hierarchy:
+    kind: str        # "svd" | "spd"
+    target: str      # "minimal" | "dominant"
+    levels: list
+    params: dict
+
+    @property
+    def spd(self):
+        return self.kind == "spd"
+
+
+def galerkin(L: Level, spd: bool) -> Level:
+    """Coarse operators of Eq. coarseOp: A_c = P^t A Q, B_c = P^t B P,
+    C_c = Q^t C Q (SPD kind: P^t A P, P^t B P)."""
+    P = L.P
+    if spd:
+        return Level(P.T @ L.A @ P, P.T @ L.B @ P)
+    Q = L.Q
+    return Level(P.T @ L.A @ Q, P.T @ L.B @ P, Q.T @ L.C @ Q)
+
+
+# --------------------------------------------------------------------------
+# relaxation (Secs. 3.4, 3.5, 5.3)
+# --------------------------------------------------------------------------
+
+def _cols_norm(M: sp.csr_matrix, X: np.ndarray) -> np.ndarray:
+    return np.sqrt(np.einsum("ij,ij->j", X, M @ X))
+
+
+def relax_boot(L: Level, spd: bool, target: str, sigma, U, V, K, T, omega: float) -> None:
+    """One block Gauss-Seidel relaxation of the boot vectors on
+    A v - s B u = kappa, A^t u - s C v = tau (Eqs. genSVDresid1-2, add) with
+    sigma fixed, in place.  Dominant: one weighted-Jacobi step for u, then
+    for v (Sec. 3.5).  Minimal: Kaczmarz blocks, v from the rows of A, then u
+    from the rows of A^t (Sec. 5.3, R1/R2); SPD: rows of A - lam B."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    if target == "minimal":
+        if spd:
+            kaczmarz_sweep(L.A, U, K, B=L.B, shift=sigma)
+            return
+        kaczmarz_sweep(L.A, V, sigma * (L.B @ U) + K)
+        kaczmarz_sweep(L.At, U, sigma * (L.C @ V) + T)
+        return
+    dB = L.B.diagonal()[:, None]
+    if spd:
+        U -= omega * (L.B @ U - (L.A @ U - K) / sigma) / dB
+        return
+    dC = L.C.diagonal()[:, None]
+    U -= omega * (L.B @ U - (L.A @ V - K) / sigma) / dB
+    V -= omega * (L.C @ V - (L.At @ U - T) / sigma) / dC
+
+
+def relax_test(L: Level, spd: bool, target: str, Ut, Vt, mu_t: int, omega: float) -> None:
+    """mu_t relaxations of the test vectors (Sec. 3.4 power method with one
+    omega-Jacobi inner step, v then u; Sec. 5.3 Kaczmarz on A v = 0 then
+    A^t u = 0 for the minimal kind), in place."""
+    m, n = L.A.shape
+    for _ in range(mu_t):
+        if target == "minimal":
+            if spd:
+                kaczmarz_sweep(L.A, Ut, np.zeros_like(Ut))
+            else:
+                kaczmarz_sweep(L.A, Vt, np.zeros((m, Vt.shape[1])))
+                kaczmarz_sweep(L.At, Ut, np.zeros((n, Ut.shape[1])))
+            continue
+        dB = L.B.diagonal()[:, None]
+        if spd:
+            xb = Ut - omega * (L.B @ Ut - L.A @ Ut) / dB
+            Ut[:] = xb / _cols_norm(L.B, xb)
+            continue
+        dC = L.C.diagonal()[:, None]
+        vb = Vt - omega * (L.C @ Vt - L.At @ Ut) / dC
+        Vt[:] = vb / _cols_norm(L.C, vb)
+        ub = Ut - omega * (L.B @ Ut - L.A @ Vt) / dB
+        Ut[:] = ub / _cols_norm(L.B, ub)
+    if target == "minimal":        # R16
+        Ut /= _cols_norm(L.B, Ut)
+        if not spd:
+            Vt /= _cols_norm(L.C, Vt)
+
+
+def relax_test_v_only(L: Level, Vt, mu_t: int) -> None:
+    """Minimal SVD kind under R21: mu_t Kaczmarz sweeps on A v = 0 for the
+    column test vectors (Sec. 5.3), then unit C norm (R16); the row test
+    vectors are derived from them."""
+    for _ in range(mu_t):
+        kaczmarz_sweep(L.A, Vt, np.zeros((L.A.shape[0], Vt.shape[1])))
+    Vt /= _cols_norm(L.C, Vt)
+
+
+def rayleigh(L: Level, spd: bool, U, V) -> np.ndarray:
+    """Rayleigh quotient (Eq. Rayleigh): u^t A v / (|u|_B |v|_C); SPD:
+    x^t A x / x^t B x."""
+    if spd:
+        return np.einsum("ij,ij->j", U, L.A @ U) / np.einsum("ij,ij->j", U, L.B @ U)
+    return np.einsum("ij,ij->j", U, L.A @ V) / (_cols_norm(L.B, U) * _cols_norm(L.C, V))
+
+
+def relax_boot_rq(L, spd, target, sigma, U, V, mu_b, omega):
+    """Multiplicative-phase boot relaxation: mu_b block-GS steps with
+    kappa = tau = 0, the sigmas updated by the Rayleigh quotient after each
+    (Sec. 3.5); minimal SVD kind flips v_j when its quotient is negative
+    (Sec. 5.3)."""
+    for _ in range(mu_b):
+        Z = np.zeros_like(U)
+        relax_boot(L, spd, target, sigma, U, V, Z, None if spd else np.zeros_like(V), omega)
+        rq = rayleigh(L, spd, U, V)
+        if target == "minimal" and not spd:
+            neg = rq < 0
+            V[:, neg] *= -1.0
+            rq = np.abs(rq)
+        sigma = rq
+    return sigma
+
+
+# --------------------------------------------------------------------------
+# coarsest level (Sec. 3.6, Thm genSVD) and pseudo-inverse solve (Sec. 4.2)
+# --------------------------------------------------------------------------
+
+def dense_XY(L: Level, spd: bool):
+    """X = [[0, A], [A^t, 0]], Y = diag(B, C) of Eq. X (SPD kind: A, B)."""
+    if spd:
+        return L.A.toarray(), L.B.toarray()
+    m, n = L.A.shape
+    A = L.A.toarray()
+    X = np.zeros((m + n, m + n))
+    X[:m, m:] = A
+    X[m:, :m] = A.T
+    Y = np.zeros((m + n, m + n))
+    Y[:m, :m] = L.B.toarray()
+    Y[m:, m:] = L.C.toarray()
+    return X, Y
+
+
+def coarsest_triplets(L: Level, spd: bool, target: str, nb: int):
+    """n_b extremal generalized singular triplets of the coarsest level by the
+    symmetric-definite eigenproblem (X - s Y) z = 0 (Thm genSVD): its l =
+    min(m, n) largest eigenvalues are the s_j >= 0 with z = [u; v] / sqrt(2)
+    for u^t B u = v^t C v = 1.  SPD kind: eigh(A, B)."""
+    X, Y = dense_XY(L, spd)
+    w, Z = sla.eigh(X, Y)
+    if spd:
+        sel = np.arange(nb) if target == "minimal" else np.arange(len(w) - 1, len(w) - 1 - nb, -1)
+        return w[sel].copy(), np.ascontiguousarray(Z[:, sel]), None
+    m, n = L.A.shape
+    l = min(m, n)
+    desc = np.argsort(-w, kind="stable")
+    if target == "dominant":
+        sel = desc[:nb]
+    else:
+        sel = desc[l - nb:l][::-1]          # ascending sigma
+    s = np.sqrt(2.0)
+    return (w[sel].copy(), np.ascontiguousarray(Z[:m, sel] * s),
+            np.ascontiguousarray(Z[m:, sel] * s))
+
+
+def coarsest_pinv_apply(XY, sigma, K, T, spd: bool):
+    """[u; v] = (X - s_j Y)^+ [kappa; tau] per column j, with the SVD
+    pseudo-inverse leaving out the single smallest singular value (Sec. 4.2,
+    R7)."""
+    X, Y = XY
+    rhs = K if spd else np.vstack([K, T])
+    out = np.zeros_like(rhs)
+    for j in range(rhs.shape[1]):
+        Uu, s, Vt = np.linalg.svd(X - sigma[j] * Y)
+        k = len(s) - 1                    # s is descending: drop the last
+        out[:, j] = Vt[:k].T @ ((Uu[:, :k].T @ rhs[:, j]) / s[:k])
+    if spd:
+        return out, None
+    m = K.shape[0]
+    return out[:m], out[m:]
+
+
+# --------------------------------------------------------------------------
+# Ritz step (Sec. 4.3) and residuals (R11)
+# --------------------------------------------------------------------------
+
+def ritz(A: sp.csr_matrix, spd: bool, target: str, U, V):
+    """Ritz projection on the finest level (B = I, C = I): orthonormalise the
+    boot blocks by Householder QR, form M = U^t A V and take its SVD, which is
+    the 2n_b generalized eigenproblem of Eq. genSVDRitz by Thm genSVD.  SPD:
+    eigh(X^t A X).  sigma sorted descending (dominant) / ascending (minimal)."""
+    if spd:
+        Xh, _ = np.linalg.qr(U)
+        M = Xh.T @ (A @ Xh)
+        w, Yv = np.linalg.eigh(M)
+        order = np.arange(len(w)) if target == "minimal" else np.arange(len(w))[::-1]
+        return w[order].copy(), np.ascontiguousarray(Xh @ Yv[:, order]), None
+    Uh, _ = np.linalg.qr(U)
+    Vh, _ = np.linalg.qr(V)
+    M = Uh.T @ (A @ Vh)
+    Yl, s, Zt = np.linalg.svd(M)
+    order = np.arange(len(s)) if target == "dominant" else np.arange(len(s))[::-1]
+    return (s[order].copy(), np.ascontiguousarray(Uh @ Yl[:, order]),
+            np.ascontiguousarray(Vh @ Zt.T[:, order]))
+
+
+def residual_norms(A: sp.csr_matrix, spd: bool, sigma, U, V) -> np.ndarray:
+    """rho_j of R11 for unit vectors."""
+    U = U / np.linalg.norm(U, axis=0)
+    if spd:
+        return np.linalg.norm(A @ U - U * sigma, axis=0) / np.abs(sigma)
+    V = V / np.linalg.norm(V, axis=0)
+    ru = np.linalg.norm(A @ V - U * sigma, axis=0)
+    rv = np.linalg.norm(A.T @ U - V * sigma, axis=0)
+    return np.sqrt(ru ** 2 + rv ** 2) / np.abs(sigma)
+
+
+# --------------------------------------------------------------------------
+# additive V-cycle (Secs. 4.1-4.2)
+# --------------------------------------------------------------------------
+
+def level_residual(L: Level, spd, sigma, U, V, K, T):
+    """r = kappa - (A v - s B u), s = tau - (A^t u - s C v) (Eq. add)."""
+    if spd:
+        return K - (L.A @ U - sigma * (L.B @ U)), None
+    r = K - (L.A @ V - sigma * (L.B @ U))
+    s = T - (L.At @ U - sigma * (L.C @ V))
+    return r, s
+
+
+def vcycle(H: Hierarchy, l: int, sigma, U, V, K, T, coarse_XY=None) -> None:
+    """One additive V-cycle for all columns at once, sigma_j fixed per
+    column (Sec. 4.2), in place on U, V."""
+    spd = H.spd
+    p = H.params
+    L = H.levels[l]
+    if l == len(H.levels) - 1:
+        XY = coarse_XY if coarse_XY is not None else dense_XY(L, spd)
+        u, v = coarsest_pinv_apply(XY, sigma, K, T, spd)
+        U[:] = u
+        if not spd:
+            V[:] = v
+        return
+    for _ in range(p["mu_b"]):
+        relax_boot(L, spd, H.target, sigma, U, V, K, T, p["omega_J"])
+    r, s = level_residual(L, spd, sigma, U, V, K, T)
+    Kc = L.P.T @ r
+    Tc = None if spd else L.Q.T @ s
+    Uc = np.zeros((L.P.shape[1], U.shape[1]))
+    Vc = None if spd else np.zeros((L.Q.shape[1], V.shape[1]))
+    vcycle(H, l + 1, sigma, Uc, Vc, Kc, Tc, coarse_XY)
+    U += L.P @ Uc
+    if not spd:
+        V += L.Q @ Vc
+    for _ in range(p["mu_b"]):
+        relax_boot(L, spd, H.target, sigma, U, V, K, T, p["omega_J"])
+
+
+# --------------------------------------------------------------------------
+# multiplicative phase (Sec. 3.3) and the whole method
+# --------------------------------------------------------------------------
+
+def _fit_weights(rq: np.ndarray, target: str) -> np.ndarray:
+    a = np.maximum(np.abs(rq), 1e-300)
+    return a if target == "dominant" else 1.0 / a
+
+
+def _jacobi_on_N(L: Level, spd: bool, side: str, Y: np.ndarray, omega: float) -> np.ndarray:
+    """One weighted Jacobi step on N x = 0 (R14), N = A A^t (u side), A^t A
+    (v side) or A (SPD kind).  The weight is omega * 2 / g with g the
+    Gershgorin bound max_i sum_k |n_ik| / n_ii of D^-1 N, so that the step
+    damps every mode; g = 2 for the 5-point operators (weight omega)."""
+    if spd:
+        N = L.A
+    elif side == "u":
+        N = _csr(L.A @ L.At)
+    else:
+        N = _csr(L.At @ L.A)
+    d = N.diagonal()
+    g = float(np.max(np.asarray(abs(N).sum(axis=1)).ravel() / d))
+    return Y - (omega * 2.0 / g) * (N @ Y) / d[:, None]
+
+
+def _induced(spd: bool, target: str, shape) -> bool:
+    """R21: the minimal SVD kind with m >= n takes its row (u) interpolation
+    from the column interpolation, P_0 = A Q_0 on the finest level and
+    P_l = Q_l below it (where A_l = B_l by construction)."""
+    return (not spd) and target == "minimal" and shape[0] >= shape[1]
+
+
+def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
+    """Multiplicative (setup) phase: n_mult bootstrap V-cycles (Sec. 3.3).
+    Returns (Hierarchy of the last cycle, sigma_b, U_b, V_b) after the final
+    Ritz step."""
+    p = dict(DEFAULTS)
+    p.update(params or {})
+    spd = kind == "spd"
+    A = _csr(A)
+    m, n = A.shape
+    om = p["omega_J"]
+    induced = _induced(spd, target, A.shape)
+    Ut = random_block(p["seed"], m, p["n_t"])
+    Vt = None if spd else random_block(p["seed"] ^ (1 << 63), n, p["n_t"])
+    if induced:
+        Ut = np.ascontiguousarray(A @ Vt)
+    sigma = Ub = Vb = None
+    levels = []
+    for cyc in range(p["n_mult"]):
+        fine = Level(A, sp.identity(m, format="csr"),
+                     None if spd else sp.identity(n, format="csr"))
+        levels = [fine]
+        ut, vt = Ut, Vt                    # fine test vectors are relaxed in place
+        ub, vb = Ub, Vb
+        while True:
+            L = levels[-1]
+            lvl = len(levels) - 1
+            ml, nl = L.A.shape
+            if max(ml, nl) <= p["coarsest_max"] or len(levels) >= p["max_levels"]:
+                break
+            # coarsening (Sec. 3.7) depends on A_l only
+            if spd:
+                Su = strength(L.A, p["theta"])
+                cfu = rs_coarsen(Su)
+                mc = nc = int(cfu.sum())
+                total_f, total_c = ml, mc
+            elif induced:
+                Sv = strength(L.At @ L.A if lvl == 0 else L.A, p["theta"])
+                cfv = rs_coarsen(Sv)
+                mc = nc = int(cfv.sum())
+                total_f, total_c = ml + nl, 2 * nc
+            else:
+                Su = strength(L.A @ L.At, p["theta"])
+                Sv = strength(L.At @ L.A, p["theta"])
+                cfu, cfv = rs_coarsen(Su), rs_coarsen(Sv)
+                mc, nc = int(cfu.sum()), int(cfv.sum())
+                total_f, total_c = ml + nl, mc + nc
+            if total_c > 0.9 * total_f or min(mc, nc) < 2 * nb:
+                break
+            # relaxation of the test (and, after the first cycle, boot) vectors
+            if induced:
+                relax_test_v_only(L, vt, p["mu_t"])
+                ut = np.ascontiguousarray(L.A @ vt if lvl == 0 else vt)
+            else:
+                relax_test(L, spd, target, ut, vt, p["mu_t"], om)
+            if cyc > 0:
+                sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
+            # LS interpolation (Sec. 3.8) on [U_t, U_b]
+            Uf = ut if cyc == 0 else np.hstack([ut, ub])
+            Vf = None if spd else (vt if cyc == 0 else np.hstack([vt, vb]))
+            rq = rayleigh(L, spd, Uf, Vf if not spd else None)
+            w = _fit_weights(rq, target)
+            if induced:
+                Yv = _jacobi_on_N(L, lvl > 0, "v", Vf, om)
+                L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
+                L.P = _csr(L.A @ L.Q) if lvl == 0 else L.Q
+            else:
+                if target == "minimal":
+                    Yu = _jacobi_on_N(L, spd, "u", Uf, om)
+                    Yv = None if spd else _jacobi_on_N(L, spd, "v", Vf, om)
+                else:
+                    Yu, Yv = Uf, Vf
+                L.P = fit_interp(Su, cfu, Yu, Uf, w)
+                if not spd:
+                    L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
+            levels.append(galerkin(L, spd))
+            # injection to the coarse level
+            if induced:
+                cv = np.flatnonzero(cfv)
+                vt = np.ascontiguousarray(vt[cv])
+                if cyc > 0:
+                    # P_0 = A Q_0: u_b = A v_b / s is interpolated by v_b[C] / s
+                    ub = np.ascontiguousarray(vb[cv] / sigma if lvl == 0 else ub[cv])
+                    vb = np.ascontiguousarray(vb[cv])
+                continue
+            cu = np.flatnonzero(cfu)
+            ut = np.ascontiguousarray(ut[cu])
+            if cyc > 0:
+                ub = np.ascontiguousarray(ub[cu])
+            if not spd:
+                cv = np.flatnonzero(cfv)
+                vt = np.ascontiguousarray(vt[cv])
+                if cyc > 0:
+                    vb = np.ascontiguousarray(vb[cv])
+        # coarsest level: new boot triplets by direct solve (Sec. 3.6)
+        sigma, ub, vb = coarsest_triplets(levels[-1], spd, target, nb)
+        # upward: interpolate (Eq. ranges), relax with RQ updates
+        for l in range(len(levels) - 2, -1, -1):
+            L = levels[l]
+            ub = np.ascontiguousarray(L.P @ ub)
+            if not spd:
+                vb = np.ascontiguousarray(L.Q @ vb)
+            sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
+        sigma, Ub, Vb = ritz(A, spd, target, ub, vb)
+    H = Hierarchy(kind, target, levels, p)
+    return H, sigma, Ub, Vb
+
+
+def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100):
+    """Additive phase (Sec. 4): V-cycle per triplet with sigma_j fixed, then a
+    Ritz step, until max_j rho_j <= tol.  Returns (sigma, U, V, history)
+    where history[i] = rho after i outer iterations."""
+    spd = H.spd
+    A = H.levels[0].A
+    U = np.array(U, dtype=np.float64, order="C")
+    V = None if spd else np.array(V, dtype=np.float64, order="C")
+    sigma = np.array(sigma, dtype=np.float64)
+    XY = dense_XY(H.levels[-1], spd)
+    hist = [residual_norms(A, spd, sigma, U, V)]
+    for _ in range(max_outer):
+        if hist[-1].max() <= tol:
+            break
+        Z = np.zeros_like(U)
+        vcycle(H, 0, sigma, U, V, Z, None if spd else np.zeros_like(V), XY)
+        sigma, U, V = ritz(A, spd, H.target, U, V)
+        hist.append(residual_norms(A, spd, sigma, U, V))
+    return sigma, U, V, hist

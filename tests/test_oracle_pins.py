@@ -1,0 +1,335 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle:
+the paper's printed values, closed forms, the mathematics of each step, and
+dense LAPACK on tiny inputs (called, never retyped)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import oracle
+import workloads as W
+from closed_forms import gradient_singular_values, laplacian5_eigs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- generators
+
+def test_splitmix64_reference_output():
+    # SplitMix64 (Steele, Lea, Flood 2014): first output from state 0 is
+    # 0xE220A8397B1DCDAF; entry (row 0, vector 0) of a block with seed 0 is
+    # 2 * (z >> 11) * 2^-53 - 1 of that output.
+    z = 0xE220A8397B1DCDAF
+    expect = 2.0 * (z >> 11) * 2.0 ** -53 - 1.0
+    assert oracle.random_block(0, 1, 1)[0, 0] == expect
+    blk = oracle.random_block(123, 1000, 3)
+    assert blk.min() >= -1.0 and blk.max() < 1.0
+    assert abs(blk.mean()) < 0.05
+
+
+def test_generators_match_their_definitions():
+    L = W.laplacian5(5).to_scipy().toarray()
+    assert np.allclose(L, L.T)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(L)), laplacian5_eigs(5), rtol=1e-12)
+    G = W.gradient(5).to_scipy()
+    assert G.shape == (2 * 5 * 6, 25)
+    assert np.allclose((G.T @ G).toarray(), L)
+    Le = W.laplacian5(6, 0.3).to_scipy().toarray()
+    assert np.allclose(np.sort(np.linalg.eigvalsh(Le)), laplacian5_eigs(6, 0.3), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- Kaczmarz
+
+def test_kaczmarz_single_row_is_exact_projection():
+    # after projecting row i, a_i . x = b_i exactly (up to rounding)
+    A = sp.csr_matrix(np.array([[2.0, -1.0, 0.5]]))
+    x = np.array([[1.0], [2.0], [3.0]])
+    oracle.kaczmarz_sweep(A, x, np.array([[7.0]]))
+    assert abs((A @ x)[0, 0] - 7.0) < 1e-14
+    # the change is along a_i: x - x0 parallel to (2, -1, 0.5)
+    d = x.ravel() - np.array([1.0, 2.0, 3.0])
+    assert np.allclose(np.cross(d, [2.0, -1.0, 0.5]), 0.0)
+
+
+def test_kaczmarz_is_sequential_not_simultaneous():
+    # hand computation on rows r1 = (1, 1), r2 = (1, -1), b = (2, 0), x0 = 0:
+    # row 1: d = 2/2 -> x = (1, 1); row 2: d = (0 - 0)/2 -> x = (1, 1).
+    # A simultaneous (Cimmino-like) update would give (0.5, 0.5) + (0, 0).
+    A = sp.csr_matrix(np.array([[1.0, 1.0], [1.0, -1.0]]))
+    x = np.zeros((2, 1))
+    oracle.kaczmarz_sweep(A, x, np.array([[2.0], [0.0]]))
+    assert np.allclose(x.ravel(), [1.0, 1.0])
+    # order matters: rows (1, 0), (1, 1) with b = (1, 3), x0 = 0
+    # row 1 -> x = (1, 0); row 2: d = (3 - 1)/2 = 1 -> x = (2, 1)
+    A = sp.csr_matrix(np.array([[1.0, 0.0], [1.0, 1.0]]))
+    x = np.zeros((2, 1))
+    oracle.kaczmarz_sweep(A, x, np.array([[1.0], [3.0]]))
+    assert np.allclose(x.ravel(), [2.0, 1.0])
+
+
+def test_kaczmarz_converges_to_solution_of_consistent_system():
+    rng = np.random.default_rng(1)
+    A = sp.csr_matrix(rng.standard_normal((12, 8)))
+    xs = rng.standard_normal((8, 3))
+    b = A @ xs
+    x = np.zeros((8, 3))
+    for _ in range(3000):
+        oracle.kaczmarz_sweep(A, x, b)
+    assert np.allclose(x, xs, atol=1e-9)
+
+
+def test_kaczmarz_shifted_rows_match_explicit_matrix():
+    # rows of A - s_j B built explicitly give the same sweep as the merged form
+    rng = np.random.default_rng(2)
+    A = sp.random(9, 9, density=0.4, random_state=3, format="csr") + sp.eye(9)
+    B = sp.random(9, 9, density=0.3, random_state=4, format="csr") + sp.eye(9)
+    s = np.array([0.3, -1.2])
+    x1 = rng.standard_normal((9, 2))
+    x2 = x1.copy()
+    rhs = rng.standard_normal((9, 2))
+    oracle.kaczmarz_sweep(oracle.samg._csr(A), x1, rhs, B=oracle.samg._csr(B), shift=s)
+    for j in range(2):
+        R = oracle.samg._csr(A - s[j] * B)
+        xj = np.ascontiguousarray(x2[:, j:j + 1])
+        oracle.kaczmarz_sweep(R, xj, rhs[:, j:j + 1])
+        x2[:, j] = xj[:, 0]
+    assert np.allclose(x1, x2, atol=1e-13)
+
+
+# ---------------------------------------------------------------- coarsening
+
+def test_rs_coarsening_1d_laplacian_hand_computed():
+    # tridiag(-1, 2, -1), n = 7: lambda = (1,2,2,2,2,2,1); pick 1 (C), F = {0, 2},
+    # lambda_3 -> 3; pick 3 (C), F = {4}, lambda_5 -> 3; pick 5 (C), F = {6}.
+    n = 7
+    T = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    S = oracle.strength(T, 0.25)
+    cf = oracle.rs_coarsen(S)
+    assert list(np.flatnonzero(cf)) == [1, 3, 5]
+
+
+def test_rs_coarsening_invariants_2d():
+    A = W.laplacian5(20, 0.4).to_scipy()
+    S = oracle.strength(A, 0.06)
+    cf = oracle.rs_coarsen(S)
+    S = S.tocsr()
+    for i in range(A.shape[0]):
+        js = S.indices[S.indptr[i]:S.indptr[i + 1]]
+        if not cf[i]:
+            assert cf[js].any(), "F point without strong C influence"
+    # C points are an independent set w.r.t. strong influence of earlier picks
+    assert 0.2 < cf.mean() < 0.8
+
+
+def test_strength_definition():
+    N = sp.csr_matrix(np.array([[4.0, -1.0, -0.1], [-1.0, 4.0, -2.0], [-0.1, -2.0, 4.0]]))
+    S = oracle.strength(N, 0.2).toarray()
+    # row 0: sum 5.1, threshold 1.02: only j=1 weak?  |n01| = 1 < 1.02 -> none
+    assert (S[0] == 0).all()
+    # row 1: sum 7, threshold 1.4: j = 2 strong (2), j = 0 weak (1)
+    assert S[1, 2] == 2.0 and S[1, 0] == 0.0
+    # row 2: sum 6.1, threshold 1.22: j = 1 strong
+    assert S[2, 1] == 2.0 and S[2, 0] == 0.0
+
+
+# ---------------------------------------------------------------- LS interpolation
+
+def test_ls_fit_recovers_exact_interpolation():
+    # vectors exactly in range(P*) with P* sparse on the C^i pattern are fitted exactly
+    A = W.laplacian5(10).to_scipy()
+    S = oracle.strength(A, 0.06)
+    cf = oracle.rs_coarsen(S)
+    nc = int(cf.sum())
+    rng = np.random.default_rng(5)
+    ptr, cols = oracle.interp_sets(S, cf, 6)
+    alpha = np.cumsum(cf) - 1
+    Pstar = sp.lil_matrix((A.shape[0], nc))
+    for i in range(A.shape[0]):
+        if cf[i]:
+            Pstar[i, alpha[i]] = 1.0
+        else:
+            for j in cols[ptr[i]:ptr[i + 1]]:
+                Pstar[i, alpha[j]] = rng.uniform(0.1, 1.0)
+    Pstar = Pstar.tocsr()
+    Y = np.ascontiguousarray(Pstar @ rng.standard_normal((nc, 12)))
+    P = oracle.fit_interp(S, cf, Y, Y, rng.uniform(0.5, 2.0, 12))
+    assert np.allclose(P.toarray(), Pstar.toarray(), atol=1e-10)
+
+
+# ---------------------------------------------------------------- Galerkin
+
+def test_galerkin_matches_dense_triple_product():
+    rng = np.random.default_rng(6)
+    A = sp.random(30, 20, density=0.2, random_state=7, format="csr")
+    P = sp.random(30, 9, density=0.3, random_state=8, format="csr")
+    Q = sp.random(20, 7, density=0.3, random_state=9, format="csr")
+    L = oracle.Level(A, sp.identity(30, format="csr"), sp.identity(20, format="csr"))
+    L.P, L.Q = P, Q
+    Lc = oracle.galerkin(L, False)
+    Ad, Pd, Qd = A.toarray(), P.toarray(), Q.toarray()
+    assert np.allclose(Lc.A.toarray(), Pd.T @ Ad @ Qd)
+    assert np.allclose(Lc.B.toarray(), Pd.T @ Pd)
+    assert np.allclose(Lc.C.toarray(), Qd.T @ Qd)
+    x = rng.standard_normal(7)
+    assert np.allclose(Lc.A @ x, P.T @ (A @ (Q @ x)))
+
+
+# ---------------------------------------------------------------- generalized SVD
+
+def _spd(n, seed):
+    r = np.random.default_rng(seed).standard_normal((n, n))
+    return r @ r.T + n * np.eye(n)
+
+
+@pytest.mark.parametrize("m,n", [(9, 6), (6, 9), (7, 7)])
+def test_generalized_svd_theorem(m, n):
+    rng = np.random.default_rng(m * 10 + n)
+    A = rng.standard_normal((m, n))
+    B, C = _spd(m, 1), _spd(n, 2)
+    L = oracle.Level(sp.csr_matrix(A), sp.csr_matrix(B), sp.csr_matrix(C))
+    X, Y = oracle.dense_XY(L, False)
+    w = np.sort(sla.eigh(X, Y, eigvals_only=True))
+    # change of variables D = B^-1/2 A C^-1/2 (proof of the existence theorem)
+    Bh = sla.sqrtm(B).real
+    Ch = sla.sqrtm(C).real
+    D = np.linalg.solve(Bh, A) @ np.linalg.inv(Ch)
+    s = np.linalg.svd(D, compute_uv=False)
+    l = min(m, n)
+    expect = np.sort(np.concatenate([s, -s, np.zeros(m + n - 2 * l)]))
+    assert np.allclose(w, expect, atol=1e-10)
+    for target in ("dominant", "minimal"):
+        sig, U, V = oracle.coarsest_triplets(L, False, target, 3)
+        ref = s[:3] if target == "dominant" else np.sort(s)[:3]
+        assert np.allclose(sig, ref, rtol=1e-10)
+        assert np.allclose(U.T @ B @ U, np.eye(3), atol=1e-10)
+        assert np.allclose(V.T @ C @ V, np.eye(3), atol=1e-10)
+        assert np.allclose(A @ V, B @ U * sig, atol=1e-9)
+        assert np.allclose(A.T @ U, C @ V * sig, atol=1e-9)
+
+
+def test_coarsest_pinv_drops_only_smallest_singular_value():
+    # symmetric diagonal S = X - s Y with Y = I: pinv leaves out the entry of
+    # smallest |d| and inverts the rest
+    d = np.array([3.0, -0.01, 2.0, -5.0])
+    X = np.diag(d + 0.5)
+    Y = np.eye(4)
+    K = np.arange(1.0, 5.0)[:, None]
+    out, _ = oracle.coarsest_pinv_apply((X, Y), np.array([0.5]), K, None, True)
+    expect = K[:, 0] / d
+    expect[1] = 0.0
+    assert np.allclose(out[:, 0], expect)
+
+
+# ---------------------------------------------------------------- Ritz
+
+def test_ritz_exact_on_exact_subspaces():
+    A = W.gradient(8).to_scipy()
+    U, s, Vt = np.linalg.svd(A.toarray(), full_matrices=False)
+    rng = np.random.default_rng(11)
+    idx = np.argsort(s)[:5]
+    R1 = rng.standard_normal((5, 5))
+    R2 = rng.standard_normal((5, 5))
+    sig, Uo, Vo = oracle.ritz(A, False, "minimal", U[:, idx] @ R1, Vt[idx].T @ R2)
+    assert np.allclose(sig, np.sort(s)[:5], rtol=1e-12)
+    assert np.allclose(A @ Vo, Uo * sig, atol=1e-10)
+    idx = np.argsort(-s)[:4]
+    sig, Uo, Vo = oracle.ritz(A, False, "dominant", U[:, idx] @ R1[:4, :4], Vt[idx].T)
+    assert np.allclose(sig, np.sort(s)[::-1][:4], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- additive cycle
+
+def test_additive_equals_multiplicative_when_x_in_range_of_P():
+    # Eq. e: with x in range(P) and an exact coarse solve, one additive
+    # two-level step (no relaxation) returns the exact eigenvector direction.
+    A = W.laplacian5(8).to_scipy()
+    w, X = np.linalg.eigh(A.toarray())
+    x = X[:, 0]
+    rng = np.random.default_rng(3)
+    Pd = np.column_stack([x, rng.standard_normal((64, 5))])
+    L0 = oracle.Level(A, sp.identity(64, format="csr"))
+    L0.P = sp.csr_matrix(Pd)
+    H = oracle.Hierarchy("spd", "minimal", [L0, oracle.galerkin(L0, True)],
+                         dict(oracle.DEFAULTS, mu_b=0))
+    u0 = np.ascontiguousarray((Pd @ rng.standard_normal(6))[:, None])
+    U = u0.copy()
+    oracle.vcycle(H, 0, np.array([w[0]]), U, None, np.zeros_like(U), None)
+    u = U[:, 0] / np.linalg.norm(U[:, 0])
+    assert abs(abs(u @ x) - 1.0) < 1e-10
+
+
+def test_defect_correction_form_equals_paper_form():
+    # R12: relaxation is affine in (iterate, rhs); a V-cycle on the error
+    # equation with zero initial guess, added to the iterate, equals the
+    # V-cycle on the iterate itself (FP64, to rounding).
+    A = W.gradient(12).to_scipy()
+    H, s, U, V = oracle.setup(A, 4, "minimal", "svd",
+                              dict(W.GRAD_PARAMS, n_mult=2, seed=5))
+    U1, V1 = U.copy(), V.copy()
+    oracle.vcycle(H, 0, s, U1, V1, np.zeros_like(U), np.zeros_like(V))
+    r, t = oracle.level_residual(H.levels[0], False, s, U, V, np.zeros_like(U), np.zeros_like(V))
+    Eu, Ev = np.zeros_like(U), np.zeros_like(V)
+    oracle.vcycle(H, 0, s, Eu, Ev, r, t)
+    assert np.allclose(U + Eu, U1, atol=1e-11 * np.abs(U1).max())
+    assert np.allclose(V + Ev, V1, atol=1e-11 * np.abs(V1).max())
+
+
+# ---------------------------------------------------------------- whole method
+
+def _table_fd():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table_values_fd.txt"))
+            if l.strip() and not l.startswith("#")]
+    return np.array([float(r[1]) for r in rows]), np.array([float(r[2]) for r in rows])
+
+
+def test_fd_minimal_matches_paper_table_values():
+    # Sec. 6.2 setting: FD 32x32, 8 minimal eigenpairs, theta = 0.06, n_t = 6,
+    # mu_t = 8, mu_b = 4, 15 multiplicative cycles, then additive cycles.
+    lge, sm = _table_fd()
+    A = W.laplacian5(32).to_scipy() / 33.0 ** 2       # unscaled 4, -1 stencil
+    H, s, U, V = oracle.setup(A, 8, "minimal", "spd", dict(W.FD_PARAMS, seed=W.problem_seed(1)))
+    assert len(H.levels) == 5                           # "Five levels are used"
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-12, max_outer=40)
+    assert hist[-1].max() <= 1e-12
+    assert len(hist) - 1 <= 30                          # machine accuracy in <= 30 cycles
+    assert np.allclose(s, sm, rtol=5e-7)
+    assert np.allclose(s, laplacian5_eigs(32)[:8] / 33.0 ** 2, rtol=1e-12)
+
+
+def test_laplacian_workload_minimal_closed_form():
+    wl = W.workload(1)
+    A = wl.build().to_scipy()
+    H, s, U, V = oracle.setup(A, wl.nb, wl.target, wl.kind,
+                              dict(wl.params, seed=W.problem_seed(1)))
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=40)
+    assert np.allclose(s, laplacian5_eigs(32)[:4], rtol=1e-10)
+    assert np.allclose(U.T @ U, np.eye(4), atol=1e-10)
+
+
+def test_gradient_minimal_closed_form_and_lapack():
+    N = 24
+    A = W.gradient(N).to_scipy()
+    H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(W.GRAD_PARAMS, seed=W.problem_seed(2)))
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=60)
+    assert hist[-1].max() <= 1e-10
+    exact = gradient_singular_values(N)[:8]
+    assert np.allclose(s, exact, rtol=1e-10)
+    lap = np.sort(np.linalg.svd(A.toarray(), compute_uv=False))[:8]
+    assert np.allclose(s, lap, rtol=1e-10)
+    assert np.allclose(A @ V, U * s, atol=1e-8 * s.max())
+    assert np.allclose(A.T @ U, V * s, atol=1e-8 * s.max())
+    assert np.allclose(U.T @ U, np.eye(8), atol=1e-10)
+    assert np.allclose(V.T @ V, np.eye(8), atol=1e-10)
+
+
+def test_dominant_svd_lapack():
+    A = W.laplacian5(16).to_scipy()
+    H, s, U, V = oracle.setup(A, 4, "dominant", "svd",
+                              dict(W.FD_PARAMS, seed=9, coarsest_max=40))
+    assert len(H.levels) >= 3
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-9, max_outer=150)
+    assert hist[-1].max() <= 1e-9
+    ref = np.sort(np.linalg.svd(A.toarray(), compute_uv=False))[::-1][:4]
+    assert np.allclose(s, ref, rtol=1e-10)

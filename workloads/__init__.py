@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs for the self-learning AMG triplet solver.
+
+This module only *builds input matrices* (CSR arrays) and names the seeds.
+It contains none of the method's arithmetic, so both the CPU oracle and the
+GPU library may consume what it produces.
+
+Matrices (0-based CSR, int64 row pointers, int32 sorted column indices,
+float64 values):
+
+* ``laplacian5(N, eps)``  5-point Dirichlet diffusion operator on an N x N
+  interior grid, h = 1/(N+1): diagonal 2(eps+1)/h^2, x-neighbours -eps/h^2,
+  y-neighbours -1/h^2, node (i, j) has index j*N + i.  eps = 1 is the FD
+  Laplacian of the paper's Sec. 6.2 (Table "values", FD columns, scaled by
+  1/h^2).
+* ``gradient(N)``  forward-difference gradient on the same grid: one row per
+  grid edge, values +-1/h, so that gradient(N)^t gradient(N) = laplacian5(N).
+  x-edge rows r = j(N+1)+i (i in [0,N], j in [0,N)), then y-edge rows
+  r = N(N+1) + i(N+1) + j (i in [0,N), j in [0,N]).
+* ``termdoc(m, n, seed)``  term-document-like sparse matrix standing in for
+  the MEDLINE matrix of Sec. 6.4 (the data set is not available): per column
+  a Zipf(1.1) number of distinct uniformly drawn rows truncated to
+  [5, 2000], values float32(log(1 + tf)) with tf ~ Geometric(0.3).
+* ``aniso_batch(count, seed)``  the (N_p, eps_p) list of the batched
+  anisotropic-diffusion workload.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+DEFAULT_SEED = 20110204
+
+
+def problem_seed(config: int, problem: int = 0) -> int:
+    """64-bit seed for one workload: the default seed mixed with the
+    workload id and the problem index (used for the method's random test
+    vectors and for random matrices)."""
+    return ((DEFAULT_SEED << 20) ^ (config << 12) ^ problem) & 0xFFFFFFFFFFFFFFFF
+
+
+@dataclasses.dataclass
+class CSR:
+    """Host CSR matrix: row_ptr int64 (m+1), col int32 (nnz), val float64."""
+
+    m: int
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((self.val, self.col, self.row_ptr), shape=(self.m, self.n))
+
+    @staticmethod
+    def from_scipy(a) -> "CSR":
+        a = a.tocsr()
+        a.sort_indices()
+        return CSR(a.shape[0], a.shape[1], a.indptr.astype(np.int64),
+                   a.indices.astype(np.int32), a.data.astype(np.float64))
+
+
+def _from_triplets(m, n, rows, cols, vals) -> CSR:
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    return CSR(m, n, row_ptr, cols.astype(np.int32), vals)
+
+
+def laplacian5(N: int, eps: float = 1.0) -> CSR:
+    """5-point Dirichlet operator, node (i, j) -> j*N + i (see module doc)."""
+    h2 = float(N + 1) ** 2
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="xy")
+    i = i.ravel()
+    j = j.ravel()
+    node = j * N + i
+    rows = [node]
+    cols = [node]
+    vals = [np.full(node.size, 2.0 * (eps + 1.0) * h2)]
+    for di, dj, w in ((-1, 0, -eps * h2), (1, 0, -eps * h2), (0, -1, -h2), (0, 1, -h2)):
+        ii, jj = i + di, j + dj
+        ok = (ii >= 0) & (ii < N) & (jj >= 0) & (jj < N)
+        rows.append(node[ok])
+        cols.append((jj * N + ii)[ok])
+        vals.append(np.full(int(ok.sum()), w))
+    return _from_triplets(N * N, N * N, np.concatenate(rows), np.concatenate(cols),
+                          np.concatenate(vals))
+
+
+def gradient(N: int) -> CSR:
+    """Forward-difference gradient, m = 2N(N+1) edge rows, n = N^2 nodes."""
+    s = float(N + 1)
+    rows, cols, vals = [], [], []
+    # x-edges: row j(N+1)+i joins node (i-1, j) [-] and node (i, j) [+]
+    i, j = np.meshgrid(np.arange(N + 1), np.arange(N), indexing="xy")
+    i = i.ravel()
+    j = j.ravel()
+    r = j * (N + 1) + i
+    ok = i < N
+    rows.append(r[ok]); cols.append((j * N + i)[ok]); vals.append(np.full(int(ok.sum()), s))
+    ok = i > 0
+    rows.append(r[ok]); cols.append((j * N + i - 1)[ok]); vals.append(np.full(int(ok.sum()), -s))
+    # y-edges: row N(N+1)+i(N+1)+j joins node (i, j-1) [-] and node (i, j) [+]
+    jj, ii = np.meshgrid(np.arange(N + 1), np.arange(N), indexing="xy")
+    ii = ii.ravel()
+    jj = jj.ravel()
+    r = N * (N + 1) + ii * (N + 1) + jj
+    ok = jj < N
+    rows.append(r[ok]); cols.append((jj * N + ii)[ok]); vals.append(np.full(int(ok.sum()), s))
+    ok = jj > 0
+    rows.append(r[ok]); cols.append(((jj - 1) * N + ii)[ok]); vals.append(np.full(int(ok.sum()), -s))
+    return _from_triplets(2 * N * (N + 1), N * N, np.concatenate(rows), np.concatenate(cols),
+                          np.concatenate(vals))
+
+
+def _zipf_truncated_inverse_cdf(u: np.ndarray, s: float, kmin: int, kmax: int) -> np.ndarray:
+    k = np.arange(kmin, kmax + 1, dtype=np.float64)
+    pmf = k ** (-s)
+    cdf = np.cumsum(pmf)
+    cdf /= cdf[-1]
+    idx = np.searchsorted(cdf, u, side="left")
+    return (kmin + np.minimum(idx, kmax - kmin)).astype(np.int64)
+
+
+def termdoc(m: int = 200000, n: int = 50000, seed: int | None = None, s: float = 1.1,
+            kmin: int = 5, kmax: int = 2000, p: float = 0.3) -> CSR:
+    """Synthetic term-document matrix (rows = terms, columns = documents)."""
+    if seed is None:
+        seed = problem_seed(4)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kmax = min(kmax, m)
+    kmin = min(kmin, kmax)
+    k = _zipf_truncated_inverse_cdf(rng.random(n), s, kmin, kmax)
+    rows = np.empty(int(k.sum()), dtype=np.int64)
+    cols = np.repeat(np.arange(n, dtype=np.int64), k)
+    pos = 0
+    for c in range(n):
+        kc = int(k[c])
+        rows[pos:pos + kc] = rng.choice(m, size=kc, replace=False)
+        pos += kc
+    tf = rng.geometric(p, size=rows.size)
+    vals = np.log1p(tf.astype(np.float64)).astype(np.float32).astype(np.float64)
+    return _from_triplets(m, n, rows, cols, vals)
+
+
+def aniso_batch(count: int = 64, seed: int | None = None):
+    """(N_p, eps_p) of the batched anisotropic workload: N_p = round(64*8^(p/63))
+    for p = 0..63 (64..512), eps_p ~ U[1e-3, 1]."""
+    if seed is None:
+        seed = problem_seed(5)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eps = 1e-3 + (1.0 - 1e-3) * rng.random(count)
+    Ns = [int(round(64 * 8 ** (p / 63.0))) for p in range(count)]
+    return list(zip(Ns, [float(e) for e in eps]))
+
+
+# --- the five workloads -----------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    kind: str          # "svd" or "spd"
+    target: str        # "minimal" or "dominant"
+    nb: int
+    params: dict
+    build: object      # callable -> CSR (or list of CSR for the batched workload)
+
+
+FD_PARAMS = dict(n_t=6, theta=0.06, mu_t=8, mu_b=4, n_mult=15)
+GRAD_PARAMS = dict(n_t=16, theta=0.06, mu_t=4, mu_b=4, n_mult=10)
+TD_PARAMS = dict(n_t=14, theta=0.03, mu_t=1, mu_b=4, n_mult=3)
+
+
+def workload(i: int) -> Workload:
+    """Workload i (1..5) with its sizes, target and setup parameters."""
+    if i == 1:
+        return Workload("laplacian5_N32_nb4_minimal", "spd", "minimal", 4, dict(FD_PARAMS),
+                        lambda: laplacian5(32))
+    if i == 2:
+        return Workload("gradient_N256_nb8_minimal", "svd", "minimal", 8, dict(GRAD_PARAMS),
+                        lambda: gradient(256))
+    if i == 3:
+        return Workload("gradient_N1024_nb8_minimal", "svd", "minimal", 8, dict(GRAD_PARAMS),
+                        lambda: gradient(1024))
+    if i == 4:
+        return Workload("termdoc_200000x50000_nb10_dominant", "svd", "dominant", 10,
+                        dict(TD_PARAMS), lambda: termdoc())
+    if i == 5:
+        return Workload("aniso5_64problems_N64to512_nb4_minimal", "spd", "minimal", 4,
+                        dict(FD_PARAMS),
+                        lambda: [laplacian5(N, e) for N, e in aniso_batch()])
+    raise ValueError(i)
