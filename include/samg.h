@@ -1,0 +1,189 @@
+/*
+ * samg.h -- C ABI of the GB300 (sm_103a) solver for a few extremal singular
+ * triplets of a sparse rectangular matrix, or eigenpairs of an SPD matrix, by
+ * the self-learning algebraic multigrid method of H. De Sterck,
+ * "A Self-learning Algebraic Multigrid Method for Extremal Singular Triplets
+ * and Eigenpairs" (arXiv:1102.0919).
+ *
+ * The library runs the multiplicative setup phase (Sec. 3) and the additive
+ * solve phase -- V-cycles with fixed interpolation (Secs. 4.1-4.2) plus the
+ * Ritz step (Sec. 4.3) -- on one GPU.  All arithmetic of the solve phase runs
+ * in the library's CUDA kernels; there is no CPU fallback: every entry point
+ * returns SAMG_E_CUDA when no usable sm_103a device is present.
+ *
+ * Conventions for every entry point:
+ *  - Host matrices are 0-based CSR with int64 row pointers, int32 sorted
+ *    column indices and float64 values.  The library copies what it needs;
+ *    the caller keeps ownership of every pointer it passes.
+ *  - Host vector blocks are row-major: entry i of vector j of an m-row block
+ *    is X[i * n_b + j] (a C-contiguous numpy array of shape (m, n_b)).
+ *  - Device pointers appear only where an argument says "device".
+ *  - A context is used by one host thread at a time.  All GPU work runs on
+ *    the CUDA stream passed at creation (NULL = the legacy default stream).
+ *  - No C++ exception crosses this interface.  A failing call returns a
+ *    status; samg_last_error(ctx) then holds a message.  After SAMG_E_TIMEOUT
+ *    or SAMG_E_CUDA the context is poisoned: only samg_destroy is valid.
+ */
+#ifndef SAMG_H
+#define SAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct samg_ctx samg_ctx; /* opaque; owns all device memory it uses */
+
+typedef enum {
+    SAMG_OK = 0,
+    SAMG_E_INVALID = 1,       /* bad argument, malformed CSR, sizes out of range */
+    SAMG_E_NOMEM = 2,         /* device or host allocation failed */
+    SAMG_E_CUDA = 3,          /* CUDA error or no sm_103a device */
+    SAMG_E_NT_TOO_SMALL = 4,  /* too few test vectors for the LS fits (Sec. 3.8) */
+    SAMG_E_NOT_CONVERGED = 5, /* max_outer reached before the tolerance */
+    SAMG_E_TIMEOUT = 6        /* a device-side wait gave up (bounded spin) */
+} samg_status;
+
+/* dominant: largest singular values (Secs. 3-4); minimal: smallest (Sec. 5.3) */
+typedef enum { SAMG_DOMINANT = 0, SAMG_MINIMAL = 1 } samg_target;
+
+/* SVD of a rectangular A, or eigenpairs of an SPD A (Sec. 5.2: operators A, B, P) */
+typedef enum { SAMG_SVD = 0, SAMG_SPD_EIG = 1 } samg_kind;
+
+/* Arithmetic of the V-cycle.  FP64: everything in float64.  FP32: relaxation,
+ * residual, transfers and coarse levels in float32 on the defect (error)
+ * equation, with the finest-level residual, the correction, the coarsest
+ * solve and the Ritz step in float64. */
+typedef enum { SAMG_FP64 = 0, SAMG_FP32 = 1 } samg_precision;
+
+typedef struct {
+    int32_t m, n;            /* rows, columns */
+    int64_t nnz;
+    const int64_t *row_ptr;  /* host, m + 1 entries, row_ptr[0] = 0 */
+    const int32_t *col;      /* host, nnz entries, sorted within each row */
+    const double *val;       /* host, nnz entries */
+} samg_csr;
+
+typedef struct {
+    int32_t n_t;          /* random test vectors (Sec. 3.3); <= 16 */
+    double theta;         /* strength parameter, Eq. strength */
+    int32_t mu_t, mu_b;   /* relaxations of test / boot vectors per level */
+    int32_t mu_tJ, mu_bJ; /* inner weighted-Jacobi steps (dominant); 1 */
+    double omega_J;       /* Jacobi weight; 0.7 */
+    int32_t n_mult;       /* multiplicative (setup) cycles */
+    int32_t coarsest_max; /* coarsest level when max(m_l, n_l) <= this */
+    int32_t max_levels;
+    uint64_t seed;        /* SplitMix64 seed of the random test vectors */
+    samg_precision prec;  /* arithmetic of the solve-phase V-cycle */
+} samg_params;
+
+/* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
+ * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
+ * seed 20110204, prec SAMG_FP32. */
+void samg_default_params(samg_params *p);
+
+/* ---------------------------------------------------------------- setup --
+ * samg_setup: multiplicative phase (Sec. 3.3): n_mult bootstrap V-cycles
+ * with test-vector relaxation (Secs. 3.4, 5.3), boot relaxation with
+ * Rayleigh-quotient updates (Sec. 3.5), Ruge-Stueben coarsening on the
+ * strength graph of Eq. strength (Sec. 3.7, Algorithm coarsening), weighted
+ * LS interpolation (Sec. 3.8, Eq. LS), Galerkin operators (Eq. coarseOp) on
+ * the GPU, a direct generalized SVD on the coarsest level (Sec. 3.6) and a
+ * Ritz step per cycle.  A is m x n (SVD) or n x n symmetric (SPD_EIG).
+ * n_b in [1, 16], n_b <= min(m, n).  Returns SAMG_E_INVALID for malformed
+ * input, SAMG_E_NT_TOO_SMALL if n_t + n_b < 2. */
+samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind kind,
+                       const samg_params *params, void *cuda_stream, samg_ctx **out);
+
+/* samg_import: build a context from an existing hierarchy instead of running
+ * the setup: the finest A, the interpolation operators P_l (m_l x m_{l+1})
+ * and, for SAMG_SVD, Q_l (n_l x n_{l+1}) for l = 0 .. n_levels-2 (Q is
+ * ignored for SPD_EIG), and the boot triplets (sigma: n_b values, U: m x n_b,
+ * V: n x n_b, V ignored for SPD_EIG).  The library forms the Galerkin
+ * operators A_{l+1} = P^t A_l Q, B_{l+1} = P^t B_l P, C_{l+1} = Q^t C_l Q
+ * (Eq. coarseOp; B_0 = I, C_0 = I) on the GPU. */
+samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, const samg_csr *Q,
+                        int n_b, samg_target target, samg_kind kind, const samg_params *params,
+                        const double *sigma, const double *U, const double *V, void *cuda_stream,
+                        samg_ctx **out);
+
+void samg_destroy(samg_ctx *ctx);
+const char *samg_last_error(const samg_ctx *ctx);
+
+/* ---------------------------------------------------------------- solve --
+ * samg_solve: additive phase (Sec. 4): per outer iteration one V-cycle for
+ * every boot triplet with sigma_j fixed (V(mu_b, mu_b), Kaczmarz block
+ * Gauss-Seidel for minimal, weighted Jacobi block Gauss-Seidel for dominant,
+ * pseudo-inverse of X - sigma_j Y without its smallest singular value on the
+ * coarsest level), then a Ritz step on the finest level (Sec. 4.3), until
+ * max_j rho_j <= tol with rho_j = sqrt(|A v_j - s_j u_j|^2 +
+ * |A^t u_j - s_j v_j|^2) / s_j (SPD: |A x_j - l_j x_j| / l_j).  The state
+ * (sigma, U, V) stays on the device.  *outer_done = iterations run.
+ * Returns SAMG_E_NOT_CONVERGED when max_outer is reached first. */
+samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done);
+
+/* Replace / read the boot triplets (host buffers; V ignored for SPD_EIG).
+ * resid (n_b values, may be NULL) receives rho_j of the current triplets. */
+samg_status samg_set_triplets(samg_ctx *ctx, const double *sigma, const double *U,
+                              const double *V);
+samg_status samg_get_triplets(samg_ctx *ctx, double *sigma, double *U, double *V,
+                              double *resid);
+
+samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec);
+
+/* Hierarchy description: levels, and per level m_l, n_l, nnz(A_l) (arrays of
+ * n_levels entries; pass NULL to query n_levels only). */
+samg_status samg_get_hierarchy_info(const samg_ctx *ctx, int *n_levels, int32_t *m, int32_t *n,
+                                    int64_t *nnz_A);
+
+/* Copy one operator of level l to host CSR buffers.  which: 0 A_l, 1 B_l,
+ * 2 C_l, 3 P_l, 4 Q_l.  With row_ptr == NULL only *rows, *cols, *nnz are set. */
+samg_status samg_get_level_matrix(const samg_ctx *ctx, int level, int which, int32_t *rows,
+                                  int32_t *cols, int64_t *nnz, int64_t *row_ptr, int32_t *col,
+                                  double *val);
+
+/* --------------------------------------------- single steps (host buffers) --
+ * One step of the V-cycle on level l in the context's current precision;
+ * used to compare the GPU path step by step with a reference.  U, V, kappa,
+ * tau, Uc, Vc have m_l / n_l / m_{l+1} / n_{l+1} rows and n_b columns. */
+
+/* count block Gauss-Seidel relaxations of A v - s B u = kappa,
+ * A^t u - s C v = tau (Eqs. genSVDresid1-2, add), in place on U, V. */
+samg_status samg_relax(samg_ctx *ctx, int level, int count, const double *sigma, double *U,
+                       double *V, const double *kappa, const double *tau);
+
+/* r = kappa - (A v - s B u), s = tau - (A^t u - s C v) (Eq. add), then
+ * kappa_c = P^t r, tau_c = Q^t s (Eq. addCoarse). */
+samg_status samg_residual_restrict(samg_ctx *ctx, int level, const double *sigma,
+                                   const double *U, const double *V, const double *kappa,
+                                   const double *tau, double *kappa_c, double *tau_c);
+
+/* U += P Uc, V += Q Vc (Eq. corrAdd). */
+samg_status samg_interpolate(samg_ctx *ctx, int level, double *U, double *V, const double *Uc,
+                             const double *Vc);
+
+/* [U; V] = (X_L - s_j Y_L)^+ [kappa; tau] on the coarsest level with the
+ * smallest singular value left out (Sec. 4.2). */
+samg_status samg_coarsest_solve(samg_ctx *ctx, const double *sigma, const double *kappa,
+                                const double *tau, double *U, double *V);
+
+/* One additive V-cycle on the finest level for all columns with sigma fixed
+ * (Sec. 4.2), in place on U, V. */
+samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V);
+
+/* Ritz step (Sec. 4.3) on host buffers: in/out sigma, U, V; resid = rho_j. */
+samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double *resid);
+
+/* ------------------------------------------- device-level building blocks --
+ * G = X^t Y for two row-major device blocks X, Y (rows x ld, first nb
+ * columns used), G row-major nb x nb on the device; float64.  Uses a
+ * device workspace of (ceil(rows / 4096) * nb * nb) doubles that it
+ * allocates and frees.  stream: CUDA stream or NULL. */
+samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
+                            double *G, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAMG_H */

@@ -1,0 +1,298 @@
+"""Python binding of the GB300 self-learning AMG triplet solver (C ABI in
+include/samg.h).  Argument marshalling only: every step of the setup and
+solve phases runs in the library's CUDA kernels (and its host C++ setup
+code).  Importing this package fails if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsamg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "paper_1102_0919_gb300: compiled library missing at %s; run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` first" % LIB_PATH)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_NT_TOO_SMALL, E_NOT_CONVERGED, E_TIMEOUT = range(7)
+STATUS = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NT_TOO_SMALL", 5: "NOT_CONVERGED",
+          6: "TIMEOUT"}
+DOMINANT, MINIMAL = 0, 1
+SVD, SPD_EIG = 0, 1
+FP64, FP32 = 0, 1
+
+
+class SamgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_t", ctypes.c_int32), ("theta", ctypes.c_double), ("mu_t", ctypes.c_int32),
+                ("mu_b", ctypes.c_int32), ("mu_tJ", ctypes.c_int32), ("mu_bJ", ctypes.c_int32),
+                ("omega_J", ctypes.c_double), ("n_mult", ctypes.c_int32),
+                ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int)]
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_CTX = ctypes.c_void_p
+_I = ctypes.c_int
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+samg_default_params = _sig("samg_default_params", None, ctypes.POINTER(Params))
+samg_setup = _sig("samg_setup", _I, ctypes.POINTER(_Csr), _I, _I, _I, ctypes.POINTER(Params), _P,
+                  ctypes.POINTER(_CTX))
+samg_import = _sig("samg_import", _I, ctypes.POINTER(_Csr), _I, ctypes.POINTER(_Csr),
+                   ctypes.POINTER(_Csr), _I, _I, _I, ctypes.POINTER(Params), _P, _P, _P, _P,
+                   ctypes.POINTER(_CTX))
+samg_destroy = _sig("samg_destroy", None, _CTX)
+samg_last_error = _sig("samg_last_error", ctypes.c_char_p, _CTX)
+samg_solve = _sig("samg_solve", _I, _CTX, ctypes.c_double, _I, ctypes.POINTER(_I))
+samg_set_triplets = _sig("samg_set_triplets", _I, _CTX, _P, _P, _P)
+samg_get_triplets = _sig("samg_get_triplets", _I, _CTX, _P, _P, _P, _P)
+samg_set_precision = _sig("samg_set_precision", _I, _CTX, _I)
+samg_get_hierarchy_info = _sig("samg_get_hierarchy_info", _I, _CTX, ctypes.POINTER(_I), _P, _P, _P)
+samg_get_level_matrix = _sig("samg_get_level_matrix", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
+samg_relax = _sig("samg_relax", _I, _CTX, _I, _I, _P, _P, _P, _P, _P)
+samg_residual_restrict = _sig("samg_residual_restrict", _I, _CTX, _I, _P, _P, _P, _P, _P, _P, _P)
+samg_interpolate = _sig("samg_interpolate", _I, _CTX, _I, _P, _P, _P, _P)
+samg_coarsest_solve = _sig("samg_coarsest_solve", _I, _CTX, _P, _P, _P, _P, _P)
+samg_vcycle = _sig("samg_vcycle", _I, _CTX, _P, _P, _P)
+samg_ritz = _sig("samg_ritz", _I, _CTX, _P, _P, _P, _P)
+samg_block_gram = _sig("samg_block_gram", _I, _P, _P, ctypes.c_int64, _I, _I, _P, _P)
+
+EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
+            "samg_solve", "samg_set_triplets", "samg_get_triplets", "samg_set_precision",
+            "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
+            "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
+            "samg_ritz", "samg_block_gram"]
+
+
+def _arr(x, dtype):
+    return None if x is None else np.ascontiguousarray(x, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(A):
+    """Host CSR view of a scipy CSR matrix or workloads.CSR (arrays kept alive)."""
+    if hasattr(A, "indptr"):
+        A = A.tocsr()
+        A.sort_indices()
+        rp, ci, v, (m, n) = A.indptr, A.indices, A.data, A.shape
+    else:
+        rp, ci, v, m, n = A.row_ptr, A.col, A.val, A.m, A.n
+    rp = _arr(rp, np.int64)
+    ci = _arr(ci, np.int32)
+    v = _arr(v, np.float64)
+    c = _Csr(int(m), int(n), int(rp[-1]), _ptr(rp), _ptr(ci), _ptr(v))
+    c._keep = (rp, ci, v)
+    return c
+
+
+def make_params(**kw) -> Params:
+    p = Params()
+    samg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "prec":
+            v = {"fp64": FP64, "fp32": FP32}.get(v, v)
+        setattr(p, k, v)
+    return p
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+class Solver:
+    """One solver context (owns its device memory)."""
+
+    def __init__(self, ctx, nb, kind, target, m, n):
+        self._ctx = ctx
+        self.nb, self.kind, self.target, self.m, self.n = nb, kind, target, m, n
+
+    # ---------------------------------------------------------- creation
+    @classmethod
+    def setup(cls, A, nb, target="minimal", kind="svd", stream=None, **params):
+        t = MINIMAL if target == "minimal" else DOMINANT
+        k = SPD_EIG if kind == "spd" else SVD
+        c = _csr(A)
+        p = make_params(**params)
+        ctx = _CTX()
+        st = samg_setup(ctypes.byref(c), nb, t, k, ctypes.byref(p), _stream(stream), ctypes.byref(ctx))
+        if st != OK:
+            raise SamgError(st, samg_last_error(None).decode())
+        return cls(ctx, nb, k, t, c.m, c.n)
+
+    @classmethod
+    def from_hierarchy(cls, A, Ps, Qs, nb, sigma, U, V, target="minimal", kind="svd",
+                       stream=None, **params):
+        t = MINIMAL if target == "minimal" else DOMINANT
+        k = SPD_EIG if kind == "spd" else SVD
+        c = _csr(A)
+        P = (_Csr * len(Ps))(*[_csr(x) for x in Ps])
+        keep = [P]
+        if k == SVD:
+            Q = (_Csr * len(Qs))(*[_csr(x) for x in Qs])
+            keep.append(Q)
+        else:
+            Q = P
+        p = make_params(**params)
+        s = _arr(sigma, np.float64)
+        u = _arr(U, np.float64)
+        v = _arr(V, np.float64)
+        ctx = _CTX()
+        st = samg_import(ctypes.byref(c), len(Ps) + 1, P, Q, nb, t, k, ctypes.byref(p), _ptr(s),
+                         _ptr(u), _ptr(v), _stream(stream), ctypes.byref(ctx))
+        if st != OK:
+            raise SamgError(st, samg_last_error(None).decode())
+        return cls(ctx, nb, k, t, c.m, c.n)
+
+    def close(self):
+        if self._ctx:
+            samg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise SamgError(st, samg_last_error(self._ctx).decode())
+
+    # ---------------------------------------------------------- queries
+    @property
+    def spd(self):
+        return self.kind == SPD_EIG
+
+    @property
+    def mu(self):
+        return self.n if self.spd else self.m
+
+    def levels(self):
+        nl = ctypes.c_int(0)
+        self._check(samg_get_hierarchy_info(self._ctx, ctypes.byref(nl), None, None, None))
+        m = np.zeros(nl.value, np.int32)
+        n = np.zeros(nl.value, np.int32)
+        z = np.zeros(nl.value, np.int64)
+        self._check(samg_get_hierarchy_info(self._ctx, ctypes.byref(nl), _ptr(m), _ptr(n), _ptr(z)))
+        return [(int(a), int(b), int(c)) for a, b, c in zip(m, n, z)]
+
+    def level_matrix(self, level, which):
+        """(row_ptr, col, val, shape) of A_l (0), B_l (1), C_l (2), P_l (3), Q_l (4)."""
+        w = {"A": 0, "B": 1, "C": 2, "P": 3, "Q": 4}.get(which, which)
+        r, c, z = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        self._check(samg_get_level_matrix(self._ctx, level, w, ctypes.byref(r), ctypes.byref(c),
+                                          ctypes.byref(z), None, None, None))
+        rp = np.zeros(r.value + 1, np.int64)
+        ci = np.zeros(max(z.value, 1), np.int32)
+        v = np.zeros(max(z.value, 1), np.float64)
+        self._check(samg_get_level_matrix(self._ctx, level, w, ctypes.byref(r), ctypes.byref(c),
+                                          ctypes.byref(z), _ptr(rp), _ptr(ci), _ptr(v)))
+        return rp, ci[:z.value], v[:z.value], (r.value, c.value)
+
+    def set_precision(self, prec):
+        self._check(samg_set_precision(self._ctx, {"fp64": FP64, "fp32": FP32}.get(prec, prec)))
+
+    # ---------------------------------------------------------- solve
+    def solve(self, tol=1e-8, max_outer=100):
+        done = ctypes.c_int(0)
+        st = samg_solve(self._ctx, tol, max_outer, ctypes.byref(done))
+        if st not in (OK, E_NOT_CONVERGED):
+            self._check(st)
+        return st == OK, done.value
+
+    def triplets(self):
+        s = np.zeros(self.nb)
+        r = np.zeros(self.nb)
+        U = np.zeros((self.mu, self.nb))
+        V = None if self.spd else np.zeros((self.n, self.nb))
+        self._check(samg_get_triplets(self._ctx, _ptr(s), _ptr(U), _ptr(V), _ptr(r)))
+        return s, U, V, r
+
+    def set_triplets(self, sigma, U, V=None):
+        s, u, v = _arr(sigma, np.float64), _arr(U, np.float64), _arr(V, np.float64)
+        self._check(samg_set_triplets(self._ctx, _ptr(s), _ptr(u), _ptr(v)))
+
+    # ---------------------------------------------------------- single steps
+    def relax(self, level, sigma, U, V, K=None, T=None, count=1):
+        U = np.array(U, dtype=np.float64, order="C")
+        V = None if V is None else np.array(V, dtype=np.float64, order="C")
+        s, k, t = _arr(sigma, np.float64), _arr(K, np.float64), _arr(T, np.float64)
+        self._check(samg_relax(self._ctx, level, count, _ptr(s), _ptr(U), _ptr(V), _ptr(k), _ptr(t)))
+        return U, V
+
+    def residual_restrict(self, level, sigma, U, V, K, T, mc, nc):
+        s, u, v, k, t = (_arr(x, np.float64) for x in (sigma, U, V, K, T))
+        Kc = np.zeros((mc, self.nb))
+        Tc = None if self.spd else np.zeros((nc, self.nb))
+        self._check(samg_residual_restrict(self._ctx, level, _ptr(s), _ptr(u), _ptr(v), _ptr(k),
+                                           _ptr(t), _ptr(Kc), _ptr(Tc)))
+        return Kc, Tc
+
+    def interpolate(self, level, U, V, Uc, Vc):
+        U = np.array(U, dtype=np.float64, order="C")
+        V = None if V is None else np.array(V, dtype=np.float64, order="C")
+        uc, vc = _arr(Uc, np.float64), _arr(Vc, np.float64)
+        self._check(samg_interpolate(self._ctx, level, _ptr(U), _ptr(V), _ptr(uc), _ptr(vc)))
+        return U, V
+
+    def coarsest_solve(self, sigma, K, T, mL, nL):
+        s, k, t = _arr(sigma, np.float64), _arr(K, np.float64), _arr(T, np.float64)
+        U = np.zeros((mL, self.nb))
+        V = None if self.spd else np.zeros((nL, self.nb))
+        self._check(samg_coarsest_solve(self._ctx, _ptr(s), _ptr(k), _ptr(t), _ptr(U), _ptr(V)))
+        return U, V
+
+    def vcycle(self, sigma, U, V=None):
+        U = np.array(U, dtype=np.float64, order="C")
+        V = None if V is None else np.array(V, dtype=np.float64, order="C")
+        s = _arr(sigma, np.float64)
+        self._check(samg_vcycle(self._ctx, _ptr(s), _ptr(U), _ptr(V)))
+        return U, V
+
+    def ritz(self, U, V=None):
+        U = np.array(U, dtype=np.float64, order="C")
+        V = None if V is None else np.array(V, dtype=np.float64, order="C")
+        s = np.zeros(self.nb)
+        r = np.zeros(self.nb)
+        self._check(samg_ritz(self._ctx, _ptr(s), _ptr(U), _ptr(V), _ptr(r)))
+        return s, U, V, r
+
+
+def block_gram(X_ptr, Y_ptr, rows, nb, ld, G_ptr, stream=None):
+    """G = X^t Y for device blocks (raw device pointers as ints)."""
+    st = samg_block_gram(ctypes.c_void_p(X_ptr), ctypes.c_void_p(Y_ptr), rows, nb, ld,
+                         ctypes.c_void_p(G_ptr), _stream(stream))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())

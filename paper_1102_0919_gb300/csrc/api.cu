@@ -1,0 +1,526 @@
+// api.cu -- the C ABI (include/samg.h): context creation from a hierarchy or
+// by the setup phase, the solve loop, and single-step entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+
+using namespace samg;
+
+namespace {
+
+samg_status fail(samg_ctx *c, samg_status st, const std::string &msg) {
+    if (c) {
+        c->err = msg;
+        if (st == SAMG_E_CUDA || st == SAMG_E_TIMEOUT) c->poisoned = true;
+    }
+    return st;
+}
+
+template <typename F>
+samg_status guarded(samg_ctx *c, F &&f) {
+    if (c && c->poisoned) return fail(c, SAMG_E_INVALID, "context is poisoned by an earlier error");
+    try {
+        f();
+        return SAMG_OK;
+    } catch (const Error &e) {
+        return fail(c, e.status, e.what());
+    } catch (const std::bad_alloc &) {
+        return fail(c, SAMG_E_NOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(c, SAMG_E_INVALID, e.what());
+    }
+}
+
+thread_local std::string g_create_error;
+
+void check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    SAMG_CHECK(e == cudaSuccess && n > 0, SAMG_E_CUDA, "no CUDA device available");
+    int dev = 0;
+    SAMG_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp p;
+    SAMG_CUDA(cudaGetDeviceProperties(&p, dev));
+    SAMG_CHECK(p.major == 10 && p.minor == 3, SAMG_E_CUDA,
+               "this library is built for sm_103a (GB300) only");
+}
+
+void check_common(int n_b, const samg_params *prm) {
+    SAMG_CHECK(n_b >= 1 && n_b <= 16, SAMG_E_INVALID, "n_b must be in [1, 16]");
+    SAMG_CHECK(prm != nullptr, SAMG_E_INVALID, "params is NULL");
+    SAMG_CHECK(prm->mu_b >= 0 && prm->mu_t >= 0, SAMG_E_INVALID, "negative relaxation count");
+    SAMG_CHECK(prm->prec == SAMG_FP64 || prm->prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
+}
+
+template <typename T>
+void put_level(samg_ctx &c, const double *h, int rows, DBuf<T> &d);
+template <>
+void put_level<double>(samg_ctx &c, const double *h, int rows, DBuf<double> &d) {
+    if (h) put_block(c, h, rows, d);
+    else d.zero(c.stream);
+}
+template <>
+void put_level<float>(samg_ctx &c, const double *h, int rows, DBuf<float> &d) {
+    if (!h) { d.zero(c.stream); return; }
+    DBuf<double> tmp((size_t)std::max(rows, 1) * c.ld);
+    tmp.zero(c.stream);
+    put_block(c, h, rows, tmp);
+    launch_convert<double, float>((size_t)rows * c.ld, tmp.p, d.p, c.stream);
+    SAMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+template <typename T>
+void get_level(samg_ctx &c, const DBuf<T> &d, int rows, double *h);
+template <>
+void get_level<double>(samg_ctx &c, const DBuf<double> &d, int rows, double *h) {
+    if (!h) return;
+    get_block(c, d, rows, h);
+    SAMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+template <>
+void get_level<float>(samg_ctx &c, const DBuf<float> &d, int rows, double *h) {
+    if (!h) return;
+    DBuf<double> tmp((size_t)std::max(rows, 1) * c.ld);
+    launch_convert<float, double>((size_t)rows * c.ld, d.p, tmp.p, c.stream);
+    get_block(c, tmp, rows, h);
+    SAMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void set_sigma(samg_ctx &c, const double *sigma) {
+    SAMG_CHECK(sigma != nullptr, SAMG_E_INVALID, "sigma is NULL");
+    std::vector<double> sg(c.ld, 1.0);
+    for (int j = 0; j < c.nb; ++j) sg[j] = sigma[j];
+    c.sigma.upload(sg.data(), c.ld, c.stream);
+}
+
+int urows(const samg_ctx &c, int l) { return c.spd() ? c.L[l].n : c.L[l].m; }
+
+void check_level(const samg_ctx &c, int l, bool need_coarser) {
+    SAMG_CHECK(l >= 0 && l < c.nlev(), SAMG_E_INVALID, "level out of range");
+    SAMG_CHECK(!need_coarser || l + 1 < c.nlev(), SAMG_E_INVALID, "level has no coarser level");
+}
+
+template <typename T>
+void step_relax(samg_ctx &c, int l, int count, double *U, double *V, const double *K,
+                const double *Tt) {
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    put_level<T>(c, U, urows(c, l), w.u);
+    put_level<T>(c, K, urows(c, l), w.k);
+    if (!c.spd()) {
+        put_level<T>(c, V, L.n, w.v);
+        put_level<T>(c, Tt, L.n, w.t);
+    }
+    for (int k = 0; k < count; ++k) relax<T>(c, l);
+    get_level<T>(c, w.u, urows(c, l), U);
+    if (!c.spd()) get_level<T>(c, w.v, L.n, V);
+}
+
+template <typename T>
+void step_restrict(samg_ctx &c, int l, const double *U, const double *V, const double *K,
+                   const double *Tt, double *Kc, double *Tc) {
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    put_level<T>(c, U, urows(c, l), w.u);
+    put_level<T>(c, K, urows(c, l), w.k);
+    if (!c.spd()) {
+        put_level<T>(c, V, L.n, w.v);
+        put_level<T>(c, Tt, L.n, w.t);
+    }
+    residual_restrict<T>(c, l);
+    Work<T> &wc = work<T>(c.L[l + 1]);
+    get_level<T>(c, wc.k, urows(c, l + 1), Kc);
+    if (!c.spd()) get_level<T>(c, wc.t, c.L[l + 1].n, Tc);
+}
+
+template <typename T>
+void step_interp(samg_ctx &c, int l, double *U, double *V, const double *Uc, const double *Vc) {
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    Work<T> &wc = work<T>(c.L[l + 1]);
+    put_level<T>(c, U, urows(c, l), w.u);
+    put_level<T>(c, Uc, urows(c, l + 1), wc.u);
+    if (!c.spd()) {
+        put_level<T>(c, V, L.n, w.v);
+        put_level<T>(c, Vc, c.L[l + 1].n, wc.v);
+    }
+    interpolate<T>(c, l);
+    get_level<T>(c, w.u, urows(c, l), U);
+    if (!c.spd()) get_level<T>(c, w.v, L.n, V);
+}
+
+template <typename T>
+void step_coarse(samg_ctx &c, const double *K, const double *Tt, double *U, double *V) {
+    int l = c.nlev() - 1;
+    Work<T> &w = work<T>(c.L[l]);
+    put_level<T>(c, K, urows(c, l), w.k);
+    if (!c.spd()) put_level<T>(c, Tt, c.L[l].n, w.t);
+    coarse_solve<T>(c);
+    get_level<T>(c, w.u, urows(c, l), U);
+    if (!c.spd()) get_level<T>(c, w.v, c.L[l].n, V);
+}
+
+void set_triplets_impl(samg_ctx &c, const double *sigma, const double *U, const double *V) {
+    SAMG_CHECK(U != nullptr && (c.spd() || V != nullptr), SAMG_E_INVALID, "U or V is NULL");
+    set_sigma(c, sigma);
+    c.U.zero(c.stream);
+    put_block(c, U, urows(c, 0), c.U);
+    if (!c.spd()) {
+        c.V.zero(c.stream);
+        put_block(c, V, c.L[0].n, c.V);
+    }
+    ritz(c, true);
+    SAMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+}  // namespace
+
+namespace samg {
+// All Kaczmarz schedules of a context report timeouts in rstat[1].
+void share_error_word(samg_ctx &c) {
+    for (auto &L : c.L) {
+        L.kA.err = c.rstat.p + 1;
+        L.kAt.err = c.rstat.p + 1;
+    }
+}
+}  // namespace samg
+
+namespace {
+
+void check_kaczmarz(samg_ctx &c) {
+    int e = 0;
+    SAMG_CUDA(cudaMemcpyAsync(&e, c.rstat.p + 1, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    SAMG_CUDA(cudaStreamSynchronize(c.stream));
+    SAMG_CHECK(e == 0, SAMG_E_TIMEOUT, "Kaczmarz sweep: a cross-band wait timed out");
+}
+
+}  // namespace
+
+extern "C" {
+
+void samg_default_params(samg_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_t = 8;
+    p->theta = 0.06;
+    p->mu_t = 8;
+    p->mu_b = 4;
+    p->mu_tJ = 1;
+    p->mu_bJ = 1;
+    p->omega_J = 0.7;
+    p->n_mult = 10;
+    p->coarsest_max = 100;
+    p->max_levels = 30;
+    p->seed = 20110204ull;
+    p->prec = SAMG_FP32;
+}
+
+const char *samg_last_error(const samg_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void samg_destroy(samg_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream == nullptr || true) cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+}
+
+samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, const samg_csr *Q,
+                        int n_b, samg_target target, samg_kind kind, const samg_params *params,
+                        const double *sigma, const double *U, const double *V, void *cuda_stream,
+                        samg_ctx **out) {
+    if (!out) return SAMG_E_INVALID;
+    *out = nullptr;
+    samg_ctx *c = new (std::nothrow) samg_ctx();
+    if (!c) return SAMG_E_NOMEM;
+    samg_status st = guarded(c, [&] {
+        check_device();
+        check_common(n_b, params);
+        SAMG_CHECK(A != nullptr && n_levels >= 2 && P != nullptr, SAMG_E_INVALID,
+                   "import needs A, P and at least two levels");
+        SAMG_CHECK(kind == SAMG_SPD_EIG || Q != nullptr, SAMG_E_INVALID, "import: Q is NULL");
+        c->stream = (cudaStream_t)cuda_stream;
+        c->kind = kind;
+        c->target = target;
+        c->prm = *params;
+        c->nb = n_b;
+        c->ld = block_ld(n_b);
+        SAMG_CHECK(kind != SAMG_SPD_EIG || A->m == A->n, SAMG_E_INVALID, "SPD_EIG needs square A");
+        SAMG_CHECK(n_b <= std::min(A->m, A->n), SAMG_E_INVALID, "n_b > min(m, n)");
+        c->L.resize(n_levels);
+        upload_csr(*A, c->L[0].A, c->stream);
+        for (int l = 0; l + 1 < n_levels; ++l) {
+            const int rows_u = l == 0 ? (kind == SAMG_SPD_EIG ? A->n : A->m) : P[l - 1].n;
+            SAMG_CHECK(P[l].m == rows_u, SAMG_E_INVALID, "P_l has the wrong number of rows");
+            upload_csr(P[l], c->L[l].P, c->stream);
+            if (kind != SAMG_SPD_EIG) {
+                const int rows_v = l == 0 ? A->n : Q[l - 1].n;
+                SAMG_CHECK(Q[l].m == rows_v, SAMG_E_INVALID, "Q_l has the wrong number of rows");
+                upload_csr(Q[l], c->L[l].Q, c->stream);
+            }
+        }
+        build_galerkin(*c);
+        finalize_hierarchy(*c);
+        alloc_finest_state(*c);
+        share_error_word(*c);
+        set_triplets_impl(*c, sigma, U, V);
+    });
+    if (st != SAMG_OK) {
+        g_create_error = c->err;
+        delete c;
+        return st;
+    }
+    *out = c;
+    return SAMG_OK;
+}
+
+samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind kind,
+                       const samg_params *params, void *cuda_stream, samg_ctx **out) {
+    if (!out) return SAMG_E_INVALID;
+    *out = nullptr;
+    samg_ctx *c = new (std::nothrow) samg_ctx();
+    if (!c) return SAMG_E_NOMEM;
+    samg_status st = guarded(c, [&] {
+        check_device();
+        check_common(n_b, params);
+        SAMG_CHECK(A != nullptr, SAMG_E_INVALID, "A is NULL");
+        SAMG_CHECK(kind != SAMG_SPD_EIG || A->m == A->n, SAMG_E_INVALID, "SPD_EIG needs square A");
+        SAMG_CHECK(n_b <= std::min(A->m, A->n), SAMG_E_INVALID, "n_b > min(m, n)");
+        SAMG_CHECK(params->n_t + n_b >= 2, SAMG_E_NT_TOO_SMALL, "n_t + n_b < 2");
+        SAMG_CHECK(params->n_t >= 1 && params->n_t <= 16, SAMG_E_INVALID, "n_t must be in [1, 16]");
+        c->stream = (cudaStream_t)cuda_stream;
+        c->kind = kind;
+        c->target = target;
+        c->prm = *params;
+        c->nb = n_b;
+        c->ld = block_ld(n_b);
+        host_setup(*c, *A);
+    });
+    if (st != SAMG_OK) {
+        g_create_error = c->err;
+        delete c;
+        return st;
+    }
+    *out = c;
+    return SAMG_OK;
+}
+
+samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(prec == SAMG_FP64 || prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
+        ctx->prm.prec = prec;
+    });
+}
+
+samg_status samg_set_triplets(samg_ctx *ctx, const double *sigma, const double *U,
+                              const double *V) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] { set_triplets_impl(*ctx, sigma, U, V); });
+}
+
+samg_status samg_get_triplets(samg_ctx *ctx, double *sigma, double *U, double *V,
+                              double *resid) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        samg_ctx &c = *ctx;
+        std::vector<double> sg(c.ld), rs(c.ld);
+        c.sigma.download(sg.data(), c.ld, c.stream);
+        c.resid.download(rs.data(), c.ld, c.stream);
+        if (U) get_block(c, c.U, urows(c, 0), U);
+        if (V && !c.spd()) get_block(c, c.V, c.L[0].n, V);
+        SAMG_CUDA(cudaStreamSynchronize(c.stream));
+        if (sigma) std::copy(sg.begin(), sg.begin() + c.nb, sigma);
+        if (resid) std::copy(rs.begin(), rs.begin() + c.nb, resid);
+    });
+}
+
+samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done) {
+    if (!ctx) return SAMG_E_INVALID;
+    int done = 0;
+    bool converged = false;
+    samg_status st = guarded(ctx, [&] {
+        samg_ctx &c = *ctx;
+        SAMG_CHECK(max_outer >= 0 && tol > 0.0, SAMG_E_INVALID, "bad tol or max_outer");
+        std::vector<double> rs(c.ld);
+        for (;;) {
+            c.resid.download(rs.data(), c.ld, c.stream);
+            SAMG_CUDA(cudaStreamSynchronize(c.stream));
+            double mx = 0.0;
+            bool finite = true;
+            for (int j = 0; j < c.nb; ++j) {
+                finite = finite && std::isfinite(rs[j]);
+                mx = std::max(mx, rs[j]);
+            }
+            if (!finite) check_kaczmarz(c);
+            SAMG_CHECK(finite, SAMG_E_INVALID, "non-finite residual");
+            if (mx <= tol) { converged = true; break; }
+            if (done >= max_outer) break;
+            if (c.prm.prec == SAMG_FP32) outer_vcycle<float>(c);
+            else outer_vcycle<double>(c);
+            ritz(c, false);
+            ++done;
+        }
+        check_kaczmarz(c);
+    });
+    if (outer_done) *outer_done = done;
+    if (st == SAMG_OK && !converged) {
+        ctx->err = "max_outer reached before the tolerance";
+        return SAMG_E_NOT_CONVERGED;
+    }
+    return st;
+}
+
+samg_status samg_get_hierarchy_info(const samg_ctx *ctx, int *n_levels, int32_t *m, int32_t *n,
+                                    int64_t *nnz_A) {
+    if (!ctx || !n_levels) return SAMG_E_INVALID;
+    *n_levels = ctx->nlev();
+    for (int l = 0; l < ctx->nlev(); ++l) {
+        if (m) m[l] = ctx->L[l].m;
+        if (n) n[l] = ctx->L[l].n;
+        if (nnz_A) nnz_A[l] = ctx->L[l].A.nnz;
+    }
+    return SAMG_OK;
+}
+
+samg_status samg_get_level_matrix(const samg_ctx *ctx, int level, int which, int32_t *rows,
+                                  int32_t *cols, int64_t *nnz, int64_t *row_ptr, int32_t *col,
+                                  double *val) {
+    if (!ctx) return SAMG_E_INVALID;
+    samg_ctx *c = const_cast<samg_ctx *>(ctx);
+    return guarded(c, [&] {
+        check_level(*c, level, which >= 3);
+        const Level &L = c->L[level];
+        const DCsr *M = nullptr;
+        switch (which) {
+            case 0: M = &L.A; break;
+            case 1: M = &L.B; break;
+            case 2: M = &L.C; break;
+            case 3: M = &L.P; break;
+            case 4: M = c->spd() ? &L.P : &L.Q; break;
+            default: throw Error(SAMG_E_INVALID, "which must be 0..4");
+        }
+        SAMG_CHECK(!M->empty(), SAMG_E_INVALID, "operator not stored (identity on level 0)");
+        if (rows) *rows = M->m;
+        if (cols) *cols = M->n;
+        if (nnz) *nnz = M->nnz;
+        if (!row_ptr) return;
+        HCsr h;
+        download_csr(*M, h, c->stream);
+        std::copy(h.rp.begin(), h.rp.end(), row_ptr);
+        std::copy(h.ci.begin(), h.ci.end(), col);
+        std::copy(h.v.begin(), h.v.end(), val);
+    });
+}
+
+samg_status samg_relax(samg_ctx *ctx, int level, int count, const double *sigma, double *U,
+                       double *V, const double *kappa, const double *tau) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        check_level(*ctx, level, false);
+        set_sigma(*ctx, sigma);
+        if (ctx->prm.prec == SAMG_FP32) step_relax<float>(*ctx, level, count, U, V, kappa, tau);
+        else step_relax<double>(*ctx, level, count, U, V, kappa, tau);
+        check_kaczmarz(*ctx);
+    });
+}
+
+samg_status samg_residual_restrict(samg_ctx *ctx, int level, const double *sigma,
+                                   const double *U, const double *V, const double *kappa,
+                                   const double *tau, double *kappa_c, double *tau_c) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        check_level(*ctx, level, true);
+        set_sigma(*ctx, sigma);
+        if (ctx->prm.prec == SAMG_FP32)
+            step_restrict<float>(*ctx, level, U, V, kappa, tau, kappa_c, tau_c);
+        else
+            step_restrict<double>(*ctx, level, U, V, kappa, tau, kappa_c, tau_c);
+    });
+}
+
+samg_status samg_interpolate(samg_ctx *ctx, int level, double *U, double *V, const double *Uc,
+                             const double *Vc) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        check_level(*ctx, level, true);
+        if (ctx->prm.prec == SAMG_FP32) step_interp<float>(*ctx, level, U, V, Uc, Vc);
+        else step_interp<double>(*ctx, level, U, V, Uc, Vc);
+    });
+}
+
+samg_status samg_coarsest_solve(samg_ctx *ctx, const double *sigma, const double *kappa,
+                                const double *tau, double *U, double *V) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        set_sigma(*ctx, sigma);
+        if (ctx->prm.prec == SAMG_FP32) step_coarse<float>(*ctx, kappa, tau, U, V);
+        else step_coarse<double>(*ctx, kappa, tau, U, V);
+    });
+}
+
+samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        samg_ctx &c = *ctx;
+        set_sigma(c, sigma);
+        c.U.zero(c.stream);
+        put_block(c, U, urows(c, 0), c.U);
+        if (!c.spd()) {
+            c.V.zero(c.stream);
+            put_block(c, V, c.L[0].n, c.V);
+        }
+        if (c.prm.prec == SAMG_FP32) outer_vcycle<float>(c);
+        else outer_vcycle<double>(c);
+        get_block(c, c.U, urows(c, 0), U);
+        if (!c.spd()) get_block(c, c.V, c.L[0].n, V);
+        SAMG_CUDA(cudaStreamSynchronize(c.stream));
+        check_kaczmarz(c);
+    });
+}
+
+samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double *resid) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        samg_ctx &c = *ctx;
+        std::vector<double> one(c.nb, 1.0);
+        set_sigma(c, one.data());
+        c.U.zero(c.stream);
+        put_block(c, U, urows(c, 0), c.U);
+        if (!c.spd()) {
+            c.V.zero(c.stream);
+            put_block(c, V, c.L[0].n, c.V);
+        }
+        ritz(c, false);
+        std::vector<double> sg(c.ld), rs(c.ld);
+        c.sigma.download(sg.data(), c.ld, c.stream);
+        c.resid.download(rs.data(), c.ld, c.stream);
+        get_block(c, c.U, urows(c, 0), U);
+        if (!c.spd()) get_block(c, c.V, c.L[0].n, V);
+        SAMG_CUDA(cudaStreamSynchronize(c.stream));
+        if (sigma) std::copy(sg.begin(), sg.begin() + c.nb, sigma);
+        if (resid) std::copy(rs.begin(), rs.begin() + c.nb, resid);
+    });
+}
+
+samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
+                            double *G, void *cuda_stream) {
+    try {
+        SAMG_CHECK(X && Y && G && rows >= 0 && nb >= 1 && nb <= 16 && ld >= nb, SAMG_E_INVALID,
+                   "block_gram: bad arguments");
+        check_device();
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        DBuf<double> work(gram_workspace(rows, nb));
+        launch_gram(X, Y, rows, nb, ld, G, work.p, s);
+        SAMG_CUDA(cudaStreamSynchronize(s));
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// ctx.cuh -- the solver context: hierarchy on the device, the finest-level
+// boot triplets, and the drivers of the additive V-cycle (Sec. 4) and of the
+// Ritz step (Sec. 4.3).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "kaczmarz.cuh"
+#include "kernels.cuh"
+
+namespace samg {
+
+template <typename T>
+struct Work {          // V-cycle vectors of one level in one precision (ld columns)
+    DBuf<T> u, v;      // iterate (error) blocks: m x ld, n x ld
+    DBuf<T> k, t;      // right-hand sides kappa, tau
+    DBuf<T> r, s;      // residuals / Kaczmarz right-hand sides
+    DBuf<T> tu, tv;    // Jacobi double buffers
+};
+
+struct Level {
+    int m = 0, n = 0;           // A_l is m x n (SPD kind: n x n)
+    DCsr A, At, B, C;           // B, C empty on the finest level (identity)
+    DCsr P, Pt, Q, Qt;          // empty on the coarsest level
+    KSched kA, kAt;             // Kaczmarz schedules (minimal target)
+    DBuf<double> dBd, dCd;      // diagonals of B, C (dominant target)
+    DBuf<float> dBf, dCf;
+    Work<float> wf;
+    Work<double> wd;
+};
+
+struct Coarse {
+    int M = 0, m1 = 0;
+    DBuf<double> X, Y, lam, W, Wt, work;
+    DBuf<int> status;
+};
+
+}  // namespace samg
+
+struct samg_ctx {
+    cudaStream_t stream = nullptr;
+    samg_kind kind = SAMG_SVD;
+    samg_target target = SAMG_MINIMAL;
+    samg_params prm{};
+    int nb = 0, ld = 0;
+    std::vector<samg::Level> L;
+    samg::Coarse co;
+    // finest-level boot triplets (float64, ld columns; padding columns 0, sigma 1)
+    samg::DBuf<double> sigma, U, V, resid;
+    // Ritz work
+    samg::DBuf<double> AV, AtU, Un, Vn, GU, GV, H, TU, TV, gwork, partu, partv;
+    samg::DBuf<int> rstat;
+    std::string err;
+    bool poisoned = false;
+    bool spd() const { return kind == SAMG_SPD_EIG; }
+    bool minimal() const { return target == SAMG_MINIMAL; }
+    int nlev() const { return (int)L.size(); }
+};
+
+namespace samg {
+
+// hierarchy completion after the interpolation operators are known
+void build_galerkin(samg_ctx &c);
+void finalize_hierarchy(samg_ctx &c);
+void prepare_level(samg_ctx &c, int l);
+void prepare_coarsest(samg_ctx &c);
+void csr_identity(int n, HCsr &h);
+void alloc_finest_state(samg_ctx &c);
+void share_error_word(samg_ctx &c);
+
+// triplets host <-> device (row-major nb columns on the host)
+void put_block(samg_ctx &c, const double *h, int rows, DBuf<double> &d);
+void get_block(samg_ctx &c, const DBuf<double> &d, int rows, double *h);
+
+// V-cycle pieces in precision T on level l (vectors in L[l].w*)
+template <typename T> Work<T> &work(Level &L);
+template <typename T> void relax(samg_ctx &c, int l);
+template <typename T> void residual_restrict(samg_ctx &c, int l);
+template <typename T> void interpolate(samg_ctx &c, int l);
+template <typename T> void coarse_solve(samg_ctx &c);
+template <typename T> void vcycle(samg_ctx &c, int l);
+template <typename T> void outer_vcycle(samg_ctx &c);   // defect form on (U, V)
+
+void ritz(samg_ctx &c, bool identity);  // identity: residuals of the current triplets only
+void host_setup(samg_ctx &c, const samg_csr &A);  // multiplicative phase (setup.cu)
+
+}  // namespace samg

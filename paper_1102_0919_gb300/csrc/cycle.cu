@@ -1,0 +1,432 @@
+// cycle.cu -- additive V-cycle (Secs. 4.1-4.2) and Ritz step (Sec. 4.3)
+// drivers, and completion of a hierarchy on the device (Eq. coarseOp).
+#include <algorithm>
+#include <cmath>
+
+#include "ctx.cuh"
+
+namespace samg {
+
+template <> Work<float> &work<float>(Level &L) { return L.wf; }
+template <> Work<double> &work<double>(Level &L) { return L.wd; }
+
+template <typename T> static const T *dgB(const Level &L);
+template <> const float *dgB<float>(const Level &L) { return L.dBf.p; }
+template <> const double *dgB<double>(const Level &L) { return L.dBd.p; }
+template <typename T> static const T *dgC(const Level &L);
+template <> const float *dgC<float>(const Level &L) { return L.dCf.p; }
+template <> const double *dgC<double>(const Level &L) { return L.dCd.p; }
+
+template <typename T> static CsrView<T> opt_view(const DCsr &a) {
+    if (a.empty()) return CsrView<T>{0, 0, nullptr, nullptr, nullptr};
+    return view<T>(a);
+}
+
+// ------------------------------------------------------------ relaxation
+// One block Gauss-Seidel relaxation of A v - s B u = kappa,
+// A^t u - s C v = tau (Eqs. genSVDresid1-2, add), sigma fixed per column.
+template <typename T>
+void relax(samg_ctx &c, int l) {
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    const int ld = c.ld;
+    cudaStream_t s = c.stream;
+    const double *sig = c.sigma.p;
+    if (c.minimal()) {
+        if (c.spd()) {  // one sweep over the rows of A - s B (Sec. 5.3)
+            launch_kaczmarz<T>(L.kA, ld, w.k.p, w.u.p, sig, s);
+            return;
+        }
+        // v from the rows of A with rhs s B u + kappa
+        Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
+        launch_combine<T, T>(L.m, ld, w.k.p, 1.0, tb, Term<T>{}, sig, w.r.p, s);
+        launch_kaczmarz<T>(L.kA, ld, w.r.p, w.v.p, nullptr, s);
+        // u from the rows of A^t with rhs s C v + tau
+        Term<T> tc{opt_view<T>(L.C), w.v.p, 1.0, true};
+        launch_combine<T, T>(L.n, ld, w.t.p, 1.0, tc, Term<T>{}, sig, w.s.p, s);
+        launch_kaczmarz<T>(L.kAt, ld, w.s.p, w.u.p, nullptr, s);
+        return;
+    }
+    // dominant: weighted Jacobi for u from Eq. genSVDresid1, then v (Sec. 3.5)
+    const double om = c.prm.omega_J;
+    if (c.spd()) {
+        launch_jacobi<T>(L.n, ld, view<T>(L.A), w.u.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p,
+                         sig, om, w.tu.p, s);
+        std::swap(w.u, w.tu);
+        return;
+    }
+    launch_jacobi<T>(L.m, ld, view<T>(L.A), w.v.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p, sig,
+                     om, w.tu.p, s);
+    std::swap(w.u, w.tu);
+    launch_jacobi<T>(L.n, ld, view<T>(L.At), w.u.p, opt_view<T>(L.C), dgC<T>(L), w.v.p, w.t.p,
+                     sig, om, w.tv.p, s);
+    std::swap(w.v, w.tv);
+}
+
+// r = kappa - (A v - s B u), s = tau - (A^t u - s C v); kappa_c = P^t r,
+// tau_c = Q^t s into level l+1 (Eqs. add, addCoarse).
+template <typename T>
+void residual_restrict(samg_ctx &c, int l) {
+    Level &L = c.L[l];
+    Level &Lc = c.L[l + 1];
+    Work<T> &w = work<T>(L);
+    Work<T> &wc = work<T>(Lc);
+    const int ld = c.ld;
+    cudaStream_t s = c.stream;
+    const double *sig = c.sigma.p;
+    if (c.spd()) {
+        Term<T> ta{view<T>(L.A), w.u.p, -1.0, false};
+        Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
+        launch_combine<T, T>(L.n, ld, w.k.p, 1.0, ta, tb, sig, w.r.p, s);
+        launch_combine<T, T>(Lc.n, ld, (const T *)nullptr, 0.0,
+                             Term<T>{view<T>(L.Pt), w.r.p, 1.0, false}, Term<T>{}, sig, wc.k.p, s);
+        return;
+    }
+    Term<T> ta{view<T>(L.A), w.v.p, -1.0, false};
+    Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
+    launch_combine<T, T>(L.m, ld, w.k.p, 1.0, ta, tb, sig, w.r.p, s);
+    Term<T> tat{view<T>(L.At), w.u.p, -1.0, false};
+    Term<T> tc{opt_view<T>(L.C), w.v.p, 1.0, true};
+    launch_combine<T, T>(L.n, ld, w.t.p, 1.0, tat, tc, sig, w.s.p, s);
+    launch_combine<T, T>(Lc.m, ld, (const T *)nullptr, 0.0,
+                         Term<T>{view<T>(L.Pt), w.r.p, 1.0, false}, Term<T>{}, sig, wc.k.p, s);
+    launch_combine<T, T>(Lc.n, ld, (const T *)nullptr, 0.0,
+                         Term<T>{view<T>(L.Qt), w.s.p, 1.0, false}, Term<T>{}, sig, wc.t.p, s);
+}
+
+// u += P u_c, v += Q v_c (Eq. corrAdd)
+template <typename T>
+void interpolate(samg_ctx &c, int l) {
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    Work<T> &wc = work<T>(c.L[l + 1]);
+    const int ld = c.ld;
+    cudaStream_t s = c.stream;
+    const double *sig = c.sigma.p;
+    if (c.spd()) {
+        launch_combine<T, T>(L.n, ld, w.u.p, 1.0, Term<T>{view<T>(L.P), wc.u.p, 1.0, false},
+                             Term<T>{}, sig, w.u.p, s);
+        return;
+    }
+    launch_combine<T, T>(L.m, ld, w.u.p, 1.0, Term<T>{view<T>(L.P), wc.u.p, 1.0, false},
+                         Term<T>{}, sig, w.u.p, s);
+    launch_combine<T, T>(L.n, ld, w.v.p, 1.0, Term<T>{view<T>(L.Q), wc.v.p, 1.0, false},
+                         Term<T>{}, sig, w.v.p, s);
+}
+
+// [u; v] = (X_L - s Y_L)^+ [kappa; tau] without the smallest singular value
+template <typename T>
+void coarse_solve(samg_ctx &c) {
+    Level &L = c.L.back();
+    Work<T> &w = work<T>(L);
+    launch_coarse_apply<T>(c.co.M, c.co.m1, c.ld, c.nb, c.co.lam.p, c.co.W.p, c.co.Wt.p,
+                           c.sigma.p, w.k.p, c.spd() ? w.k.p : w.t.p, w.u.p,
+                           c.spd() ? w.u.p : w.v.p, c.stream);
+}
+
+template <typename T>
+void vcycle(samg_ctx &c, int l) {
+    if (l == c.nlev() - 1) {
+        coarse_solve<T>(c);
+        return;
+    }
+    for (int k = 0; k < c.prm.mu_b; ++k) relax<T>(c, l);
+    residual_restrict<T>(c, l);
+    Work<T> &wc = work<T>(c.L[l + 1]);
+    wc.u.zero(c.stream);
+    if (!c.spd()) wc.v.zero(c.stream);
+    vcycle<T>(c, l + 1);
+    interpolate<T>(c, l);
+    for (int k = 0; k < c.prm.mu_b; ++k) relax<T>(c, l);
+}
+
+// Defect-correction form of one outer V-cycle: (r, s) = -(A V - s U,
+// A^t U - s V) in float64, the whole cycle on the error equation with zero
+// initial guess in precision T, then U += e_u, V += e_v in float64.  The
+// relaxations are affine in (iterate, rhs), so this equals the V-cycle on the
+// iterate itself.
+template <typename T>
+void outer_vcycle(samg_ctx &c) {
+    Level &L0 = c.L[0];
+    Work<T> &w = work<T>(L0);
+    const int ld = c.ld;
+    cudaStream_t s = c.stream;
+    const double *sig = c.sigma.p;
+    if (c.spd()) {
+        Term<double> ta{view<double>(L0.A), c.U.p, -1.0, false};
+        Term<double> tu{CsrView<double>{0, 0, nullptr, nullptr, nullptr}, c.U.p, 1.0, true};
+        launch_combine<double, T>(L0.n, ld, nullptr, 0.0, ta, tu, sig, w.k.p, s);
+        w.u.zero(s);
+        vcycle<T>(c, 0);
+        launch_add_to<T>((size_t)L0.n * ld, c.U.p, w.u.p, s);
+        return;
+    }
+    Term<double> ta{view<double>(L0.A), c.V.p, -1.0, false};
+    Term<double> tu{CsrView<double>{0, 0, nullptr, nullptr, nullptr}, c.U.p, 1.0, true};
+    launch_combine<double, T>(L0.m, ld, nullptr, 0.0, ta, tu, sig, w.k.p, s);
+    Term<double> tat{view<double>(L0.At), c.U.p, -1.0, false};
+    Term<double> tv{CsrView<double>{0, 0, nullptr, nullptr, nullptr}, c.V.p, 1.0, true};
+    launch_combine<double, T>(L0.n, ld, nullptr, 0.0, tat, tv, sig, w.t.p, s);
+    w.u.zero(s);
+    w.v.zero(s);
+    vcycle<T>(c, 0);
+    launch_add_to<T>((size_t)L0.m * ld, c.U.p, w.u.p, s);
+    launch_add_to<T>((size_t)L0.n * ld, c.V.p, w.v.p, s);
+}
+
+template void relax<float>(samg_ctx &, int);
+template void relax<double>(samg_ctx &, int);
+template void residual_restrict<float>(samg_ctx &, int);
+template void residual_restrict<double>(samg_ctx &, int);
+template void interpolate<float>(samg_ctx &, int);
+template void interpolate<double>(samg_ctx &, int);
+template void coarse_solve<float>(samg_ctx &);
+template void coarse_solve<double>(samg_ctx &);
+template void vcycle<float>(samg_ctx &, int);
+template void vcycle<double>(samg_ctx &, int);
+template void outer_vcycle<float>(samg_ctx &);
+template void outer_vcycle<double>(samg_ctx &);
+
+// ------------------------------------------------------------------ Ritz
+// Sec. 4.3 on the finest level (B = I, C = I): Gram matrices, M = U^t A V
+// through Cholesky factors, its SVD, U <- U R_U^-1 Y, V <- V R_V^-1 Z, and
+// rho_j from A V_new = (A V) R_V^-1 Z, A^t U_new = (A^t U) R_U^-1 Y.
+// identity = true keeps the triplets and only evaluates rho_j.
+__global__ void k_identity(int ld, double *T) {
+    int q = threadIdx.x;
+    if (q < ld * ld) T[q] = (q / ld == q % ld) ? 1.0 : 0.0;
+}
+
+void ritz(samg_ctx &c, bool identity) {
+    Level &L0 = c.L[0];
+    const int ld = c.ld, nb = c.nb;
+    cudaStream_t s = c.stream;
+    const int64_t n = L0.n;
+    const int64_t mu = c.spd() ? L0.n : L0.m;
+    Term<double> none{};
+    if (c.spd()) {
+        launch_combine<double, double>(L0.n, ld, nullptr, 0.0,
+                                       Term<double>{view<double>(L0.A), c.U.p, 1.0, false}, none,
+                                       c.sigma.p, c.AV.p, s);
+    } else {
+        launch_combine<double, double>(L0.m, ld, nullptr, 0.0,
+                                       Term<double>{view<double>(L0.A), c.V.p, 1.0, false}, none,
+                                       c.sigma.p, c.AV.p, s);
+        launch_combine<double, double>(L0.n, ld, nullptr, 0.0,
+                                       Term<double>{view<double>(L0.At), c.U.p, 1.0, false}, none,
+                                       c.sigma.p, c.AtU.p, s);
+    }
+    if (identity) {
+        k_identity<<<1, 256, 0, s>>>(ld, c.TU.p);
+        k_identity<<<1, 256, 0, s>>>(ld, c.TV.p);
+    } else {
+        launch_gram(c.U.p, c.U.p, mu, nb, ld, c.GU.p, c.gwork.p, s);
+        if (!c.spd()) launch_gram(c.V.p, c.V.p, n, nb, ld, c.GV.p, c.gwork.p, s);
+        launch_gram(c.U.p, c.AV.p, mu, nb, ld, c.H.p, c.gwork.p, s);
+        launch_ritz_small(c.GU.p, c.spd() ? c.GU.p : c.GV.p, c.H.p, nb, ld, c.spd(),
+                          !c.minimal(), c.sigma.p, c.TU.p, c.TV.p, c.rstat.p, s);
+    }
+    launch_ritz_update(c.U.p, c.AV.p, c.TU.p, c.spd() ? c.TU.p : c.TV.p, c.sigma.p, mu, nb, ld,
+                       c.Un.p, c.partu.p, s);
+    if (!c.spd())
+        launch_ritz_update(c.V.p, c.AtU.p, c.TV.p, c.TU.p, c.sigma.p, n, nb, ld, c.Vn.p,
+                           c.partv.p, s);
+    launch_ritz_resid(c.partu.p, mu, c.spd() ? nullptr : c.partv.p, n, nb, c.sigma.p,
+                      c.resid.p, s);
+    std::swap(c.U, c.Un);
+    if (!c.spd()) std::swap(c.V, c.Vn);
+    if (!identity) {
+        int st = 0;
+        SAMG_CUDA(cudaMemcpyAsync(&st, c.rstat.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SAMG_CUDA(cudaStreamSynchronize(s));
+        SAMG_CHECK(st == 0, SAMG_E_INVALID, "ritz: boot vectors are linearly dependent");
+    }
+}
+
+// ------------------------------------------------------------ hierarchy
+void csr_identity(int n, HCsr &h) {
+    h.m = h.n = n;
+    h.rp.resize(n + 1);
+    h.ci.resize(n);
+    h.v.assign(n, 1.0);
+    for (int i = 0; i <= n; ++i) h.rp[i] = i;
+    for (int i = 0; i < n; ++i) h.ci[i] = i;
+}
+
+// A_{l+1} = P^t A_l Q, B_{l+1} = P^t B_l P, C_{l+1} = Q^t C_l Q (Eq. coarseOp)
+// for every level whose P (and Q) are set; transposes P^t, Q^t.
+void build_galerkin(samg_ctx &c) {
+    cudaStream_t s = c.stream;
+    for (int l = 0; l + 1 < c.nlev(); ++l) {
+        Level &L = c.L[l];
+        Level &Lc = c.L[l + 1];
+        transpose(L.P, L.Pt, s);
+        DCsr tmp, tmp2;
+        if (c.spd()) {
+            spgemm(L.A, L.P, tmp, s);
+            spgemm(L.Pt, tmp, Lc.A, s);
+            if (L.B.empty()) {
+                spgemm(L.Pt, L.P, Lc.B, s);
+            } else {
+                spgemm(L.B, L.P, tmp2, s);
+                spgemm(L.Pt, tmp2, Lc.B, s);
+            }
+            Lc.m = Lc.n = Lc.A.m;
+            continue;
+        }
+        transpose(L.Q, L.Qt, s);
+        spgemm(L.A, L.Q, tmp, s);
+        spgemm(L.Pt, tmp, Lc.A, s);
+        if (L.B.empty()) {
+            spgemm(L.Pt, L.P, Lc.B, s);
+        } else {
+            spgemm(L.B, L.P, tmp2, s);
+            spgemm(L.Pt, tmp2, Lc.B, s);
+        }
+        DCsr tmp3;
+        if (L.C.empty()) {
+            spgemm(L.Qt, L.Q, Lc.C, s);
+        } else {
+            spgemm(L.C, L.Q, tmp3, s);
+            spgemm(L.Qt, tmp3, Lc.C, s);
+        }
+        Lc.m = Lc.A.m;
+        Lc.n = Lc.A.n;
+    }
+}
+
+template <typename T>
+static void alloc_work(Work<T> &w, int m, int n, int ld, bool spd, cudaStream_t s) {
+    size_t mu = (size_t)(spd ? n : m) * ld, nv = (size_t)n * ld;
+    w.u.alloc(mu); w.k.alloc(mu); w.r.alloc(mu); w.tu.alloc(mu);
+    w.u.zero(s); w.k.zero(s); w.r.zero(s); w.tu.zero(s);
+    if (!spd) {
+        w.v.alloc(nv); w.t.alloc(nv); w.s.alloc(nv); w.tv.alloc(nv);
+        w.v.zero(s); w.t.zero(s); w.s.zero(s); w.tv.zero(s);
+    }
+}
+
+// Per-level data used by the cycle: A^t, Kaczmarz schedules (minimal) or
+// diagonals of B, C (dominant), and the work vectors.  Schedules already built
+// for the same operator are kept.
+void prepare_level(samg_ctx &c, int l) {
+    cudaStream_t s = c.stream;
+    Level &L = c.L[l];
+    L.m = L.A.m;
+    L.n = L.A.n;
+    if (!c.spd() && L.At.m != L.A.n) transpose(L.A, L.At, s);
+    if (c.minimal()) {
+        if (L.kA.nbands == 0) {
+            HCsr hA;
+            download_csr(L.A, hA, s);
+            if (c.spd()) {
+                HCsr hB;
+                if (L.B.empty()) csr_identity(L.n, hB);
+                else download_csr(L.B, hB, s);
+                build_kschedule(hA, &hB, L.kA, s);
+            } else {
+                HCsr hAt;
+                download_csr(L.At, hAt, s);
+                build_kschedule(hA, nullptr, L.kA, s);
+                build_kschedule(hAt, nullptr, L.kAt, s);
+            }
+        }
+        if (c.rstat.n >= 2) {
+            L.kA.err = c.rstat.p + 1;
+            L.kAt.err = c.rstat.p + 1;
+        }
+    } else {
+        if (!L.B.empty()) launch_diagonal(L.B, L.dBd, L.dBf, s);
+        if (!c.spd() && !L.C.empty()) launch_diagonal(L.C, L.dCd, L.dCf, s);
+    }
+    const size_t want = (size_t)(c.spd() ? L.n : L.m) * c.ld;
+    if (L.wd.u.n != want) {
+        alloc_work(L.wf, L.m, L.n, c.ld, c.spd(), s);
+        alloc_work(L.wd, L.m, L.n, c.ld, c.spd(), s);
+    }
+}
+
+// Coarsest level: X = [[0, A], [A^t, 0]], Y = diag(B, C) (SPD: A, B) and its
+// generalized eigendecomposition X W = Y W Lam, W^t Y W = I.
+void prepare_coarsest(samg_ctx &c) {
+    cudaStream_t s = c.stream;
+    Level &Lc = c.L.back();
+    Coarse &co = c.co;
+    co.m1 = c.spd() ? Lc.n : Lc.m;
+    co.M = c.spd() ? Lc.n : Lc.m + Lc.n;
+    SAMG_CHECK(co.M <= 2048, SAMG_E_INVALID, "coarsest level larger than 2048");
+    const size_t MM = (size_t)co.M * co.M;
+    co.X.alloc(MM); co.Y.alloc(MM); co.W.alloc(MM); co.Wt.alloc(MM);
+    co.lam.alloc(co.M); co.work.alloc(2 * MM); co.status.alloc(1);
+    co.X.zero(s);
+    co.Y.zero(s);
+    HCsr hI;
+    DCsr dI;
+    auto fill_mass = [&](const DCsr &Bm, int n, int off) {
+        if (!Bm.empty()) {
+            dense_fill(Bm, off, off, co.M, co.Y.p, false, s);
+        } else {
+            csr_identity(n, hI);
+            upload_csr(hI, dI, s);
+            dense_fill(dI, off, off, co.M, co.Y.p, false, s);
+        }
+    };
+    if (c.spd()) {
+        dense_fill(Lc.A, 0, 0, co.M, co.X.p, false, s);
+        fill_mass(Lc.B, Lc.n, 0);
+    } else {
+        dense_fill(Lc.A, 0, Lc.m, co.M, co.X.p, false, s);
+        dense_fill(Lc.A, 0, Lc.m, co.M, co.X.p, true, s);
+        fill_mass(Lc.B, Lc.m, 0);
+        fill_mass(Lc.C, Lc.n, Lc.m);
+    }
+    launch_coarse_geneig(co.M, co.X.p, co.Y.p, co.work.p, co.lam.p, co.W.p, co.Wt.p,
+                         co.status.p, s);
+    int st = 0;
+    SAMG_CUDA(cudaMemcpyAsync(&st, co.status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SAMG_CUDA(cudaStreamSynchronize(s));
+    SAMG_CHECK(st == 0, SAMG_E_INVALID, "coarsest level: Y is not positive definite");
+}
+
+void finalize_hierarchy(samg_ctx &c) {
+    for (int l = 0; l < c.nlev(); ++l) prepare_level(c, l);
+    prepare_coarsest(c);
+}
+
+void alloc_finest_state(samg_ctx &c) {
+    Level &L0 = c.L[0];
+    const int ld = c.ld, nb = c.nb;
+    cudaStream_t s = c.stream;
+    size_t mu = (size_t)(c.spd() ? L0.n : L0.m) * ld, nv = (size_t)L0.n * ld;
+    c.sigma.alloc(ld);
+    c.resid.alloc(ld);
+    c.U.alloc(mu); c.Un.alloc(mu); c.AV.alloc(mu);
+    c.U.zero(s); c.Un.zero(s); c.AV.zero(s);
+    if (!c.spd()) {
+        c.V.alloc(nv); c.Vn.alloc(nv); c.AtU.alloc(nv);
+        c.V.zero(s); c.Vn.zero(s); c.AtU.zero(s);
+    }
+    c.GU.alloc(256); c.GV.alloc(256); c.H.alloc(256); c.TU.alloc(256); c.TV.alloc(256);
+    int64_t rows = std::max<int64_t>(c.spd() ? L0.n : L0.m, L0.n);
+    c.gwork.alloc(gram_workspace(rows, nb));
+    c.partu.alloc(gram_workspace(rows, 1) * nb + nb);
+    c.partv.alloc(gram_workspace(rows, 1) * nb + nb);
+    c.rstat.alloc(2);
+    c.rstat.zero(s);
+    std::vector<double> one(ld, 1.0);
+    c.sigma.upload(one.data(), ld, s);
+}
+
+void put_block(samg_ctx &c, const double *h, int rows, DBuf<double> &d) {
+    if (rows == 0) return;
+    SAMG_CUDA(cudaMemcpy2DAsync(d.p, c.ld * sizeof(double), h, c.nb * sizeof(double),
+                                c.nb * sizeof(double), rows, cudaMemcpyHostToDevice, c.stream));
+}
+
+void get_block(samg_ctx &c, const DBuf<double> &d, int rows, double *h) {
+    if (rows == 0) return;
+    SAMG_CUDA(cudaMemcpy2DAsync(h, c.nb * sizeof(double), d.p, c.ld * sizeof(double),
+                                c.nb * sizeof(double), rows, cudaMemcpyDeviceToHost, c.stream));
+}
+
+}  // namespace samg
