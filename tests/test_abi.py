@@ -9,8 +9,12 @@ import pytest
 
 @pytest.fixture(scope="module")
 def lib(repo_root):
-    from paper_1102_0919_gb300 import build as libbuild
+    import importlib.util
 
+    spec = importlib.util.spec_from_file_location(
+        "_samg_build", os.path.join(repo_root, "paper_1102_0919_gb300", "build.py"))
+    libbuild = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(libbuild)
     path = libbuild.build()
     return ctypes.CDLL(path), path
 
