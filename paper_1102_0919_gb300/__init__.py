@@ -157,13 +157,15 @@ class Solver:
         t = MINIMAL if target == "minimal" else DOMINANT
         k = SPD_EIG if kind == "spd" else SVD
         c = _csr(A)
-        P = (_Csr * len(Ps))(*[_csr(x) for x in Ps])
-        keep = [P]
+        # the _Csr objects own the numpy arrays their pointers refer to; the
+        # ctypes arrays below hold copies of the structs, so keep both alive
+        Pl = [_csr(x) for x in Ps]
+        P = (_Csr * len(Pl))(*Pl)
         if k == SVD:
-            Q = (_Csr * len(Qs))(*[_csr(x) for x in Qs])
-            keep.append(Q)
+            Ql = [_csr(x) for x in Qs]
+            Q = (_Csr * len(Ql))(*Ql)
         else:
-            Q = P
+            Ql, Q = Pl, P
         p = make_params(**params)
         s = _arr(sigma, np.float64)
         u = _arr(U, np.float64)
@@ -171,6 +173,7 @@ class Solver:
         ctx = _CTX()
         st = samg_import(ctypes.byref(c), len(Ps) + 1, P, Q, nb, t, k, ctypes.byref(p), _ptr(s),
                          _ptr(u), _ptr(v), _stream(stream), ctypes.byref(ctx))
+        del Pl, Ql
         if st != OK:
             raise SamgError(st, samg_last_error(None).decode())
         return cls(ctx, nb, k, t, c.m, c.n)
