@@ -354,7 +354,7 @@ void prepare_coarsest(samg_ctx &c) {
     Coarse &co = c.co;
     co.m1 = c.spd() ? Lc.n : Lc.m;
     co.M = c.spd() ? Lc.n : Lc.m + Lc.n;
-    SAMG_CHECK(co.M <= 2048, SAMG_E_INVALID, "coarsest level larger than 2048");
+    SAMG_CHECK(co.M <= 1280, SAMG_E_INVALID, "coarsest level larger than 1280");
     const size_t MM = (size_t)co.M * co.M;
     co.X.alloc(MM); co.Y.alloc(MM); co.W.alloc(MM); co.Wt.alloc(MM);
     co.lam.alloc(co.M); co.work.alloc(2 * MM); co.status.alloc(1);

@@ -501,12 +501,48 @@ void launch_coarse_geneig(int M, const double *X, const double *Y, double *work,
 
 // Per column j (one CTA each): z = (X - s_j Y)^+ rhs without the smallest
 // singular value.  With X W = Y W Lam, W^t Y W = I: S^-1 = W (Lam - s)^-1 W^t.
-// The dropped singular vector w of S (eigenvector of smallest |mu|) is the
-// dominant eigenvector of S^-1, found by power iteration on S^-1 from the
-// generalized eigenvector nearest s_j; then z = S^-1 (r - w w^t r), projected
-// once more against w.  rhs/out: float or double blocks (rows = M, ld cols),
-// with the first m1 rows taken from/for the first block and the rest from the
+// The dropped singular vector w of the symmetric S (eigenvector of smallest
+// |mu|) is found by subspace iteration on S^-1 with KB vectors started from
+// the generalized eigenvectors nearest s_j, followed by a Rayleigh-Ritz step,
+// so that near-ties among the smallest |mu| (degenerate singular values) are
+// resolved.  Then z = S^-1 (r - w w^t r), projected once more against w.
+// rhs/out: the first m1 rows from/for the first block, the rest from/for the
 // second (SVD kind: [kappa; tau] -> [u; v]).
+constexpr int KB = 4;
+
+__device__ void small_sym_eig(double *H, double *V, int n) {  // thread-local Jacobi
+    for (int i = 0; i < n * n; ++i) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += H[p * n + q] * H[p * n + q];
+        if (off < 1e-300) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = H[p * n + q];
+                if (apq == 0.0) continue;
+                double th = (H[q * n + q] - H[p * n + p]) / (2.0 * apq);
+                double t = copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double a = H[k * n + p], b = H[k * n + q];
+                    H[k * n + p] = c * a - sn * b;
+                    H[k * n + q] = sn * a + c * b;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double a = H[p * n + k], b = H[q * n + k];
+                    H[p * n + k] = c * a - sn * b;
+                    H[q * n + k] = sn * a + c * b;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double a = V[k * n + p], b = V[k * n + q];
+                    V[k * n + p] = c * a - sn * b;
+                    V[k * n + q] = sn * a + c * b;
+                }
+            }
+    }
+}
+
 template <typename T>
 __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__ lam,
                                const double *__restrict__ W, const double *__restrict__ Wt,
@@ -516,13 +552,16 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
     const int j = blockIdx.x;
     if (j >= nb) return;
     extern __shared__ double sm[];
-    double *d = sm;            // M
-    double *w = d + M;         // M
-    double *y = w + M;         // M
-    double *r = y + M;         // M
-    double *tmp = r + M;       // M
+    double *d = sm;               // M
+    double *Q = d + M;            // KB x M
+    double *Z = Q + KB * M;       // KB x M
+    double *r = Z + KB * M;       // M
+    double *y = r + M;            // M
+    double *tq = y + M;           // KB x M (coefficients in the W basis)
     __shared__ double red[32];
     __shared__ double s_val;
+    __shared__ double sH[KB * KB], sV[KB * KB];
+    __shared__ int s_sel[KB];
     const int t = threadIdx.x, nt = blockDim.x;
     const double sj = sigma[j];
     auto bsum = [&](double v) -> double {
@@ -539,62 +578,126 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
         __syncthreads();
         return res;
     };
-    // y <- S^-1 x  (x in smem `src`, result in `dst`), via W and Wt
-    auto apply_inv = [&](const double *src, double *dst) {
-        for (int k = t; k < M; k += nt) {  // tmp_k = d_k * (W^t src)_k
-            double v = 0.0;
-            for (int i = 0; i < M; ++i) v = fma(Wt[(size_t)k * M + i], src[i], v);
-            tmp[k] = d[k] * v;
+    auto dot = [&](const double *a, const double *b) {
+        double v = 0.0;
+        for (int i = t; i < M; i += nt) v = fma(a[i], b[i], v);
+        return bsum(v);
+    };
+    // Z[b] = S^-1 Q[b] for nq vectors (one pass over W^t and W for all of them)
+    auto apply_inv = [&](const double *src, double *dst, int nq) {
+        for (int k = t; k < M; k += nt) {
+            double acc[KB] = {0.0, 0.0, 0.0, 0.0};
+            for (int i = 0; i < M; ++i) {
+                const double w = Wt[(size_t)k * M + i];
+                for (int b = 0; b < nq; ++b) acc[b] = fma(w, src[b * M + i], acc[b]);
+            }
+            for (int b = 0; b < nq; ++b) tq[b * M + k] = d[k] * acc[b];
         }
         __syncthreads();
         for (int i = t; i < M; i += nt) {
-            double v = 0.0;
-            for (int k = 0; k < M; ++k) v = fma(W[(size_t)i * M + k], tmp[k], v);
-            dst[i] = v;
+            double acc[KB] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = 0; k < M; ++k) {
+                const double w = W[(size_t)i * M + k];
+                for (int b = 0; b < nq; ++b) acc[b] = fma(w, tq[b * M + k], acc[b]);
+            }
+            for (int b = 0; b < nq; ++b) dst[b * M + i] = acc[b];
         }
         __syncthreads();
     };
-    int kbest = 0;
-    double best = -1.0;
-    for (int k = 0; k < M; ++k) {
-        double den = lam[k] - sj;
-        double a = fabs(den) > 0.0 ? 1.0 / fabs(den) : 1e300;
-        if (a > best) { best = a; kbest = k; }
-    }
+    auto orthonormalize = [&](double *B, int nq) {  // modified Gram-Schmidt
+        for (int a = 0; a < nq; ++a) {
+            for (int b = 0; b < a; ++b) {
+                double pr = dot(B + a * M, B + b * M);
+                for (int i = t; i < M; i += nt) B[a * M + i] -= pr * B[b * M + i];
+                __syncthreads();
+            }
+            double nr = sqrt(dot(B + a * M, B + a * M));
+            for (int i = t; i < M; i += nt) B[a * M + i] = nr > 0.0 ? B[a * M + i] / nr : 0.0;
+            __syncthreads();
+        }
+    };
+    const int kb = M < KB ? M : KB;
     for (int k = t; k < M; k += nt) {
         double den = lam[k] - sj;
         d[k] = den != 0.0 ? 1.0 / den : 1e300;
     }
+    __syncthreads();
+    if (t == 0) {  // start: the kb generalized eigenvectors nearest sigma_j
+        for (int b = 0; b < kb; ++b) {
+            int best = -1;
+            double bv = -1.0;
+            for (int k = 0; k < M; ++k) {
+                bool used = false;
+                for (int c2 = 0; c2 < b; ++c2) used = used || (s_sel[c2] == k);
+                double a = fabs(d[k]);
+                if (!used && a > bv) { bv = a; best = k; }
+            }
+            s_sel[b] = best;
+        }
+    }
+    __syncthreads();
     for (int i = t; i < M; i += nt) {
-        w[i] = W[(size_t)i * M + kbest];
+        for (int b = 0; b < kb; ++b) Q[b * M + i] = W[(size_t)i * M + s_sel[b]];
         r[i] = (i < m1) ? (double)k1[(size_t)i * ld + j] : (double)k2[(size_t)(i - m1) * ld + j];
     }
     __syncthreads();
-    double nw = sqrt(bsum([&] { double v = 0; for (int i = t; i < M; i += nt) v += w[i] * w[i]; return v; }()));
+    orthonormalize(Q, kb);
+    double prev = 0.0;
+    for (int it = 0; it < 60; ++it) {
+        apply_inv(Q, Z, kb);
+        // Rayleigh quotient of the leading direction, for the stopping test
+        double th = 0.0;
+        for (int b = 0; b < kb; ++b) {
+            double v = dot(Q + b * M, Z + b * M);
+            th = fmax(th, fabs(v));
+        }
+        for (int i = t; i < kb * M; i += nt) Q[i] = Z[i];
+        __syncthreads();
+        orthonormalize(Q, kb);
+        if (it > 1 && fabs(th - prev) <= 1e-15 * th) break;
+        prev = th;
+    }
+    // Rayleigh-Ritz on span(Q): H = Q^t S^-1 Q, pick the largest |1/mu|
+    apply_inv(Q, Z, kb);
+    for (int a = 0; a < kb; ++a)
+        for (int b = 0; b < kb; ++b) {
+            double v = dot(Q + a * M, Z + b * M);
+            if (t == 0) sH[a * kb + b] = v;
+        }
+    __syncthreads();
+    if (t == 0) {
+        for (int a = 0; a < kb; ++a)
+            for (int b = 0; b < a; ++b) {
+                double v = 0.5 * (sH[a * kb + b] + sH[b * kb + a]);
+                sH[a * kb + b] = v;
+                sH[b * kb + a] = v;
+            }
+        small_sym_eig(sH, sV, kb);
+        int best = 0;
+        for (int a = 1; a < kb; ++a)
+            if (fabs(sH[a * kb + a]) > fabs(sH[best * kb + best])) best = a;
+        s_sel[0] = best;
+    }
+    __syncthreads();
+    const int bsel = s_sel[0];
+    double *w = y;  // reuse: w = Q sV[:, bsel]
+    for (int i = t; i < M; i += nt) {
+        double v = 0.0;
+        for (int a = 0; a < kb; ++a) v += Q[a * M + i] * sV[a * kb + bsel];
+        w[i] = v;
+    }
+    __syncthreads();
+    double nw = sqrt(dot(w, w));
     for (int i = t; i < M; i += nt) w[i] /= nw;
     __syncthreads();
-    for (int it = 0; it < 100; ++it) {
-        apply_inv(w, y);
-        double ny = sqrt(bsum([&] { double v = 0; for (int i = t; i < M; i += nt) v += y[i] * y[i]; return v; }()));
-        double dotwy = bsum([&] { double v = 0; for (int i = t; i < M; i += nt) v += w[i] * y[i]; return v; }());
-        double sgn = dotwy >= 0.0 ? 1.0 : -1.0;
-        double diff = bsum([&] {
-            double v = 0;
-            for (int i = t; i < M; i += nt) { double e = sgn * y[i] / ny - w[i]; v += e * e; }
-            return v;
-        }());
-        for (int i = t; i < M; i += nt) w[i] = sgn * y[i] / ny;
-        __syncthreads();
-        if (diff < 1e-30) break;
-    }
-    // r' = r - w (w^t r)
-    double wr = bsum([&] { double v = 0; for (int i = t; i < M; i += nt) v += w[i] * r[i]; return v; }());
+    // r' = r - w (w^t r);  z = S^-1 r';  z -= w (w^t z)
+    double wr = dot(w, r);
     for (int i = t; i < M; i += nt) r[i] -= wr * w[i];
     __syncthreads();
-    apply_inv(r, y);
-    double wy = bsum([&] { double v = 0; for (int i = t; i < M; i += nt) v += w[i] * y[i]; return v; }());
+    apply_inv(r, Z, 1);
+    double wz = dot(w, Z);
     for (int i = t; i < M; i += nt) {
-        double z = y[i] - wy * w[i];
+        double z = Z[i] - wz * w[i];
         if (i < m1) o1[(size_t)i * ld + j] = (T)z;
         else o2[(size_t)(i - m1) * ld + j] = (T)z;
     }
@@ -604,7 +707,7 @@ template <typename T>
 void launch_coarse_apply(int M, int m1, int ld, int nb, const double *lam, const double *W,
                          const double *Wt, const double *sigma, const T *k1, const T *k2, T *o1,
                          T *o2, cudaStream_t s) {
-    size_t smem = (size_t)5 * M * sizeof(double);
+    size_t smem = (size_t)(4 + 3 * KB) * M * sizeof(double);
     auto kern = k_coarse_apply<T>;
     if (smem > 48 * 1024)
         SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
