@@ -130,7 +130,26 @@ samg_status samg_set_triplets(samg_ctx *ctx, const double *sigma, const double *
 samg_status samg_get_triplets(samg_ctx *ctx, double *sigma, double *U, double *V,
                               double *resid);
 
+/* As samg_set_triplets with device pointers (row-major n_b columns; V
+ * ignored for SPD_EIG); copies are ordered on the context's stream. */
+samg_status samg_set_triplets_device(samg_ctx *ctx, const double *sigma, const double *U,
+                                     const double *V);
+
 samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec);
+
+/* Kernel timing: with profiling on, every launch of the solve phase is
+ * bracketed by CUDA events on the context's stream.  samg_profile_read
+ * returns, for one kernel class (0 Kaczmarz sweep, 1 block SpMM pass
+ * (residual, restriction, interpolation, right-hand sides), 2 Jacobi step,
+ * 3 coarsest solve, 4 Ritz step), the number of launches, their total device
+ * time in ms and their algorithmic bytes (what the method must move: matrix
+ * values and indices, right-hand sides read, iterates read and written),
+ * accumulated since the last reset (reset != 0 clears after reading). */
+samg_status samg_profile(samg_ctx *ctx, int enable);
+/* Number of kernel launches the library has issued in this process. */
+uint64_t samg_launch_count(void);
+samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_t *launches,
+                              double *total_ms, double *alg_bytes);
 
 /* Hierarchy description: levels, and per level m_l, n_l, nnz(A_l) (arrays of
  * n_levels entries; pass NULL to query n_levels only). */

@@ -43,7 +43,11 @@ silent the readings below are used (numbers as in the design notes):
   range A range(Q_0) holds u = A v / s for v in range(Q_0); below the
   finest level A_l = B_l is symmetric, so Sec. 5.2's specialization applies
   (coarsening on A_l, P_l = Q_l).  Row test vectors are A v_t (finest) or
-  v_t (coarser); the coarse boot u is v_b[C] / s (finest) or u_b[C].
+  v_t (coarser); the coarse boot u is v_b[C] / s (finest) or u_b[C].  The
+  Ritz step takes the left basis A V_b (Rayleigh-Ritz for A^t A on span V_b):
+  components of u in null(A^t) -- left there by rounding -- are invisible to
+  every relaxation and correction and to the two-sided projection, and would
+  otherwise stall the residual at the rounding level of the cycle.
 """
 from __future__ import annotations
 
@@ -409,6 +413,10 @@ def ritz(A: sp.csr_matrix, spd: bool, target: str, U, V):
         w, Yv = np.linalg.eigh(M)
         order = np.arange(len(w)) if target == "minimal" else np.arange(len(w))[::-1]
         return w[order].copy(), np.ascontiguousarray(Xh @ Yv[:, order]), None
+    if target == "minimal" and A.shape[0] >= A.shape[1]:
+        # R21: the left basis is A V_b, which excludes the null(A^t) modes
+        # (the spurious zero modes of Thm genSVD) from the projection
+        U = np.ascontiguousarray(A @ V)
     Uh, _ = np.linalg.qr(U)
     Vh, _ = np.linalg.qr(V)
     M = Uh.T @ (A @ Vh)

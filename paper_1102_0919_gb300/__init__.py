@@ -81,12 +81,18 @@ samg_coarsest_solve = _sig("samg_coarsest_solve", _I, _CTX, _P, _P, _P, _P, _P)
 samg_vcycle = _sig("samg_vcycle", _I, _CTX, _P, _P, _P)
 samg_ritz = _sig("samg_ritz", _I, _CTX, _P, _P, _P, _P)
 samg_block_gram = _sig("samg_block_gram", _I, _P, _P, ctypes.c_int64, _I, _I, _P, _P)
+samg_set_triplets_device = _sig("samg_set_triplets_device", _I, _CTX, _P, _P, _P)
+samg_profile = _sig("samg_profile", _I, _CTX, _I)
+samg_launch_count = _sig("samg_launch_count", ctypes.c_uint64)
+samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
             "samg_solve", "samg_set_triplets", "samg_get_triplets", "samg_set_precision",
             "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
-            "samg_ritz", "samg_block_gram"]
+            "samg_ritz", "samg_block_gram", "samg_set_triplets_device", "samg_profile",
+            "samg_profile_read", "samg_launch_count"]
 
 
 def _arr(x, dtype):
@@ -246,6 +252,26 @@ class Solver:
     def set_triplets(self, sigma, U, V=None):
         s, u, v = _arr(sigma, np.float64), _arr(U, np.float64), _arr(V, np.float64)
         self._check(samg_set_triplets(self._ctx, _ptr(s), _ptr(u), _ptr(v)))
+
+    def set_triplets_device(self, sigma_ptr, U_ptr, V_ptr=None):
+        """Device pointers (ints), row-major n_b columns."""
+        self._check(samg_set_triplets_device(self._ctx, ctypes.c_void_p(sigma_ptr),
+                                             ctypes.c_void_p(U_ptr),
+                                             None if V_ptr is None else ctypes.c_void_p(V_ptr)))
+
+    KERNELS = ("kaczmarz_sweep", "block_spmm", "jacobi", "coarsest_solve", "ritz")
+
+    def profile(self, on=True):
+        self._check(samg_profile(self._ctx, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        out = {}
+        for k, name in enumerate(self.KERNELS):
+            n, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            self._check(samg_profile_read(self._ctx, k, 1 if (reset and k == 4) else 0,
+                                          ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+            out[name] = dict(launches=n.value, ms=ms.value, bytes=b.value)
+        return out
 
     # ---------------------------------------------------------- single steps
     def relax(self, level, sigma, U, V, K=None, T=None, count=1):

@@ -197,7 +197,16 @@ void check_kaczmarz(samg_ctx &c) {
 
 }  // namespace
 
+namespace samg {
+uint64_t &launch_counter() {
+    static uint64_t n = 0;
+    return n;
+}
+}  // namespace samg
+
 extern "C" {
+
+uint64_t samg_launch_count(void) { return samg::launch_counter(); }
 
 void samg_default_params(samg_params *p) {
     if (!p) return;
@@ -304,6 +313,49 @@ samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind
     }
     *out = c;
     return SAMG_OK;
+}
+
+samg_status samg_set_triplets_device(samg_ctx *ctx, const double *sigma, const double *U,
+                                     const double *V) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        samg_ctx &c = *ctx;
+        SAMG_CHECK(sigma && U && (c.spd() || V), SAMG_E_INVALID, "null device pointer");
+        cudaStream_t s = c.stream;
+        std::vector<double> one(c.ld, 1.0);
+        c.sigma.upload(one.data(), c.ld, s);  // padding columns keep sigma = 1
+        SAMG_CUDA(cudaMemcpyAsync(c.sigma.p, sigma, c.nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        const int mu = urows(c, 0);
+        SAMG_CUDA(cudaMemcpy2DAsync(c.U.p, c.ld * sizeof(double), U, c.nb * sizeof(double),
+                                    c.nb * sizeof(double), mu, cudaMemcpyDeviceToDevice, s));
+        if (!c.spd())
+            SAMG_CUDA(cudaMemcpy2DAsync(c.V.p, c.ld * sizeof(double), V, c.nb * sizeof(double),
+                                        c.nb * sizeof(double), c.L[0].n, cudaMemcpyDeviceToDevice, s));
+        ritz(c, true);
+    });
+}
+
+samg_status samg_profile(samg_ctx *ctx, int enable) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] { ctx->prof.on = enable != 0; });
+}
+
+samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_t *launches,
+                              double *total_ms, double *alg_bytes) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(kernel_class >= 0 && kernel_class < 5, SAMG_E_INVALID, "kernel class 0..4");
+        ctx->prof.collect();
+        if (launches) *launches = ctx->prof.launches[kernel_class];
+        if (total_ms) *total_ms = ctx->prof.ms[kernel_class];
+        if (alg_bytes) *alg_bytes = ctx->prof.bytes[kernel_class];
+        if (reset)
+            for (int k = 0; k < 5; ++k) {
+                ctx->prof.launches[k] = 0;
+                ctx->prof.ms[k] = 0.0;
+                ctx->prof.bytes[k] = 0.0;
+            }
+    });
 }
 
 samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec) {

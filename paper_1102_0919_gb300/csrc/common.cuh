@@ -114,6 +114,10 @@ struct HCsr {
 
 inline int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
+// Count of kernel launches issued by the library (samg_launch_count).
+uint64_t &launch_counter();
+#define SAMG_COUNT_LAUNCH() (++::samg::launch_counter())
+
 // Columns of a device vector block: n_b padded to a multiple of 4 (16-byte rows
 // in float32, 32-byte rows in float64); padding columns are kept at zero.
 inline int block_ld(int nb) { return round_up(nb, 4); }

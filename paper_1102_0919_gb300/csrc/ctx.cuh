@@ -32,6 +32,64 @@ struct Level {
     Work<double> wd;
 };
 
+// Launch timing with CUDA events on the context's stream (samg_profile).
+struct Profiler {
+    bool on = false;
+    struct Rec { int cls; cudaEvent_t a, b; double bytes; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[5] = {0, 0, 0, 0, 0};
+    double ms[5] = {0, 0, 0, 0, 0}, bytes[5] = {0, 0, 0, 0, 0};
+    cudaEvent_t get() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            SAMG_CUDA(cudaEventCreate(&e));
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(cudaStream_t s, int cls, double b, cudaEvent_t *out) {
+        if (!on) return;
+        *out = get();
+        SAMG_CUDA(cudaEventRecord(*out, s));
+        recs.push_back({cls, *out, nullptr, b});
+    }
+    void end(cudaStream_t s) {
+        if (!on) return;
+        cudaEvent_t e = get();
+        SAMG_CUDA(cudaEventRecord(e, s));
+        recs.back().b = e;
+    }
+    void collect() {  // synchronizes on the recorded events
+        for (auto &r : recs) {
+            float t = 0.f;
+            SAMG_CUDA(cudaEventSynchronize(r.b));
+            SAMG_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+            launches[r.cls]++;
+            ms[r.cls] += t;
+            bytes[r.cls] += r.bytes;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+    ~Profiler() {
+        for (auto &r : recs) { cudaEventDestroy(r.a); if (r.b) cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// RAII bracket of one launch
+struct Prof {
+    Profiler &p;
+    cudaStream_t s;
+    cudaEvent_t e = nullptr;
+    Prof(Profiler &pp, cudaStream_t ss, int cls, double bytes) : p(pp), s(ss) { p.begin(s, cls, bytes, &e); }
+    ~Prof() { if (e) p.end(s); }
+};
+
 struct Coarse {
     int M = 0, m1 = 0;
     DBuf<double> X, Y, lam, W, Wt, work;
@@ -53,6 +111,7 @@ struct samg_ctx {
     // Ritz work
     samg::DBuf<double> AV, AtU, Un, Vn, GU, GV, H, TU, TV, gwork, partu, partv;
     samg::DBuf<int> rstat;
+    samg::Profiler prof;
     std::string err;
     bool poisoned = false;
     bool spd() const { return kind == SAMG_SPD_EIG; }

@@ -22,6 +22,20 @@ template <typename T> static CsrView<T> opt_view(const DCsr &a) {
     return view<T>(a);
 }
 
+// Algorithmic bytes of one pass (what the method must move, no credit for
+// reuse): matrix values + column indices + row offsets, the right-hand side
+// read, the iterate read and written; n_b columns counted (not the padding).
+static double kz_bytes(const KSched &k, int nb, size_t s) {
+    const double val = k.shifted ? 2.0 * s : (double)s;
+    return (double)k.nent * (val + 4.0) + 4.0 * (k.rows + 1.0) + (double)k.rows * nb * s +
+           2.0 * k.cols * nb * s;
+}
+static double spmv_bytes(const DCsr &M, int nb, size_t s) {  // y = M x
+    if (M.empty()) return 0.0;
+    return (double)M.nnz * (s + 4.0) + 4.0 * (M.m + 1.0) + (double)M.n * nb * s +
+           (double)M.m * nb * s;
+}
+
 // ------------------------------------------------------------ relaxation
 // One block Gauss-Seidel relaxation of A v - s B u = kappa,
 // A^t u - s C v = tau (Eqs. genSVDresid1-2, add), sigma fixed per column.
@@ -33,22 +47,39 @@ void relax(samg_ctx &c, int l) {
     cudaStream_t s = c.stream;
     const double *sig = c.sigma.p;
     if (c.minimal()) {
+        const int nb = c.nb;
+        const size_t sz = sizeof(T);
         if (c.spd()) {  // one sweep over the rows of A - s B (Sec. 5.3)
+            Prof pr(c.prof, s, 0, kz_bytes(L.kA, nb, sz));
             launch_kaczmarz<T>(L.kA, ld, w.k.p, w.u.p, sig, s);
             return;
         }
         // v from the rows of A with rhs s B u + kappa
         Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
-        launch_combine<T, T>(L.m, ld, w.k.p, 1.0, tb, Term<T>{}, sig, w.r.p, s);
-        launch_kaczmarz<T>(L.kA, ld, w.r.p, w.v.p, nullptr, s);
+        {
+            Prof pr(c.prof, s, 1, spmv_bytes(L.B, nb, sz) + 2.0 * L.m * nb * sz);
+            launch_combine<T, T>(L.m, ld, w.k.p, 1.0, tb, Term<T>{}, sig, w.r.p, s);
+        }
+        {
+            Prof pr(c.prof, s, 0, kz_bytes(L.kA, nb, sz));
+            launch_kaczmarz<T>(L.kA, ld, w.r.p, w.v.p, nullptr, s);
+        }
         // u from the rows of A^t with rhs s C v + tau
         Term<T> tc{opt_view<T>(L.C), w.v.p, 1.0, true};
-        launch_combine<T, T>(L.n, ld, w.t.p, 1.0, tc, Term<T>{}, sig, w.s.p, s);
-        launch_kaczmarz<T>(L.kAt, ld, w.s.p, w.u.p, nullptr, s);
+        {
+            Prof pr(c.prof, s, 1, spmv_bytes(L.C, nb, sz) + 2.0 * L.n * nb * sz);
+            launch_combine<T, T>(L.n, ld, w.t.p, 1.0, tc, Term<T>{}, sig, w.s.p, s);
+        }
+        {
+            Prof pr(c.prof, s, 0, kz_bytes(L.kAt, nb, sz));
+            launch_kaczmarz<T>(L.kAt, ld, w.s.p, w.u.p, nullptr, s);
+        }
         return;
     }
     // dominant: weighted Jacobi for u from Eq. genSVDresid1, then v (Sec. 3.5)
     const double om = c.prm.omega_J;
+    Prof pr(c.prof, s, 2,
+            2.0 * (spmv_bytes(L.A, c.nb, sizeof(T)) + spmv_bytes(L.B, c.nb, sizeof(T))));
     if (c.spd()) {
         launch_jacobi<T>(L.n, ld, view<T>(L.A), w.u.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p,
                          sig, om, w.tu.p, s);
@@ -74,6 +105,12 @@ void residual_restrict(samg_ctx &c, int l) {
     const int ld = c.ld;
     cudaStream_t s = c.stream;
     const double *sig = c.sigma.p;
+    const size_t sz = sizeof(T);
+    const int nb = c.nb;
+    Prof pr(c.prof, s, 1,
+            spmv_bytes(L.A, nb, sz) + spmv_bytes(L.B, nb, sz) + spmv_bytes(L.Pt, nb, sz) +
+                (c.spd() ? 0.0 : spmv_bytes(L.At, nb, sz) + spmv_bytes(L.C, nb, sz) +
+                                     spmv_bytes(L.Qt, nb, sz)));
     if (c.spd()) {
         Term<T> ta{view<T>(L.A), w.u.p, -1.0, false};
         Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
@@ -103,6 +140,9 @@ void interpolate(samg_ctx &c, int l) {
     const int ld = c.ld;
     cudaStream_t s = c.stream;
     const double *sig = c.sigma.p;
+    Prof pr(c.prof, s, 1,
+            spmv_bytes(L.P, c.nb, sizeof(T)) + (double)L.P.m * c.nb * sizeof(T) +
+                (c.spd() ? 0.0 : spmv_bytes(L.Q, c.nb, sizeof(T)) + (double)L.Q.m * c.nb * sizeof(T)));
     if (c.spd()) {
         launch_combine<T, T>(L.n, ld, w.u.p, 1.0, Term<T>{view<T>(L.P), wc.u.p, 1.0, false},
                              Term<T>{}, sig, w.u.p, s);
@@ -119,6 +159,7 @@ template <typename T>
 void coarse_solve(samg_ctx &c) {
     Level &L = c.L.back();
     Work<T> &w = work<T>(L);
+    Prof pr(c.prof, c.stream, 3, 2.0 * (double)c.co.M * c.co.M * 8.0);
     launch_coarse_apply<T>(c.co.M, c.co.m1, c.ld, c.nb, c.co.lam.p, c.co.W.p, c.co.Wt.p,
                            c.sigma.p, w.k.p, c.spd() ? w.k.p : w.t.p, w.u.p,
                            c.spd() ? w.u.p : w.v.p, c.stream);
@@ -201,9 +242,19 @@ void ritz(samg_ctx &c, bool identity) {
     Level &L0 = c.L[0];
     const int ld = c.ld, nb = c.nb;
     cudaStream_t s = c.stream;
+    Prof pr(c.prof, s, 4,
+            identity ? 0.0
+                     : 10.0 * ((double)L0.m + L0.n) * nb * 8.0 + 12.0 * (double)L0.A.nnz);
     const int64_t n = L0.n;
     const int64_t mu = c.spd() ? L0.n : L0.m;
     Term<double> none{};
+    if (!identity && c.minimal() && !c.spd() && L0.m >= L0.n) {
+        // left basis A V (Rayleigh-Ritz for A^t A on span V): excludes the
+        // null(A^t) modes that no relaxation or correction can remove
+        launch_combine<double, double>(L0.m, ld, nullptr, 0.0,
+                                       Term<double>{view<double>(L0.A), c.V.p, 1.0, false}, none,
+                                       c.sigma.p, c.U.p, s);
+    }
     if (c.spd()) {
         launch_combine<double, double>(L0.n, ld, nullptr, 0.0,
                                        Term<double>{view<double>(L0.A), c.U.p, 1.0, false}, none,
@@ -217,7 +268,9 @@ void ritz(samg_ctx &c, bool identity) {
                                        c.sigma.p, c.AtU.p, s);
     }
     if (identity) {
+        SAMG_COUNT_LAUNCH();
         k_identity<<<1, 256, 0, s>>>(ld, c.TU.p);
+        SAMG_COUNT_LAUNCH();
         k_identity<<<1, 256, 0, s>>>(ld, c.TV.p);
     } else {
         launch_gram(c.U.p, c.U.p, mu, nb, ld, c.GU.p, c.gwork.p, s);

@@ -60,7 +60,9 @@ void launch_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
         SAMG_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * nb * nb, s));
         return;
     }
+    SAMG_COUNT_LAUNCH();
     k_gram_partial<<<chunks, 256, 0, s>>>(X, Y, rows, nb, ld, work);
+    SAMG_COUNT_LAUNCH();
     k_gram_final<<<1, 256, 0, s>>>(work, chunks, nb, G);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -254,6 +256,7 @@ __global__ void k_ritz_small(const double *GU, const double *GV, const double *H
 void launch_ritz_small(const double *GU, const double *GV, const double *H, int nb, int ld,
                        bool spd, bool dominant, double *sigma, double *TU, double *TV,
                        int *status, cudaStream_t s) {
+    SAMG_COUNT_LAUNCH();
     k_ritz_small<<<1, 32, 0, s>>>(GU, GV, H, nb, ld, spd ? 1 : 0, dominant ? 1 : 0, sigma, TU,
                                   TV, status);
     SAMG_CUDA(cudaGetLastError());
@@ -315,6 +318,7 @@ void launch_ritz_update(const double *X, const double *W, const double *T, const
                         double *part, cudaStream_t s) {
     int chunks = (int)((rows + GRAM_ROWS - 1) / GRAM_ROWS);
     if (!chunks) return;
+    SAMG_COUNT_LAUNCH();
     k_ritz_update<<<chunks, 256, 0, s>>>(X, W, T, T2, sigma, rows, nb, ld, Xn, part);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -323,6 +327,7 @@ void launch_ritz_resid(const double *pu, int64_t rows_u, const double *pv, int64
                        int nb, const double *sigma, double *resid, cudaStream_t s) {
     int cu = (int)((rows_u + GRAM_ROWS - 1) / GRAM_ROWS);
     int cv = pv ? (int)((rows_v + GRAM_ROWS - 1) / GRAM_ROWS) : 0;
+    SAMG_COUNT_LAUNCH();
     k_ritz_resid<<<1, 32, 0, s>>>(pu, cu, pv, cv, nb, sigma, resid);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -343,6 +348,7 @@ __global__ void k_dense_fill(int rows, const int *rp, const int *ci, const doubl
 void dense_fill(const DCsr &a, int r_off, int c_off, int Mdim, double *D, bool transpose,
                 cudaStream_t s) {
     if (!a.m) return;
+    SAMG_COUNT_LAUNCH();
     k_dense_fill<<<(a.m + 127) / 128, 128, 0, s>>>(a.m, a.rp.p, a.ci.p, a.vd.p, r_off, c_off, Mdim,
                                                   D, transpose ? 1 : 0);
     SAMG_CUDA(cudaGetLastError());
@@ -495,6 +501,7 @@ __global__ void k_coarse_geneig(int M, const double *X, const double *Yd, double
 
 void launch_coarse_geneig(int M, const double *X, const double *Y, double *work, double *lam,
                           double *W, double *Wt, int *status, cudaStream_t s) {
+    SAMG_COUNT_LAUNCH();
     k_coarse_geneig<<<1, 256, 0, s>>>(M, X, Y, work, lam, W, Wt, status);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -711,6 +718,7 @@ void launch_coarse_apply(int M, int m1, int ld, int nb, const double *lam, const
     auto kern = k_coarse_apply<T>;
     if (smem > 48 * 1024)
         SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SAMG_COUNT_LAUNCH();
     kern<<<nb, 256, smem, s>>>(M, m1, ld, lam, W, Wt, sigma, k1, k2, o1, o2, nb);
     SAMG_CUDA(cudaGetLastError());
 }

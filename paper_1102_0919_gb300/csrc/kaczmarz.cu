@@ -235,6 +235,7 @@ void launch_one(const KSched &ks, const T *ea, const T *eb, const T *inv, const 
     int grid = std::min(ks.nbands, nsm * bps);
     KView kv{ks.err ? ks.err : &ks.ctl.p->err, ks.nbands, ks.band_lvl.p, ks.lvl.p, ks.srow.p, ks.eoff.p,
              ks.ecol.p, ks.eslot.p, ks.req.p, ks.progress.p, ks.ctl.p};
+    SAMG_COUNT_LAUNCH();
     kern<<<grid, KZ_THREADS, smem, s>>>(kv, ea, eb, inv, rhs, x, shift);
     SAMG_CUDA(cudaGetLastError());
 }

@@ -483,9 +483,11 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     // random test vectors (Sec. 3.3)
     const int mu0 = spd ? n : m;
     st.Ut.alloc((size_t)mu0 * ldt);
+    SAMG_COUNT_LAUNCH();
     k_random_block<<<(unsigned)(((int64_t)mu0 * ldt + 255) / 256), 256, 0, s>>>(p.seed, mu0, p.n_t, ldt, st.Ut.p);
     if (!spd) {
         st.Vt.alloc((size_t)n * ldt);
+        SAMG_COUNT_LAUNCH();
         k_random_block<<<(unsigned)(((int64_t)n * ldt + 255) / 256), 256, 0, s>>>(
             p.seed ^ (1ull << 63), n, p.n_t, ldt, st.Vt.p);
         if (st.induced)

@@ -73,8 +73,11 @@ void exclusive_scan(const int64_t *in, int64_t *out, int n, cudaStream_t s) {
     int nb = (n + SCAN_B - 1) / SCAN_B;
     SAMG_CHECK(nb <= SCAN_B, SAMG_E_INVALID, "exclusive_scan: too many elements");
     DBuf<int64_t> bsum(nb + 1), bscan(nb + 1);
+    SAMG_COUNT_LAUNCH();
     k_scan_blocks<<<nb, SCAN_T, 0, s>>>(in, out, bsum.p, n);
+    SAMG_COUNT_LAUNCH();
     k_scan_blocks<<<1, SCAN_T, 0, s>>>(bsum.p, bscan.p, bsum.p + nb, nb);
+    SAMG_COUNT_LAUNCH();
     k_scan_add<<<nb, SCAN_T, 0, s>>>(out, bscan.p, n);
     SAMG_CUDA(cudaGetLastError());
     // out[n] = total = sum of the block sums
@@ -183,23 +186,30 @@ void transpose(const DCsr &A, DCsr &C, cudaStream_t s) {
     C.nnz = A.nnz;
     DBuf<int64_t> cnt(A.n + 1), off(A.n + 1);
     cnt.zero(s);
-    if (A.nnz)
+    if (A.nnz) {
+        SAMG_COUNT_LAUNCH();
         k_count_cols<<<(unsigned)((A.nnz + 255) / 256), 256, 0, s>>>(A.nnz, A.ci.p, cnt.p);
+    }
     exclusive_scan(cnt.p, off.p, A.n, s);
     C.rp.alloc(A.n + 1);
+    SAMG_COUNT_LAUNCH();
     k_i64_to_i32<<<(A.n + 1 + 255) / 256, 256, 0, s>>>(A.n + 1, off.p, C.rp.p);
     DBuf<int> fill(A.n > 0 ? A.n : 1);
     fill.zero(s);
     DBuf<int> ctmp(A.nnz ? A.nnz : 1);
     DBuf<double> vtmp(A.nnz ? A.nnz : 1);
-    if (A.m)
+    if (A.m) {
+        SAMG_COUNT_LAUNCH();
         k_scatter_t<<<(A.m + 255) / 256, 256, 0, s>>>(A.m, A.rp.p, A.ci.p, A.vd.p, off.p, fill.p,
                                                      ctmp.p, vtmp.p);
+    }
     C.ci.alloc(A.nnz ? A.nnz : 1);
     C.vd.alloc(A.nnz ? A.nnz : 1);
-    if (C.m)
+    if (C.m) {
+        SAMG_COUNT_LAUNCH();
         k_rank_sort_rows<<<(unsigned)(((int64_t)C.m * 32 + 255) / 256), 256, 0, s>>>(
             C.m, C.rp.p, ctmp.p, vtmp.p, C.ci.p, C.vd.p);
+    }
     SAMG_CUDA(cudaGetLastError());
     refresh_float(C, s);
     SAMG_CUDA(cudaStreamSynchronize(s));
@@ -290,8 +300,10 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     C.m = m;
     C.n = B.n;
     DBuf<int64_t> ub(m + 1), hs(m + 1), hoff(m + 1);
-    if (m)
+    if (m) {
+        SAMG_COUNT_LAUNCH();
         k_row_bounds<<<(m + 255) / 256, 256, 0, s>>>(m, A.rp.p, A.ci.p, B.rp.p, ub.p, hs.p);
+    }
     exclusive_scan(hs.p, hoff.p, m, s);
     int64_t H = 0;
     SAMG_CUDA(cudaMemcpyAsync(&H, hoff.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -302,8 +314,10 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     vals.zero(s);
     unsigned wb = (unsigned)(((int64_t)m * 32 + 255) / 256);
     if (m) {
+        SAMG_COUNT_LAUNCH();
         k_hash_insert<<<wb, 256, 0, s>>>(m, A.rp.p, A.ci.p, A.vd.p, B.rp.p, B.ci.p, B.vd.p, hoff.p,
                                          keys.p, vals.p);
+        SAMG_COUNT_LAUNCH();
         k_hash_count<<<wb, 256, 0, s>>>(m, hoff.p, keys.p, ub.p);
     }
     DBuf<int64_t> rp64(m + 1);
@@ -314,10 +328,12 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     SAMG_CHECK(nnz < ((int64_t)1 << 31), SAMG_E_INVALID, "spgemm: result nnz >= 2^31");
     C.nnz = nnz;
     C.rp.alloc(m + 1);
+    SAMG_COUNT_LAUNCH();
     k_i64_to_i32<<<(m + 1 + 255) / 256, 256, 0, s>>>(m + 1, rp64.p, C.rp.p);
     C.ci.alloc(nnz ? nnz : 1);
     C.vd.alloc(nnz ? nnz : 1);
-    if (m) k_hash_compact<<<wb, 256, 0, s>>>(m, hoff.p, keys.p, vals.p, rp64.p, C.ci.p, C.vd.p);
+    if (m) { SAMG_COUNT_LAUNCH(); k_hash_compact<<<wb, 256, 0, s>>>(m, hoff.p, keys.p, vals.p, rp64.p, C.ci.p, C.vd.p);
+    }
     SAMG_CUDA(cudaGetLastError());
     refresh_float(C, s);
     SAMG_CUDA(cudaStreamSynchronize(s));

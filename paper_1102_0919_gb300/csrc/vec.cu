@@ -97,6 +97,7 @@ void launch_combine(int rows, int ld, const TI *in0, double a0, const Term<TI> &
     TermD<TI> d2{t2.M, t2.x, (TI)t2.c, t2.sig ? 1 : 0};
     int64_t n = (int64_t)rows * (ld / 4);
     int bs = 256;
+    SAMG_COUNT_LAUNCH();
     k_combine<TI, TO><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rows, ld, in0, (TI)a0, d1, d2,
                                                                     sigma, out);
     SAMG_CUDA(cudaGetLastError());
@@ -145,6 +146,7 @@ void launch_jacobi(int rows, int ld, CsrView<T> A, const T *y, CsrView<T> B, con
     if (rows == 0) return;
     int64_t n = (int64_t)rows * (ld / 4);
     int bs = 256;
+    SAMG_COUNT_LAUNCH();
     k_jacobi<T><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rows, ld, A, y, B, dB, x, kappa,
                                                              sigma, (T)omega, out);
     SAMG_CUDA(cudaGetLastError());
@@ -165,6 +167,7 @@ __global__ void k_convert(size_t n, const TA *__restrict__ a, TB *__restrict__ b
 template <typename TA, typename TB>
 void launch_convert(size_t count, const TA *a, TB *b, cudaStream_t s) {
     if (!count) return;
+    SAMG_COUNT_LAUNCH();
     k_convert<TA, TB><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, a, b);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -179,6 +182,7 @@ __global__ void k_add_to(size_t n, double *__restrict__ x, const TY *__restrict_
 template <typename TY>
 void launch_add_to(size_t count, double *x, const TY *y, cudaStream_t s) {
     if (!count) return;
+    SAMG_COUNT_LAUNCH();
     k_add_to<TY><<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, x, y);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -221,6 +225,7 @@ void launch_coldot(int rows, int nb, int ld, const T *x, CsrView<T> M, const T *
     int bs = 240;
     int64_t g = (n + bs - 1) / bs;
     if (g > 1216) g = 1216;
+    SAMG_COUNT_LAUNCH();
     k_coldot<T><<<(unsigned)g, bs, 0, s>>>(rows, nb, ld, x, M, y, out);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -239,6 +244,7 @@ template <typename T>
 void launch_scale_cols(int rows, int ld, T *x, const double *scale, cudaStream_t s) {
     int64_t n = (int64_t)rows * ld;
     if (!n) return;
+    SAMG_COUNT_LAUNCH();
     k_scale_cols<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rows, ld, x, scale);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -259,6 +265,7 @@ void launch_gather_rows(int k, int ld, const int *idx, const T *x, const double 
                         T *out, cudaStream_t s) {
     int64_t n = (int64_t)k * ld;
     if (!n) return;
+    SAMG_COUNT_LAUNCH();
     k_gather_rows<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(k, ld, idx, x, inv_colscale, out);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -281,6 +288,7 @@ void launch_inv_rownorm2(const DCsr &a, DBuf<double> &outd, DBuf<float> &outf, c
     outd.alloc(a.m);
     outf.alloc(a.m);
     if (!a.m) return;
+    SAMG_COUNT_LAUNCH();
     k_inv_rownorm2<<<(a.m + 255) / 256, 256, 0, s>>>(a.m, a.rp.p, a.vd.p, outd.p, outf.p);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -299,6 +307,7 @@ void launch_diagonal(const DCsr &a, DBuf<double> &outd, DBuf<float> &outf, cudaS
     outd.alloc(a.m);
     outf.alloc(a.m);
     if (!a.m) return;
+    SAMG_COUNT_LAUNCH();
     k_diagonal<<<(a.m + 255) / 256, 256, 0, s>>>(a.m, a.rp.p, a.ci.p, a.vd.p, outd.p, outf.p);
     SAMG_CUDA(cudaGetLastError());
 }

@@ -64,7 +64,7 @@ def test_gradient_256_full_size(prec):
     A = wl.build().to_scipy()
     s = samg.Solver.setup(A, wl.nb, wl.target, wl.kind, prec=prec,
                           **dict(wl.params, seed=W.problem_seed(2)))
-    ok, it = s.solve(1e-8, 120)
+    ok, it = s.solve(1e-8, 300)
     sig, U, V, res = s.triplets()
     s.close()
     assert ok and res.max() <= 1e-8, (it, res)
