@@ -38,6 +38,11 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def log(msg):
+    sys.stderr.write("[bench] %s\n" % msg)
+    sys.stderr.flush()
+
+
 def _env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -193,6 +198,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     levels = s.levels()
+    log("setup %.1f s, levels %s" % (t_setup, levels))
     sig0, U0, V0, res0 = s.triplets()
     # initial boot triplets resident in HBM (torch owns the memory)
     dsig = torch.tensor(sig0, device=dev, dtype=torch.float64)
@@ -213,7 +219,10 @@ def run_gpu(args):
         s.set_precision(prec)
         for _ in range(args.warmup):
             reset()
+            tw = time.perf_counter()
             ok, it = s.solve(args.tol, args.max_outer)
+            log("%s warm-up solve: %d iterations, converged %s, %.2f s" %
+                (prec, it, ok, time.perf_counter() - tw))
         iters = []
         barrier()
         launches0 = samg.samg_launch_count()
@@ -240,6 +249,9 @@ def run_gpu(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         results[prec] = dict(ms=float(t.item()), iters=iters, launches=launches,
                              clocks=clk.summary(), prof=pr if prof else None)
+        log("%s: %.1f ms/solve, iterations %s" % (prec, ms, iters))
+        if prof:
+            log("kernels: %s" % json.dumps(pr))
         _, _, _, rf = s.triplets()
         results[prec]["resid"] = float(rf.max())
     # end to end through the C ABI with host buffers (mixed precision)

@@ -292,7 +292,7 @@ void ritz(samg_ctx &c, bool identity) {
         int st = 0;
         SAMG_CUDA(cudaMemcpyAsync(&st, c.rstat.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SAMG_CUDA(cudaStreamSynchronize(s));
-        SAMG_CHECK(st == 0, SAMG_E_INVALID, "ritz: boot vectors are linearly dependent");
+        SAMG_CHECK(st != 1, SAMG_E_INVALID, "ritz: boot vectors are linearly dependent");
     }
 }
 

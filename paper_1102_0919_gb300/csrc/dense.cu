@@ -70,12 +70,13 @@ void launch_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
 // ================================================================ Ritz (small)
 // Single-thread dense kernels for n_b <= 16: Cholesky, triangular inverse,
 // one-sided (Hestenes) Jacobi SVD, cyclic Jacobi eigensolver.
-__device__ bool chol_upper(double *R, const double *G, int n) {  // G = R^t R
+// G = R^t R.  shift is added to the diagonal (0 for the plain factorization).
+__device__ bool chol_upper(double *R, const double *G, int n, double shift = 0.0) {
     for (int i = 0; i < n * n; ++i) R[i] = 0.0;
     for (int j = 0; j < n; ++j) {
-        double d = G[j * n + j];
+        double d = G[j * n + j] + shift;
         for (int k = 0; k < j; ++k) d -= R[k * n + j] * R[k * n + j];
-        if (!(d > 0.0)) return false;
+        if (!(d > 1e-13 * (G[j * n + j] + shift))) return false;
         d = sqrt(d);
         R[j * n + j] = d;
         for (int i = j + 1; i < n; ++i) {
@@ -182,7 +183,19 @@ __global__ void k_ritz_small(const double *GU, const double *GV, const double *H
     int ord[16];
     const int n = nb;
     status[0] = 0;
-    if (!chol_upper(RU, GU, n) || (!spd && !chol_upper(RV, GV, n))) {
+    // Boot vectors that (nearly) coincide -- two members of a degenerate
+    // cluster relaxed onto the same vector -- make a Gram matrix singular.
+    // The basis is then taken from the factor of G + delta I, delta = 1e-12
+    // max_j G_jj, which keeps n_b directions (the added one is the amplified
+    // remainder of the dependent column) for the projection to sort out.
+    auto factor = [&](double *R, const double *G) {
+        if (chol_upper(R, G, n)) return true;
+        double dmax = 0.0;
+        for (int j = 0; j < n; ++j) dmax = fmax(dmax, G[j * n + j]);
+        status[0] = 2;
+        return chol_upper(R, G, n, 1e-12 * dmax);
+    };
+    if (!factor(RU, GU) || (!spd && !factor(RV, GV))) {
         status[0] = 1;
         return;
     }
