@@ -12,7 +12,9 @@ namespace {
 constexpr int KZ_THREADS = 256;
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
 constexpr int MAX_BAND_ROWS = 1 << 17;
-constexpr int SLOT_CAP = 1600;       // window slots: 1600 * 16 cols * 8 B = 200 KiB
+constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
+// staging chunk limits: levels, rows, entries, staged first values
+constexpr int KZ_CHL = 32, KZ_CHR = 256, KZ_CHE = 1024, KZ_CHX = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any wait
 
 struct Pattern {                      // merged rows: a (and b) coefficients
@@ -112,100 +114,228 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// asynchronous global -> shared copies (sizes 4, 8 or 16 bytes, both aligned)
+template <int S>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (S == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(S)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 struct KView {
     int *err;
     int nbands;
-    const int *band_lvl;
-    const int4 *lvl;
-    const int *srow, *eoff, *ecol, *eslot;
+    const int *band_chunk;   // nbands + 1
+    const int4 *chunk;       // 2 per chunk: {L0, L1, R0, R1}, {E0, E1, X0, X1}
+    const int4 *lvl;         // {first row, first req, publish, 0} + sentinel
+    const int2 *rinfo;       // {original row, first entry}
+    const int2 *ent;         // {column, flags}
+    const int *xsc;          // columns staged per chunk
     const int2 *req;
     unsigned long long *progress;
     KCtl *ctl;
+};
+
+// Shared-memory layout of one staging buffer (byte offsets, 16-byte aligned).
+constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+template <typename T, int LD, bool SHIFT>
+struct Stage {
+    static constexpr int VB = LD * (int)sizeof(T);          // bytes of one vector row
+    static constexpr bool VALS = VB <= 64;                   // stage rhs / first values
+    static constexpr size_t o_lv = 0;
+    static constexpr size_t o_ri = al16(o_lv + 16 * (KZ_CHL + 1));
+    static constexpr size_t o_inv = al16(o_ri + 8 * (KZ_CHR + 1));
+    static constexpr size_t o_ent = al16(o_inv + 8 * KZ_CHR);
+    static constexpr size_t o_a = al16(o_ent + 8 * KZ_CHE);
+    static constexpr size_t o_b = al16(o_a + sizeof(T) * KZ_CHE);
+    static constexpr size_t o_xc = al16(o_b + (SHIFT ? sizeof(T) * KZ_CHE : 0));
+    static constexpr size_t o_rhs = al16(o_xc + 4 * KZ_CHX);
+    static constexpr size_t o_xs = al16(o_rhs + (VALS ? (size_t)VB * KZ_CHR : 0));
+    static constexpr size_t bytes = al16(o_xs + (VALS ? (size_t)VB * KZ_CHX : 0));
+    static constexpr size_t stride = (bytes + 127) / 128 * 128;
 };
 
 template <typename T, int LD, bool SHIFT>
 __global__ void __launch_bounds__(KZ_THREADS)
     k_kaczmarz(KView kv, const T *__restrict__ ea, const T *__restrict__ eb,
                const T *__restrict__ inv, const T *__restrict__ rhs, T *x,
-               const double *__restrict__ shift) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+               const double *__restrict__ shift, int window_slots) {
+    using SG = Stage<T, LD, SHIFT>;
+    extern __shared__ __align__(128) unsigned char smraw[];
     T *win = reinterpret_cast<T *>(smraw);
+    unsigned char *bufs = smraw + ((size_t)window_slots * LD * sizeof(T) + 127) / 128 * 128;
     __shared__ int s_band;
     __shared__ int s_abort;
-    constexpr int RPP = KZ_THREADS / LD;  // rows per pass
+    __shared__ unsigned long long s_pc[64];  // cache: band << 32 | observed level
+    constexpr int RPP = KZ_THREADS / LD;      // rows per pass
     const int tr = threadIdx.x / LD;
     const int j = threadIdx.x % LD;
     const unsigned long long epoch = *((volatile unsigned long long *)&kv.ctl->epoch);
     if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x < 64) s_pc[threadIdx.x] = ~0ull;
     const T sh = SHIFT ? (T)shift[j] : T(0);
+
+    // issue the copies of chunk c's schedule arrays into buffer bi
+    auto load_sched = [&](int c, int bi) {
+        unsigned char *B = bufs + (size_t)bi * SG::stride;
+        const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
+        const int nl = c0.y - c0.x, nr = c0.w - c0.z, ne = c1.y - c1.x, nx = c1.w - c1.z;
+        for (int q = threadIdx.x; q <= nl; q += blockDim.x)
+            cp_async<16>(B + SG::o_lv + 16 * q, kv.lvl + c0.x + q);
+        for (int q = threadIdx.x; q <= nr; q += blockDim.x)
+            cp_async<8>(B + SG::o_ri + 8 * q, kv.rinfo + c0.z + q);
+        for (int q = threadIdx.x; q < nr; q += blockDim.x)
+            cp_async<sizeof(T)>(B + SG::o_inv + sizeof(T) * q, inv + c0.z + q);
+        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+            cp_async<8>(B + SG::o_ent + 8 * q, kv.ent + c1.x + q);
+            cp_async<sizeof(T)>(B + SG::o_a + sizeof(T) * q, ea + c1.x + q);
+            if (SHIFT) cp_async<sizeof(T)>(B + SG::o_b + sizeof(T) * q, eb + c1.x + q);
+        }
+        for (int q = threadIdx.x; q < nx; q += blockDim.x)
+            cp_async<4>(B + SG::o_xc + 4 * q, kv.xsc + c1.z + q);
+        cp_commit();
+    };
+    // right-hand sides of the chunk's rows and the first values no other band writes
+    auto load_vals = [&](int c, int bi) {
+        unsigned char *B = bufs + (size_t)bi * SG::stride;
+        if (SG::VALS) {
+            const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
+            const int nr = c0.w - c0.z, nx = c1.w - c1.z;
+            const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
+            const int *xc = reinterpret_cast<const int *>(B + SG::o_xc);
+            constexpr int P = SG::VB / 16;  // 16-byte pieces per vector row
+            if (rhs)
+                for (int q = threadIdx.x; q < nr * P; q += blockDim.x) {
+                    const int r = q / P, p = q % P;
+                    cp_async<16>(B + SG::o_rhs + (size_t)SG::VB * r + 16 * p,
+                                 reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + 16 * p);
+                }
+            for (int q = threadIdx.x; q < nx * P; q += blockDim.x) {
+                const int r = q / P, p = q % P;
+                cp_async<16>(B + SG::o_xs + (size_t)SG::VB * r + 16 * p,
+                             reinterpret_cast<const unsigned char *>(x + (size_t)xc[r] * LD) + 16 * p);
+            }
+        }
+        cp_commit();
+    };
+
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_band = (int)atomicAdd(&kv.ctl->ticket, 1u);
         __syncthreads();
         const int b = s_band;
         if (b >= kv.nbands || s_abort) break;
-        const int L0 = kv.band_lvl[b], L1 = kv.band_lvl[b + 1];
-        for (int L = L0; L < L1; ++L) {
-            const int4 lv = kv.lvl[L];
-            const int4 ln = kv.lvl[L + 1];
-            if (ln.y > lv.y) {  // cross-band requirements of this level
-                for (int q = lv.y + threadIdx.x; q < ln.y; q += blockDim.x) {
-                    const int2 rq = kv.req[q];
-                    const unsigned long long target = (epoch << 32) | (unsigned)rq.y;
-                    const unsigned long long t0 = gtimer();
-                    while (ld_acquire(&kv.progress[rq.x]) < target) {
-                        if (*((volatile int *)kv.err) || gtimer() - t0 > WAIT_NS) {
-                            atomicExch(kv.err, 1);
-                            s_abort = 1;
-                            break;
+        const int cb = kv.band_chunk[b], ce = kv.band_chunk[b + 1];
+        const int Lband = kv.chunk[2 * cb].x;
+        load_sched(cb, 0);
+        for (int c = cb; c < ce && !s_abort; ++c) {
+            const int bi = (c - cb) & 1;
+            unsigned char *B = bufs + (size_t)bi * SG::stride;
+            cp_wait<0>();
+            __syncthreads();
+            load_vals(c, bi);
+            if (c + 1 < ce) {
+                load_sched(c + 1, bi ^ 1);
+                cp_wait<1>();
+            } else {
+                cp_wait<0>();
+            }
+            __syncthreads();
+            const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
+            const int4 *lv = reinterpret_cast<const int4 *>(B + SG::o_lv);
+            const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
+            const T *sinv = reinterpret_cast<const T *>(B + SG::o_inv);
+            const int2 *se = reinterpret_cast<const int2 *>(B + SG::o_ent);
+            const T *sa = reinterpret_cast<const T *>(B + SG::o_a);
+            const T *sb = reinterpret_cast<const T *>(B + SG::o_b);
+            const T *srhs = reinterpret_cast<const T *>(B + SG::o_rhs);
+            const T *sxs = reinterpret_cast<const T *>(B + SG::o_xs);
+            for (int L = 0; L < c0.y - c0.x; ++L) {
+                const int4 l0 = lv[L], l1 = lv[L + 1];
+                if (l1.y > l0.y) {  // cross-band requirements of this level
+                    for (int q = l0.y + threadIdx.x; q < l1.y; q += blockDim.x) {
+                        const int2 rq = kv.req[q];
+                        const unsigned long long key = s_pc[rq.x & 63];
+                        if ((int)(key >> 32) == rq.x && (unsigned)key >= (unsigned)rq.y) continue;
+                        const unsigned long long target = (epoch << 32) | (unsigned)rq.y;
+                        const unsigned long long t0 = gtimer();
+                        unsigned long long v;
+                        while ((v = ld_acquire(&kv.progress[rq.x])) < target) {
+                            if (*((volatile int *)kv.err) || gtimer() - t0 > WAIT_NS) {
+                                atomicExch(kv.err, 1);
+                                s_abort = 1;
+                                break;
+                            }
+                            __nanosleep(20);
                         }
-                        __nanosleep(32);
+                        if ((v >> 32) == epoch)
+                            s_pc[rq.x & 63] = ((unsigned long long)(unsigned)rq.x << 32) | (v & 0xffffffffull);
+                    }
+                    __syncthreads();
+                    if (s_abort) break;
+                }
+                if (tr < RPP) {
+                    for (int k = l0.x - c0.z + tr; k < l1.x - c0.z; k += RPP) {
+                        const int2 rk = ri[k];
+                        const int e0 = rk.y - c1.x, e1 = ri[k + 1].y - c1.x;
+                        T vals[8];
+                        T dot = T(0), nrm = T(0);
+                        for (int e = e0; e < e1; ++e) {
+                            const int2 en = se[e];
+                            const int fl = en.y;
+                            const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
+                            T val;
+                            if (fl & 1)
+                                val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
+                                                             : __ldcg(x + (size_t)en.x * LD + j);
+                            else
+                                val = win[((fl >> 3) & 0xfff) * LD + j];
+                            if (e - e0 < 8) vals[e - e0] = val;
+                            dot = fma(coef, val, dot);
+                            if (SHIFT) nrm = fma(coef, coef, nrm);
+                        }
+                        const T bi2 = rhs ? (SG::VALS ? srhs[k * LD + j] : rhs[(size_t)rk.x * LD + j]) : T(0);
+                        T d = bi2 - dot;
+                        if (SHIFT)
+                            d = nrm > T(0) ? d / nrm : T(0);
+                        else
+                            d *= sinv[k];
+                        for (int e = e0; e < e1; ++e) {
+                            const int2 en = se[e];
+                            const int fl = en.y;
+                            const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
+                            T val;
+                            if (e - e0 < 8) {
+                                val = vals[e - e0];
+                            } else if (fl & 1) {
+                                val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
+                                                             : __ldcg(x + (size_t)en.x * LD + j);
+                            } else {
+                                val = win[((fl >> 3) & 0xfff) * LD + j];
+                            }
+                            const T nv = fma(d, coef, val);
+                            if (fl & 2)
+                                __stcg(x + (size_t)en.x * LD + j, nv);
+                            else
+                                win[((fl >> 3) & 0xfff) * LD + j] = nv;
+                        }
                     }
                 }
                 __syncthreads();
-                if (s_abort) break;
-            }
-            if (tr < RPP) {
-                for (int k = lv.x + tr; k < ln.x; k += RPP) {
-                    const int row = kv.srow[k];
-                    const int e0 = kv.eoff[k], e1 = kv.eoff[k + 1];
-                    T dot = T(0), nrm = T(0);
-                    for (int e = e0; e < e1; ++e) {
-                        const int sl = kv.eslot[e];
-                        const T coef = SHIFT ? ea[e] - sh * eb[e] : ea[e];
-                        const T val = (sl & 1) ? __ldcg(x + (size_t)kv.ecol[e] * LD + j)
-                                               : win[(sl >> 2) * LD + j];
-                        dot = fma(coef, val, dot);
-                        if (SHIFT) nrm = fma(coef, coef, nrm);
-                    }
-                    T d = (rhs ? rhs[(size_t)row * LD + j] : T(0)) - dot;
-                    if (SHIFT)
-                        d = nrm > T(0) ? d / nrm : T(0);
-                    else
-                        d *= inv[k];
-                    for (int e = e0; e < e1; ++e) {
-                        const int sl = kv.eslot[e];
-                        const T coef = SHIFT ? ea[e] - sh * eb[e] : ea[e];
-                        T *gp = x + (size_t)kv.ecol[e] * LD + j;
-                        const T val = (sl & 1) ? __ldcg(gp) : win[(sl >> 2) * LD + j];
-                        const T nv = fma(d, coef, val);
-                        if (sl & 2)
-                            __stcg(gp, nv);
-                        else
-                            win[(sl >> 2) * LD + j] = nv;
-                    }
-                }
-            }
-            __syncthreads();
-            if (lv.z && threadIdx.x == 0) {
-                __threadfence();
-                st_release(&kv.progress[b], (epoch << 32) | (unsigned)(L - L0 + 1));
+                if (l0.z && threadIdx.x == 0)
+                    st_release(&kv.progress[b], (epoch << 32) | (unsigned)(c0.x + L - Lband + 1));
             }
         }
+        cp_wait<0>();
         if (threadIdx.x == 0 && !s_abort) {
-            __threadfence();
-            st_release(&kv.progress[b], (epoch << 32) | (unsigned)(L1 - L0));
+            const int Lend = kv.chunk[2 * (ce - 1)].y;
+            st_release(&kv.progress[b], (epoch << 32) | (unsigned)(Lend - Lband));
         }
     }
     __syncthreads();
@@ -221,22 +351,34 @@ __global__ void __launch_bounds__(KZ_THREADS)
     }
 }
 
+struct LaunchCfg { int grid = 0; size_t smem = 0; };
+
 template <typename T, int LD, bool SHIFT>
 void launch_one(const KSched &ks, const T *ea, const T *eb, const T *inv, const T *rhs, T *x,
                 const double *shift, cudaStream_t s) {
-    size_t smem = (size_t)std::max(ks.max_slots, 1) * LD * sizeof(T);
+    using SG = Stage<T, LD, SHIFT>;
+    static int cached_slots = -1;
+    static LaunchCfg cfg;
+    static int nsm = 0;
     auto kern = k_kaczmarz<T, LD, SHIFT>;
-    SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, nsm = 0, bps = 0;
-    SAMG_CUDA(cudaGetDevice(&dev));
-    SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    SAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, KZ_THREADS, smem));
-    SAMG_CHECK(bps > 0, SAMG_E_CUDA, "kaczmarz: window does not fit in shared memory");
-    int grid = std::min(ks.nbands, nsm * bps);
-    KView kv{ks.err ? ks.err : &ks.ctl.p->err, ks.nbands, ks.band_lvl.p, ks.lvl.p, ks.srow.p, ks.eoff.p,
-             ks.ecol.p, ks.eslot.p, ks.req.p, ks.progress.p, ks.ctl.p};
+    const int slots = std::max(ks.max_slots, 1);
+    const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + 2 * SG::stride;
+    if (cached_slots != slots) {
+        SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, bps = 0;
+        SAMG_CUDA(cudaGetDevice(&dev));
+        SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        SAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, KZ_THREADS, smem));
+        SAMG_CHECK(bps > 0, SAMG_E_CUDA, "kaczmarz: staging buffers do not fit in shared memory");
+        cfg.grid = nsm * bps;
+        cfg.smem = smem;
+        cached_slots = slots;
+    }
+    const int grid = std::min(ks.nbands, cfg.grid);
+    KView kv{ks.err ? ks.err : &ks.ctl.p->err, ks.nbands, ks.band_chunk.p, ks.chunk.p, ks.lvl.p,
+             ks.rinfo.p, ks.ent.p, ks.xsc.p, ks.req.p, ks.progress.p, ks.ctl.p};
     SAMG_COUNT_LAUNCH();
-    kern<<<grid, KZ_THREADS, smem, s>>>(kv, ea, eb, inv, rhs, x, shift);
+    kern<<<grid, KZ_THREADS, smem, s>>>(kv, ea, eb, inv, rhs, x, shift, slots);
     SAMG_CUDA(cudaGetLastError());
 }
 
@@ -249,7 +391,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     ks.cols = cols;
     ks.shifted = (B != nullptr);
     BandWork w(cols);
-    // 1. bands
+    // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
     std::vector<int> bstart;
     int slots = 0;
     for (int r0 = 0; r0 < rows;) {
@@ -272,27 +414,26 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     const int nb = (int)bstart.size();
     bstart.push_back(rows);
     ks.nbands = nb;
-    // 2. levels, slots, entries, requirements
-    std::vector<int> band_lvl(nb + 1, 0);
-    std::vector<int4> lvl;
-    std::vector<int> srow, eoff, ecol, eslot;
+    // 2. per band: levels, window slots, sub-levels (<= chunk limits), chunks
+    std::vector<int> band_chunk(nb + 1, 0);
+    std::vector<int4> lvl, chunk;
+    std::vector<int2> rinfo, ent, req;
+    std::vector<int> xsc;
     std::vector<double> ea, eb, inv;
-    std::vector<int2> req;
-    std::vector<int> g_band(cols, -1), g_lvl(cols, 0), slot(cols, 0);
+    std::vector<int> g_band(cols, -1), g_sub(cols, 0), slot(cols, 0), last_sub(cols, 0);
     std::vector<int> waited(nb, 0), waited_stamp(nb, -1);
+    ent.reserve(p.ci.size());
     ea.reserve(p.ci.size());
-    ecol.reserve(p.ci.size());
-    eslot.reserve(p.ci.size());
     if (ks.shifted) eb.reserve(p.ci.size());
     int max_slots = 0;
-    std::vector<std::vector<int>> pub;  // per band: levels to publish
-    pub.resize(nb);
-    struct PendReq { int lvl, band, need; };
+    std::vector<std::vector<int>> pub(nb);  // per band: band-local sub-levels to publish
+    std::vector<int> band_lvl0(nb + 1, 0);
+    struct PendReq { int sub, band, need; };
+    struct RowRec { int row, sub; };
     for (int b = 0; b < nb; ++b) {
         const int r0 = bstart[b], r1 = bstart[b + 1];
         int nl = analyze_band(p, r0, r1, w, &slots);
         max_slots = std::max(max_slots, slots);
-        band_lvl[b] = (int)lvl.size();
         // rows grouped by level (ascending row order inside a level)
         std::vector<int> lcount(nl + 1, 0);
         for (int r = r0; r < r1; ++r) lcount[w.rowlv[r - r0] + 1]++;
@@ -302,56 +443,129 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
             std::vector<int> fillp(lcount.begin(), lcount.end() - 1);
             for (int r = r0; r < r1; ++r) order[fillp[w.rowlv[r - r0]]++] = r;
         }
-        // slot assignment by interval colouring over levels
+        // window slots by interval colouring over levels
         std::vector<std::vector<int>> starts(nl), ends(nl);
         for (int c : w.touched)
             if (w.cnt[c] >= 2) {
                 starts[w.firstlv[c]].push_back(c);
                 ends[w.lastlv[c]].push_back(c);
             }
-        std::vector<int> freel;
-        int next = 0;
-        for (int l = 0; l < nl; ++l) {
-            for (int c : starts[l]) {
-                if (!freel.empty()) { slot[c] = freel.back(); freel.pop_back(); }
-                else slot[c] = next++;
+        {
+            std::vector<int> freel;
+            int next = 0;
+            for (int l = 0; l < nl; ++l) {
+                for (int c : starts[l]) {
+                    if (!freel.empty()) { slot[c] = freel.back(); freel.pop_back(); }
+                    else slot[c] = next++;
+                }
+                for (int c : ends[l]) freel.push_back(slot[c]);
             }
-            for (int c : ends[l]) freel.push_back(slot[c]);
         }
-        // entries and requirements
-        std::vector<PendReq> pend;
+        // sub-levels: a level's independent rows split so that each piece fits
+        // one staging chunk
+        std::vector<RowRec> rr;
+        std::vector<int> sub_rows, sub_ents, sub_xs;  // per sub-level counts
         for (int l = 0; l < nl; ++l) {
-            int4 L4;
-            L4.x = (int)srow.size();
-            L4.y = 0; L4.z = 0; L4.w = 0;
-            lvl.push_back(L4);
+            int cr = 0, ce = 0, cx = 0;
+            bool open = false;
             for (int k = lcount[l]; k < lcount[l + 1]; ++k) {
                 const int r = order[k];
-                srow.push_back(r);
-                eoff.push_back((int)ecol.size());
+                const int ne = (int)(p.rp[r + 1] - p.rp[r]);
+                int nx = 0;
+                for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
+                    const int c = p.ci[e];
+                    if (w.firstlv[c] == l && g_band[c] < 0) ++nx;
+                }
+                if (!open || cr + 1 > KZ_CHR || ce + ne > KZ_CHE || cx + nx > KZ_CHX) {
+                    sub_rows.push_back(0); sub_ents.push_back(0); sub_xs.push_back(0);
+                    cr = ce = cx = 0;
+                    open = true;
+                }
+                SAMG_CHECK(ne <= KZ_CHE && nx <= KZ_CHX, SAMG_E_INVALID,
+                           "kaczmarz: a row has more entries than a staging chunk holds");
+                cr += 1; ce += ne; cx += nx;
+                sub_rows.back() = cr; sub_ents.back() = ce; sub_xs.back() = cx;
+                rr.push_back({r, (int)sub_rows.size() - 1});
+            }
+        }
+        const int nsub = (int)sub_rows.size();
+        // chunks of consecutive sub-levels
+        std::vector<int> sub_chunk(nsub), chunk_first_sub;
+        {
+            int cl = 0, cr = 0, ce = 0, cx = 0;
+            for (int q = 0; q < nsub; ++q) {
+                if (q == 0 || cl + 1 > KZ_CHL || cr + sub_rows[q] > KZ_CHR ||
+                    ce + sub_ents[q] > KZ_CHE || cx + sub_xs[q] > KZ_CHX) {
+                    chunk_first_sub.push_back(q);
+                    cl = cr = ce = cx = 0;
+                }
+                cl += 1; cr += sub_rows[q]; ce += sub_ents[q]; cx += sub_xs[q];
+                sub_chunk[q] = (int)chunk_first_sub.size() - 1;
+            }
+        }
+        for (const RowRec &x : rr)
+            for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e)
+                if (w.lastlv[p.ci[e]] == w.rowlv[x.row - r0]) last_sub[p.ci[e]] = x.sub;
+        // emit levels, rows, entries, chunk records, requirements
+        const int L0 = (int)lvl.size();
+        band_lvl0[b] = L0;
+        band_chunk[b] = (int)chunk.size() / 2;
+        std::vector<PendReq> pend;
+        size_t ri = 0;
+        int cur_chunk = -1, xs_local = 0;
+        int4 crec0{0, 0, 0, 0}, crec1{0, 0, 0, 0};
+        auto close_chunk = [&]() {
+            if (cur_chunk < 0) return;
+            crec0.y = (int)lvl.size();
+            crec0.w = (int)rinfo.size();
+            crec1.y = (int)ent.size();
+            crec1.w = (int)xsc.size();
+            chunk.push_back(crec0);
+            chunk.push_back(crec1);
+        };
+        for (int q = 0; q < nsub; ++q) {
+            if (sub_chunk[q] != cur_chunk) {
+                close_chunk();
+                cur_chunk = sub_chunk[q];
+                crec0 = int4{(int)lvl.size(), 0, (int)rinfo.size(), 0};
+                crec1 = int4{(int)ent.size(), 0, (int)xsc.size(), 0};
+                xs_local = 0;
+            }
+            int4 L4{(int)rinfo.size(), 0, 0, 0};
+            lvl.push_back(L4);
+            for (; ri < rr.size() && rr[ri].sub == q; ++ri) {
+                const int r = rr[ri].row;
+                const int lv = w.rowlv[r - r0];
+                rinfo.push_back(make_int2(r, (int)ent.size()));
                 double n2 = 0.0;
                 for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
                     const int c = p.ci[e];
-                    const int first = (w.firstlv[c] == l), last = (w.lastlv[c] == l);
+                    const int first = (w.firstlv[c] == lv), last = (w.lastlv[c] == lv);
                     const int sl = (w.cnt[c] >= 2) ? slot[c] : 0;
-                    ecol.push_back(c);
-                    eslot.push_back((sl << 2) | (first ? 1 : 0) | (last ? 2 : 0));
+                    int staged = 0, xi = 0;
+                    if (first && g_band[c] < 0) {
+                        staged = 1;
+                        xi = xs_local++;
+                        xsc.push_back(c);
+                    }
+                    ent.push_back(make_int2(c, first | (last << 1) | (staged << 2) | (sl << 3) | (xi << 15)));
                     ea.push_back(p.a[e]);
                     if (ks.shifted) eb.push_back(p.b[e]);
                     n2 += p.a[e] * p.a[e];
-                    if (first && g_band[c] >= 0) pend.push_back({l, g_band[c], g_lvl[c] + 1});
+                    if (first && g_band[c] >= 0) pend.push_back({q, g_band[c], g_sub[c] + 1});
                 }
                 inv.push_back(n2 > 0.0 ? 1.0 / n2 : 0.0);
             }
         }
-        // per level: max need per band, dropping needs already waited for
+        close_chunk();
+        // per sub-level: max need per band, dropping needs already waited for
         std::sort(pend.begin(), pend.end(), [](const PendReq &a, const PendReq &b2) {
-            return a.lvl != b2.lvl ? a.lvl < b2.lvl : (a.band != b2.band ? a.band < b2.band : a.need > b2.need);
+            return a.sub != b2.sub ? a.sub < b2.sub : (a.band != b2.band ? a.band < b2.band : a.need > b2.need);
         });
         size_t q = 0;
-        for (int l = 0; l < nl; ++l) {
-            lvl[band_lvl[b] + l].y = (int)req.size();
-            while (q < pend.size() && pend[q].lvl == l) {
+        for (int l = 0; l < nsub; ++l) {
+            lvl[L0 + l].y = (int)req.size();
+            while (q < pend.size() && pend[q].sub == l) {
                 const PendReq &pr = pend[q];
                 if (waited_stamp[pr.band] != b || waited[pr.band] < pr.need) {
                     waited_stamp[pr.band] = b;
@@ -359,35 +573,32 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                     req.push_back(make_int2(pr.band, pr.need));
                     pub[pr.band].push_back(pr.need - 1);
                 }
-                // skip the rest of this (level, band) group
                 const int bb = pr.band;
-                while (q < pend.size() && pend[q].lvl == l && pend[q].band == bb) ++q;
+                while (q < pend.size() && pend[q].sub == l && pend[q].band == bb) ++q;
             }
         }
         for (int c : w.touched) {
             g_band[c] = b;
-            g_lvl[c] = w.lastlv[c];
+            g_sub[c] = last_sub[c];
         }
     }
-    band_lvl[nb] = (int)lvl.size();
+    band_chunk[nb] = (int)chunk.size() / 2;
+    band_lvl0[nb] = (int)lvl.size();
     for (int b = 0; b < nb; ++b)
-        for (int l : pub[b]) lvl[band_lvl[b] + l].z = 1;
-    int4 sentinel;
-    sentinel.x = (int)srow.size();
-    sentinel.y = (int)req.size();
-    sentinel.z = 0; sentinel.w = 0;
-    lvl.push_back(sentinel);
-    eoff.push_back((int)ecol.size());
+        for (int l : pub[b]) lvl[band_lvl0[b] + l].z = 1;
+    lvl.push_back(int4{(int)rinfo.size(), (int)req.size(), 0, 0});
+    rinfo.push_back(make_int2(0, (int)ent.size()));
     ks.nlevels = (int)lvl.size() - 1;
     ks.max_slots = max_slots;
-    ks.nent = (int64_t)ecol.size();
+    ks.nent = (int64_t)ent.size();
+    ks.nchunks = (int)chunk.size() / 2;
     // 3. upload
-    ks.band_lvl.upload(band_lvl.data(), band_lvl.size(), s);
+    ks.band_chunk.upload(band_chunk.data(), band_chunk.size(), s);
+    ks.chunk.upload(chunk.data(), chunk.size(), s);
     ks.lvl.upload(lvl.data(), lvl.size(), s);
-    ks.srow.upload(srow.data(), srow.size(), s);
-    ks.eoff.upload(eoff.data(), eoff.size(), s);
-    ks.ecol.upload(ecol.data(), ecol.size(), s);
-    ks.eslot.upload(eslot.data(), eslot.size(), s);
+    ks.rinfo.upload(rinfo.data(), rinfo.size(), s);
+    if (ent.empty()) ent.push_back(make_int2(0, 0));
+    ks.ent.upload(ent.data(), ent.size(), s);
     ks.ea_d.upload(ea.data(), ea.size(), s);
     std::vector<float> f(ea.begin(), ea.end());
     ks.ea_f.upload(f.data(), f.size(), s);
@@ -399,6 +610,8 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     ks.inv_d.upload(inv.data(), inv.size(), s);
     std::vector<float> fi(inv.begin(), inv.end());
     ks.inv_f.upload(fi.data(), fi.size(), s);
+    if (xsc.empty()) xsc.push_back(0);
+    ks.xsc.upload(xsc.data(), xsc.size(), s);
     if (req.empty()) req.push_back(make_int2(0, 0));
     ks.req.upload(req.data(), req.size(), s);
     ks.progress.alloc(std::max(nb, 1));

@@ -29,16 +29,16 @@ struct KCtl {                 // device control block of one schedule
 };
 
 struct KSched {
-    int rows = 0, cols = 0, nbands = 0, nlevels = 0;
+    int rows = 0, cols = 0, nbands = 0, nlevels = 0, nchunks = 0;
     int max_slots = 0;
     int64_t nent = 0;
     bool shifted = false;      // rows of A - shift_j B (SPD kind)
-    DBuf<int> band_lvl;        // nbands + 1: first global level of each band
+    DBuf<int> band_chunk;      // nbands + 1: first staging chunk of each band
+    DBuf<int4> chunk;          // 2 per chunk: {L0, L1, R0, R1}, {E0, E1, X0, X1}
     DBuf<int4> lvl;            // nlevels + 1: {first sched row, first req, publish, 0}
-    DBuf<int> srow;            // scheduled row -> original row
-    DBuf<int> eoff;            // scheduled row -> first entry (+1 sentinel)
-    DBuf<int> ecol;            // entry column
-    DBuf<int> eslot;           // slot << 2 | 1 (first touch) | 2 (last touch)
+    DBuf<int2> rinfo;          // scheduled row -> {original row, first entry} (+ sentinel)
+    DBuf<int2> ent;            // {column, 1 first | 2 last | 4 staged | slot << 3 | xs << 15}
+    DBuf<int> xsc;             // per chunk: columns whose first values are staged
     DBuf<double> ea_d, eb_d;   // entry coefficients (a; b for the shifted form)
     DBuf<float> ea_f, eb_f;
     DBuf<double> inv_d;        // 1 / ||r_i||^2 per scheduled row (unshifted form)
