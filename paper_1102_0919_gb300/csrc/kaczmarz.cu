@@ -10,6 +10,7 @@ namespace samg {
 namespace {
 
 constexpr int KZ_THREADS = 256;
+constexpr int KZ_COMPUTE = 224;    // compute threads (7 warps); warp 7 communicates
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
 constexpr int MAX_BAND_ROWS = 1 << 17;
 constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
@@ -161,6 +162,22 @@ struct Stage {
     static constexpr size_t stride = (bytes + 127) / 128 * 128;
 };
 
+__device__ __forceinline__ void bar_compute() {  // named barrier of the compute warps
+    asm volatile("bar.sync 1, %0;" ::"n"(KZ_COMPUTE) : "memory");
+}
+__device__ __forceinline__ int ld_acq_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel_cta(int *p, int v) {
+    asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
+// Warps 0 .. KZ_COMPUTE/32 - 1 compute; the last warp communicates: it
+// publishes the band's progress (release, coalescing levels) and polls the
+// progress that upcoming levels require (acquire), so that the compute warps
+// only synchronize through a named barrier and shared-memory flags.
 template <typename T, int LD, bool SHIFT>
 __global__ void __launch_bounds__(KZ_THREADS)
     k_kaczmarz(KView kv, const T *__restrict__ ea, const T *__restrict__ eb,
@@ -172,36 +189,35 @@ __global__ void __launch_bounds__(KZ_THREADS)
     unsigned char *bufs = smraw + ((size_t)window_slots * LD * sizeof(T) + 127) / 128 * 128;
     __shared__ int s_band;
     __shared__ int s_abort;
-    __shared__ unsigned long long s_pc[64];  // cache: band << 32 | observed level
-    constexpr int RPP = KZ_THREADS / LD;      // rows per pass
+    __shared__ int s_done;   // band-local levels completed by the compute warps
+    __shared__ int s_ready;  // band-local levels whose requirements are met
+    constexpr int RPP = KZ_COMPUTE / LD;  // rows per pass
+    const bool comm = threadIdx.x >= KZ_COMPUTE;
     const int tr = threadIdx.x / LD;
     const int j = threadIdx.x % LD;
     const unsigned long long epoch = *((volatile unsigned long long *)&kv.ctl->epoch);
     if (threadIdx.x == 0) s_abort = 0;
-    if (threadIdx.x < 64) s_pc[threadIdx.x] = ~0ull;
     const T sh = SHIFT ? (T)shift[j] : T(0);
 
-    // issue the copies of chunk c's schedule arrays into buffer bi
     auto load_sched = [&](int c, int bi) {
         unsigned char *B = bufs + (size_t)bi * SG::stride;
         const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
         const int nl = c0.y - c0.x, nr = c0.w - c0.z, ne = c1.y - c1.x, nx = c1.w - c1.z;
-        for (int q = threadIdx.x; q <= nl; q += blockDim.x)
+        for (int q = threadIdx.x; q <= nl; q += KZ_COMPUTE)
             cp_async<16>(B + SG::o_lv + 16 * q, kv.lvl + c0.x + q);
-        for (int q = threadIdx.x; q <= nr; q += blockDim.x)
+        for (int q = threadIdx.x; q <= nr; q += KZ_COMPUTE)
             cp_async<8>(B + SG::o_ri + 8 * q, kv.rinfo + c0.z + q);
-        for (int q = threadIdx.x; q < nr; q += blockDim.x)
+        for (int q = threadIdx.x; q < nr; q += KZ_COMPUTE)
             cp_async<sizeof(T)>(B + SG::o_inv + sizeof(T) * q, inv + c0.z + q);
-        for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+        for (int q = threadIdx.x; q < ne; q += KZ_COMPUTE) {
             cp_async<8>(B + SG::o_ent + 8 * q, kv.ent + c1.x + q);
             cp_async<sizeof(T)>(B + SG::o_a + sizeof(T) * q, ea + c1.x + q);
             if (SHIFT) cp_async<sizeof(T)>(B + SG::o_b + sizeof(T) * q, eb + c1.x + q);
         }
-        for (int q = threadIdx.x; q < nx; q += blockDim.x)
+        for (int q = threadIdx.x; q < nx; q += KZ_COMPUTE)
             cp_async<4>(B + SG::o_xc + 4 * q, kv.xsc + c1.z + q);
         cp_commit();
     };
-    // right-hand sides of the chunk's rows and the first values no other band writes
     auto load_vals = [&](int c, int bi) {
         unsigned char *B = bufs + (size_t)bi * SG::stride;
         if (SG::VALS) {
@@ -209,14 +225,14 @@ __global__ void __launch_bounds__(KZ_THREADS)
             const int nr = c0.w - c0.z, nx = c1.w - c1.z;
             const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
             const int *xc = reinterpret_cast<const int *>(B + SG::o_xc);
-            constexpr int P = SG::VB / 16;  // 16-byte pieces per vector row
+            constexpr int P = SG::VB / 16;
             if (rhs)
-                for (int q = threadIdx.x; q < nr * P; q += blockDim.x) {
+                for (int q = threadIdx.x; q < nr * P; q += KZ_COMPUTE) {
                     const int r = q / P, p = q % P;
                     cp_async<16>(B + SG::o_rhs + (size_t)SG::VB * r + 16 * p,
                                  reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + 16 * p);
                 }
-            for (int q = threadIdx.x; q < nx * P; q += blockDim.x) {
+            for (int q = threadIdx.x; q < nx * P; q += KZ_COMPUTE) {
                 const int r = q / P, p = q % P;
                 cp_async<16>(B + SG::o_xs + (size_t)SG::VB * r + 16 * p,
                              reinterpret_cast<const unsigned char *>(x + (size_t)xc[r] * LD) + 16 * p);
@@ -227,115 +243,151 @@ __global__ void __launch_bounds__(KZ_THREADS)
 
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_band = (int)atomicAdd(&kv.ctl->ticket, 1u);
+        if (threadIdx.x == 0) {
+            s_band = (int)atomicAdd(&kv.ctl->ticket, 1u);
+            s_done = 0;
+            s_ready = 0;
+        }
         __syncthreads();
         const int b = s_band;
         if (b >= kv.nbands || s_abort) break;
         const int cb = kv.band_chunk[b], ce = kv.band_chunk[b + 1];
         const int Lband = kv.chunk[2 * cb].x;
-        load_sched(cb, 0);
-        for (int c = cb; c < ce && !s_abort; ++c) {
-            const int bi = (c - cb) & 1;
-            unsigned char *B = bufs + (size_t)bi * SG::stride;
-            cp_wait<0>();
-            __syncthreads();
-            load_vals(c, bi);
-            if (c + 1 < ce) {
-                load_sched(c + 1, bi ^ 1);
-                cp_wait<1>();
-            } else {
-                cp_wait<0>();
-            }
-            __syncthreads();
-            const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
-            const int4 *lv = reinterpret_cast<const int4 *>(B + SG::o_lv);
-            const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
-            const T *sinv = reinterpret_cast<const T *>(B + SG::o_inv);
-            const int2 *se = reinterpret_cast<const int2 *>(B + SG::o_ent);
-            const T *sa = reinterpret_cast<const T *>(B + SG::o_a);
-            const T *sb = reinterpret_cast<const T *>(B + SG::o_b);
-            const T *srhs = reinterpret_cast<const T *>(B + SG::o_rhs);
-            const T *sxs = reinterpret_cast<const T *>(B + SG::o_xs);
-            for (int L = 0; L < c0.y - c0.x; ++L) {
-                const int4 l0 = lv[L], l1 = lv[L + 1];
-                if (l1.y > l0.y) {  // cross-band requirements of this level
-                    for (int q = l0.y + threadIdx.x; q < l1.y; q += blockDim.x) {
+        const int Lend = kv.chunk[2 * (ce - 1)].y;
+        const int nlev = Lend - Lband;
+        if (comm) {
+            // ---------------------------------------------- communication warp
+            const int lane = threadIdx.x & 31;
+            int published = 0, ready = 0;
+            unsigned long long t0 = gtimer();  // re-armed whenever something advances
+            while (published < nlev) {
+                bool aborted = *((volatile int *)&s_abort) != 0;
+                if (!aborted && (*((volatile int *)kv.err) || gtimer() - t0 > WAIT_NS)) {
+                    if (lane == 0) {
+                        atomicExch(kv.err, 1);
+                        s_abort = 1;
+                    }
+                    aborted = true;
+                }
+                if (aborted) {
+                    if (lane == 0) st_rel_cta(&s_ready, nlev);  // release the compute warps
+                    break;
+                }
+                // requirements of the next levels, a few at a time
+                int adv = 0;
+                while (ready < nlev && adv < 8) {
+                    const int4 l0 = kv.lvl[Lband + ready], l1 = kv.lvl[Lband + ready + 1];
+                    bool ok = true;
+                    for (int q = l0.y + lane; q < l1.y; q += 32) {
                         const int2 rq = kv.req[q];
-                        const unsigned long long key = s_pc[rq.x & 63];
-                        if ((int)(key >> 32) == rq.x && (unsigned)key >= (unsigned)rq.y) continue;
                         const unsigned long long target = (epoch << 32) | (unsigned)rq.y;
-                        const unsigned long long t0 = gtimer();
-                        unsigned long long v;
-                        while ((v = ld_acquire(&kv.progress[rq.x])) < target) {
-                            if (*((volatile int *)kv.err) || gtimer() - t0 > WAIT_NS) {
-                                atomicExch(kv.err, 1);
-                                s_abort = 1;
-                                break;
-                            }
-                            __nanosleep(20);
-                        }
-                        if ((v >> 32) == epoch)
-                            s_pc[rq.x & 63] = ((unsigned long long)(unsigned)rq.x << 32) | (v & 0xffffffffull);
+                        ok = ok && (ld_acquire(&kv.progress[rq.x]) >= target);
                     }
-                    __syncthreads();
-                    if (s_abort) break;
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    ++ready;
+                    ++adv;
                 }
-                if (tr < RPP) {
-                    for (int k = l0.x - c0.z + tr; k < l1.x - c0.z; k += RPP) {
-                        const int2 rk = ri[k];
-                        const int e0 = rk.y - c1.x, e1 = ri[k + 1].y - c1.x;
-                        T vals[8];
-                        T dot = T(0), nrm = T(0);
-                        for (int e = e0; e < e1; ++e) {
-                            const int2 en = se[e];
-                            const int fl = en.y;
-                            const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
-                            T val;
-                            if (fl & 1)
-                                val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
-                                                             : __ldcg(x + (size_t)en.x * LD + j);
-                            else
-                                val = win[((fl >> 3) & 0xfff) * LD + j];
-                            if (e - e0 < 8) vals[e - e0] = val;
-                            dot = fma(coef, val, dot);
-                            if (SHIFT) nrm = fma(coef, coef, nrm);
-                        }
-                        const T bi2 = rhs ? (SG::VALS ? srhs[k * LD + j] : rhs[(size_t)rk.x * LD + j]) : T(0);
-                        T d = bi2 - dot;
-                        if (SHIFT)
-                            d = nrm > T(0) ? d / nrm : T(0);
-                        else
-                            d *= sinv[k];
-                        for (int e = e0; e < e1; ++e) {
-                            const int2 en = se[e];
-                            const int fl = en.y;
-                            const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
-                            T val;
-                            if (e - e0 < 8) {
-                                val = vals[e - e0];
-                            } else if (fl & 1) {
-                                val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
-                                                             : __ldcg(x + (size_t)en.x * LD + j);
-                            } else {
-                                val = win[((fl >> 3) & 0xfff) * LD + j];
-                            }
-                            const T nv = fma(d, coef, val);
-                            if (fl & 2)
-                                __stcg(x + (size_t)en.x * LD + j, nv);
-                            else
-                                win[((fl >> 3) & 0xfff) * LD + j] = nv;
-                        }
-                    }
+                if (adv && lane == 0) st_rel_cta(&s_ready, ready);
+                if (adv) t0 = gtimer();
+                // publish what the compute warps completed
+                const int done = ld_acq_cta(&s_done);
+                if (done > published) {
+                    bool need = done == nlev;
+                    for (int q = published + lane; q < done && !need; q += 32)
+                        need = need || kv.lvl[Lband + q].z;
+                    need = __any_sync(0xffffffffu, need);
+                    if (need && lane == 0) st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
+                    published = done;  // later bands only wait on flagged levels
+                    t0 = gtimer();
                 }
-                __syncthreads();
-                if (l0.z && threadIdx.x == 0)
-                    st_release(&kv.progress[b], (epoch << 32) | (unsigned)(c0.x + L - Lband + 1));
+                if (!adv && done == published) __nanosleep(20);
             }
-        }
-        cp_wait<0>();
-        if (threadIdx.x == 0 && !s_abort) {
-            const int Lend = kv.chunk[2 * (ce - 1)].y;
-            st_release(&kv.progress[b], (epoch << 32) | (unsigned)(Lend - Lband));
+        } else {
+            // ---------------------------------------------- compute warps
+            load_sched(cb, 0);
+            for (int c = cb; c < ce; ++c) {
+                const int bi = (c - cb) & 1;
+                unsigned char *B = bufs + (size_t)bi * SG::stride;
+                cp_wait<0>();
+                bar_compute();
+                load_vals(c, bi);
+                if (c + 1 < ce) {
+                    load_sched(c + 1, bi ^ 1);
+                    cp_wait<1>();
+                } else {
+                    cp_wait<0>();
+                }
+                bar_compute();
+                const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
+                const int4 *lv = reinterpret_cast<const int4 *>(B + SG::o_lv);
+                const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
+                const T *sinv = reinterpret_cast<const T *>(B + SG::o_inv);
+                const int2 *se = reinterpret_cast<const int2 *>(B + SG::o_ent);
+                const T *sa = reinterpret_cast<const T *>(B + SG::o_a);
+                const T *sb = reinterpret_cast<const T *>(B + SG::o_b);
+                const T *srhs = reinterpret_cast<const T *>(B + SG::o_rhs);
+                const T *sxs = reinterpret_cast<const T *>(B + SG::o_xs);
+                for (int L = 0; L < c0.y - c0.x; ++L) {
+                    const int4 l0 = lv[L], l1 = lv[L + 1];
+                    const int lb = c0.x + L - Lband;  // band-local level
+                    if (l1.y > l0.y) {
+                        // requirements of this level: wait for the comm warp,
+                        // which releases every wait when it gives up.  The
+                        // compute warps never leave the loop early, so every
+                        // named barrier is reached by all of them.
+                        const unsigned long long t0 = gtimer();
+                        while (ld_acq_cta(&s_ready) <= lb) {
+                            if (gtimer() - t0 > 2 * WAIT_NS) break;
+                        }
+                    }
+                    if (tr < RPP) {
+                        for (int k = l0.x - c0.z + tr; k < l1.x - c0.z; k += RPP) {
+                            const int2 rk = ri[k];
+                            const int e0 = rk.y - c1.x, e1 = ri[k + 1].y - c1.x;
+                            T dot = T(0), nrm = T(0);
+                            for (int e = e0; e < e1; ++e) {
+                                const int2 en = se[e];
+                                const int fl = en.y;
+                                const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
+                                T val;
+                                if (fl & 1)
+                                    val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
+                                                                 : __ldcg(x + (size_t)en.x * LD + j);
+                                else
+                                    val = win[((fl >> 3) & 0xfff) * LD + j];
+                                dot = fma(coef, val, dot);
+                                if (SHIFT) nrm = fma(coef, coef, nrm);
+                            }
+                            const T bi2 = rhs ? (SG::VALS ? srhs[k * LD + j] : rhs[(size_t)rk.x * LD + j]) : T(0);
+                            T d = bi2 - dot;
+                            if (SHIFT)
+                                d = nrm > T(0) ? d / nrm : T(0);
+                            else
+                                d *= sinv[k];
+                            for (int e = e0; e < e1; ++e) {
+                                const int2 en = se[e];
+                                const int fl = en.y;
+                                const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
+                                T val;
+                                if (fl & 1)
+                                    val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
+                                                                 : __ldcg(x + (size_t)en.x * LD + j);
+                                else
+                                    val = win[((fl >> 3) & 0xfff) * LD + j];
+                                const T nv = fma(d, coef, val);
+                                if (fl & 2)
+                                    __stcg(x + (size_t)en.x * LD + j, nv);
+                                else
+                                    win[((fl >> 3) & 0xfff) * LD + j] = nv;
+                            }
+                        }
+                    }
+                    bar_compute();
+                    if (threadIdx.x == 0) st_rel_cta(&s_done, lb + 1);
+                }
+            }
+            cp_wait<0>();
         }
     }
     __syncthreads();
