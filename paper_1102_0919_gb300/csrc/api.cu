@@ -2,6 +2,8 @@
 // by the setup phase, the solve loop, and single-step entry points.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "ctx.cuh"
@@ -346,11 +348,21 @@ samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_
     return guarded(ctx, [&] {
         SAMG_CHECK(kernel_class >= 0 && kernel_class < 5, SAMG_E_INVALID, "kernel class 0..4");
         ctx->prof.collect();
+        if (std::getenv("SAMG_PROFILE_LEVELS") && kernel_class == 0)
+            for (int l = 0; l < ctx->nlev() && l < 32; ++l)
+                fprintf(stderr, "[samg] level %d (%d x %d): kaczmarz %lld launches %.3f ms avg %.1f us"
+                        " | A: bands %d levels %d chunks %d reqs %lld slots %d | At: bands %d levels %d chunks %d\n",
+                        l, ctx->L[l].m, ctx->L[l].n, (long long)ctx->prof.lvl_n[0][l], ctx->prof.lvl_ms[0][l],
+                        1e3 * ctx->prof.lvl_ms[0][l] / std::max<int64_t>(1, ctx->prof.lvl_n[0][l]),
+                        ctx->L[l].kA.nbands, ctx->L[l].kA.nlevels, ctx->L[l].kA.nchunks,
+                        (long long)ctx->L[l].kA.req.n, ctx->L[l].kA.max_slots, ctx->L[l].kAt.nbands,
+                        ctx->L[l].kAt.nlevels, ctx->L[l].kAt.nchunks);
         if (launches) *launches = ctx->prof.launches[kernel_class];
         if (total_ms) *total_ms = ctx->prof.ms[kernel_class];
         if (alg_bytes) *alg_bytes = ctx->prof.bytes[kernel_class];
         if (reset)
             for (int k = 0; k < 5; ++k) {
+                for (int l = 0; l < 32; ++l) { ctx->prof.lvl_ms[k][l] = 0.0; ctx->prof.lvl_n[k][l] = 0; }
                 ctx->prof.launches[k] = 0;
                 ctx->prof.ms[k] = 0.0;
                 ctx->prof.bytes[k] = 0.0;

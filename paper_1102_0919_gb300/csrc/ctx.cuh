@@ -35,7 +35,10 @@ struct Level {
 // Launch timing with CUDA events on the context's stream (samg_profile).
 struct Profiler {
     bool on = false;
-    struct Rec { int cls; cudaEvent_t a, b; double bytes; };
+    struct Rec { int cls; cudaEvent_t a, b; double bytes; int level; };
+    int cur_level = -1;
+    double lvl_ms[5][32] = {};
+    int64_t lvl_n[5][32] = {};
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     int64_t launches[5] = {0, 0, 0, 0, 0};
@@ -54,7 +57,7 @@ struct Profiler {
         if (!on) return;
         *out = get();
         SAMG_CUDA(cudaEventRecord(*out, s));
-        recs.push_back({cls, *out, nullptr, b});
+        recs.push_back({cls, *out, nullptr, b, cur_level});
     }
     void end(cudaStream_t s) {
         if (!on) return;
@@ -70,6 +73,10 @@ struct Profiler {
             launches[r.cls]++;
             ms[r.cls] += t;
             bytes[r.cls] += r.bytes;
+            if (r.level >= 0 && r.level < 32) {
+                lvl_ms[r.cls][r.level] += t;
+                lvl_n[r.cls][r.level]++;
+            }
             pool.push_back(r.a);
             pool.push_back(r.b);
         }

@@ -41,6 +41,7 @@ static double spmv_bytes(const DCsr &M, int nb, size_t s) {  // y = M x
 // A^t u - s C v = tau (Eqs. genSVDresid1-2, add), sigma fixed per column.
 template <typename T>
 void relax(samg_ctx &c, int l) {
+    c.prof.cur_level = l;
     Level &L = c.L[l];
     Work<T> &w = work<T>(L);
     const int ld = c.ld;
