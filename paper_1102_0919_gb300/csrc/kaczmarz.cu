@@ -403,30 +403,35 @@ __global__ void __launch_bounds__(KZ_THREADS)
     }
 }
 
-struct LaunchCfg { int grid = 0; size_t smem = 0; };
 
 template <typename T, int LD, bool SHIFT>
 void launch_one(const KSched &ks, const T *ea, const T *eb, const T *inv, const T *rhs, T *x,
                 const double *shift, cudaStream_t s) {
     using SG = Stage<T, LD, SHIFT>;
-    static int cached_slots = -1;
-    static LaunchCfg cfg;
-    static int nsm = 0;
     auto kern = k_kaczmarz<T, LD, SHIFT>;
     const int slots = std::max(ks.max_slots, 1);
     const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + 2 * SG::stride;
-    if (cached_slots != slots) {
+    // per kernel instance: the largest dynamic shared memory set so far, and
+    // the SM count; per schedule and instance: the resident CTA count
+    static size_t smem_set = 0;
+    static int nsm = 0;
+    if (smem > smem_set) {
         SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0, bps = 0;
+        smem_set = smem;
+    }
+    if (!nsm) {
+        int dev = 0;
         SAMG_CUDA(cudaGetDevice(&dev));
         SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int key = (int)sizeof(T) * 64 + LD * 2 + (SHIFT ? 1 : 0);
+    int &grid = ks.grid_cache[key & 255];
+    if (!grid) {
+        int bps = 0;
         SAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, KZ_THREADS, smem));
         SAMG_CHECK(bps > 0, SAMG_E_CUDA, "kaczmarz: staging buffers do not fit in shared memory");
-        cfg.grid = nsm * bps;
-        cfg.smem = smem;
-        cached_slots = slots;
+        grid = std::min(ks.nbands, nsm * bps);
     }
-    const int grid = std::min(ks.nbands, cfg.grid);
     KView kv{ks.err ? ks.err : &ks.ctl.p->err, ks.nbands, ks.band_chunk.p, ks.chunk.p, ks.lvl.p,
              ks.rinfo.p, ks.ent.p, ks.xsc.p, ks.req.p, ks.progress.p, ks.ctl.p};
     SAMG_COUNT_LAUNCH();

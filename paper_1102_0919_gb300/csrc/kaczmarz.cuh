@@ -46,6 +46,7 @@ struct KSched {
     DBuf<int2> req;            // {band, level that band must have completed}
     DBuf<unsigned long long> progress;  // nbands
     DBuf<KCtl> ctl;
+    mutable int grid_cache[256] = {};  // resident CTAs per kernel instance
     int *err = nullptr;        // error word shared by a context's schedules
                                // (null: the schedule's own ctl->err)
 };
