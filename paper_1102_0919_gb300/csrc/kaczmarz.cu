@@ -191,13 +191,11 @@ __global__ void __launch_bounds__(KZ_THREADS)
     __shared__ int s_abort;
     __shared__ int s_done;   // band-local levels completed by the compute warps
     __shared__ int s_ready;  // band-local levels whose requirements are met
-    constexpr int RPP = KZ_COMPUTE / LD;  // rows per pass
+    __shared__ unsigned long long s_pc[64];  // comm warp: band << 32 | observed level
     const bool comm = threadIdx.x >= KZ_COMPUTE;
-    const int tr = threadIdx.x / LD;
-    const int j = threadIdx.x % LD;
     const unsigned long long epoch = *((volatile unsigned long long *)&kv.ctl->epoch);
     if (threadIdx.x == 0) s_abort = 0;
-    const T sh = SHIFT ? (T)shift[j] : T(0);
+    if (threadIdx.x < 64) s_pc[threadIdx.x] = ~0ull;
 
     auto load_sched = [&](int c, int bi) {
         unsigned char *B = bufs + (size_t)bi * SG::stride;
@@ -280,8 +278,12 @@ __global__ void __launch_bounds__(KZ_THREADS)
                     bool ok = true;
                     for (int q = l0.y + lane; q < l1.y; q += 32) {
                         const int2 rq = kv.req[q];
-                        const unsigned long long target = (epoch << 32) | (unsigned)rq.y;
-                        ok = ok && (ld_acquire(&kv.progress[rq.x]) >= target);
+                        const unsigned long long key = s_pc[rq.x & 63];
+                        if ((int)(key >> 32) == rq.x && (unsigned)key >= (unsigned)rq.y) continue;
+                        const unsigned long long v = ld_acquire(&kv.progress[rq.x]);
+                        if ((v >> 32) == epoch)
+                            s_pc[rq.x & 63] = ((unsigned long long)(unsigned)rq.x << 32) | (v & 0xffffffffull);
+                        ok = ok && (v >= ((epoch << 32) | (unsigned)rq.y));
                     }
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
@@ -341,45 +343,78 @@ __global__ void __launch_bounds__(KZ_THREADS)
                             if (gtimer() - t0 > 2 * WAIT_NS) break;
                         }
                     }
-                    if (tr < RPP) {
-                        for (int k = l0.x - c0.z + tr; k < l1.x - c0.z; k += RPP) {
-                            const int2 rk = ri[k];
-                            const int e0 = rk.y - c1.x, e1 = ri[k + 1].y - c1.x;
+                    {
+                        // lane team: TE lanes per (row, column) split the row's
+                        // entries; G = LD * TE consecutive threads per row
+                        int TE = l0.w;
+                        if (TE > 32 / LD) TE = 32 / LD;
+                        if ((32 % LD) != 0 || TE < 1) TE = 1;
+                        const int G = LD * TE;
+                        const int rpp = KZ_COMPUTE / G;
+                        const int rs = threadIdx.x / G, within = threadIdx.x % G;
+                        const int jj = within % LD, te = within / LD;
+                        const T shj = SHIFT ? (T)shift[jj] : T(0);
+                        const int kbeg = l0.x - c0.z, kend = l1.x - c0.z;
+                        const int npass = (kend - kbeg + rpp - 1) / rpp;
+                        for (int pass = 0; pass < npass; ++pass) {
+                            const int k = kbeg + pass * rpp + rs;
+                            const bool act = rs < rpp && k < kend;
                             T dot = T(0), nrm = T(0);
-                            for (int e = e0; e < e1; ++e) {
-                                const int2 en = se[e];
-                                const int fl = en.y;
-                                const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
-                                T val;
-                                if (fl & 1)
-                                    val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
-                                                                 : __ldcg(x + (size_t)en.x * LD + j);
-                                else
-                                    val = win[((fl >> 3) & 0xfff) * LD + j];
-                                dot = fma(coef, val, dot);
-                                if (SHIFT) nrm = fma(coef, coef, nrm);
+                            T vals[4];
+                            int e0 = 0, e1 = 0;
+                            if (act) {
+                                const int2 rk = ri[k];
+                                e0 = rk.y - c1.x;
+                                e1 = ri[k + 1].y - c1.x;
+                                int n = 0;
+                                for (int e = e0 + te; e < e1; e += TE, ++n) {
+                                    const int2 en = se[e];
+                                    const int fl = en.y;
+                                    const T coef = SHIFT ? sa[e] - shj * sb[e] : sa[e];
+                                    T val;
+                                    if (fl & 1)
+                                        val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + jj]
+                                                                     : __ldcg(x + (size_t)en.x * LD + jj);
+                                    else
+                                        val = win[((fl >> 3) & 0xfff) * LD + jj];
+                                    if (n < 4) vals[n] = val;
+                                    dot = fma(coef, val, dot);
+                                    if (SHIFT) nrm = fma(coef, coef, nrm);
+                                }
                             }
-                            const T bi2 = rhs ? (SG::VALS ? srhs[k * LD + j] : rhs[(size_t)rk.x * LD + j]) : T(0);
-                            T d = bi2 - dot;
-                            if (SHIFT)
-                                d = nrm > T(0) ? d / nrm : T(0);
-                            else
-                                d *= sinv[k];
-                            for (int e = e0; e < e1; ++e) {
-                                const int2 en = se[e];
-                                const int fl = en.y;
-                                const T coef = SHIFT ? sa[e] - sh * sb[e] : sa[e];
-                                T val;
-                                if (fl & 1)
-                                    val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + j]
-                                                                 : __ldcg(x + (size_t)en.x * LD + j);
+                            if (TE > 1) {
+                                for (int o = LD; o < G; o <<= 1) {
+                                    dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                                    if (SHIFT) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+                                }
+                            }
+                            if (act) {
+                                const int2 rk = ri[k];
+                                const T bi2 = rhs ? (SG::VALS ? srhs[k * LD + jj] : rhs[(size_t)rk.x * LD + jj]) : T(0);
+                                T d = bi2 - dot;
+                                if (SHIFT)
+                                    d = nrm > T(0) ? d / nrm : T(0);
                                 else
-                                    val = win[((fl >> 3) & 0xfff) * LD + j];
-                                const T nv = fma(d, coef, val);
-                                if (fl & 2)
-                                    __stcg(x + (size_t)en.x * LD + j, nv);
-                                else
-                                    win[((fl >> 3) & 0xfff) * LD + j] = nv;
+                                    d *= sinv[k];
+                                int n = 0;
+                                for (int e = e0 + te; e < e1; e += TE, ++n) {
+                                    const int2 en = se[e];
+                                    const int fl = en.y;
+                                    const T coef = SHIFT ? sa[e] - shj * sb[e] : sa[e];
+                                    T val;
+                                    if (n < 4)
+                                        val = vals[n];
+                                    else if (fl & 1)
+                                        val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + jj]
+                                                                     : __ldcg(x + (size_t)en.x * LD + jj);
+                                    else
+                                        val = win[((fl >> 3) & 0xfff) * LD + jj];
+                                    const T nv = fma(d, coef, val);
+                                    if (fl & 2)
+                                        __stcg(x + (size_t)en.x * LD + jj, nv);
+                                    else
+                                        win[((fl >> 3) & 0xfff) * LD + jj] = nv;
+                                }
                             }
                         }
                     }
@@ -521,7 +556,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
         // sub-levels: a level's independent rows split so that each piece fits
         // one staging chunk
         std::vector<RowRec> rr;
-        std::vector<int> sub_rows, sub_ents, sub_xs;  // per sub-level counts
+        std::vector<int> sub_rows, sub_ents, sub_xs, sub_maxe;  // per sub-level counts
         for (int l = 0; l < nl; ++l) {
             int cr = 0, ce = 0, cx = 0;
             bool open = false;
@@ -535,6 +570,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                 }
                 if (!open || cr + 1 > KZ_CHR || ce + ne > KZ_CHE || cx + nx > KZ_CHX) {
                     sub_rows.push_back(0); sub_ents.push_back(0); sub_xs.push_back(0);
+                    sub_maxe.push_back(0);
                     cr = ce = cx = 0;
                     open = true;
                 }
@@ -542,6 +578,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                            "kaczmarz: a row has more entries than a staging chunk holds");
                 cr += 1; ce += ne; cx += nx;
                 sub_rows.back() = cr; sub_ents.back() = ce; sub_xs.back() = cx;
+                sub_maxe.back() = std::max(sub_maxe.back(), ne);
                 rr.push_back({r, (int)sub_rows.size() - 1});
             }
         }
@@ -588,7 +625,11 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                 crec1 = int4{(int)ent.size(), 0, (int)xsc.size(), 0};
                 xs_local = 0;
             }
-            int4 L4{(int)rinfo.size(), 0, 0, 0};
+            // lanes per row and column: enough that no lane walks more than
+            // three entries of its row (1, 2, 4 or 8; the kernel caps it)
+            int te = 1;
+            while (te < 8 && (sub_maxe[q] + te - 1) / te > 3) te *= 2;
+            int4 L4{(int)rinfo.size(), 0, 0, te};
             lvl.push_back(L4);
             for (; ri < rr.size() && rr[ri].sub == q; ++ri) {
                 const int r = rr[ri].row;
