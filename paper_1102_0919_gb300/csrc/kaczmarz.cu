@@ -9,8 +9,9 @@ namespace samg {
 
 namespace {
 
-constexpr int KZ_THREADS = 256;
-constexpr int KZ_COMPUTE = 224;    // compute threads (7 warps); warp 7 communicates
+constexpr int KZ_THREADS = 512;
+constexpr int KZ_COMPUTE = 480;    // compute threads (15 warps); warp 15 communicates
+constexpr int KZ_NBUF = 3;          // staging buffers: schedule two chunks ahead, values one
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
 constexpr int MAX_BAND_ROWS = 1 << 17;
 constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
@@ -307,20 +308,25 @@ __global__ void __launch_bounds__(KZ_THREADS)
             }
         } else {
             // ---------------------------------------------- compute warps
+            // pipeline over chunks: schedule arrays two chunks ahead, right-hand
+            // sides and first values one chunk ahead, so that only the chunk
+            // being processed is waited for
             load_sched(cb, 0);
+            cp_wait<0>();
+            bar_compute();
+            load_vals(cb, 0);
+            if (cb + 1 < ce) load_sched(cb + 1, 1);
+            else cp_commit();
             for (int c = cb; c < ce; ++c) {
-                const int bi = (c - cb) & 1;
+                const int bi = (c - cb) % KZ_NBUF;
                 unsigned char *B = bufs + (size_t)bi * SG::stride;
+                // sched(c+1) and vals(c) were issued one step earlier
                 cp_wait<0>();
                 bar_compute();
-                load_vals(c, bi);
-                if (c + 1 < ce) {
-                    load_sched(c + 1, bi ^ 1);
-                    cp_wait<1>();
-                } else {
-                    cp_wait<0>();
-                }
-                bar_compute();
+                if (c + 1 < ce) load_vals(c + 1, (c + 1 - cb) % KZ_NBUF);
+                else cp_commit();
+                if (c + 2 < ce) load_sched(c + 2, (c + 2 - cb) % KZ_NBUF);
+                else cp_commit();
                 const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
                 const int4 *lv = reinterpret_cast<const int4 *>(B + SG::o_lv);
                 const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
@@ -445,7 +451,7 @@ void launch_one(const KSched &ks, const T *ea, const T *eb, const T *inv, const 
     using SG = Stage<T, LD, SHIFT>;
     auto kern = k_kaczmarz<T, LD, SHIFT>;
     const int slots = std::max(ks.max_slots, 1);
-    const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + 2 * SG::stride;
+    const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + KZ_NBUF * SG::stride;
     // per kernel instance: the largest dynamic shared memory set so far, and
     // the SM count; per schedule and instance: the resident CTA count
     static size_t smem_set = 0;

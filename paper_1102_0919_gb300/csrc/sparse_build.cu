@@ -2,9 +2,10 @@
 // the Galerkin triple products A_c = P^t A Q, B_c = P^t B P, C_c = Q^t C Q
 // (Eq. coarseOp), built once per hierarchy.
 //
-// C = A B uses row-wise Gustavson accumulation in per-row open-addressing
-// hash tables in global memory (sized 2 * upper bound, power of two), then a
-// compaction that writes each row in increasing column order.
+// C = A B: the column pattern of each row is collected in a per-row
+// open-addressing hash table in global memory (sized 2 * upper bound, power of
+// two) and written in increasing column order; the values are then summed by
+// one thread per row in a fixed order, so the product is deterministic.
 #include <cmath>
 
 #include "kernels.cuh"
@@ -236,9 +237,8 @@ __global__ void k_row_bounds(int m, const int *arp, const int *aci, const int *b
 
 __device__ __forceinline__ unsigned hash_col(int c) { return (unsigned)c * 2654435761u; }
 
-__global__ void k_hash_insert(int m, const int *arp, const int *aci, const double *av,
-                              const int *brp, const int *bci, const double *bv,
-                              const int64_t *hoff, int *keys, double *vals) {
+__global__ void k_hash_insert(int m, const int *arp, const int *aci, const int *brp,
+                              const int *bci, const int64_t *hoff, int *keys) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (warp >= m) return;
@@ -247,19 +247,40 @@ __global__ void k_hash_insert(int m, const int *arp, const int *aci, const doubl
     if (hoff[warp + 1] == h0) return;
     for (int e = arp[warp] + lane; e < arp[warp + 1]; e += 32) {
         int k = aci[e];
-        double a = av[e];
         for (int f = brp[k]; f < brp[k + 1]; ++f) {
             int c = bci[f];
-            double p = a * bv[f];
             unsigned h = hash_col(c) & mask;
             for (;;) {
                 int old = atomicCAS(&keys[h0 + h], -1, c);
-                if (old == -1 || old == c) {
-                    atomicAdd(&vals[h0 + h], p);
-                    break;
-                }
+                if (old == -1 || old == c) break;
                 h = (h + 1) & mask;
             }
+        }
+    }
+}
+
+// Values of C = A B, one thread per row, products accumulated in the order of
+// A's row and B's rows (deterministic); the sorted column list of the row is
+// searched by bisection.
+__global__ void k_spgemm_values(int m, const int *arp, const int *aci, const double *av,
+                                const int *brp, const int *bci, const double *bv,
+                                const int64_t *crp, const int *cci, double *cv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t c0 = crp[i], c1 = crp[i + 1];
+    for (int64_t q = c0; q < c1; ++q) cv[q] = 0.0;
+    for (int e = arp[i]; e < arp[i + 1]; ++e) {
+        const int k = aci[e];
+        const double a = av[e];
+        for (int f = brp[k]; f < brp[k + 1]; ++f) {
+            const int c = bci[f];
+            int64_t lo = c0, hi = c1 - 1;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (cci[mid] < c) lo = mid + 1;
+                else hi = mid;
+            }
+            cv[lo] += a * bv[f];
         }
     }
 }
@@ -274,8 +295,8 @@ __global__ void k_hash_count(int m, const int64_t *hoff, const int *keys, int64_
     if (lane == 0) cnt[warp] = c;
 }
 
-__global__ void k_hash_compact(int m, const int64_t *hoff, const int *keys, const double *vals,
-                               const int64_t *rp, int *ci, double *v) {
+__global__ void k_hash_compact(int m, const int64_t *hoff, const int *keys, const int64_t *rp,
+                               int *ci) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (warp >= m) return;
@@ -290,7 +311,6 @@ __global__ void k_hash_compact(int m, const int64_t *hoff, const int *keys, cons
             rank += (k2 >= 0 && k2 < key);
         }
         ci[base + rank] = key;
-        v[base + rank] = vals[h];
     }
 }
 
@@ -309,14 +329,11 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     SAMG_CUDA(cudaMemcpyAsync(&H, hoff.p + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SAMG_CUDA(cudaStreamSynchronize(s));
     DBuf<int> keys(H ? H : 1);
-    DBuf<double> vals(H ? H : 1);
     SAMG_CUDA(cudaMemsetAsync(keys.p, 0xff, keys.n * sizeof(int), s));
-    vals.zero(s);
     unsigned wb = (unsigned)(((int64_t)m * 32 + 255) / 256);
     if (m) {
         SAMG_COUNT_LAUNCH();
-        k_hash_insert<<<wb, 256, 0, s>>>(m, A.rp.p, A.ci.p, A.vd.p, B.rp.p, B.ci.p, B.vd.p, hoff.p,
-                                         keys.p, vals.p);
+        k_hash_insert<<<wb, 256, 0, s>>>(m, A.rp.p, A.ci.p, B.rp.p, B.ci.p, hoff.p, keys.p);
         SAMG_COUNT_LAUNCH();
         k_hash_count<<<wb, 256, 0, s>>>(m, hoff.p, keys.p, ub.p);
     }
@@ -332,7 +349,12 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     k_i64_to_i32<<<(m + 1 + 255) / 256, 256, 0, s>>>(m + 1, rp64.p, C.rp.p);
     C.ci.alloc(nnz ? nnz : 1);
     C.vd.alloc(nnz ? nnz : 1);
-    if (m) { SAMG_COUNT_LAUNCH(); k_hash_compact<<<wb, 256, 0, s>>>(m, hoff.p, keys.p, vals.p, rp64.p, C.ci.p, C.vd.p);
+    if (m) {
+        SAMG_COUNT_LAUNCH();
+        k_hash_compact<<<wb, 256, 0, s>>>(m, hoff.p, keys.p, rp64.p, C.ci.p);
+        SAMG_COUNT_LAUNCH();
+        k_spgemm_values<<<(m + 127) / 128, 128, 0, s>>>(m, A.rp.p, A.ci.p, A.vd.p, B.rp.p, B.ci.p,
+                                                        B.vd.p, rp64.p, C.ci.p, C.vd.p);
     }
     SAMG_CUDA(cudaGetLastError());
     refresh_float(C, s);

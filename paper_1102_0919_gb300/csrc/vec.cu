@@ -190,33 +190,44 @@ template void launch_add_to<float>(size_t, double *, const float *, cudaStream_t
 template void launch_add_to<double>(size_t, double *, const double *, cudaStream_t);
 
 // ----------------------------------------------------------- column dots
+// Column-wise x_j^t (M y)_j: per-block partial sums in a fixed order, then one
+// block adds the partials in block order (deterministic).
 template <typename T>
 __global__ void k_coldot(int rows, int nb, int ld, const T *__restrict__ x, CsrView<T> M,
-                         const T *__restrict__ y, double *__restrict__ out) {
-    __shared__ double red[16];
+                         const T *__restrict__ y, double *__restrict__ part) {
+    __shared__ double red[240][4];
     const int q4 = ld >> 2;
-    if (threadIdx.x < 16) red[threadIdx.x] = 0.0;
-    __syncthreads();
     double acc[4] = {0, 0, 0, 0};
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;  // multiple of q4 (blockDim = 240)
-    int c0 = 0;
-    for (int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tid < (int64_t)rows * q4;
-         tid += stride) {
-        int i = (int)(tid / q4);
-        c0 = (int)(tid % q4) * 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // multiple of q4 (blockDim = 240)
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c0 = (int)(t0 % q4) * 4;
+    for (int64_t tid = t0; tid < (int64_t)rows * q4; tid += stride) {
+        const int i = (int)(tid / q4);
         V4<T> my = row_apply(M, y, i, ld, c0);
         V4<T> xi = ld4(x + (size_t)i * ld + c0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[k] += (double)xi.a[k] * (double)my.a[k];
     }
-    int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    c0 = (int)(t0 % q4) * 4;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (c0 + k < nb && acc[k] != 0.0) atomicAdd(&red[c0 + k], acc[k]);
+    for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = acc[k];
     __syncthreads();
-    if (threadIdx.x < nb) atomicAdd(&out[threadIdx.x], red[threadIdx.x]);
+    if (threadIdx.x < nb) {  // column j: threads with c0 + k == j, in thread order
+        const int jc = threadIdx.x;
+        double s = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t)
+            if ((t % q4) * 4 == (jc & ~3)) s += red[t][jc & 3];
+        part[(size_t)blockIdx.x * 16 + jc] = s;
+    }
 }
+
+__global__ void k_coldot_final(const double *part, int nblk, int nb, double *out) {
+    const int j = threadIdx.x;
+    if (j >= nb) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 16 + j];
+    out[j] += s;
+}
+
 template <typename T>
 void launch_coldot(int rows, int nb, int ld, const T *x, CsrView<T> M, const T *y, double *out,
                    cudaStream_t s) {
@@ -225,9 +236,13 @@ void launch_coldot(int rows, int nb, int ld, const T *x, CsrView<T> M, const T *
     int bs = 240;
     int64_t g = (n + bs - 1) / bs;
     if (g > 1216) g = 1216;
+    DBuf<double> part((size_t)g * 16);
     SAMG_COUNT_LAUNCH();
-    k_coldot<T><<<(unsigned)g, bs, 0, s>>>(rows, nb, ld, x, M, y, out);
+    k_coldot<T><<<(unsigned)g, bs, 0, s>>>(rows, nb, ld, x, M, y, part.p);
+    SAMG_COUNT_LAUNCH();
+    k_coldot_final<<<1, 32, 0, s>>>(part.p, (int)g, nb, out);
     SAMG_CUDA(cudaGetLastError());
+    SAMG_CUDA(cudaStreamSynchronize(s));  // part is released on return
 }
 template void launch_coldot<float>(int, int, int, const float *, CsrView<float>, const float *,
                                    double *, cudaStream_t);
