@@ -12,6 +12,7 @@ namespace {
 constexpr int KZ_THREADS = 512;
 constexpr int KZ_COMPUTE = 480;    // compute threads (15 warps); warp 15 communicates
 constexpr int KZ_NBUF = 3;          // staging buffers: schedule two chunks ahead, values one
+constexpr int KZ_PUB = 8;           // publish granularity (levels)
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
 constexpr int MAX_BAND_ROWS = 1 << 17;
 constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
@@ -175,10 +176,11 @@ __device__ __forceinline__ void st_rel_cta(int *p, int v) {
     asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
 
-// Warps 0 .. KZ_COMPUTE/32 - 1 compute; the last warp communicates: it
-// publishes the band's progress (release, coalescing levels) and polls the
-// progress that upcoming levels require (acquire), so that the compute warps
-// only synchronize through a named barrier and shared-memory flags.
+// Warps 0 .. KZ_COMPUTE/32 - 1 compute; the last warp polls (acquire) the
+// progress that upcoming levels require from earlier bands, so that the
+// compute warps only wait on a shared-memory flag.  Thread 0 publishes the
+// band's progress (release) at most every KZ_PUB levels when a later band
+// waits on it, and at the end of the band.
 template <typename T, int LD, bool SHIFT>
 __global__ void __launch_bounds__(KZ_THREADS)
     k_kaczmarz(KView kv, const T *__restrict__ ea, const T *__restrict__ eb,
@@ -293,21 +295,17 @@ __global__ void __launch_bounds__(KZ_THREADS)
                 }
                 if (adv && lane == 0) st_rel_cta(&s_ready, ready);
                 if (adv) t0 = gtimer();
-                // publish what the compute warps completed
-                const int done = ld_acq_cta(&s_done);
+                // the compute warps publish; follow their progress to finish
+                const int done = *((volatile int *)&s_done);
                 if (done > published) {
-                    bool need = done == nlev;
-                    for (int q = published + lane; q < done && !need; q += 32)
-                        need = need || kv.lvl[Lband + q].z;
-                    need = __any_sync(0xffffffffu, need);
-                    if (need && lane == 0) st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
-                    published = done;  // later bands only wait on flagged levels
+                    published = done;
                     t0 = gtimer();
                 }
                 if (!adv && done == published) __nanosleep(20);
             }
         } else {
             // ---------------------------------------------- compute warps
+            bool pend_pub = false;  // thread 0: a flagged level awaits publication
             // pipeline over chunks: schedule arrays two chunks ahead, right-hand
             // sides and first values one chunk ahead, so that only the chunk
             // being processed is waited for
@@ -425,10 +423,21 @@ __global__ void __launch_bounds__(KZ_THREADS)
                         }
                     }
                     bar_compute();
-                    if (threadIdx.x == 0) st_rel_cta(&s_done, lb + 1);
+                    if (threadIdx.x == 0) {
+                        pend_pub = pend_pub || l0.z;
+                        // the release makes every compute thread's stores of the
+                        // finished levels visible (cumulative over the barrier)
+                        if (pend_pub && ((lb + 1) % KZ_PUB == 0 || lb + 1 == nlev)) {
+                            st_release(&kv.progress[b], (epoch << 32) | (unsigned)(lb + 1));
+                            pend_pub = false;
+                        }
+                        *((volatile int *)&s_done) = lb + 1;
+                    }
                 }
             }
             cp_wait<0>();
+            bar_compute();
+            if (threadIdx.x == 0) st_release(&kv.progress[b], (epoch << 32) | (unsigned)nlev);
         }
     }
     __syncthreads();
