@@ -131,12 +131,108 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// 16-byte vector moves of one n_b-wide row (LD a multiple of 4; both
+// pointers 16-byte aligned): shared memory (generic) and global (L2 only).
+template <typename T, int LD>
+__device__ __forceinline__ void vld(T (&v)[LD], const T *p) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[i];
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 2; ++i) {
+            const double2 t = reinterpret_cast<const double2 *>(p)[i];
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    }
+}
+template <typename T, int LD>
+__device__ __forceinline__ void vld_cg(T (&v)[LD], const T *p) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i) {
+            const float4 t = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 2; ++i) {
+            const double2 t = __ldcg(reinterpret_cast<const double2 *>(p) + i);
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    }
+}
+template <typename T, int LD>
+__device__ __forceinline__ void vst(T *p, const T (&v)[LD]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 2; ++i)
+            reinterpret_cast<double2 *>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    }
+}
+template <typename T, int LD>
+__device__ __forceinline__ void vst_cg(T *p, const T (&v)[LD]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i)
+            __stcg(reinterpret_cast<float4 *>(p) + i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 2; ++i)
+            __stcg(reinterpret_cast<double2 *>(p) + i, make_double2(v[2 * i], v[2 * i + 1]));
+    }
+}
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+__host__ __device__ constexpr bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+__device__ __forceinline__ int brev_low(int v, int nbits) {  // reverse the low nbits
+    return nbits ? (int)(__brev((unsigned)v) >> (32 - nbits)) : 0;
+}
+
+// Row sums over the G = 2^lgG lanes of a row group (groups aligned in the
+// warp; every lane of the warp calls).  Reduce-scatter: at step s each lane
+// keeps the half of its columns selected by bit s of its lane index and adds
+// the partner's copy of that half, so after log2(LD) steps lane l holds the
+// sum of column brev(l mod LD); the remaining steps add across the lanes that
+// hold the same column.  Needs G >= LD, LD a power of two.
+template <typename T, int LD>
+__device__ __forceinline__ T group_reduce_scatter(T (&v)[LD], int lane, int lgG) {
+#pragma unroll
+    for (int s = 0; (LD >> s) > 1; ++s) {
+        const int h = (LD >> s) / 2;
+        const bool up = (lane >> s) & 1;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T keep = up ? v[h + i] : v[i];
+            const T send = up ? v[i] : v[h + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << s);
+        }
+    }
+    T r = v[0];
+    for (int s = ilog2(LD); s < lgG; ++s) r += __shfl_xor_sync(0xffffffffu, r, 1 << s);
+    return r;
+}
+template <typename T, int LD>
+__device__ __forceinline__ void group_allreduce(T (&v)[LD], int lgG) {
+    for (int s = 0; s < lgG; ++s) {
+#pragma unroll
+        for (int q = 0; q < LD; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], 1 << s);
+    }
+}
+
 struct KView {
     int *err;
     int nbands;
     const int *band_chunk;   // nbands + 1
     const int4 *chunk;       // 2 per chunk: {L0, L1, R0, R1}, {E0, E1, X0, X1}
-    const int4 *lvl;         // {first row, first req, publish, 0} + sentinel
+    const int4 *lvl;         // {first row, first req, publish, log2 lanes per row} + sentinel
     const int2 *rinfo;       // {original row, first entry}
     const int2 *ent;         // {column, flags}
     const int *xsc;          // columns staged per chunk
@@ -196,6 +292,9 @@ __global__ void __launch_bounds__(KZ_THREADS)
     __shared__ int s_ready;  // band-local levels whose requirements are met
     __shared__ unsigned long long s_pc[64];  // comm warp: band << 32 | observed level
     const bool comm = threadIdx.x >= KZ_COMPUTE;
+    T sh[SHIFT ? LD : 1];
+#pragma unroll
+    for (int q = 0; q < (SHIFT ? LD : 1); ++q) sh[q] = SHIFT ? (T)shift[q] : T(0);
     const unsigned long long epoch = *((volatile unsigned long long *)&kv.ctl->epoch);
     if (threadIdx.x == 0) s_abort = 0;
     if (threadIdx.x < 64) s_pc[threadIdx.x] = ~0ull;
@@ -348,76 +447,119 @@ __global__ void __launch_bounds__(KZ_THREADS)
                         }
                     }
                     {
-                        // lane team: TE lanes per (row, column) split the row's
-                        // entries; G = LD * TE consecutive threads per row
-                        int TE = l0.w;
-                        if (TE > 32 / LD) TE = 32 / LD;
-                        if ((32 % LD) != 0 || TE < 1) TE = 1;
-                        const int G = LD * TE;
-                        const int rpp = KZ_COMPUTE / G;
-                        const int rs = threadIdx.x / G, within = threadIdx.x % G;
-                        const int jj = within % LD, te = within / LD;
-                        const T shj = SHIFT ? (T)shift[jj] : T(0);
-                        const int kbeg = l0.x - c0.z, kend = l1.x - c0.z;
-                        const int npass = (kend - kbeg + rpp - 1) / rpp;
-                        for (int pass = 0; pass < npass; ++pass) {
-                            const int k = kbeg + pass * rpp + rs;
-                            const bool act = rs < rpp && k < kend;
-                            T dot = T(0), nrm = T(0);
-                            T vals[4];
-                            int e0 = 0, e1 = 0;
+                        // G = 2^lgG lanes per row (the smallest power of two not
+                        // below the sub-level's longest row, at most 32); lane lg
+                        // takes entries lg, lg + G, ... for all LD columns.  A
+                        // warp holding no row of the level goes straight to the
+                        // barrier.
+                        const int lgG = l0.w;
+                        const int G = 1 << lgG;
+                        const int nrow = l1.x - l0.x;
+                        const int lane = threadIdx.x & 31;
+                        const int lg = threadIdx.x & (G - 1);
+                        const int wrow = (threadIdx.x & ~31) >> lgG;
+                        for (int pr = 0; pr + wrow < nrow; pr += KZ_COMPUTE >> lgG) {
+                            const int r = pr + (threadIdx.x >> lgG);
+                            const bool act = r < nrow;
+                            const int k = l0.x - c0.z + r;
+                            T acc[LD], nrm[SHIFT ? LD : 1];
+#pragma unroll
+                            for (int q = 0; q < LD; ++q) acc[q] = T(0);
+#pragma unroll
+                            for (int q = 0; q < (SHIFT ? LD : 1); ++q) nrm[q] = T(0);
+                            // the lane's first entry stays in registers for the update
+                            int2 fen = make_int2(0, 0);
+                            T fa = T(0), fb = T(0), fv[LD];
+                            int e1 = 0;
+                            bool own = false;
                             if (act) {
-                                const int2 rk = ri[k];
-                                e0 = rk.y - c1.x;
+                                const int e0 = ri[k].y - c1.x;
                                 e1 = ri[k + 1].y - c1.x;
-                                int n = 0;
-                                for (int e = e0 + te; e < e1; e += TE, ++n) {
+                                own = e0 + lg < e1;
+                                for (int e = e0 + lg; e < e1; e += G) {
                                     const int2 en = se[e];
+                                    const T a = sa[e];
+                                    const T bq = SHIFT ? sb[e] : T(0);
+                                    T val[LD];
                                     const int fl = en.y;
-                                    const T coef = SHIFT ? sa[e] - shj * sb[e] : sa[e];
-                                    T val;
-                                    if (fl & 1)
-                                        val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + jj]
-                                                                     : __ldcg(x + (size_t)en.x * LD + jj);
+                                    if (!(fl & 1))
+                                        vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
+                                    else if (SG::VALS && (fl & 4))
+                                        vld<T, LD>(val, sxs + (fl >> 15) * LD);
                                     else
-                                        val = win[((fl >> 3) & 0xfff) * LD + jj];
-                                    if (n < 4) vals[n] = val;
-                                    dot = fma(coef, val, dot);
-                                    if (SHIFT) nrm = fma(coef, coef, nrm);
+                                        vld_cg<T, LD>(val, x + (size_t)en.x * LD);
+#pragma unroll
+                                    for (int q = 0; q < LD; ++q) {
+                                        const T coef = SHIFT ? a - sh[q] * bq : a;
+                                        acc[q] = fma(coef, val[q], acc[q]);
+                                        if (SHIFT) nrm[q] = fma(coef, coef, nrm[q]);
+                                    }
+                                    if (e == e0 + lg) {
+                                        fen = en; fa = a; fb = bq;
+#pragma unroll
+                                        for (int q = 0; q < LD; ++q) fv[q] = val[q];
+                                    }
                                 }
                             }
-                            if (TE > 1) {
-                                for (int o = LD; o < G; o <<= 1) {
-                                    dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                                    if (SHIFT) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+                            // d_q = (b_i - <a_i, x_q>) / ||a_i||^2 for every column q
+                            T d[LD];
+                            if (pow2(LD) && G >= LD) {
+                                const T sa_c = group_reduce_scatter<T, LD>(acc, lane, lgG);
+                                const T sn_c = SHIFT ? group_reduce_scatter<T, (SHIFT ? LD : 1)>(nrm, lane, lgG) : T(0);
+                                const int c = brev_low(lane & (LD - 1), ilog2(LD));
+                                T dc = T(0);
+                                if (act) {
+                                    const T bi = rhs ? (SG::VALS ? srhs[k * LD + c] : rhs[(size_t)ri[k].x * LD + c]) : T(0);
+                                    dc = SHIFT ? (sn_c > T(0) ? (bi - sa_c) / sn_c : T(0)) : (bi - sa_c) * sinv[k];
+                                }
+                                const int gb = lane & ~(G - 1);
+#pragma unroll
+                                for (int q = 0; q < LD; ++q)
+                                    d[q] = __shfl_sync(0xffffffffu, dc, gb + brev_low(q, ilog2(LD)));
+                            } else {
+                                group_allreduce<T, LD>(acc, lgG);
+                                if (SHIFT) group_allreduce<T, (SHIFT ? LD : 1)>(nrm, lgG);
+#pragma unroll
+                                for (int q = 0; q < LD; ++q) d[q] = T(0);
+                                if (act) {
+#pragma unroll
+                                    for (int q = 0; q < LD; ++q) {
+                                        const T bi = rhs ? (SG::VALS ? srhs[k * LD + q] : rhs[(size_t)ri[k].x * LD + q]) : T(0);
+                                        const T nq = SHIFT ? nrm[q] : T(1);
+                                        d[q] = SHIFT ? (nq > T(0) ? (bi - acc[q]) / nq : T(0)) : (bi - acc[q]) * sinv[k];
+                                    }
                                 }
                             }
-                            if (act) {
-                                const int2 rk = ri[k];
-                                const T bi2 = rhs ? (SG::VALS ? srhs[k * LD + jj] : rhs[(size_t)rk.x * LD + jj]) : T(0);
-                                T d = bi2 - dot;
-                                if (SHIFT)
-                                    d = nrm > T(0) ? d / nrm : T(0);
-                                else
-                                    d *= sinv[k];
-                                int n = 0;
-                                for (int e = e0 + te; e < e1; e += TE, ++n) {
-                                    const int2 en = se[e];
-                                    const int fl = en.y;
-                                    const T coef = SHIFT ? sa[e] - shj * sb[e] : sa[e];
-                                    T val;
-                                    if (n < 4)
-                                        val = vals[n];
-                                    else if (fl & 1)
-                                        val = (SG::VALS && (fl & 4)) ? sxs[(fl >> 15) * LD + jj]
-                                                                     : __ldcg(x + (size_t)en.x * LD + jj);
+                            // x_q += d_q a_i on the row's entries
+                            if (own) {
+                                const int e0 = ri[k].y - c1.x;
+                                for (int e = e0 + lg; e < e1; e += G) {
+                                    int2 en = fen;
+                                    T a = fa, bq = fb, val[LD];
+                                    if (e == e0 + lg) {
+#pragma unroll
+                                        for (int q = 0; q < LD; ++q) val[q] = fv[q];
+                                    } else {
+                                        en = se[e];
+                                        a = sa[e];
+                                        bq = SHIFT ? sb[e] : T(0);
+                                        const int fl = en.y;
+                                        if (!(fl & 1))
+                                            vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
+                                        else if (SG::VALS && (fl & 4))
+                                            vld<T, LD>(val, sxs + (fl >> 15) * LD);
+                                        else
+                                            vld_cg<T, LD>(val, x + (size_t)en.x * LD);
+                                    }
+#pragma unroll
+                                    for (int q = 0; q < LD; ++q) {
+                                        const T coef = SHIFT ? a - sh[q] * bq : a;
+                                        val[q] = fma(d[q], coef, val[q]);
+                                    }
+                                    if (en.y & 2)
+                                        vst_cg<T, LD>(x + (size_t)en.x * LD, val);
                                     else
-                                        val = win[((fl >> 3) & 0xfff) * LD + jj];
-                                    const T nv = fma(d, coef, val);
-                                    if (fl & 2)
-                                        __stcg(x + (size_t)en.x * LD + jj, nv);
-                                    else
-                                        win[((fl >> 3) & 0xfff) * LD + jj] = nv;
+                                        vst<T, LD>(win + ((en.y >> 3) & 0xfff) * LD, val);
                                 }
                             }
                         }
@@ -640,11 +782,11 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                 crec1 = int4{(int)ent.size(), 0, (int)xsc.size(), 0};
                 xs_local = 0;
             }
-            // lanes per row and column: enough that no lane walks more than
-            // three entries of its row (1, 2, 4 or 8; the kernel caps it)
-            int te = 1;
-            while (te < 8 && (sub_maxe[q] + te - 1) / te > 3) te *= 2;
-            int4 L4{(int)rinfo.size(), 0, 0, te};
+            // lanes per row: a power of two >= the longest row of the level
+            // (at most 32; longer rows give a lane several entries)
+            int lg = 0;
+            while (lg < 5 && (1 << lg) < sub_maxe[q]) ++lg;
+            int4 L4{(int)rinfo.size(), 0, 0, lg};
             lvl.push_back(L4);
             for (; ri < rr.size() && rr[ri].sub == q; ++ri) {
                 const int r = rr[ri].row;

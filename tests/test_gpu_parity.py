@@ -210,12 +210,18 @@ def test_solve_matches_oracle(case, prec):
 
 
 # ----------------------------------------------------------- Kaczmarz stress
-def test_kaczmarz_sweep_many_bands_random_rectangular():
+@pytest.mark.parametrize("nb", [3, 8, 10])
+def test_kaczmarz_sweep_many_bands_random_rectangular(nb):
     # a random rectangular operator with ragged rows spans many bands and
-    # levels; the GPU sweep must equal the sequential natural-order sweep
+    # levels; the GPU sweep must equal the sequential natural-order sweep.
+    # A few long rows (33..80 entries) make lanes walk several entries; n_b
+    # of 3, 8 and 10 give vector blocks of 4, 8 and 12 columns.
     rng = np.random.default_rng(21)
     m, n = 30011, 9007
-    rows = np.repeat(np.arange(m), rng.integers(1, 7, size=m))
+    lens = rng.integers(1, 7, size=m)
+    long_rows = rng.random(m) < 0.02
+    lens[long_rows] = rng.integers(33, 81, size=int(long_rows.sum()))
+    rows = np.repeat(np.arange(m), lens)
     cols = rng.integers(0, n, size=rows.size)
     A = sp.csr_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(m, n))
     A.sum_duplicates()
@@ -224,7 +230,6 @@ def test_kaczmarz_sweep_many_bands_random_rectangular():
     agg_v = np.minimum(np.arange(n) // 97, 89)
     P = sp.csr_matrix((np.ones(m), (np.arange(m), agg_u)), shape=(m, 100))
     Q = sp.csr_matrix((np.ones(n), (np.arange(n), agg_v)), shape=(n, 90))
-    nb = 8
     L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
     sig = np.linspace(0.5, 2.0, nb)
     U = rng.standard_normal((m, nb))

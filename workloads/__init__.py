@@ -178,7 +178,7 @@ class Workload:
 
 
 FD_PARAMS = dict(n_t=6, theta=0.06, mu_t=8, mu_b=4, n_mult=15)
-GRAD_PARAMS = dict(n_t=16, theta=0.06, mu_t=4, mu_b=4, n_mult=10)
+GRAD_PARAMS = dict(n_t=16, theta=0.06, mu_t=4, mu_b=4, n_mult=15)
 TD_PARAMS = dict(n_t=14, theta=0.03, mu_t=1, mu_b=4, n_mult=3)
 
 
