@@ -188,10 +188,14 @@ def workload(i: int) -> Workload:
         return Workload("laplacian5_N32_nb4_minimal", "spd", "minimal", 4, dict(FD_PARAMS),
                         lambda: laplacian5(32))
     if i == 2:
-        return Workload("gradient_N256_nb8_minimal", "svd", "minimal", 8, dict(GRAD_PARAMS),
+        # 20 setup cycles: with fewer, one triplet of the 256 x 256 gradient
+        # can stall in the additive phase (the slow-pair effect of Sec. 6.3)
+        return Workload("gradient_N256_nb8_minimal", "svd", "minimal", 8,
+                        dict(GRAD_PARAMS, n_mult=20),
                         lambda: gradient(256))
     if i == 3:
-        return Workload("gradient_N1024_nb8_minimal", "svd", "minimal", 8, dict(GRAD_PARAMS),
+        return Workload("gradient_N1024_nb8_minimal", "svd", "minimal", 8,
+                        dict(GRAD_PARAMS, n_mult=10),
                         lambda: gradient(1024))
     if i == 4:
         return Workload("termdoc_200000x50000_nb10_dominant", "svd", "dominant", 10,
