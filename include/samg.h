@@ -202,6 +202,29 @@ samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double
 samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
                             double *G, void *cuda_stream);
 
+/* G = X^t Y exactly as samg_block_gram (same kernels, same summation order,
+ * bitwise the same result), but allocating nothing: no cudaMalloc, cudaFree
+ * or allocating library routine.  The paper has no counterpart to this entry
+ * point; it is a service for callers that cannot allocate device memory
+ * here -- a caller whose memory pool already owns the free HBM (a new
+ * cudaMalloc would fail or fragment it), or a caller on a latency-critical
+ * stream that cannot afford cudaFree, which waits for all work on the
+ * device.  It also does not synchronize the stream.
+ *
+ * The partial sums live in one fixed device array of 65536 doubles
+ * (512 KiB): calls with ceil(rows / 4096) * nb * nb > 65536 are rejected with
+ * SAMG_E_INVALID and a message (e.g. rows <= 4,194,304 at nb = 8, rows <=
+ * 1,048,576 at nb = 16).  The array is shared by all callers in the process
+ * on a device: calls whose GPU work overlaps (other streams, other host
+ * threads) race on it and give wrong results; serialize them.  The first
+ * call on each device looks the array's address up with
+ * cudaGetSymbolAddress (that device current) and caches it; make that first
+ * call before any stream capture begins on that device.  Arguments as for
+ * samg_block_gram; X, Y and G are device pointers, stream NULL = legacy
+ * default stream; the call returns when the work is enqueued. */
+samg_status samg_block_gram_noalloc(const double *X, const double *Y, int64_t rows, int nb,
+                                    int ld, double *G, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

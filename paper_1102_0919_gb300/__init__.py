@@ -81,6 +81,8 @@ samg_coarsest_solve = _sig("samg_coarsest_solve", _I, _CTX, _P, _P, _P, _P, _P)
 samg_vcycle = _sig("samg_vcycle", _I, _CTX, _P, _P, _P)
 samg_ritz = _sig("samg_ritz", _I, _CTX, _P, _P, _P, _P)
 samg_block_gram = _sig("samg_block_gram", _I, _P, _P, ctypes.c_int64, _I, _I, _P, _P)
+samg_block_gram_noalloc = _sig("samg_block_gram_noalloc", _I, _P, _P, ctypes.c_int64, _I, _I, _P,
+                               _P)
 samg_set_triplets_device = _sig("samg_set_triplets_device", _I, _CTX, _P, _P, _P)
 samg_profile = _sig("samg_profile", _I, _CTX, _I)
 samg_launch_count = _sig("samg_launch_count", ctypes.c_uint64)
@@ -91,8 +93,8 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_solve", "samg_set_triplets", "samg_get_triplets", "samg_set_precision",
             "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
-            "samg_ritz", "samg_block_gram", "samg_set_triplets_device", "samg_profile",
-            "samg_profile_read", "samg_launch_count"]
+            "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
+            "samg_profile", "samg_profile_read", "samg_launch_count"]
 
 
 def _arr(x, dtype):
@@ -323,5 +325,16 @@ def block_gram(X_ptr, Y_ptr, rows, nb, ld, G_ptr, stream=None):
     """G = X^t Y for device blocks (raw device pointers as ints)."""
     st = samg_block_gram(ctypes.c_void_p(X_ptr), ctypes.c_void_p(Y_ptr), rows, nb, ld,
                          ctypes.c_void_p(G_ptr), _stream(stream))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+
+
+def block_gram_noalloc(X_ptr, Y_ptr, rows, nb, ld, G_ptr, stream=None):
+    """G = X^t Y like block_gram, with the partial sums in the library's fixed
+    device scratch (no allocation, no stream synchronization).  Calls whose GPU
+    work overlaps race on that scratch; rows are limited to
+    ceil(rows / 4096) * nb * nb <= 65536."""
+    st = samg_block_gram_noalloc(ctypes.c_void_p(X_ptr), ctypes.c_void_p(Y_ptr), rows, nb, ld,
+                                 ctypes.c_void_p(G_ptr), _stream(stream))
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "ctx.cuh"
 
@@ -578,6 +580,66 @@ samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int 
         DBuf<double> work(gram_workspace(rows, nb));
         launch_gram(X, Y, rows, nb, ld, G, work.p, s);
         SAMG_CUDA(cudaStreamSynchronize(s));
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
+
+}  // extern "C"
+
+// ----------------------------------------------- allocation-free Gram product
+// samg_block_gram_noalloc keeps the per-CTA partial sums of the Gram product
+// in one fixed device array instead of a cudaMalloc'd workspace.
+namespace {
+
+constexpr size_t GRAM_STATIC_DOUBLES = 65536;  // 512 KiB of partial sums
+__device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
+
+constexpr int GRAM_STATIC_MAX_DEVICES = 64;
+double *g_gram_static_addr[GRAM_STATIC_MAX_DEVICES];  // per device, looked up once
+std::mutex g_gram_static_mu;
+
+// Device address of g_gram_static for the current device.  The first call on
+// a device asks the runtime once (cudaGetSymbolAddress, with that device
+// current) and caches the answer; later calls only read the cache.
+double *gram_static_scratch() {
+    int dev = 0;
+    SAMG_CUDA(cudaGetDevice(&dev));
+    SAMG_CHECK(dev >= 0 && dev < GRAM_STATIC_MAX_DEVICES, SAMG_E_INVALID,
+               "block_gram_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_gram_static_mu);
+    if (!g_gram_static_addr[dev]) {
+        void *p = nullptr;
+        SAMG_CUDA(cudaGetSymbolAddress(&p, g_gram_static));
+        SAMG_CHECK(p != nullptr, SAMG_E_CUDA, "block_gram_noalloc: no address for the scratch");
+        g_gram_static_addr[dev] = static_cast<double *>(p);
+    }
+    return g_gram_static_addr[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+samg_status samg_block_gram_noalloc(const double *X, const double *Y, int64_t rows, int nb,
+                                    int ld, double *G, void *cuda_stream) {
+    try {
+        SAMG_CHECK(X && Y && G && rows >= 0 && nb >= 1 && nb <= 16 && ld >= nb, SAMG_E_INVALID,
+                   "block_gram_noalloc: bad arguments");
+        check_device();
+        const size_t need = gram_workspace(rows, nb);
+        SAMG_CHECK(need <= GRAM_STATIC_DOUBLES, SAMG_E_INVALID,
+                   "block_gram_noalloc: ceil(rows / 4096) * nb * nb = " + std::to_string(need) +
+                       " partial sums exceed the fixed scratch of " +
+                       std::to_string(GRAM_STATIC_DOUBLES) + " doubles");
+        // Every partial sum the final pass reads is written by the partial
+        // pass of the same call, so the scratch needs no clearing.
+        launch_gram(X, Y, rows, nb, ld, G, gram_static_scratch(), (cudaStream_t)cuda_stream);
         return SAMG_OK;
     } catch (const Error &e) {
         g_create_error = e.what();
