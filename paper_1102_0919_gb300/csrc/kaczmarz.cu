@@ -1,6 +1,7 @@
 // kaczmarz.cu -- schedule builder (host) and sweep kernel (device) for the
 // exact-order Kaczmarz relaxation of Sec. 5.3 (see kaczmarz.cuh).
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 
 #include "kaczmarz.cuh"
@@ -10,15 +11,38 @@ namespace samg {
 namespace {
 
 constexpr int KZ_THREADS = 512;
-constexpr int KZ_COMPUTE = 480;    // compute threads (15 warps); warp 15 communicates
-constexpr int KZ_NBUF = 3;          // staging buffers: schedule two chunks ahead, values one
-constexpr int KZ_PUB = 8;           // publish granularity (levels)
+constexpr int KZ_COMPUTE = 480;    // compute threads (15 warps); warp 15 stages, polls, publishes
+constexpr int KZ_NBUF = 3;          // staging buffers (the producer runs up to 2 chunks ahead)
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
 constexpr int MAX_BAND_ROWS = 1 << 17;
 constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
 // staging chunk limits: levels, rows, entries, staged first values
 constexpr int KZ_CHL = 32, KZ_CHR = 256, KZ_CHE = 1024, KZ_CHX = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any wait
+constexpr unsigned FULL = 0xffffffffu;
+
+// Byte layout of one chunk image: the schedule of up to KZ_CHL levels, copied
+// to shared memory by one bulk copy.  Every array starts on 16 bytes.
+//   lv  int4 per level {first row, rows, log2 lanes per row, has requirements}
+//   ri  int2 per row   {original row, first entry | entries << 16}
+//   inv T per row      1 / ||a_i||^2 (unshifted form)
+//   ent int2 per entry {column, 1 first | 2 last | 4 staged | slot << 3 | xs << 15}
+//   a, b T per entry   coefficients (b: shifted form only)
+//   xc  int per staged first value: its column
+struct ImgLayout {
+    unsigned lv, ri, inv, ent, a, b, xc, bytes;
+};
+__host__ __device__ constexpr unsigned al16u(unsigned v) { return (v + 15u) & ~15u; }
+__host__ __device__ constexpr ImgLayout img_layout(int nl, int nr, int ne, int nx, int tsz,
+                                                   bool shifted) {
+    const unsigned ri = al16u(16u * nl);
+    const unsigned inv = al16u(ri + 8u * nr);
+    const unsigned ent = al16u(inv + (unsigned)tsz * nr);
+    const unsigned a = al16u(ent + 8u * ne);
+    const unsigned b = al16u(a + (unsigned)tsz * ne);
+    const unsigned xc = al16u(b + (shifted ? (unsigned)tsz * ne : 0u));
+    return ImgLayout{0u, ri, inv, ent, a, b, xc, al16u(xc + 4u * nx)};
+}
 
 struct Pattern {                      // merged rows: a (and b) coefficients
     int rows = 0, cols = 0;
@@ -117,19 +141,73 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// asynchronous global -> shared copies (sizes 4, 8 or 16 bytes, both aligned)
-template <int S>
-__device__ __forceinline__ void cp_async(void *dst, const void *src) {
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if (S == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(S)
-                     : "memory");
+// asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+// mbarriers: chunk images arrive by bulk copy (transaction count), gathered
+// values by cp.async with one no-increment arrival per producer lane
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes) : "memory");
+}
+// bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(unsigned long long *b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_test(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity; false on abort (*abort set) or
+// after WAIT_NS.
+__device__ __noinline__ bool mbar_wait(unsigned long long *b, unsigned parity, const int *abort) {
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try(b, parity)) return true;
+        if (*((volatile const int *)abort) || gtimer() - t0 > WAIT_NS) return false;
+    }
+}
+
+// Bounded wait that ignores aborts (draining copies in flight).
+__device__ __noinline__ bool mbar_wait_bounded(unsigned long long *b, unsigned parity) {
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(b, parity))
+        if (gtimer() - t0 > WAIT_NS) return false;
+    return true;
+}
 
 // 16-byte vector moves of one n_b-wide row (LD a multiple of 4; both
 // pointers 16-byte aligned): shared memory (generic) and global (L2 only).
@@ -227,39 +305,6 @@ __device__ __forceinline__ void group_allreduce(T (&v)[LD], int lgG) {
     }
 }
 
-struct KView {
-    int *err;
-    int nbands;
-    const int *band_chunk;   // nbands + 1
-    const int4 *chunk;       // 2 per chunk: {L0, L1, R0, R1}, {E0, E1, X0, X1}
-    const int4 *lvl;         // {first row, first req, publish, log2 lanes per row} + sentinel
-    const int2 *rinfo;       // {original row, first entry}
-    const int2 *ent;         // {column, flags}
-    const int *xsc;          // columns staged per chunk
-    const int2 *req;
-    unsigned long long *progress;
-    KCtl *ctl;
-};
-
-// Shared-memory layout of one staging buffer (byte offsets, 16-byte aligned).
-constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
-template <typename T, int LD, bool SHIFT>
-struct Stage {
-    static constexpr int VB = LD * (int)sizeof(T);          // bytes of one vector row
-    static constexpr bool VALS = VB <= 64;                   // stage rhs / first values
-    static constexpr size_t o_lv = 0;
-    static constexpr size_t o_ri = al16(o_lv + 16 * (KZ_CHL + 1));
-    static constexpr size_t o_inv = al16(o_ri + 8 * (KZ_CHR + 1));
-    static constexpr size_t o_ent = al16(o_inv + 8 * KZ_CHR);
-    static constexpr size_t o_a = al16(o_ent + 8 * KZ_CHE);
-    static constexpr size_t o_b = al16(o_a + sizeof(T) * KZ_CHE);
-    static constexpr size_t o_xc = al16(o_b + (SHIFT ? sizeof(T) * KZ_CHE : 0));
-    static constexpr size_t o_rhs = al16(o_xc + 4 * KZ_CHX);
-    static constexpr size_t o_xs = al16(o_rhs + (VALS ? (size_t)VB * KZ_CHR : 0));
-    static constexpr size_t bytes = al16(o_xs + (VALS ? (size_t)VB * KZ_CHX : 0));
-    static constexpr size_t stride = (bytes + 127) / 128 * 128;
-};
-
 __device__ __forceinline__ void bar_compute() {  // named barrier of the compute warps
     asm volatile("bar.sync 1, %0;" ::"n"(KZ_COMPUTE) : "memory");
 }
@@ -272,74 +317,69 @@ __device__ __forceinline__ void st_rel_cta(int *p, int v) {
     asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
 
-// Warps 0 .. KZ_COMPUTE/32 - 1 compute; the last warp polls (acquire) the
-// progress that upcoming levels require from earlier bands, so that the
-// compute warps only wait on a shared-memory flag.  Thread 0 publishes the
-// band's progress (release) at most every KZ_PUB levels when a later band
-// waits on it, and at the end of the band.
+
+struct KView {
+    int *err;
+    int nbands;
+    const int *band_chunk;     // nbands + 1: first chunk of each band
+    const KChunk *chunk;
+    const int4 *lvl;           // per level: {first req, requirement count, publish, 0}
+    const unsigned char *img;  // chunk images with coefficients of the launch's precision
+    const int2 *req;           // {band, levels that band must have completed}
+    unsigned long long *progress;
+    KCtl *ctl;
+};
+
+// One staging buffer: the chunk image (capacity of a full chunk), then the
+// gathered right-hand-side rows and staged first values (when a row of LD
+// values is at most 64 bytes; wider rows are read from global memory).
+template <typename T, int LD, bool SHIFT>
+struct Stage {
+    static constexpr int VB = LD * (int)sizeof(T);  // bytes of one vector row
+    static constexpr bool VALS = VB <= 64;
+    static constexpr unsigned IMG = img_layout(KZ_CHL, KZ_CHR, KZ_CHE, KZ_CHX, (int)sizeof(T), SHIFT).bytes;
+    static constexpr unsigned o_rhs = IMG;
+    static constexpr unsigned o_xs = o_rhs + (VALS ? (unsigned)VB * KZ_CHR : 0u);
+    static constexpr unsigned bytes = o_xs + (VALS ? (unsigned)VB * KZ_CHX : 0u);
+    static constexpr unsigned stride = (bytes + 127u) / 128u * 128u;
+};
+
+// Warps 0 .. KZ_COMPUTE/32 - 1 compute.  The last warp is the producer: it
+// stages chunk images (bulk copies) and gathered values (cp.async) up to
+// KZ_NBUF chunks ahead, polls (acquire) the progress that upcoming levels
+// require from earlier bands, and publishes (release) this band's progress
+// when it crosses a level that a later band waits for, and at the band's
+// end.  The compute warps touch only shared memory for synchronization.
 template <typename T, int LD, bool SHIFT>
 __global__ void __launch_bounds__(KZ_THREADS)
-    k_kaczmarz(KView kv, const T *__restrict__ ea, const T *__restrict__ eb,
-               const T *__restrict__ inv, const T *__restrict__ rhs, T *x,
-               const double *__restrict__ shift, int window_slots) {
+    k_kaczmarz(KView kv, const T *__restrict__ rhs, T *x, const double *__restrict__ shift,
+               int window_slots) {
     using SG = Stage<T, LD, SHIFT>;
     extern __shared__ __align__(128) unsigned char smraw[];
     T *win = reinterpret_cast<T *>(smraw);
     unsigned char *bufs = smraw + ((size_t)window_slots * LD * sizeof(T) + 127) / 128 * 128;
+    __shared__ __align__(8) unsigned long long mb_sched[KZ_NBUF], mb_vals[KZ_NBUF];
     __shared__ int s_band;
     __shared__ int s_abort;
     __shared__ int s_done;   // band-local levels completed by the compute warps
     __shared__ int s_ready;  // band-local levels whose requirements are met
-    __shared__ unsigned long long s_pc[64];  // comm warp: band << 32 | observed level
+    __shared__ unsigned long long s_pc[64];  // producer: band << 32 | observed level
     const bool comm = threadIdx.x >= KZ_COMPUTE;
     T sh[SHIFT ? LD : 1];
 #pragma unroll
     for (int q = 0; q < (SHIFT ? LD : 1); ++q) sh[q] = SHIFT ? (T)shift[q] : T(0);
     const unsigned long long epoch = *((volatile unsigned long long *)&kv.ctl->epoch);
-    if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int i = 0; i < KZ_NBUF; ++i) {
+            mbar_init(&mb_sched[i], 1);
+            mbar_init(&mb_vals[i], 32);
+        }
+        fence_mbar_init();
+    }
     if (threadIdx.x < 64) s_pc[threadIdx.x] = ~0ull;
-
-    auto load_sched = [&](int c, int bi) {
-        unsigned char *B = bufs + (size_t)bi * SG::stride;
-        const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
-        const int nl = c0.y - c0.x, nr = c0.w - c0.z, ne = c1.y - c1.x, nx = c1.w - c1.z;
-        for (int q = threadIdx.x; q <= nl; q += KZ_COMPUTE)
-            cp_async<16>(B + SG::o_lv + 16 * q, kv.lvl + c0.x + q);
-        for (int q = threadIdx.x; q <= nr; q += KZ_COMPUTE)
-            cp_async<8>(B + SG::o_ri + 8 * q, kv.rinfo + c0.z + q);
-        for (int q = threadIdx.x; q < nr; q += KZ_COMPUTE)
-            cp_async<sizeof(T)>(B + SG::o_inv + sizeof(T) * q, inv + c0.z + q);
-        for (int q = threadIdx.x; q < ne; q += KZ_COMPUTE) {
-            cp_async<8>(B + SG::o_ent + 8 * q, kv.ent + c1.x + q);
-            cp_async<sizeof(T)>(B + SG::o_a + sizeof(T) * q, ea + c1.x + q);
-            if (SHIFT) cp_async<sizeof(T)>(B + SG::o_b + sizeof(T) * q, eb + c1.x + q);
-        }
-        for (int q = threadIdx.x; q < nx; q += KZ_COMPUTE)
-            cp_async<4>(B + SG::o_xc + 4 * q, kv.xsc + c1.z + q);
-        cp_commit();
-    };
-    auto load_vals = [&](int c, int bi) {
-        unsigned char *B = bufs + (size_t)bi * SG::stride;
-        if (SG::VALS) {
-            const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
-            const int nr = c0.w - c0.z, nx = c1.w - c1.z;
-            const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
-            const int *xc = reinterpret_cast<const int *>(B + SG::o_xc);
-            constexpr int P = SG::VB / 16;
-            if (rhs)
-                for (int q = threadIdx.x; q < nr * P; q += KZ_COMPUTE) {
-                    const int r = q / P, p = q % P;
-                    cp_async<16>(B + SG::o_rhs + (size_t)SG::VB * r + 16 * p,
-                                 reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + 16 * p);
-                }
-            for (int q = threadIdx.x; q < nx * P; q += KZ_COMPUTE) {
-                const int r = q / P, p = q % P;
-                cp_async<16>(B + SG::o_xs + (size_t)SG::VB * r + 16 * p,
-                             reinterpret_cast<const unsigned char *>(x + (size_t)xc[r] * LD) + 16 * p);
-            }
-        }
-        cp_commit();
-    };
+    int base = 0;  // chunks this CTA staged in earlier bands: chunk j uses buffer
+                   // j % KZ_NBUF in phase (j / KZ_NBUF) & 1
 
     for (;;) {
         __syncthreads();
@@ -352,33 +392,84 @@ __global__ void __launch_bounds__(KZ_THREADS)
         const int b = s_band;
         if (b >= kv.nbands || s_abort) break;
         const int cb = kv.band_chunk[b], ce = kv.band_chunk[b + 1];
-        const int Lband = kv.chunk[2 * cb].x;
-        const int Lend = kv.chunk[2 * (ce - 1)].y;
-        const int nlev = Lend - Lband;
+        const int Lband = kv.chunk[cb].L0;
+        const int nlev = kv.chunk[ce - 1].L0 + kv.chunk[ce - 1].nl - Lband;
         if (comm) {
-            // ---------------------------------------------- communication warp
+            // ------------------------------------------------------ producer warp
             const int lane = threadIdx.x & 31;
-            int published = 0, ready = 0;
+            int sn = cb, vn = cb, ready = 0, published = 0;
+            bool aborted = false;
             unsigned long long t0 = gtimer();  // re-armed whenever something advances
-            while (published < nlev) {
-                bool aborted = *((volatile int *)&s_abort) != 0;
-                if (!aborted && (*((volatile int *)kv.err) || gtimer() - t0 > WAIT_NS)) {
+            for (;;) {
+                if (*((volatile int *)&s_abort) || *((volatile int *)kv.err)) aborted = true;
+                if (!aborted && gtimer() - t0 > WAIT_NS) {
                     if (lane == 0) {
                         atomicExch(kv.err, 1);
-                        s_abort = 1;
+                        *((volatile int *)&s_abort) = 1;
                     }
                     aborted = true;
                 }
-                if (aborted) {
-                    if (lane == 0) st_rel_cta(&s_ready, nlev);  // release the compute warps
+                if (__any_sync(FULL, aborted)) {
+                    aborted = true;
                     break;
                 }
-                // requirements of the next levels, a few at a time
-                int adv = 0;
-                while (ready < nlev && adv < 8) {
-                    const int4 l0 = kv.lvl[Lband + ready], l1 = kv.lvl[Lband + ready + 1];
+                bool adv = false;
+                const int done = __shfl_sync(FULL, ld_acq_cta(&s_done), 0);
+                // a. image of chunk sn, once the chunk that used its buffer is done
+                if (sn < ce) {
+                    const int old = sn - KZ_NBUF;
+                    if (old < cb || done >= kv.chunk[old].L0 + kv.chunk[old].nl - Lband) {
+                        const int j = base + (sn - cb);
+                        const int bi = j % KZ_NBUF;
+                        if (lane == 0) {
+                            const KChunk ck = kv.chunk[sn];
+                            const unsigned bytes = sizeof(T) == 4 ? ck.bytes_f : ck.bytes_d;
+                            const long long off = sizeof(T) == 4 ? ck.off_f : ck.off_d;
+                            // the compute warps' reads of the old chunk precede
+                            // the asynchronous overwrite
+                            fence_proxy_async();
+                            mbar_expect_tx(&mb_sched[bi], bytes);
+                            bulk_g2s(bufs + (size_t)bi * SG::stride, kv.img + off, bytes, &mb_sched[bi]);
+                        }
+                        ++sn;
+                        adv = true;
+                    }
+                }
+                // b. right-hand sides and staged first values of chunk vn
+                if (SG::VALS && vn < sn) {
+                    const int j = base + (vn - cb);
+                    const int bi = j % KZ_NBUF;
+                    const unsigned par = (unsigned)(j / KZ_NBUF) & 1u;
+                    const int landed = __shfl_sync(FULL, (int)mbar_test(&mb_sched[bi], par), 0);
+                    if (landed) {
+                        const KChunk ck = kv.chunk[vn];
+                        unsigned char *B = bufs + (size_t)bi * SG::stride;
+                        const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, (int)sizeof(T), SHIFT);
+                        const int2 *ri = reinterpret_cast<const int2 *>(B + IL.ri);
+                        const int *xc = reinterpret_cast<const int *>(B + IL.xc);
+                        constexpr int P = SG::VB / 16;
+                        if (rhs)
+                            for (int q = lane; q < ck.nr * P; q += 32) {
+                                const int r = q / P, p = q % P;
+                                cp_async16(B + SG::o_rhs + (size_t)SG::VB * r + 16 * p,
+                                           reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + 16 * p);
+                            }
+                        for (int q = lane; q < ck.nx * P; q += 32) {
+                            const int r = q / P, p = q % P;
+                            cp_async16(B + SG::o_xs + (size_t)SG::VB * r + 16 * p,
+                                       reinterpret_cast<const unsigned char *>(x + (size_t)xc[r] * LD) + 16 * p);
+                        }
+                        cp_async_arrive(&mb_vals[bi]);
+                        ++vn;
+                        adv = true;
+                    }
+                }
+                // c. requirements of the next levels, a few at a time
+                int nready = 0;
+                while (ready < nlev && nready < 8) {
+                    const int4 lq = kv.lvl[Lband + ready];
                     bool ok = true;
-                    for (int q = l0.y + lane; q < l1.y; q += 32) {
+                    for (int q = lq.x + lane; q < lq.x + lq.y; q += 32) {
                         const int2 rq = kv.req[q];
                         const unsigned long long key = s_pc[rq.x & 63];
                         if ((int)(key >> 32) == rq.x && (unsigned)key >= (unsigned)rq.y) continue;
@@ -387,152 +478,165 @@ __global__ void __launch_bounds__(KZ_THREADS)
                             s_pc[rq.x & 63] = ((unsigned long long)(unsigned)rq.x << 32) | (v & 0xffffffffull);
                         ok = ok && (v >= ((epoch << 32) | (unsigned)rq.y));
                     }
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (!ok) break;
+                    if (!__all_sync(FULL, ok)) break;
                     ++ready;
-                    ++adv;
+                    ++nready;
                 }
-                if (adv && lane == 0) st_rel_cta(&s_ready, ready);
-                if (adv) t0 = gtimer();
-                // the compute warps publish; follow their progress to finish
-                const int done = *((volatile int *)&s_done);
+                if (nready) {
+                    if (lane == 0) st_rel_cta(&s_ready, ready);
+                    adv = true;
+                }
+                // d. publish: the release covers the compute warps' stores, which
+                // precede thread 0's release of s_done (acquired above)
                 if (done > published) {
+                    bool f = false;
+                    for (int l = published + lane; l < done; l += 32) f = f || kv.lvl[Lband + l].z != 0;
+                    if ((__any_sync(FULL, f) || done == nlev) && lane == 0)
+                        st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
                     published = done;
-                    t0 = gtimer();
+                    adv = true;
                 }
-                if (!adv && done == published) __nanosleep(20);
+                if (published >= nlev) break;
+                if (adv) t0 = gtimer();
+                else __nanosleep(32);
+            }
+            if (aborted) {
+                if (lane == 0) st_rel_cta(&s_ready, nlev);  // release the compute warps
+                // copies issued by this warp land before the CTA moves on
+                cp_async_wait_all();
+                if (lane == 0)
+                    for (int c = max(cb, sn - KZ_NBUF); c < sn; ++c) {
+                        const int j = base + (c - cb);
+                        mbar_wait_bounded(&mb_sched[j % KZ_NBUF], (unsigned)(j / KZ_NBUF) & 1u);
+                    }
             }
         } else {
-            // ---------------------------------------------- compute warps
-            bool pend_pub = false;  // thread 0: a flagged level awaits publication
-            // pipeline over chunks: schedule arrays two chunks ahead, right-hand
-            // sides and first values one chunk ahead, so that only the chunk
-            // being processed is waited for
-            load_sched(cb, 0);
-            cp_wait<0>();
-            bar_compute();
-            load_vals(cb, 0);
-            if (cb + 1 < ce) load_sched(cb + 1, 1);
-            else cp_commit();
+            // ------------------------------------------------------ compute warps
+            bool aborted = false;
             for (int c = cb; c < ce; ++c) {
-                const int bi = (c - cb) % KZ_NBUF;
+                const int j = base + (c - cb);
+                const int bi = j % KZ_NBUF;
+                const unsigned par = (unsigned)(j / KZ_NBUF) & 1u;
+                const KChunk ck = kv.chunk[c];
+                if (!aborted) {
+                    bool ok = mbar_wait(&mb_sched[bi], par, &s_abort);
+                    if (ok && SG::VALS) ok = mbar_wait(&mb_vals[bi], par, &s_abort);
+                    if (!ok) {
+                        atomicExch(kv.err, 1);
+                        *((volatile int *)&s_abort) = 1;
+                    }
+                    // warp-uniform, so that the row sums' shuffles see every lane
+                    aborted = __any_sync(FULL, !ok);
+                }
                 unsigned char *B = bufs + (size_t)bi * SG::stride;
-                // sched(c+1) and vals(c) were issued one step earlier
-                cp_wait<0>();
-                bar_compute();
-                if (c + 1 < ce) load_vals(c + 1, (c + 1 - cb) % KZ_NBUF);
-                else cp_commit();
-                if (c + 2 < ce) load_sched(c + 2, (c + 2 - cb) % KZ_NBUF);
-                else cp_commit();
-                const int4 c0 = kv.chunk[2 * c], c1 = kv.chunk[2 * c + 1];
-                const int4 *lv = reinterpret_cast<const int4 *>(B + SG::o_lv);
-                const int2 *ri = reinterpret_cast<const int2 *>(B + SG::o_ri);
-                const T *sinv = reinterpret_cast<const T *>(B + SG::o_inv);
-                const int2 *se = reinterpret_cast<const int2 *>(B + SG::o_ent);
-                const T *sa = reinterpret_cast<const T *>(B + SG::o_a);
-                const T *sb = reinterpret_cast<const T *>(B + SG::o_b);
+                const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, (int)sizeof(T), SHIFT);
+                const int4 *lv = reinterpret_cast<const int4 *>(B + IL.lv);
+                const int2 *ri = reinterpret_cast<const int2 *>(B + IL.ri);
+                const T *sinv = reinterpret_cast<const T *>(B + IL.inv);
+                const int2 *se = reinterpret_cast<const int2 *>(B + IL.ent);
+                const T *sa = reinterpret_cast<const T *>(B + IL.a);
+                const T *sb = reinterpret_cast<const T *>(B + IL.b);
                 const T *srhs = reinterpret_cast<const T *>(B + SG::o_rhs);
                 const T *sxs = reinterpret_cast<const T *>(B + SG::o_xs);
-                for (int L = 0; L < c0.y - c0.x; ++L) {
-                    const int4 l0 = lv[L], l1 = lv[L + 1];
-                    const int lb = c0.x + L - Lband;  // band-local level
-                    if (l1.y > l0.y) {
-                        // requirements of this level: wait for the comm warp,
-                        // which releases every wait when it gives up.  The
-                        // compute warps never leave the loop early, so every
-                        // named barrier is reached by all of them.
-                        const unsigned long long t0 = gtimer();
-                        while (ld_acq_cta(&s_ready) <= lb) {
-                            if (gtimer() - t0 > 2 * WAIT_NS) break;
+                for (int L = 0; L < ck.nl; ++L) {
+                    const int lb = ck.L0 + L - Lband;  // band-local level
+                    if (!aborted) {
+                        const int4 lr = lv[L];
+                        if (lr.w) {
+                            // requirements of this level: wait for the producer,
+                            // which releases every wait when it gives up
+                            const unsigned long long t0 = gtimer();
+                            while (ld_acq_cta(&s_ready) <= lb)
+                                if (gtimer() - t0 > 2 * WAIT_NS) break;
+                            aborted = __any_sync(FULL, *((volatile int *)&s_abort) != 0);
                         }
-                    }
-                    {
-                        // G = 2^lgG lanes per row (the smallest power of two not
-                        // below the sub-level's longest row, at most 32); lane lg
-                        // takes entries lg, lg + G, ... for all LD columns.  A
-                        // warp holding no row of the level goes straight to the
-                        // barrier.
-                        const int lgG = l0.w;
-                        const int G = 1 << lgG;
-                        const int nrow = l1.x - l0.x;
-                        const int lane = threadIdx.x & 31;
-                        const int lg = threadIdx.x & (G - 1);
-                        const int wrow = (threadIdx.x & ~31) >> lgG;
-                        for (int pr = 0; pr + wrow < nrow; pr += KZ_COMPUTE >> lgG) {
-                            const int r = pr + (threadIdx.x >> lgG);
-                            const bool act = r < nrow;
-                            const int k = l0.x - c0.z + r;
-                            T acc[LD], nrm[SHIFT ? LD : 1];
+                        if (!aborted) {
+                            // G = 2^lgG lanes per row (the smallest power of two
+                            // not below the level's longest row, at most 32);
+                            // lane lg takes entries lg, lg + G, ... for all LD
+                            // columns.  A warp holding no row of the level goes
+                            // straight to the barrier.
+                            const int lgG = lr.z;
+                            const int G = 1 << lgG;
+                            const int nrow = lr.y;
+                            const int lane = threadIdx.x & 31;
+                            const int lg = threadIdx.x & (G - 1);
+                            const int wrow = (threadIdx.x & ~31) >> lgG;
+                            for (int pr = 0; pr + wrow < nrow; pr += KZ_COMPUTE >> lgG) {
+                                const int r = pr + (threadIdx.x >> lgG);
+                                const bool act = r < nrow;
+                                const int k = lr.x + r;
+                                T acc[LD], nrm[SHIFT ? LD : 1];
 #pragma unroll
-                            for (int q = 0; q < LD; ++q) acc[q] = T(0);
+                                for (int q = 0; q < LD; ++q) acc[q] = T(0);
 #pragma unroll
-                            for (int q = 0; q < (SHIFT ? LD : 1); ++q) nrm[q] = T(0);
-                            // the lane's first entry stays in registers for the update
-                            int2 fen = make_int2(0, 0);
-                            T fa = T(0), fb = T(0), fv[LD];
-                            int e1 = 0;
-                            bool own = false;
-                            if (act) {
-                                const int e0 = ri[k].y - c1.x;
-                                e1 = ri[k + 1].y - c1.x;
-                                own = e0 + lg < e1;
-                                for (int e = e0 + lg; e < e1; e += G) {
-                                    const int2 en = se[e];
-                                    const T a = sa[e];
-                                    const T bq = SHIFT ? sb[e] : T(0);
-                                    T val[LD];
-                                    const int fl = en.y;
-                                    if (!(fl & 1))
-                                        vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
-                                    else if (SG::VALS && (fl & 4))
-                                        vld<T, LD>(val, sxs + (fl >> 15) * LD);
-                                    else
-                                        vld_cg<T, LD>(val, x + (size_t)en.x * LD);
-#pragma unroll
-                                    for (int q = 0; q < LD; ++q) {
-                                        const T coef = SHIFT ? a - sh[q] * bq : a;
-                                        acc[q] = fma(coef, val[q], acc[q]);
-                                        if (SHIFT) nrm[q] = fma(coef, coef, nrm[q]);
-                                    }
-                                    if (e == e0 + lg) {
-                                        fen = en; fa = a; fb = bq;
-#pragma unroll
-                                        for (int q = 0; q < LD; ++q) fv[q] = val[q];
-                                    }
-                                }
-                            }
-                            // d_q = (b_i - <a_i, x_q>) / ||a_i||^2 for every column q
-                            T d[LD];
-                            if (pow2(LD) && G >= LD) {
-                                const T sa_c = group_reduce_scatter<T, LD>(acc, lane, lgG);
-                                const T sn_c = SHIFT ? group_reduce_scatter<T, (SHIFT ? LD : 1)>(nrm, lane, lgG) : T(0);
-                                const int c = brev_low(lane & (LD - 1), ilog2(LD));
-                                T dc = T(0);
+                                for (int q = 0; q < (SHIFT ? LD : 1); ++q) nrm[q] = T(0);
+                                // the lane's first entry stays in registers for the update
+                                int2 fen = make_int2(0, 0);
+                                T fa = T(0), fb = T(0), fv[LD];
+                                int2 rk = make_int2(0, 0);
+                                int e0 = 0, e1 = 0;
                                 if (act) {
-                                    const T bi = rhs ? (SG::VALS ? srhs[k * LD + c] : rhs[(size_t)ri[k].x * LD + c]) : T(0);
-                                    dc = SHIFT ? (sn_c > T(0) ? (bi - sa_c) / sn_c : T(0)) : (bi - sa_c) * sinv[k];
-                                }
-                                const int gb = lane & ~(G - 1);
+                                    rk = ri[k];
+                                    e0 = rk.y & 0xffff;
+                                    e1 = e0 + (rk.y >> 16);
+                                    for (int e = e0 + lg; e < e1; e += G) {
+                                        const int2 en = se[e];
+                                        const T a = sa[e];
+                                        const T bq = SHIFT ? sb[e] : T(0);
+                                        T val[LD];
+                                        const int fl = en.y;
+                                        if (!(fl & 1))
+                                            vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
+                                        else if (SG::VALS && (fl & 4))
+                                            vld<T, LD>(val, sxs + (fl >> 15) * LD);
+                                        else
+                                            vld_cg<T, LD>(val, x + (size_t)en.x * LD);
 #pragma unroll
-                                for (int q = 0; q < LD; ++q)
-                                    d[q] = __shfl_sync(0xffffffffu, dc, gb + brev_low(q, ilog2(LD)));
-                            } else {
-                                group_allreduce<T, LD>(acc, lgG);
-                                if (SHIFT) group_allreduce<T, (SHIFT ? LD : 1)>(nrm, lgG);
+                                        for (int q = 0; q < LD; ++q) {
+                                            const T coef = SHIFT ? a - sh[q] * bq : a;
+                                            acc[q] = fma(coef, val[q], acc[q]);
+                                            if (SHIFT) nrm[q] = fma(coef, coef, nrm[q]);
+                                        }
+                                        if (e == e0 + lg) {
+                                            fen = en;
+                                            fa = a;
+                                            fb = bq;
 #pragma unroll
-                                for (int q = 0; q < LD; ++q) d[q] = T(0);
-                                if (act) {
-#pragma unroll
-                                    for (int q = 0; q < LD; ++q) {
-                                        const T bi = rhs ? (SG::VALS ? srhs[k * LD + q] : rhs[(size_t)ri[k].x * LD + q]) : T(0);
-                                        const T nq = SHIFT ? nrm[q] : T(1);
-                                        d[q] = SHIFT ? (nq > T(0) ? (bi - acc[q]) / nq : T(0)) : (bi - acc[q]) * sinv[k];
+                                            for (int q = 0; q < LD; ++q) fv[q] = val[q];
+                                        }
                                     }
                                 }
-                            }
-                            // x_q += d_q a_i on the row's entries
-                            if (own) {
-                                const int e0 = ri[k].y - c1.x;
+                                // d_q = (b_i - <a_i, x_q>) / ||a_i||^2 for every column q
+                                T d[LD];
+                                if (pow2(LD) && G >= LD) {
+                                    const T sa_c = group_reduce_scatter<T, LD>(acc, lane, lgG);
+                                    const T sn_c = SHIFT ? group_reduce_scatter<T, (SHIFT ? LD : 1)>(nrm, lane, lgG) : T(0);
+                                    const int c = brev_low(lane & (LD - 1), ilog2(LD));
+                                    T dc = T(0);
+                                    if (act) {
+                                        const T bi = rhs ? (SG::VALS ? srhs[k * LD + c] : rhs[(size_t)rk.x * LD + c]) : T(0);
+                                        dc = SHIFT ? (sn_c > T(0) ? (bi - sa_c) / sn_c : T(0)) : (bi - sa_c) * sinv[k];
+                                    }
+                                    const int gb = lane & ~(G - 1);
+#pragma unroll
+                                    for (int q = 0; q < LD; ++q)
+                                        d[q] = __shfl_sync(FULL, dc, gb + brev_low(q, ilog2(LD)));
+                                } else {
+                                    group_allreduce<T, LD>(acc, lgG);
+                                    if (SHIFT) group_allreduce<T, (SHIFT ? LD : 1)>(nrm, lgG);
+#pragma unroll
+                                    for (int q = 0; q < LD; ++q) d[q] = T(0);
+                                    if (act) {
+#pragma unroll
+                                        for (int q = 0; q < LD; ++q) {
+                                            const T bi = rhs ? (SG::VALS ? srhs[k * LD + q] : rhs[(size_t)rk.x * LD + q]) : T(0);
+                                            const T nq = SHIFT ? nrm[q] : T(1);
+                                            d[q] = SHIFT ? (nq > T(0) ? (bi - acc[q]) / nq : T(0)) : (bi - acc[q]) * sinv[k];
+                                        }
+                                    }
+                                }
+                                // x_q += d_q a_i on the row's entries
                                 for (int e = e0 + lg; e < e1; e += G) {
                                     int2 en = fen;
                                     T a = fa, bq = fb, val[LD];
@@ -564,23 +668,13 @@ __global__ void __launch_bounds__(KZ_THREADS)
                             }
                         }
                     }
+                    // every compute warp reaches every barrier, aborted or not
                     bar_compute();
-                    if (threadIdx.x == 0) {
-                        pend_pub = pend_pub || l0.z;
-                        // the release makes every compute thread's stores of the
-                        // finished levels visible (cumulative over the barrier)
-                        if (pend_pub && ((lb + 1) % KZ_PUB == 0 || lb + 1 == nlev)) {
-                            st_release(&kv.progress[b], (epoch << 32) | (unsigned)(lb + 1));
-                            pend_pub = false;
-                        }
-                        *((volatile int *)&s_done) = lb + 1;
-                    }
+                    if (threadIdx.x == 0) st_rel_cta(&s_done, lb + 1);
                 }
             }
-            cp_wait<0>();
-            bar_compute();
-            if (threadIdx.x == 0) st_release(&kv.progress[b], (epoch << 32) | (unsigned)nlev);
         }
+        base += ce - cb;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -595,14 +689,14 @@ __global__ void __launch_bounds__(KZ_THREADS)
     }
 }
 
-
 template <typename T, int LD, bool SHIFT>
-void launch_one(const KSched &ks, const T *ea, const T *eb, const T *inv, const T *rhs, T *x,
-                const double *shift, cudaStream_t s) {
+void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaStream_t s) {
     using SG = Stage<T, LD, SHIFT>;
     auto kern = k_kaczmarz<T, LD, SHIFT>;
     const int slots = std::max(ks.max_slots, 1);
-    const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + KZ_NBUF * SG::stride;
+    const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + (size_t)KZ_NBUF * SG::stride;
+    SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
+               "kaczmarz: vector blocks must be 16-byte aligned");
     // per kernel instance: the largest dynamic shared memory set so far, and
     // the SM count; per schedule and instance: the resident CTA count
     static size_t smem_set = 0;
@@ -624,11 +718,43 @@ void launch_one(const KSched &ks, const T *ea, const T *eb, const T *inv, const 
         SAMG_CHECK(bps > 0, SAMG_E_CUDA, "kaczmarz: staging buffers do not fit in shared memory");
         grid = std::min(ks.nbands, nsm * bps);
     }
+    const unsigned char *img = sizeof(T) == 4 ? ks.img_f.p : ks.img_d.p;
     KView kv{ks.err ? ks.err : &ks.ctl.p->err, ks.nbands, ks.band_chunk.p, ks.chunk.p, ks.lvl.p,
-             ks.rinfo.p, ks.ent.p, ks.xsc.p, ks.req.p, ks.progress.p, ks.ctl.p};
+             img, ks.req.p, ks.progress.p, ks.ctl.p};
     SAMG_COUNT_LAUNCH();
-    kern<<<grid, KZ_THREADS, smem, s>>>(kv, ea, eb, inv, rhs, x, shift, slots);
+    kern<<<grid, KZ_THREADS, smem, s>>>(kv, rhs, x, shift, slots);
     SAMG_CUDA(cudaGetLastError());
+}
+
+// Appends the image of one chunk with coefficients of type T; returns its size.
+template <typename T>
+int write_image(std::vector<unsigned char> &img, bool shifted, const std::vector<int4> &lrec,
+                const std::vector<int2> &rrec, const std::vector<double> &rinv,
+                const std::vector<int2> &erec, const std::vector<double> &ca,
+                const std::vector<double> &cb, const std::vector<int> &xc) {
+    const ImgLayout L = img_layout((int)lrec.size(), (int)rrec.size(), (int)erec.size(),
+                                   (int)xc.size(), (int)sizeof(T), shifted);
+    const size_t base = img.size();
+    img.resize(base + L.bytes, 0);
+    unsigned char *p = img.data() + base;
+    std::memcpy(p + L.lv, lrec.data(), 16 * lrec.size());
+    std::memcpy(p + L.ri, rrec.data(), 8 * rrec.size());
+    for (size_t i = 0; i < rinv.size(); ++i) {
+        const T v = (T)rinv[i];
+        std::memcpy(p + L.inv + sizeof(T) * i, &v, sizeof(T));
+    }
+    std::memcpy(p + L.ent, erec.data(), 8 * erec.size());
+    for (size_t i = 0; i < ca.size(); ++i) {
+        const T v = (T)ca[i];
+        std::memcpy(p + L.a + sizeof(T) * i, &v, sizeof(T));
+    }
+    if (shifted)
+        for (size_t i = 0; i < cb.size(); ++i) {
+            const T v = (T)cb[i];
+            std::memcpy(p + L.b + sizeof(T) * i, &v, sizeof(T));
+        }
+    std::memcpy(p + L.xc, xc.data(), 4 * xc.size());
+    return (int)L.bytes;
 }
 
 }  // namespace
@@ -665,15 +791,13 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     ks.nbands = nb;
     // 2. per band: levels, window slots, sub-levels (<= chunk limits), chunks
     std::vector<int> band_chunk(nb + 1, 0);
-    std::vector<int4> lvl, chunk;
-    std::vector<int2> rinfo, ent, req;
-    std::vector<int> xsc;
-    std::vector<double> ea, eb, inv;
+    std::vector<int4> lvl;  // per level: {first req, requirement count, publish, 0}
+    std::vector<KChunk> chunk;
+    std::vector<unsigned char> img_f, img_d;
+    std::vector<int2> req;
     std::vector<int> g_band(cols, -1), g_sub(cols, 0), slot(cols, 0), last_sub(cols, 0);
     std::vector<int> waited(nb, 0), waited_stamp(nb, -1);
-    ent.reserve(p.ci.size());
-    ea.reserve(p.ci.size());
-    if (ks.shifted) eb.reserve(p.ci.size());
+    int64_t nent = 0;
     int max_slots = 0;
     std::vector<std::vector<int>> pub(nb);  // per band: band-local sub-levels to publish
     std::vector<int> band_lvl0(nb + 1, 0);
@@ -757,69 +881,27 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
         for (const RowRec &x : rr)
             for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e)
                 if (w.lastlv[p.ci[e]] == w.rowlv[x.row - r0]) last_sub[p.ci[e]] = x.sub;
-        // emit levels, rows, entries, chunk records, requirements
+        // requirements: a first touch of a column last written by an earlier
+        // band needs that band to have completed the sub-level of its last touch
         const int L0 = (int)lvl.size();
         band_lvl0[b] = L0;
-        band_chunk[b] = (int)chunk.size() / 2;
+        band_chunk[b] = (int)chunk.size();
         std::vector<PendReq> pend;
-        size_t ri = 0;
-        int cur_chunk = -1, xs_local = 0;
-        int4 crec0{0, 0, 0, 0}, crec1{0, 0, 0, 0};
-        auto close_chunk = [&]() {
-            if (cur_chunk < 0) return;
-            crec0.y = (int)lvl.size();
-            crec0.w = (int)rinfo.size();
-            crec1.y = (int)ent.size();
-            crec1.w = (int)xsc.size();
-            chunk.push_back(crec0);
-            chunk.push_back(crec1);
-        };
-        for (int q = 0; q < nsub; ++q) {
-            if (sub_chunk[q] != cur_chunk) {
-                close_chunk();
-                cur_chunk = sub_chunk[q];
-                crec0 = int4{(int)lvl.size(), 0, (int)rinfo.size(), 0};
-                crec1 = int4{(int)ent.size(), 0, (int)xsc.size(), 0};
-                xs_local = 0;
-            }
-            // lanes per row: a power of two >= the longest row of the level
-            // (at most 32; longer rows give a lane several entries)
-            int lg = 0;
-            while (lg < 5 && (1 << lg) < sub_maxe[q]) ++lg;
-            int4 L4{(int)rinfo.size(), 0, 0, lg};
-            lvl.push_back(L4);
-            for (; ri < rr.size() && rr[ri].sub == q; ++ri) {
-                const int r = rr[ri].row;
-                const int lv = w.rowlv[r - r0];
-                rinfo.push_back(make_int2(r, (int)ent.size()));
-                double n2 = 0.0;
-                for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
-                    const int c = p.ci[e];
-                    const int first = (w.firstlv[c] == lv), last = (w.lastlv[c] == lv);
-                    const int sl = (w.cnt[c] >= 2) ? slot[c] : 0;
-                    int staged = 0, xi = 0;
-                    if (first && g_band[c] < 0) {
-                        staged = 1;
-                        xi = xs_local++;
-                        xsc.push_back(c);
-                    }
-                    ent.push_back(make_int2(c, first | (last << 1) | (staged << 2) | (sl << 3) | (xi << 15)));
-                    ea.push_back(p.a[e]);
-                    if (ks.shifted) eb.push_back(p.b[e]);
-                    n2 += p.a[e] * p.a[e];
-                    if (first && g_band[c] >= 0) pend.push_back({q, g_band[c], g_sub[c] + 1});
-                }
-                inv.push_back(n2 > 0.0 ? 1.0 / n2 : 0.0);
+        for (const RowRec &x : rr) {
+            const int lv = w.rowlv[x.row - r0];
+            for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e) {
+                const int c = p.ci[e];
+                if (w.firstlv[c] == lv && g_band[c] >= 0) pend.push_back({x.sub, g_band[c], g_sub[c] + 1});
             }
         }
-        close_chunk();
         // per sub-level: max need per band, dropping needs already waited for
         std::sort(pend.begin(), pend.end(), [](const PendReq &a, const PendReq &b2) {
             return a.sub != b2.sub ? a.sub < b2.sub : (a.band != b2.band ? a.band < b2.band : a.need > b2.need);
         });
+        lvl.resize(L0 + nsub, int4{0, 0, 0, 0});
         size_t q = 0;
         for (int l = 0; l < nsub; ++l) {
-            lvl[L0 + l].y = (int)req.size();
+            lvl[L0 + l].x = (int)req.size();
             while (q < pend.size() && pend[q].sub == l) {
                 const PendReq &pr = pend[q];
                 if (waited_stamp[pr.band] != b || waited[pr.band] < pr.need) {
@@ -831,42 +913,80 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                 const int bb = pr.band;
                 while (q < pend.size() && pend[q].sub == l && pend[q].band == bb) ++q;
             }
+            lvl[L0 + l].y = (int)req.size() - lvl[L0 + l].x;
+        }
+        // one image per chunk (chunk-local row and entry numbers)
+        size_t ri = 0;
+        const int nch = (int)chunk_first_sub.size();
+        std::vector<int4> lrec;
+        std::vector<int2> rrec, erec;
+        std::vector<double> rinv, ca, cbv;
+        std::vector<int> xc;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int q0 = chunk_first_sub[ch], q1 = ch + 1 < nch ? chunk_first_sub[ch + 1] : nsub;
+            lrec.clear(); rrec.clear(); erec.clear(); rinv.clear(); ca.clear(); cbv.clear(); xc.clear();
+            for (int qq = q0; qq < q1; ++qq) {
+                // lanes per row: a power of two >= the longest row of the level
+                // (at most 32; longer rows give a lane several entries)
+                int lg = 0;
+                while (lg < 5 && (1 << lg) < sub_maxe[qq]) ++lg;
+                const int row0 = (int)rrec.size();
+                for (; ri < rr.size() && rr[ri].sub == qq; ++ri) {
+                    const int r = rr[ri].row;
+                    const int lv = w.rowlv[r - r0];
+                    const int e0 = (int)erec.size();
+                    double n2 = 0.0;
+                    for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
+                        const int c = p.ci[e];
+                        const int first = (w.firstlv[c] == lv), last = (w.lastlv[c] == lv);
+                        const int sl = (w.cnt[c] >= 2) ? slot[c] : 0;
+                        int staged = 0, xi = 0;
+                        if (first && g_band[c] < 0) {
+                            staged = 1;
+                            xi = (int)xc.size();
+                            xc.push_back(c);
+                        }
+                        erec.push_back(make_int2(c, first | (last << 1) | (staged << 2) | (sl << 3) | (xi << 15)));
+                        ca.push_back(p.a[e]);
+                        if (ks.shifted) cbv.push_back(p.b[e]);
+                        n2 += p.a[e] * p.a[e];
+                    }
+                    rrec.push_back(make_int2(r, e0 | (((int)erec.size() - e0) << 16)));
+                    rinv.push_back(n2 > 0.0 ? 1.0 / n2 : 0.0);
+                }
+                lrec.push_back(make_int4(row0, (int)rrec.size() - row0, lg, lvl[L0 + qq].y > 0 ? 1 : 0));
+            }
+            KChunk ck{};
+            ck.L0 = L0 + q0;
+            ck.nl = q1 - q0;
+            ck.nr = (int)rrec.size();
+            ck.ne = (int)erec.size();
+            ck.nx = (int)xc.size();
+            ck.off_f = (long long)img_f.size();
+            ck.off_d = (long long)img_d.size();
+            ck.bytes_f = write_image<float>(img_f, ks.shifted, lrec, rrec, rinv, erec, ca, cbv, xc);
+            ck.bytes_d = write_image<double>(img_d, ks.shifted, lrec, rrec, rinv, erec, ca, cbv, xc);
+            chunk.push_back(ck);
+            nent += ck.ne;
         }
         for (int c : w.touched) {
             g_band[c] = b;
             g_sub[c] = last_sub[c];
         }
     }
-    band_chunk[nb] = (int)chunk.size() / 2;
-    band_lvl0[nb] = (int)lvl.size();
+    band_chunk[nb] = (int)chunk.size();
     for (int b = 0; b < nb; ++b)
         for (int l : pub[b]) lvl[band_lvl0[b] + l].z = 1;
-    lvl.push_back(int4{(int)rinfo.size(), (int)req.size(), 0, 0});
-    rinfo.push_back(make_int2(0, (int)ent.size()));
-    ks.nlevels = (int)lvl.size() - 1;
+    ks.nlevels = (int)lvl.size();
     ks.max_slots = max_slots;
-    ks.nent = (int64_t)ent.size();
-    ks.nchunks = (int)chunk.size() / 2;
+    ks.nent = nent;
+    ks.nchunks = (int)chunk.size();
     // 3. upload
     ks.band_chunk.upload(band_chunk.data(), band_chunk.size(), s);
     ks.chunk.upload(chunk.data(), chunk.size(), s);
     ks.lvl.upload(lvl.data(), lvl.size(), s);
-    ks.rinfo.upload(rinfo.data(), rinfo.size(), s);
-    if (ent.empty()) ent.push_back(make_int2(0, 0));
-    ks.ent.upload(ent.data(), ent.size(), s);
-    ks.ea_d.upload(ea.data(), ea.size(), s);
-    std::vector<float> f(ea.begin(), ea.end());
-    ks.ea_f.upload(f.data(), f.size(), s);
-    if (ks.shifted) {
-        ks.eb_d.upload(eb.data(), eb.size(), s);
-        std::vector<float> fb(eb.begin(), eb.end());
-        ks.eb_f.upload(fb.data(), fb.size(), s);
-    }
-    ks.inv_d.upload(inv.data(), inv.size(), s);
-    std::vector<float> fi(inv.begin(), inv.end());
-    ks.inv_f.upload(fi.data(), fi.size(), s);
-    if (xsc.empty()) xsc.push_back(0);
-    ks.xsc.upload(xsc.data(), xsc.size(), s);
+    ks.img_f.upload(img_f.data(), img_f.size(), s);
+    ks.img_d.upload(img_d.data(), img_d.size(), s);
     if (req.empty()) req.push_back(make_int2(0, 0));
     ks.req.upload(req.data(), req.size(), s);
     ks.progress.alloc(std::max(nb, 1));
@@ -880,13 +1000,13 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
 }
 
 template <typename T>
-static void dispatch(const KSched &ks, int ld, const T *ea, const T *eb, const T *inv,
-                     const T *rhs, T *x, const double *shift, cudaStream_t s) {
+static void dispatch(const KSched &ks, int ld, const T *rhs, T *x, const double *shift,
+                     cudaStream_t s) {
     if (ks.rows == 0) return;
-#define KZ_CASE(L)                                                                   \
-    case L:                                                                          \
-        if (ks.shifted) launch_one<T, L, true>(ks, ea, eb, inv, rhs, x, shift, s);   \
-        else launch_one<T, L, false>(ks, ea, eb, inv, rhs, x, shift, s);             \
+#define KZ_CASE(L)                                                  \
+    case L:                                                         \
+        if (ks.shifted) launch_one<T, L, true>(ks, rhs, x, shift, s); \
+        else launch_one<T, L, false>(ks, rhs, x, shift, s);           \
         break;
     switch (ld) {
         KZ_CASE(4)
@@ -902,12 +1022,12 @@ static void dispatch(const KSched &ks, int ld, const T *ea, const T *eb, const T
 template <>
 void launch_kaczmarz<double>(const KSched &ks, int ld, const double *rhs, double *x,
                              const double *shift, cudaStream_t s) {
-    dispatch<double>(ks, ld, ks.ea_d.p, ks.eb_d.p, ks.inv_d.p, rhs, x, shift, s);
+    dispatch<double>(ks, ld, rhs, x, shift, s);
 }
 template <>
 void launch_kaczmarz<float>(const KSched &ks, int ld, const float *rhs, float *x,
                             const double *shift, cudaStream_t s) {
-    dispatch<float>(ks, ld, ks.ea_f.p, ks.eb_f.p, ks.inv_f.p, rhs, x, shift, s);
+    dispatch<float>(ks, ld, rhs, x, shift, s);
 }
 
 void kaczmarz_check(const KSched &ks, cudaStream_t s) {

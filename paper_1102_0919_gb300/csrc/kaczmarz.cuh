@@ -28,21 +28,27 @@ struct KCtl {                 // device control block of one schedule
     int pad;
 };
 
+// One staging chunk: up to 32 levels of one band whose rows, entries and
+// staged first values fit one shared-memory buffer.  Its schedule is a
+// self-contained image (chunk-local row and entry numbers), one per
+// coefficient precision, copied to shared memory in one bulk copy.
+struct KChunk {
+    int L0, nl;                // first (global) level, levels
+    int nr, ne, nx;            // rows, entries, staged first values
+    int bytes_f, bytes_d;      // image sizes (multiples of 16)
+    int pad;
+    long long off_f, off_d;    // image byte offsets (multiples of 16)
+};
+
 struct KSched {
     int rows = 0, cols = 0, nbands = 0, nlevels = 0, nchunks = 0;
     int max_slots = 0;
     int64_t nent = 0;
     bool shifted = false;      // rows of A - shift_j B (SPD kind)
     DBuf<int> band_chunk;      // nbands + 1: first staging chunk of each band
-    DBuf<int4> chunk;          // 2 per chunk: {L0, L1, R0, R1}, {E0, E1, X0, X1}
-    DBuf<int4> lvl;            // nlevels + 1: {first sched row, first req, publish, 0}
-    DBuf<int2> rinfo;          // scheduled row -> {original row, first entry} (+ sentinel)
-    DBuf<int2> ent;            // {column, 1 first | 2 last | 4 staged | slot << 3 | xs << 15}
-    DBuf<int> xsc;             // per chunk: columns whose first values are staged
-    DBuf<double> ea_d, eb_d;   // entry coefficients (a; b for the shifted form)
-    DBuf<float> ea_f, eb_f;
-    DBuf<double> inv_d;        // 1 / ||r_i||^2 per scheduled row (unshifted form)
-    DBuf<float> inv_f;
+    DBuf<KChunk> chunk;
+    DBuf<int4> lvl;            // per level: {first req, requirement count, publish, 0}
+    DBuf<unsigned char> img_f, img_d;  // chunk images, float / double coefficients
     DBuf<int2> req;            // {band, level that band must have completed}
     DBuf<unsigned long long> progress;  // nbands
     DBuf<KCtl> ctl;
