@@ -86,19 +86,36 @@ struct BandWork {
     explicit BandWork(int cols) : stamp(cols, -1), firstlv(cols), lastlv(cols), cnt(cols) {}
 };
 
-// Levels and window slots of rows [r0, r1).  Returns levels; *slots = peak
-// number of columns live (touched >= 2 times) at one level.
-int analyze_band(const Pattern &p, int r0, int r1, BandWork &w, int *slots) {
+// Dependency level of every row in natural order over the whole operator:
+// 1 + the level of the latest earlier row that shares a column.
+std::vector<int> global_levels(const Pattern &p) {
+    std::vector<int> last(p.cols, -1), lv(p.rows, 0);
+    for (int r = 0; r < p.rows; ++r) {
+        int l = 0;
+        for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) l = std::max(l, last[p.ci[e]] + 1);
+        lv[r] = l;
+        for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) last[p.ci[e]] = l;
+    }
+    return lv;
+}
+
+// Levels and window slots of rows [r0, r1).  A row's band level is the rank
+// of its global level among the global levels present in the band, so every
+// band steps through the same global wavefront and a band waits for an
+// earlier band only as long as a true dependency requires.  Returns levels;
+// *slots = peak number of columns live (touched >= 2 times) at one level.
+int analyze_band(const Pattern &p, const std::vector<int> &glv, int r0, int r1, BandWork &w,
+                 int *slots) {
     const int id = ++w.id;
     w.touched.clear();
     w.rowlv.resize(r1 - r0);
-    int nlev = 0;
+    // ranks of the band's global levels
+    std::vector<int> g(glv.begin() + r0, glv.begin() + r1);
+    std::sort(g.begin(), g.end());
+    g.erase(std::unique(g.begin(), g.end()), g.end());
+    const int nlev = (int)g.size();
     for (int r = r0; r < r1; ++r) {
-        int lv = 0;
-        for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
-            int c = p.ci[e];
-            if (w.stamp[c] == id) lv = std::max(lv, w.lastlv[c] + 1);
-        }
+        const int lv = (int)(std::lower_bound(g.begin(), g.end(), glv[r]) - g.begin());
         for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
             int c = p.ci[e];
             if (w.stamp[c] != id) {
@@ -111,7 +128,6 @@ int analyze_band(const Pattern &p, int r0, int r1, BandWork &w, int *slots) {
             w.cnt[c]++;
         }
         w.rowlv[r - r0] = lv;
-        nlev = std::max(nlev, lv + 1);
     }
     std::vector<int> diff(nlev + 2, 0);
     for (int c : w.touched)
@@ -766,13 +782,14 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     ks.cols = cols;
     ks.shifted = (B != nullptr);
     BandWork w(cols);
+    const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
     std::vector<int> bstart;
     int slots = 0;
     for (int r0 = 0; r0 < rows;) {
         int R = std::min(256, rows - r0), good = 0;
         for (;;) {
-            int nl = analyze_band(p, r0, r0 + R, w, &slots);
+            int nl = analyze_band(p, glv, r0, r0 + R, w, &slots);
             if (slots > SLOT_CAP) {
                 if (good) break;
                 R = std::max(1, R / 2);
@@ -805,7 +822,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     struct RowRec { int row, sub; };
     for (int b = 0; b < nb; ++b) {
         const int r0 = bstart[b], r1 = bstart[b + 1];
-        int nl = analyze_band(p, r0, r1, w, &slots);
+        int nl = analyze_band(p, glv, r0, r1, w, &slots);
         max_slots = std::max(max_slots, slots);
         // rows grouped by level (ascending row order inside a level)
         std::vector<int> lcount(nl + 1, 0);
