@@ -26,7 +26,7 @@ constexpr unsigned FULL = 0xffffffffu;
 //   lv  int4 per level {first row, rows, log2 lanes per row, has requirements}
 //   ri  int2 per row   {original row, first entry | entries << 16}
 //   inv T per row      1 / ||a_i||^2 (unshifted form)
-//   ent int2 per entry {column, 1 first | 2 last | 4 staged | slot << 3 | xs << 15}
+//   ent int2 per entry {column, 1 first | 2 last | 4 staged | (slot + 1) << 3 | xs << 15}
 //   a, b T per entry   coefficients (b: shifted form only)
 //   xc  int per staged first value: its column
 struct ImgLayout {
@@ -602,12 +602,12 @@ __global__ void __launch_bounds__(KZ_THREADS)
                                         const T bq = SHIFT ? sb[e] : T(0);
                                         T val[LD];
                                         const int fl = en.y;
-                                        if (!(fl & 1))
-                                            vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
-                                        else if (SG::VALS && (fl & 4))
-                                            vld<T, LD>(val, sxs + (fl >> 15) * LD);
-                                        else
+                                        // first touches not staged come from global memory, the rest
+                                        // from the staged values or the window (no divergence)
+                                        if ((fl & 1) && !(SG::VALS && (fl & 4)))
                                             vld_cg<T, LD>(val, x + (size_t)en.x * LD);
+                                        else
+                                            vld<T, LD>(val, (fl & 1) ? sxs + (fl >> 15) * LD : win + ((fl >> 3) & 0xfff) * LD);
 #pragma unroll
                                         for (int q = 0; q < LD; ++q) {
                                             const T coef = SHIFT ? a - sh[q] * bq : a;
@@ -664,22 +664,23 @@ __global__ void __launch_bounds__(KZ_THREADS)
                                         a = sa[e];
                                         bq = SHIFT ? sb[e] : T(0);
                                         const int fl = en.y;
-                                        if (!(fl & 1))
-                                            vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
-                                        else if (SG::VALS && (fl & 4))
-                                            vld<T, LD>(val, sxs + (fl >> 15) * LD);
-                                        else
+                                        // first touches not staged come from global memory, the rest
+                                        // from the staged values or the window (no divergence)
+                                        if ((fl & 1) && !(SG::VALS && (fl & 4)))
                                             vld_cg<T, LD>(val, x + (size_t)en.x * LD);
+                                        else
+                                            vld<T, LD>(val, (fl & 1) ? sxs + (fl >> 15) * LD : win + ((fl >> 3) & 0xfff) * LD);
                                     }
 #pragma unroll
                                     for (int q = 0; q < LD; ++q) {
                                         const T coef = SHIFT ? a - sh[q] * bq : a;
                                         val[q] = fma(d[q], coef, val[q]);
                                     }
-                                    if (en.y & 2)
-                                        vst_cg<T, LD>(x + (size_t)en.x * LD, val);
-                                    else
-                                        vst<T, LD>(win + ((en.y >> 3) & 0xfff) * LD, val);
+                                    // every lane stores to its slot (slot 0: scratch), so
+                                    // the warp does not diverge; last touches also go
+                                    // to global memory
+                                    vst<T, LD>(win + ((en.y >> 3) & 0xfff) * LD, val);
+                                    if (en.y & 2) vst_cg<T, LD>(x + (size_t)en.x * LD, val);
                                 }
                             }
                         }
@@ -709,7 +710,7 @@ template <typename T, int LD, bool SHIFT>
 void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaStream_t s) {
     using SG = Stage<T, LD, SHIFT>;
     auto kern = k_kaczmarz<T, LD, SHIFT>;
-    const int slots = std::max(ks.max_slots, 1);
+    const int slots = ks.max_slots + 1;  // slot 0: scratch
     const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + (size_t)KZ_NBUF * SG::stride;
     SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
                "kaczmarz: vector blocks must be 16-byte aligned");
@@ -956,7 +957,8 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                     for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
                         const int c = p.ci[e];
                         const int first = (w.firstlv[c] == lv), last = (w.lastlv[c] == lv);
-                        const int sl = (w.cnt[c] >= 2) ? slot[c] : 0;
+                        // window slot + 1; slot 0 is scratch for columns touched once
+                        const int sl = (w.cnt[c] >= 2) ? slot[c] + 1 : 0;
                         int staged = 0, xi = 0;
                         if (first && g_band[c] < 0) {
                             staged = 1;
