@@ -219,7 +219,7 @@ def run_gpu(args):
 
     results = {}
     log("launches after setup: %d" % samg.samg_launch_count())
-    for prec in ("fp64", "fp32"):
+    for prec in args.arms.split(","):
         s.set_precision(prec)
         warm = args.warmup if prec == "fp32" else max(1, args.warmup // 3)
         steps = args.steps if prec == "fp32" else max(1, args.steps // 3)
@@ -284,7 +284,8 @@ def run_gpu(args):
     if rank != 0:
         return 0
     peaks, how = _peaks()
-    mixed, f64 = results["fp32"], results["fp64"]
+    mixed = results["fp32"]
+    f64 = results.get("fp64", {"ms": float("nan"), "steps": 0, "iters": [(False, 0)], "resid": float("nan")})
     kz = mixed["prof"]["kaczmarz_sweep"]
     achieved = kz["bytes"] / (kz["ms"] * 1e-3) / 1e9 if kz["ms"] > 0 else 0.0
     cpu = oracle_sample(args.workload, mixed["iters"][-1][1]) if world == 1 and not args.no_cpu else None
@@ -340,6 +341,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-outer", type=int, default=300)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--arms", default="fp64,fp32",
+                    help="precision arms to time, in order (the JSON line needs both)")
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed mixed-precision solves with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")

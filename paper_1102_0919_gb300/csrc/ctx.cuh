@@ -101,6 +101,8 @@ struct Coarse {
     int M = 0, m1 = 0;
     DBuf<double> X, Y, lam, W, Wt, work;
     DBuf<int> status;
+    DBuf<double> qwarm;  // per column: the pseudo-inverse's subspace basis of the last call
+    bool warm = false;
 };
 
 }  // namespace samg

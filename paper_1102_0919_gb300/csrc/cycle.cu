@@ -161,9 +161,15 @@ void coarse_solve(samg_ctx &c) {
     Level &L = c.L.back();
     Work<T> &w = work<T>(L);
     Prof pr(c.prof, c.stream, 3, 2.0 * (double)c.co.M * c.co.M * 8.0);
+    const size_t nq = coarse_warm_size(c.co.M, c.nb);
+    if (c.co.qwarm.n != nq) {
+        c.co.qwarm.alloc(nq);
+        c.co.warm = false;
+    }
     launch_coarse_apply<T>(c.co.M, c.co.m1, c.ld, c.nb, c.co.lam.p, c.co.W.p, c.co.Wt.p,
                            c.sigma.p, w.k.p, c.spd() ? w.k.p : w.t.p, w.u.p,
-                           c.spd() ? w.u.p : w.v.p, c.stream);
+                           c.spd() ? w.u.p : w.v.p, c.co.qwarm.p, c.co.warm ? 1 : 0, c.stream);
+    c.co.warm = true;
 }
 
 template <typename T>
@@ -403,6 +409,7 @@ void prepare_level(samg_ctx &c, int l) {
 // Coarsest level: X = [[0, A], [A^t, 0]], Y = diag(B, C) (SPD: A, B) and its
 // generalized eigendecomposition X W = Y W Lam, W^t Y W = I.
 void prepare_coarsest(samg_ctx &c) {
+    c.co.warm = false;  // a new coarsest operator: start the pseudo-inverse afresh
     cudaStream_t s = c.stream;
     Level &Lc = c.L.back();
     Coarse &co = c.co;

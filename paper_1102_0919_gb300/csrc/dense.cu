@@ -568,7 +568,7 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
                                const double *__restrict__ W, const double *__restrict__ Wt,
                                const double *__restrict__ sigma, const T *__restrict__ k1,
                                const T *__restrict__ k2, T *__restrict__ o1, T *__restrict__ o2,
-                               int nb) {
+                               int nb, double *__restrict__ qwarm, int warm) {
     const int j = blockIdx.x;
     if (j >= nb) return;
     extern __shared__ double sm[];
@@ -642,7 +642,7 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
         d[k] = den != 0.0 ? 1.0 / den : 1e300;
     }
     __syncthreads();
-    if (t == 0) {  // start: the kb generalized eigenvectors nearest sigma_j
+    if (t == 0) {  // the kb generalized eigenvectors nearest sigma_j
         for (int b = 0; b < kb; ++b) {
             int best = -1;
             double bv = -1.0;
@@ -656,8 +656,13 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
         }
     }
     __syncthreads();
+    // warm start: the two leading Ritz vectors of this column's previous call
+    // (sigma_j moves little between outer iterations) replace the first two of
+    // the nearest generalized eigenvectors
+    const int nwarm = warm ? (kb < 2 ? kb : 2) : 0;
     for (int i = t; i < M; i += nt) {
-        for (int b = 0; b < kb; ++b) Q[b * M + i] = W[(size_t)i * M + s_sel[b]];
+        for (int b = 0; b < kb; ++b)
+            Q[b * M + i] = b < nwarm ? qwarm[((size_t)j * 2 + b) * M + i] : W[(size_t)i * M + s_sel[b - nwarm]];
         r[i] = (i < m1) ? (double)k1[(size_t)i * ld + j] : (double)k2[(size_t)(i - m1) * ld + j];
     }
     __syncthreads();
@@ -693,12 +698,24 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
                 sH[b * kb + a] = v;
             }
         small_sym_eig(sH, sV, kb);
-        int best = 0;
-        for (int a = 1; a < kb; ++a)
-            if (fabs(sH[a * kb + a]) > fabs(sH[best * kb + best])) best = a;
-        s_sel[0] = best;
+        // Ritz values by decreasing |1/mu|: s_sel[0] picks w, s_sel[1] the next
+        for (int a = 0; a < kb; ++a) s_sel[a] = a;
+        for (int a = 0; a < kb; ++a)
+            for (int b = a + 1; b < kb; ++b)
+                if (fabs(sH[s_sel[b] * kb + s_sel[b]]) > fabs(sH[s_sel[a] * kb + s_sel[a]])) {
+                    const int tmp = s_sel[a];
+                    s_sel[a] = s_sel[b];
+                    s_sel[b] = tmp;
+                }
     }
     __syncthreads();
+    // keep the two leading Ritz vectors as the next call's starting basis
+    for (int i = t; i < M; i += nt)
+        for (int a = 0; a < (kb < 2 ? kb : 2); ++a) {
+            double v = 0.0;
+            for (int b = 0; b < kb; ++b) v += Q[b * M + i] * sV[b * kb + s_sel[a]];
+            qwarm[((size_t)j * 2 + a) * M + i] = v;
+        }
     const int bsel = s_sel[0];
     double *w = y;  // reuse: w = Q sV[:, bsel]
     for (int i = t; i < M; i += nt) {
@@ -726,20 +743,23 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
 template <typename T>
 void launch_coarse_apply(int M, int m1, int ld, int nb, const double *lam, const double *W,
                          const double *Wt, const double *sigma, const T *k1, const T *k2, T *o1,
-                         T *o2, cudaStream_t s) {
+                         T *o2, double *qwarm, int warm, cudaStream_t s) {
     size_t smem = (size_t)(4 + 3 * KB) * M * sizeof(double);
     auto kern = k_coarse_apply<T>;
     if (smem > 48 * 1024)
         SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SAMG_COUNT_LAUNCH();
-    kern<<<nb, 256, smem, s>>>(M, m1, ld, lam, W, Wt, sigma, k1, k2, o1, o2, nb);
+    kern<<<nb, 256, smem, s>>>(M, m1, ld, lam, W, Wt, sigma, k1, k2, o1, o2, nb, qwarm, warm);
     SAMG_CUDA(cudaGetLastError());
 }
+size_t coarse_warm_size(int M, int nb) { return (size_t)nb * 2 * M; }
 template void launch_coarse_apply<float>(int, int, int, int, const double *, const double *,
                                          const double *, const double *, const float *,
-                                         const float *, float *, float *, cudaStream_t);
+                                         const float *, float *, float *, double *, int,
+                                         cudaStream_t);
 template void launch_coarse_apply<double>(int, int, int, int, const double *, const double *,
                                           const double *, const double *, const double *,
-                                          const double *, double *, double *, cudaStream_t);
+                                          const double *, double *, double *, double *, int,
+                                          cudaStream_t);
 
 }  // namespace samg

@@ -30,10 +30,12 @@ void launch_coarse_geneig(int M, const double *X, const double *Y, double *work,
                           double *W, double *Wt, int *status, cudaStream_t s);
 
 // Pseudo-inverse solve of (X - sigma_j Y) without its smallest singular value,
-// one CTA per column (Sec. 4.2).
+// one CTA per column (Sec. 4.2).  qwarm (coarse_warm_size doubles) keeps each
+// column's subspace-iteration basis between calls; warm = 0 starts afresh.
 template <typename T>
 void launch_coarse_apply(int M, int m1, int ld, int nb, const double *lam, const double *W,
                          const double *Wt, const double *sigma, const T *k1, const T *k2, T *o1,
-                         T *o2, cudaStream_t s);
+                         T *o2, double *qwarm, int warm, cudaStream_t s);
+size_t coarse_warm_size(int M, int nb);
 
 }  // namespace samg
