@@ -367,7 +367,7 @@ struct Stage {
 // when it crosses a level that a later band waits for, and at the band's
 // end.  The compute warps touch only shared memory for synchronization.
 template <typename T, int LD, bool SHIFT>
-__global__ void __launch_bounds__(KZ_THREADS)
+__global__ void __launch_bounds__(KZ_THREADS, 1)
     k_kaczmarz(KView kv, const T *__restrict__ rhs, T *x, const double *__restrict__ shift,
                int window_slots) {
     using SG = Stage<T, LD, SHIFT>;
@@ -570,9 +570,12 @@ __global__ void __launch_bounds__(KZ_THREADS)
                             // G = 2^lgG lanes per row (the smallest power of two
                             // not below the level's longest row, at most 32);
                             // lane lg takes entries lg, lg + G, ... for all LD
-                            // columns.  A warp holding no row of the level goes
+                            // columns.  When rows exceed 32 entries (lr.z = 6)
+                            // a lane's second entry is loaded together with its
+                            // first.  A warp holding no row of the level goes
                             // straight to the barrier.
-                            const int lgG = lr.z;
+                            const int lgG = min(lr.z, 5);
+                            const bool two = lr.z > 5;
                             const int G = 1 << lgG;
                             const int nrow = lr.y;
                             const int lane = threadIdx.x & 31;
@@ -587,39 +590,58 @@ __global__ void __launch_bounds__(KZ_THREADS)
                                 for (int q = 0; q < LD; ++q) acc[q] = T(0);
 #pragma unroll
                                 for (int q = 0; q < (SHIFT ? LD : 1); ++q) nrm[q] = T(0);
-                                // the lane's first entry stays in registers for the update
-                                int2 fen = make_int2(0, 0);
-                                T fa = T(0), fb = T(0), fv[LD];
+                                // the lane's first (and second) entry stay in registers
+                                // for the update
+                                int2 fen = make_int2(0, 0), sen = make_int2(0, 0);
+                                T fa = T(0), fb = T(0), fv[LD], sa2 = T(0), sb2 = T(0), sv[LD];
+                                bool own = false, hb = false;
                                 int2 rk = make_int2(0, 0);
                                 int e0 = 0, e1 = 0;
+                                auto load_val = [&](T (&val)[LD], int2 en) {
+                                    const int fl = en.y;
+                                    // first touches not staged come from global memory, the
+                                    // rest from the staged values or the window
+                                    if ((fl & 1) && !(SG::VALS && (fl & 4)))
+                                        vld_cg<T, LD>(val, x + (size_t)en.x * LD);
+                                    else
+                                        vld<T, LD>(val, (fl & 1) ? sxs + (fl >> 15) * LD : win + ((fl >> 3) & 0xfff) * LD);
+                                };
+                                auto accumulate = [&](T a, T bq, const T (&val)[LD]) {
+#pragma unroll
+                                    for (int q = 0; q < LD; ++q) {
+                                        const T coef = SHIFT ? a - sh[q] * bq : a;
+                                        acc[q] = fma(coef, val[q], acc[q]);
+                                        if (SHIFT) nrm[q] = fma(coef, coef, nrm[q]);
+                                    }
+                                };
                                 if (act) {
                                     rk = ri[k];
                                     e0 = rk.y & 0xffff;
                                     e1 = e0 + (rk.y >> 16);
-                                    for (int e = e0 + lg; e < e1; e += G) {
-                                        const int2 en = se[e];
-                                        const T a = sa[e];
-                                        const T bq = SHIFT ? sb[e] : T(0);
-                                        T val[LD];
-                                        const int fl = en.y;
-                                        // first touches not staged come from global memory, the rest
-                                        // from the staged values or the window (no divergence)
-                                        if ((fl & 1) && !(SG::VALS && (fl & 4)))
-                                            vld_cg<T, LD>(val, x + (size_t)en.x * LD);
-                                        else
-                                            vld<T, LD>(val, (fl & 1) ? sxs + (fl >> 15) * LD : win + ((fl >> 3) & 0xfff) * LD);
-#pragma unroll
-                                        for (int q = 0; q < LD; ++q) {
-                                            const T coef = SHIFT ? a - sh[q] * bq : a;
-                                            acc[q] = fma(coef, val[q], acc[q]);
-                                            if (SHIFT) nrm[q] = fma(coef, coef, nrm[q]);
+                                    const int ea = e0 + lg;
+                                    own = ea < e1;
+                                    if (own) {
+                                        // the second entry's loads are issued with the first's;
+                                        // a lane without one reloads its first (weight 0)
+                                        hb = two && ea + G < e1;
+                                        const int eb = hb ? ea + G : ea;
+                                        fen = se[ea];
+                                        fa = sa[ea];
+                                        fb = SHIFT ? sb[ea] : T(0);
+                                        if (two) {
+                                            sen = se[eb];
+                                            sa2 = hb ? sa[eb] : T(0);
+                                            sb2 = (SHIFT && hb) ? sb[eb] : T(0);
                                         }
-                                        if (e == e0 + lg) {
-                                            fen = en;
-                                            fa = a;
-                                            fb = bq;
-#pragma unroll
-                                            for (int q = 0; q < LD; ++q) fv[q] = val[q];
+                                        load_val(fv, fen);
+                                        if (two) load_val(sv, sen);
+                                        accumulate(fa, fb, fv);
+                                        if (two) accumulate(sa2, sb2, sv);
+                                        for (int e = ea + (hb ? 2 : 1) * G; e < e1; e += G) {
+                                            T val[LD];
+                                            const int2 en = se[e];
+                                            load_val(val, en);
+                                            accumulate(sa[e], SHIFT ? sb[e] : T(0), val);
                                         }
                                     }
                                 }
@@ -652,35 +674,27 @@ __global__ void __launch_bounds__(KZ_THREADS)
                                         }
                                     }
                                 }
-                                // x_q += d_q a_i on the row's entries
-                                for (int e = e0 + lg; e < e1; e += G) {
-                                    int2 en = fen;
-                                    T a = fa, bq = fb, val[LD];
-                                    if (e == e0 + lg) {
-#pragma unroll
-                                        for (int q = 0; q < LD; ++q) val[q] = fv[q];
-                                    } else {
-                                        en = se[e];
-                                        a = sa[e];
-                                        bq = SHIFT ? sb[e] : T(0);
-                                        const int fl = en.y;
-                                        // first touches not staged come from global memory, the rest
-                                        // from the staged values or the window (no divergence)
-                                        if ((fl & 1) && !(SG::VALS && (fl & 4)))
-                                            vld_cg<T, LD>(val, x + (size_t)en.x * LD);
-                                        else
-                                            vld<T, LD>(val, (fl & 1) ? sxs + (fl >> 15) * LD : win + ((fl >> 3) & 0xfff) * LD);
-                                    }
+                                // x_q += d_q a_i on the row's entries; every lane stores
+                                // to its slot (slot 0: scratch), so the warp does not
+                                // diverge; last touches also go to global memory
+                                auto update = [&](int2 en, T a, T bq, T (&val)[LD]) {
 #pragma unroll
                                     for (int q = 0; q < LD; ++q) {
                                         const T coef = SHIFT ? a - sh[q] * bq : a;
                                         val[q] = fma(d[q], coef, val[q]);
                                     }
-                                    // every lane stores to its slot (slot 0: scratch), so
-                                    // the warp does not diverge; last touches also go
-                                    // to global memory
                                     vst<T, LD>(win + ((en.y >> 3) & 0xfff) * LD, val);
                                     if (en.y & 2) vst_cg<T, LD>(x + (size_t)en.x * LD, val);
+                                };
+                                if (own) {
+                                    update(fen, fa, fb, fv);
+                                    if (hb) update(sen, sa2, sb2, sv);
+                                    for (int e = e0 + lg + (hb ? 2 : 1) * G; e < e1; e += G) {
+                                        T val[LD];
+                                        const int2 en = se[e];
+                                        load_val(val, en);
+                                        update(en, sa[e], SHIFT ? sb[e] : T(0), val);
+                                    }
                                 }
                             }
                         }
@@ -945,9 +959,10 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
             lrec.clear(); rrec.clear(); erec.clear(); rinv.clear(); ca.clear(); cbv.clear(); xc.clear();
             for (int qq = q0; qq < q1; ++qq) {
                 // lanes per row: a power of two >= the longest row of the level
-                // (at most 32; longer rows give a lane several entries)
+                // (at most 32; 6 marks rows of more than 32 entries, whose lanes
+                // take two or more entries)
                 int lg = 0;
-                while (lg < 5 && (1 << lg) < sub_maxe[qq]) ++lg;
+                while (lg < 6 && (1 << lg) < sub_maxe[qq]) ++lg;
                 const int row0 = (int)rrec.size();
                 for (; ri < rr.size() && rr[ri].sub == qq; ++ri) {
                     const int r = rr[ri].row;
