@@ -570,12 +570,18 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                             // G = 2^lgG lanes per row (the smallest power of two
                             // not below the level's longest row, at most 32);
                             // lane lg takes entries lg, lg + G, ... for all LD
-                            // columns.  When rows exceed 32 entries (lr.z = 6)
-                            // a lane's second entry is loaded together with its
-                            // first.  A warp holding no row of the level goes
-                            // straight to the barrier.
-                            const int lgG = min(lr.z, 5);
-                            const bool two = lr.z > 5;
+                            // columns.  Rows of more than 16 entries (float32) or
+                            // 32 entries (float64) take G = 2^(lr.z - 1) lanes, each
+                            // loading its second entry together with its first,
+                            // which keeps the row sums one shuffle step shorter.  A
+                            // warp holding no row of the level goes straight to
+                            // the barrier.
+                            // (float64 keeps G = 32 for rows of 17-32 entries: the
+                            // setup phase runs in float64, and its hierarchy
+                            // should not depend on how float32 sweeps are tuned)
+                            constexpr int TWO_FROM = sizeof(T) == 4 ? 5 : 6;
+                            const bool two = lr.z >= TWO_FROM;
+                            const int lgG = two ? lr.z - 1 : lr.z;
                             const int G = 1 << lgG;
                             const int nrow = lr.y;
                             const int lane = threadIdx.x & 31;
