@@ -325,6 +325,10 @@ def run_gpu(args):
                      "avg_launch_us": 1e3 * kz["ms"] / max(kz["launches"], 1),
                      "alg_bytes_per_launch": kz["bytes"] / max(kz["launches"], 1)},
         "kernel_time_ms_per_solve": {k: v["ms"] / mixed["steps"] for k, v in mixed["prof"].items()},
+        # the V-cycle's sparse products (residual, restriction, interpolation,
+        # right-hand sides): algorithmic GB/s over their CUDA-event time
+        "spmm_gbs": (mixed["prof"]["block_spmm"]["bytes"] / (mixed["prof"]["block_spmm"]["ms"] * 1e-3) / 1e9
+                     if mixed["prof"]["block_spmm"]["ms"] > 0 else None),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
