@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -60,7 +61,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples (SAMG_CLOCKS_CSV, else a temporary file)
+        self.path = os.environ.get("SAMG_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), "samg_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
