@@ -239,6 +239,65 @@ def test_ritz_exact_on_exact_subspaces():
     assert np.allclose(sig, np.sort(s)[::-1][:4], rtol=1e-12)
 
 
+# ---------------------------------------------------------------- relaxation fixed points
+
+def _exact_pairs(A, idx):
+    # dense LAPACK SVD (called): exact singular triplets of a tiny operator
+    U, s, Vt = np.linalg.svd(A.toarray(), full_matrices=False)
+    return s[idx], U[:, idx].copy(), Vt[idx].T.copy()
+
+
+def test_rayleigh_quotient_of_exact_triplets():
+    # Eq. Rayleigh on exact pairs returns sigma_j; flipping v flips its sign
+    A = W.gradient(7).to_scipy()
+    m, n = A.shape
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    s, U, V = _exact_pairs(A, np.arange(4))
+    assert np.allclose(oracle.rayleigh(L0, False, 3.0 * U, 0.5 * V), s, rtol=1e-12)
+    assert np.allclose(oracle.rayleigh(L0, False, U, -V), -s, rtol=1e-12)
+
+
+def test_minimal_block_gauss_seidel_fixes_exact_triplets():
+    # A v = s u and A^t u = s v make every Kaczmarz row residual of
+    # A v - s u = 0 and A^t u - s v = 0 vanish: the relaxation (Sec. 5.3,
+    # kappa = tau = 0) leaves exact triplets unchanged, and moves a perturbed one
+    A = W.gradient(7).to_scipy()
+    m, n = A.shape
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    s, U, V = _exact_pairs(A, np.argsort(np.linalg.svd(A.toarray(), compute_uv=False))[:3])
+    U0, V0 = U.copy(), V.copy()
+    oracle.relax_boot(L0, False, "minimal", s, U, V, np.zeros_like(U), np.zeros_like(V), 0.7)
+    assert np.abs(U - U0).max() < 1e-12 and np.abs(V - V0).max() < 1e-12
+    oracle.relax_boot(L0, False, "minimal", -s, U, V, np.zeros_like(U), np.zeros_like(V), 0.7)
+    assert np.abs(V - V0).max() > 1e-3  # the sign of the shift matters
+
+
+def test_dominant_jacobi_fixes_exact_triplets():
+    # u <- u - w D^-1 (u - (A v - kappa) / s) vanishes for A v = s u (Sec. 3.5)
+    A = W.gradient(7).to_scipy()
+    m, n = A.shape
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    s, U, V = _exact_pairs(A, np.arange(3))
+    U0, V0 = U.copy(), V.copy()
+    oracle.relax_boot(L0, False, "dominant", s, U, V, np.zeros_like(U), np.zeros_like(V), 0.7)
+    assert np.abs(U - U0).max() < 1e-12 and np.abs(V - V0).max() < 1e-12
+    oracle.relax_boot(L0, False, "dominant", 1.1 * s, U, V, np.zeros_like(U), np.zeros_like(V), 0.7)
+    assert np.abs(U - U0).max() > 1e-3
+
+
+def test_spd_shifted_kaczmarz_fixes_exact_eigenpairs():
+    # rows of A - lam B with B = I: (A - lam I) x = 0 for an exact eigenpair
+    A = W.laplacian5(6).to_scipy()
+    n = A.shape[0]
+    L0 = oracle.Level(A, sp.identity(n, format="csr"), None)
+    lam, X = np.linalg.eigh(A.toarray())
+    lam, X = lam[:3], X[:, :3].copy()
+    X0 = X.copy()
+    oracle.relax_boot(L0, True, "minimal", lam, X, None, np.zeros_like(X), None, 0.7)
+    assert np.abs(X - X0).max() < 1e-12
+    assert np.allclose(lam, laplacian5_eigs(6)[:3], rtol=1e-12)
+
+
 # ---------------------------------------------------------------- additive cycle
 
 def test_additive_equals_multiplicative_when_x_in_range_of_P():
