@@ -194,6 +194,15 @@ samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V
 /* Ritz step (Sec. 4.3) on host buffers: in/out sigma, U, V; resid = rho_j. */
 samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double *resid);
 
+/* Test hook for the bounded device waits (the paper has no counterpart):
+ * from now on band `band` of the Kaczmarz schedule of level `level`
+ * (which: 0 rows of A, 1 rows of A^t) never publishes its progress, so a
+ * later band that needs it gives up after its 2 s bounded wait; the sweep
+ * then returns SAMG_E_TIMEOUT and the context is poisoned (only
+ * samg_destroy is valid).  band = -1 restores publishing.  Returns
+ * SAMG_E_INVALID for a level, operator or band out of range. */
+samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band);
+
 /* ------------------------------------------- device-level building blocks --
  * G = X^t Y for two row-major device blocks X, Y (rows x ld, first nb
  * columns used), G row-major nb x nb on the device; float64.  Uses a

@@ -81,6 +81,7 @@ samg_coarsest_solve = _sig("samg_coarsest_solve", _I, _CTX, _P, _P, _P, _P, _P)
 samg_vcycle = _sig("samg_vcycle", _I, _CTX, _P, _P, _P)
 samg_ritz = _sig("samg_ritz", _I, _CTX, _P, _P, _P, _P)
 samg_block_gram = _sig("samg_block_gram", _I, _P, _P, ctypes.c_int64, _I, _I, _P, _P)
+samg_debug_mute_band = _sig("samg_debug_mute_band", _I, _CTX, _I, _I, _I)
 samg_block_gram_noalloc = _sig("samg_block_gram_noalloc", _I, _P, _P, ctypes.c_int64, _I, _I, _P,
                                _P)
 samg_set_triplets_device = _sig("samg_set_triplets_device", _I, _CTX, _P, _P, _P)
@@ -94,7 +95,7 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
-            "samg_profile", "samg_profile_read", "samg_launch_count"]
+            "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band"]
 
 
 def _arr(x, dtype):
@@ -274,6 +275,11 @@ class Solver:
                                           ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
             out[name] = dict(launches=n.value, ms=ms.value, bytes=b.value)
         return out
+
+    def debug_mute_band(self, level, which, band):
+        """Test hook: band `band` of level `level`'s sweep over the rows of A
+        (which 0) or A^t (1) stops publishing its progress (-1 restores)."""
+        self._check(samg_debug_mute_band(self._ctx, level, which, band))
 
     # ---------------------------------------------------------- single steps
     def relax(self, level, sigma, U, V, K=None, T=None, count=1):

@@ -570,6 +570,16 @@ samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double
     });
 }
 
+samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(level >= 0 && level < (int)ctx->L.size() && (which == 0 || which == 1),
+                   SAMG_E_INVALID, "debug_mute_band: bad level or operator");
+        Level &L = ctx->L[level];
+        kaczmarz_mute_band(which == 0 ? L.kA : L.kAt, band, ctx->stream);
+    });
+}
+
 samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
                             double *G, void *cuda_stream) {
     try {

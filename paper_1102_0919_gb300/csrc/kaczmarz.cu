@@ -415,9 +415,14 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
             const int lane = threadIdx.x & 31;
             int sn = cb, vn = cb, ready = 0, published = 0;
             bool aborted = false;
+            const bool mute = *((volatile int *)&kv.ctl->mute) == b;
             unsigned long long t0 = gtimer();  // re-armed whenever something advances
             for (;;) {
-                if (*((volatile int *)&s_abort) || *((volatile int *)kv.err)) aborted = true;
+                if (*((volatile int *)&s_abort) || *((volatile int *)kv.err)) {
+                    // another CTA gave up: release this CTA's compute warps too
+                    if (lane == 0) *((volatile int *)&s_abort) = 1;
+                    aborted = true;
+                }
                 if (!aborted && gtimer() - t0 > WAIT_NS) {
                     if (lane == 0) {
                         atomicExch(kv.err, 1);
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                 if (done > published) {
                     bool f = false;
                     for (int l = published + lane; l < done; l += 32) f = f || kv.lvl[Lband + l].z != 0;
-                    if ((__any_sync(FULL, f) || done == nlev) && lane == 0)
+                    if ((__any_sync(FULL, f) || done == nlev) && lane == 0 && !mute)
                         st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
                     published = done;
                     adv = true;
@@ -1035,6 +1040,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     KCtl c0;
     std::memset(&c0, 0, sizeof(c0));
     c0.epoch = 1;
+    c0.mute = -1;
     ks.ctl.upload(&c0, 1, s);
     SAMG_CUDA(cudaStreamSynchronize(s));
 }
@@ -1068,6 +1074,13 @@ template <>
 void launch_kaczmarz<float>(const KSched &ks, int ld, const float *rhs, float *x,
                             const double *shift, cudaStream_t s) {
     dispatch<float>(ks, ld, rhs, x, shift, s);
+}
+
+void kaczmarz_mute_band(KSched &ks, int band, cudaStream_t s) {
+    if (ks.rows == 0) return;
+    SAMG_CHECK(band >= -1 && band < ks.nbands, SAMG_E_INVALID, "kaczmarz: band out of range");
+    SAMG_CUDA(cudaMemcpyAsync(&ks.ctl.p->mute, &band, sizeof(int), cudaMemcpyHostToDevice, s));
+    SAMG_CUDA(cudaStreamSynchronize(s));
 }
 
 void kaczmarz_check(const KSched &ks, cudaStream_t s) {

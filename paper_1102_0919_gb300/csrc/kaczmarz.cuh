@@ -25,7 +25,8 @@ struct KCtl {                 // device control block of one schedule
     unsigned int ticket;
     unsigned int done;
     int err;                   // 1 = a wait timed out
-    int pad;
+    int mute;                  // band that never publishes its progress (testing the
+                               // bounded waits); -1 = none
 };
 
 // One staging chunk: up to 32 levels of one band whose rows, entries and
@@ -66,6 +67,10 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s);
 template <typename T>
 void launch_kaczmarz(const KSched &ks, int ld, const T *rhs, T *x, const double *shift,
                      cudaStream_t s);
+
+// Test hook: the given band (-1: none) never publishes its progress, so later
+// bands that need it give up after their bounded wait.
+void kaczmarz_mute_band(KSched &ks, int band, cudaStream_t s);
 
 // Reads the error flag (synchronizes the stream); throws SAMG_E_TIMEOUT if set.
 void kaczmarz_check(const KSched &ks, cudaStream_t s);
