@@ -341,6 +341,67 @@ def run_gpu(args):
     return 0
 
 
+def run_sweep_roofline(args):
+    """Roofline of the relaxation at the workload's full size: block
+    Gauss-Seidel relaxations (Kaczmarz sweeps over the rows of A and A^t,
+    with their right-hand sides) on level 0 of a two-level aggregation
+    hierarchy (no setup phase).  Prints one JSON line with the algorithmic
+    GB/s of the sweep and sparse-product kernels per precision (CUDA events
+    on the library's stream)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+
+    import paper_1102_0919_gb300 as samg
+
+    torch.cuda.set_device(0)
+    wl, prm = workload(args.workload)
+    A = wl.build().to_scipy()
+    m, n = A.shape
+    nb = wl.nb
+    rng = np.random.default_rng(11)
+    P = sp.csr_matrix((np.ones(m), (np.arange(m), np.minimum(np.arange(m) * 100 // m, 99))),
+                      shape=(m, 100))
+    Q = sp.csr_matrix((np.ones(n), (np.arange(n), np.minimum(np.arange(n) * 90 // n, 89))),
+                      shape=(n, 90))
+    sig = np.linspace(4.0, 12.0, nb)
+    U = rng.standard_normal((m, nb))
+    V = rng.standard_normal((n, nb))
+    K = rng.standard_normal((m, nb))
+    T = rng.standard_normal((n, nb))
+    g = samg.Solver.from_hierarchy(A, [P], [Q], nb, sig, U, V, wl.target, wl.kind, prec="fp64",
+                                   mu_b=1)
+    peaks, how = _peaks()
+    line = {"mode": "sweep_roofline", "workload": wl.name, "m": m, "n": n, "nnz": int(A.nnz),
+            "n_b": nb, "steps": args.steps, "warmup": args.warmup, "peak_gbs": peaks["hbm_gbs"],
+            "peak_source": how}
+    for prec in args.arms.split(","):
+        g.set_precision(prec)
+        for _ in range(args.warmup):
+            g.relax(0, sig, U, V, K, T, count=1)
+        g.profile(True)
+        g.profile_read(reset=True)
+        if args.ncu_range and prec == "fp32":
+            torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            g.relax(0, sig, U, V, K, T, count=1)
+        if args.ncu_range and prec == "fp32":
+            torch.cuda.profiler.stop()
+        pr = g.profile_read()
+        g.profile(False)
+        kz, spm = pr["kaczmarz_sweep"], pr["block_spmm"]
+        line[prec] = {
+            "kaczmarz_gbs": kz["bytes"] / (kz["ms"] * 1e-3) / 1e9,
+            "kaczmarz_us_per_launch": 1e3 * kz["ms"] / max(kz["launches"], 1),
+            "kaczmarz_bytes_per_launch": kz["bytes"] / max(kz["launches"], 1),
+            "kaczmarz_frac": kz["bytes"] / (kz["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "spmm_gbs": spm["bytes"] / (spm["ms"] * 1e-3) / 1e9 if spm["ms"] > 0 else None,
+        }
+    g.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,7 +417,12 @@ def main():
     ap.add_argument("--ncu-range", action="store_true",
                     help="bracket the timed mixed-precision solves with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
+    ap.add_argument("--sweep-roofline", action="store_true",
+                    help="time only level-0 relaxations at full size on a two-level "
+                         "aggregation hierarchy and print their algorithmic GB/s")
     args = ap.parse_args()
+    if args.sweep_roofline:
+        return run_sweep_roofline(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
