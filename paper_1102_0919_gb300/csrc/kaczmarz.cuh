@@ -3,15 +3,20 @@
 // A sweep projects x onto the hyperplanes r_i . x = b_i for i = 0 .. rows-1
 // in natural row order.  Two rows commute exactly when they share no column,
 // so the sweep is scheduled without changing its result:
-//  * rows are cut into contiguous bands; inside a band every row gets a level
-//    = 1 + the level of the latest earlier in-band row that shares a column,
-//    and the rows of one level (disjoint columns) are updated in parallel;
+//  * every row gets a global level = 1 + the level of the latest earlier row
+//    that shares a column; rows are cut into contiguous bands, a row's band
+//    level is the rank of its global level inside its band, and the rows of
+//    one level (disjoint columns) are updated in parallel;
 //  * a band that touches a column last written by an earlier band waits until
 //    that band has published the level of its last touch (bounded spin on a
 //    progress word; a timeout sets an error flag and the kernel returns);
 //  * values of columns touched more than once inside a band live in a
 //    shared-memory window slot between their first and last touch; the first
-//    touch loads from global memory, the last touch stores to it.
+//    touch loads from global memory (staged ahead by the producer warp when no
+//    earlier band writes the column), the last touch stores to it;
+//  * a band's levels are packed into chunks whose schedules are copied to
+//    shared memory by bulk copies a producer warp issues ahead of the compute
+//    warps.
 // Bands are handed out in increasing order by an atomic ticket, so a band only
 // ever waits for bands that are already running or finished.
 #pragma once
