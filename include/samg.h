@@ -195,8 +195,10 @@ samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V
 samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double *resid);
 
 /* Test hook for the bounded device waits (the paper has no counterpart):
- * from now on band `band` of the Kaczmarz schedule of level `level`
- * (which: 0 rows of A, 1 rows of A^t) never publishes its progress, so a
+ * from now on band `band` of the Kaczmarz schedules of level `level`
+ * (which: 0 the single sweep over the rows of A, 1 over the rows of A^t,
+ * 2 every fused relaxation program built so far) never publishes its
+ * progress, so a
  * later band that needs it gives up after its 2 s bounded wait; the sweep
  * then returns SAMG_E_TIMEOUT and the context is poisoned (only
  * samg_destroy is valid).  band = -1 restores publishing.  Returns

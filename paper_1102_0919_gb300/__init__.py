@@ -278,7 +278,8 @@ class Solver:
 
     def debug_mute_band(self, level, which, band):
         """Test hook: band `band` of level `level`'s sweep over the rows of A
-        (which 0) or A^t (1) stops publishing its progress (-1 restores)."""
+        (which 0), of A^t (1), or of every fused relaxation program built so
+        far (2) stops publishing its progress (-1 restores)."""
         self._check(samg_debug_mute_band(self._ctx, level, which, band))
 
     # ---------------------------------------------------------- single steps

@@ -116,7 +116,7 @@ void step_relax(samg_ctx &c, int l, int count, double *U, double *V, const doubl
         put_level<T>(c, V, L.n, w.v);
         put_level<T>(c, Tt, L.n, w.t);
     }
-    for (int k = 0; k < count; ++k) relax<T>(c, l);
+    relax_phase<T>(c, l, count);
     get_level<T>(c, w.u, urows(c, l), U);
     if (!c.spd()) get_level<T>(c, w.v, L.n, V);
 }
@@ -573,10 +573,15 @@ samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double
 samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {
-        SAMG_CHECK(level >= 0 && level < (int)ctx->L.size() && (which == 0 || which == 1),
+        SAMG_CHECK(level >= 0 && level < (int)ctx->L.size() && which >= 0 && which <= 2,
                    SAMG_E_INVALID, "debug_mute_band: bad level or operator");
         Level &L = ctx->L[level];
-        kaczmarz_mute_band(which == 0 ? L.kA : L.kAt, band, ctx->stream);
+        if (which < 2) {
+            kaczmarz_mute_band(which == 0 ? L.kA : L.kAt, band, ctx->stream);
+        } else {
+            for (KSched &k : L.kF)
+                if (k.rows) kaczmarz_mute_band(k, band, ctx->stream);
+        }
     });
 }
 

@@ -19,6 +19,7 @@ struct Work {          // V-cycle vectors of one level in one precision (ld colu
     DBuf<T> k, t;      // right-hand sides kappa, tau
     DBuf<T> r, s;      // residuals / Kaczmarz right-hand sides
     DBuf<T> tu, tv;    // Jacobi double buffers
+    DBuf<T> z, kt;     // fused relaxations: unknown [v; u] and right-hand side [kappa; tau]
 };
 
 struct Level {
@@ -26,6 +27,7 @@ struct Level {
     DCsr A, At, B, C;           // B, C empty on the finest level (identity)
     DCsr P, Pt, Q, Qt;          // empty on the coarsest level
     KSched kA, kAt;             // Kaczmarz schedules (minimal target)
+    std::vector<KSched> kF;     // fused programs of `count` relaxations, by count
     DBuf<double> dBd, dCd;      // diagonals of B, C (dominant target)
     DBuf<float> dBf, dCf;
     Work<float> wf;
@@ -146,6 +148,7 @@ void get_block(samg_ctx &c, const DBuf<double> &d, int rows, double *h);
 // V-cycle pieces in precision T on level l (vectors in L[l].w*)
 template <typename T> Work<T> &work(Level &L);
 template <typename T> void relax(samg_ctx &c, int l);
+template <typename T> void relax_phase(samg_ctx &c, int l, int count);
 template <typename T> void residual_restrict(samg_ctx &c, int l);
 template <typename T> void interpolate(samg_ctx &c, int l);
 template <typename T> void coarse_solve(samg_ctx &c);

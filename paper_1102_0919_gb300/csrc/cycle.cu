@@ -95,6 +95,61 @@ void relax(samg_ctx &c, int l) {
     std::swap(w.v, w.tv);
 }
 
+// count relaxations of the minimal kind as one fused sweep program (the
+// schedule is built on first use for each count); other kinds relax one at a
+// time.  The result is that of count calls of relax() up to the rounding
+// order inside each row.
+template <typename T>
+void relax_phase(samg_ctx &c, int l, int count) {
+    if (!c.minimal() || count <= 0) {
+        for (int k = 0; k < count; ++k) relax<T>(c, l);
+        return;
+    }
+    c.prof.cur_level = l;
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    cudaStream_t s = c.stream;
+    const int ld = c.ld;
+    if ((int)L.kF.size() <= count) L.kF.resize(count + 1);
+    KSched &ks = L.kF[count];
+    if (ks.rows == 0) {
+        HCsr hA, hB;
+        download_csr(L.A, hA, s);
+        if (L.B.empty()) csr_identity(c.spd() ? L.n : L.m, hB);
+        else download_csr(L.B, hB, s);
+        if (c.spd()) {
+            build_kschedule_stacked(hA, hB, count, ks, s);
+        } else {
+            HCsr hAt, hC;
+            download_csr(L.At, hAt, s);
+            if (L.C.empty()) csr_identity(L.n, hC);
+            else download_csr(L.C, hC, s);
+            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s);
+        }
+        if (c.rstat.n >= 2) ks.err = c.rstat.p + 1;
+    }
+    Prof pr(c.prof, s, 0, kz_bytes(ks, c.nb, sizeof(T)));
+    if (c.spd()) {
+        launch_kaczmarz<T>(ks, ld, w.k.p, w.u.p, c.sigma.p, s);
+        return;
+    }
+    const size_t nv = (size_t)L.n * ld, nu = (size_t)L.m * ld;
+    if (w.z.n != nu + nv) {
+        w.z.alloc(nu + nv);
+        w.kt.alloc(nu + nv);
+    }
+    // unknown [v; u], right-hand side [kappa; tau]
+    SAMG_CUDA(cudaMemcpyAsync(w.z.p, w.v.p, nv * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.z.p + nv, w.u.p, nu * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.kt.p, w.k.p, nu * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.kt.p + nu, w.t.p, nv * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    launch_kaczmarz<T>(ks, ld, w.kt.p, w.z.p, c.sigma.p, s);
+    SAMG_CUDA(cudaMemcpyAsync(w.v.p, w.z.p, nv * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.u.p, w.z.p + nv, nu * sizeof(T), cudaMemcpyDeviceToDevice, s));
+}
+template void relax_phase<float>(samg_ctx &, int, int);
+template void relax_phase<double>(samg_ctx &, int, int);
+
 // r = kappa - (A v - s B u), s = tau - (A^t u - s C v); kappa_c = P^t r,
 // tau_c = Q^t s into level l+1 (Eqs. add, addCoarse).
 template <typename T>
@@ -178,14 +233,14 @@ void vcycle(samg_ctx &c, int l) {
         coarse_solve<T>(c);
         return;
     }
-    for (int k = 0; k < c.prm.mu_b; ++k) relax<T>(c, l);
+    relax_phase<T>(c, l, c.prm.mu_b);
     residual_restrict<T>(c, l);
     Work<T> &wc = work<T>(c.L[l + 1]);
     wc.u.zero(c.stream);
     if (!c.spd()) wc.v.zero(c.stream);
     vcycle<T>(c, l + 1);
     interpolate<T>(c, l);
-    for (int k = 0; k < c.prm.mu_b; ++k) relax<T>(c, l);
+    relax_phase<T>(c, l, c.prm.mu_b);
 }
 
 // Defect-correction form of one outer V-cycle: (r, s) = -(A V - s U,

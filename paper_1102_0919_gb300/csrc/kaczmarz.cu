@@ -44,11 +44,12 @@ __host__ __device__ constexpr ImgLayout img_layout(int nl, int nr, int ne, int n
     return ImgLayout{0u, ri, inv, ent, a, b, xc, al16u(xc + 4u * nx)};
 }
 
-struct Pattern {                      // merged rows: a (and b) coefficients
+struct Pattern {                      // rows of a sweep program: a (and b) coefficients
     int rows = 0, cols = 0;
     std::vector<int64_t> rp;
     std::vector<int> ci;
     std::vector<double> a, b;
+    std::vector<int> rhs;             // right-hand-side row of each row (empty: its own)
 };
 
 Pattern merge_pattern(const HCsr &A, const HCsr *B) {
@@ -366,10 +367,15 @@ struct Stage {
 // require from earlier bands, and publishes (release) this band's progress
 // when it crosses a level that a later band waits for, and at the band's
 // end.  The compute warps touch only shared memory for synchronization.
-template <typename T, int LD, bool SHIFT>
+// MODE 0: rows of A (norms given).  MODE 1: rows of A - s_j B (entries carry
+// b; norms formed per column).  MODE 2: fused relaxations (entries carry b;
+// the accumulation uses a - s_j b, the update only a; norms given).
+template <typename T, int LD, int MODE>
 __global__ void __launch_bounds__(KZ_THREADS, 1)
     k_kaczmarz(KView kv, const T *__restrict__ rhs, T *x, const double *__restrict__ shift,
                int window_slots) {
+    constexpr bool SHIFT = MODE != 0;  // entries carry b
+    constexpr bool NRM = MODE == 1;    // row norms formed per column
     using SG = Stage<T, LD, SHIFT>;
     extern __shared__ __align__(128) unsigned char smraw[];
     T *win = reinterpret_cast<T *>(smraw);
@@ -596,11 +602,11 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                 const int r = pr + (threadIdx.x >> lgG);
                                 const bool act = r < nrow;
                                 const int k = lr.x + r;
-                                T acc[LD], nrm[SHIFT ? LD : 1];
+                                T acc[LD], nrm[NRM ? LD : 1];
 #pragma unroll
                                 for (int q = 0; q < LD; ++q) acc[q] = T(0);
 #pragma unroll
-                                for (int q = 0; q < (SHIFT ? LD : 1); ++q) nrm[q] = T(0);
+                                for (int q = 0; q < (NRM ? LD : 1); ++q) nrm[q] = T(0);
                                 // the lane's first (and second) entry stay in registers
                                 // for the update
                                 int2 fen = make_int2(0, 0), sen = make_int2(0, 0);
@@ -622,7 +628,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                     for (int q = 0; q < LD; ++q) {
                                         const T coef = SHIFT ? a - sh[q] * bq : a;
                                         acc[q] = fma(coef, val[q], acc[q]);
-                                        if (SHIFT) nrm[q] = fma(coef, coef, nrm[q]);
+                                        if (NRM) nrm[q] = fma(coef, coef, nrm[q]);
                                     }
                                 };
                                 if (act) {
@@ -660,12 +666,12 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                 T d[LD];
                                 if (pow2(LD) && G >= LD) {
                                     const T sa_c = group_reduce_scatter<T, LD>(acc, lane, lgG);
-                                    const T sn_c = SHIFT ? group_reduce_scatter<T, (SHIFT ? LD : 1)>(nrm, lane, lgG) : T(0);
+                                    const T sn_c = NRM ? group_reduce_scatter<T, (NRM ? LD : 1)>(nrm, lane, lgG) : T(0);
                                     const int c = brev_low(lane & (LD - 1), ilog2(LD));
                                     T dc = T(0);
                                     if (act) {
                                         const T bi = rhs ? (SG::VALS ? srhs[k * LD + c] : rhs[(size_t)rk.x * LD + c]) : T(0);
-                                        dc = SHIFT ? (sn_c > T(0) ? (bi - sa_c) / sn_c : T(0)) : (bi - sa_c) * sinv[k];
+                                        dc = NRM ? (sn_c > T(0) ? (bi - sa_c) / sn_c : T(0)) : (bi - sa_c) * sinv[k];
                                     }
                                     const int gb = lane & ~(G - 1);
 #pragma unroll
@@ -673,15 +679,15 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                         d[q] = __shfl_sync(FULL, dc, gb + brev_low(q, ilog2(LD)));
                                 } else {
                                     group_allreduce<T, LD>(acc, lgG);
-                                    if (SHIFT) group_allreduce<T, (SHIFT ? LD : 1)>(nrm, lgG);
+                                    if (NRM) group_allreduce<T, (NRM ? LD : 1)>(nrm, lgG);
 #pragma unroll
                                     for (int q = 0; q < LD; ++q) d[q] = T(0);
                                     if (act) {
 #pragma unroll
                                         for (int q = 0; q < LD; ++q) {
                                             const T bi = rhs ? (SG::VALS ? srhs[k * LD + q] : rhs[(size_t)rk.x * LD + q]) : T(0);
-                                            const T nq = SHIFT ? nrm[q] : T(1);
-                                            d[q] = SHIFT ? (nq > T(0) ? (bi - acc[q]) / nq : T(0)) : (bi - acc[q]) * sinv[k];
+                                            const T nq = NRM ? nrm[q] : T(1);
+                                            d[q] = NRM ? (nq > T(0) ? (bi - acc[q]) / nq : T(0)) : (bi - acc[q]) * sinv[k];
                                         }
                                     }
                                 }
@@ -691,7 +697,9 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                 auto update = [&](int2 en, T a, T bq, T (&val)[LD]) {
 #pragma unroll
                                     for (int q = 0; q < LD; ++q) {
-                                        const T coef = SHIFT ? a - sh[q] * bq : a;
+                                        // fused relaxations update along a only: the
+                                        // b entries belong to the other unknown
+                                        const T coef = NRM ? a - sh[q] * bq : a;
                                         val[q] = fma(d[q], coef, val[q]);
                                     }
                                     vst<T, LD>(win + ((en.y >> 3) & 0xfff) * LD, val);
@@ -731,10 +739,10 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
     }
 }
 
-template <typename T, int LD, bool SHIFT>
+template <typename T, int LD, int MODE>
 void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaStream_t s) {
-    using SG = Stage<T, LD, SHIFT>;
-    auto kern = k_kaczmarz<T, LD, SHIFT>;
+    using SG = Stage<T, LD, MODE != 0>;
+    auto kern = k_kaczmarz<T, LD, MODE>;
     const int slots = ks.max_slots + 1;  // slot 0: scratch
     const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + (size_t)KZ_NBUF * SG::stride;
     SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
@@ -752,7 +760,7 @@ void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaS
         SAMG_CUDA(cudaGetDevice(&dev));
         SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     }
-    const int key = (int)sizeof(T) * 64 + LD * 2 + (SHIFT ? 1 : 0);
+    const int key = (int)sizeof(T) * 64 + LD * 4 + MODE;
     int &grid = ks.grid_cache[key & 255];
     if (!grid) {
         int bps = 0;
@@ -801,12 +809,18 @@ int write_image(std::vector<unsigned char> &img, bool shifted, const std::vector
 
 }  // namespace
 
-void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
-    Pattern p = merge_pattern(A, B);
+namespace {
+
+// Schedule of one sweep program (rows in program order).  mode: 0 plain rows
+// of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
+// block Gauss-Seidel relaxations (b entries read the other unknown with
+// coefficient -s_j and are not updated; norms from a).
+void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s) {
     const int rows = p.rows, cols = p.cols;
     ks.rows = rows;
     ks.cols = cols;
-    ks.shifted = (B != nullptr);
+    ks.shifted = mode != 0;
+    ks.mode = mode;
     BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
@@ -996,7 +1010,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
                         if (ks.shifted) cbv.push_back(p.b[e]);
                         n2 += p.a[e] * p.a[e];
                     }
-                    rrec.push_back(make_int2(r, e0 | (((int)erec.size() - e0) << 16)));
+                    rrec.push_back(make_int2(p.rhs.empty() ? r : p.rhs[r], e0 | (((int)erec.size() - e0) << 16)));
                     rinv.push_back(n2 > 0.0 ? 1.0 / n2 : 0.0);
                 }
                 lrec.push_back(make_int4(row0, (int)rrec.size() - row0, lg, lvl[L0 + qq].y > 0 ? 1 : 0));
@@ -1045,14 +1059,75 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     SAMG_CUDA(cudaStreamSynchronize(s));
 }
 
+void append_row(Pattern &p, const HCsr &M, int i, int col_off, bool as_b) {
+    for (int64_t e = M.rp[i]; e < M.rp[i + 1]; ++e) {
+        p.ci.push_back(M.ci[e] + col_off);
+        p.a.push_back(as_b ? 0.0 : M.v[e]);
+        p.b.push_back(as_b ? M.v[e] : 0.0);
+    }
+}
+
+}  // namespace
+
+void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
+    build_from_pattern(merge_pattern(A, B), B ? 1 : 0, ks, s);
+}
+
+void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s) {
+    const Pattern one = merge_pattern(A, &B);
+    Pattern p;
+    p.rows = one.rows * count;
+    p.cols = one.cols;
+    p.rp.assign(1, 0);
+    for (int k = 0; k < count; ++k) {
+        for (int i = 0; i < one.rows; ++i) {
+            for (int64_t e = one.rp[i]; e < one.rp[i + 1]; ++e) {
+                p.ci.push_back(one.ci[e]);
+                p.a.push_back(one.a[e]);
+                p.b.push_back(one.b[e]);
+            }
+            p.rp.push_back((int64_t)p.ci.size());
+            p.rhs.push_back(i);
+        }
+    }
+    build_from_pattern(p, 1, ks, s);
+}
+
+void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
+                           KSched &ks, cudaStream_t s) {
+    const int m = A.m, n = A.n;
+    Pattern p;
+    p.rows = count * (m + n);
+    p.cols = n + m;  // unknown [v; u]
+    p.rp.assign(1, 0);
+    for (int k = 0; k < count; ++k) {
+        // rows of A for v: a_i . v - s_j (B u)_i = kappa_i (v columns, then u)
+        for (int i = 0; i < m; ++i) {
+            append_row(p, A, i, 0, false);
+            append_row(p, B, i, n, true);
+            p.rp.push_back((int64_t)p.ci.size());
+            p.rhs.push_back(i);
+        }
+        // rows of A^t for u: a^t_j . u - s_j (C v)_j = tau_j (v columns, then u)
+        for (int j = 0; j < n; ++j) {
+            append_row(p, C, j, 0, true);
+            append_row(p, At, j, n, false);
+            p.rp.push_back((int64_t)p.ci.size());
+            p.rhs.push_back(m + j);
+        }
+    }
+    build_from_pattern(p, 2, ks, s);
+}
+
 template <typename T>
 static void dispatch(const KSched &ks, int ld, const T *rhs, T *x, const double *shift,
                      cudaStream_t s) {
     if (ks.rows == 0) return;
-#define KZ_CASE(L)                                                  \
-    case L:                                                         \
-        if (ks.shifted) launch_one<T, L, true>(ks, rhs, x, shift, s); \
-        else launch_one<T, L, false>(ks, rhs, x, shift, s);           \
+#define KZ_CASE(L)                                                       \
+    case L:                                                              \
+        if (ks.mode == 1) launch_one<T, L, 1>(ks, rhs, x, shift, s);      \
+        else if (ks.mode == 2) launch_one<T, L, 2>(ks, rhs, x, shift, s); \
+        else launch_one<T, L, 0>(ks, rhs, x, shift, s);                   \
         break;
     switch (ld) {
         KZ_CASE(4)

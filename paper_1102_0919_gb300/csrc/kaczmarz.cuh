@@ -50,7 +50,8 @@ struct KSched {
     int rows = 0, cols = 0, nbands = 0, nlevels = 0, nchunks = 0;
     int max_slots = 0;
     int64_t nent = 0;
-    bool shifted = false;      // rows of A - shift_j B (SPD kind)
+    bool shifted = false;      // entries carry b coefficients (modes 1 and 2)
+    int mode = 0;              // 0 rows of A; 1 rows of A - s_j B; 2 fused relaxations
     DBuf<int> band_chunk;      // nbands + 1: first staging chunk of each band
     DBuf<KChunk> chunk;
     DBuf<int4> lvl;            // per level: {first req, requirement count, publish, 0}
@@ -66,6 +67,19 @@ struct KSched {
 // Build the schedule of the rows of A (shift form when B != nullptr: rows of
 // A - s B over the union pattern).  Host CSR inputs.
 void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s);
+
+// count sweeps over the rows of A - s B in sequence (SPD kind): one program,
+// so a sweep's rows start as soon as the rows they depend on are done.
+void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s);
+
+// count block Gauss-Seidel relaxations of the minimal SVD kind as one
+// program over the unknown [v; u] (n + m rows of ld values): per relaxation
+// the rows of A (v updated, s_j B u read, right-hand side kappa_i) and then
+// the rows of A^t (u updated, s_j C v read, right-hand side tau_j); the
+// right-hand side block is [kappa; tau] (m + n rows).  The order of every
+// row's updates is that of the sequential relaxations.
+void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
+                           KSched &ks, cudaStream_t s);
 
 // One sweep: x (cols x ld) updated in place; rhs (rows x ld) or null for 0;
 // shift: ld device values (shifted form).  Returns after queuing the kernel.

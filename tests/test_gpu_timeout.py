@@ -44,7 +44,7 @@ def test_cross_band_wait_times_out_and_the_gpu_stays_usable():
     K = rng.standard_normal(U.shape)
     T = rng.standard_normal(V.shape)
     g.relax(0, sig, U, V, K, T, count=1)  # publishes normally
-    g.debug_mute_band(0, 0, 0)
+    g.debug_mute_band(0, 2, 0)  # the fused relaxation program the call above built
     t0 = time.time()
     with pytest.raises(samg.SamgError) as err:
         g.relax(0, sig, U, V, K, T, count=1)
