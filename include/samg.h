@@ -194,6 +194,20 @@ samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V
 /* Ritz step (Sec. 4.3) on host buffers: in/out sigma, U, V; resid = rho_j. */
 samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double *resid);
 
+/* Host-only analysis of the exact-order Kaczmarz schedule (no GPU needed):
+ * the dependency level of every row of a sweep program in natural order
+ * (1 + the level of the latest earlier row sharing a column; rows of one
+ * level share no column and are updated in parallel, Sec. 5.3), the program's
+ * depth (levels in sequence) and its number of bands.  fused_count = 0: one
+ * sweep over the rows of A (m rows); fused_count = k >= 1: k block
+ * Gauss-Seidel relaxations of the minimal SVD kind on level 0 as one program
+ * (per relaxation the m rows of A over [v; u], then the n rows of A^t;
+ * k (m + n) rows).  row_level (host, may be NULL) receives the levels when
+ * capacity is large enough.  Returns SAMG_E_INVALID for a malformed CSR or a
+ * short row_level. */
+samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_level,
+                            int64_t capacity, int *depth, int *nbands);
+
 /* Test hook for the bounded device waits (the paper has no counterpart):
  * from now on band `band` of the Kaczmarz schedules of level `level`
  * (which: 0 the single sweep over the rows of A, 1 over the rows of A^t,

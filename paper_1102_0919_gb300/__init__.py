@@ -82,6 +82,8 @@ samg_vcycle = _sig("samg_vcycle", _I, _CTX, _P, _P, _P)
 samg_ritz = _sig("samg_ritz", _I, _CTX, _P, _P, _P, _P)
 samg_block_gram = _sig("samg_block_gram", _I, _P, _P, ctypes.c_int64, _I, _I, _P, _P)
 samg_debug_mute_band = _sig("samg_debug_mute_band", _I, _CTX, _I, _I, _I)
+samg_sweep_plan = _sig("samg_sweep_plan", _I, _P, _I, _P, ctypes.c_int64, ctypes.POINTER(_I),
+                       ctypes.POINTER(_I))
 samg_block_gram_noalloc = _sig("samg_block_gram_noalloc", _I, _P, _P, ctypes.c_int64, _I, _I, _P,
                                _P)
 samg_set_triplets_device = _sig("samg_set_triplets_device", _I, _CTX, _P, _P, _P)
@@ -95,7 +97,8 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
-            "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band"]
+            "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band",
+            "samg_sweep_plan"]
 
 
 def _arr(x, dtype):
@@ -345,3 +348,18 @@ def block_gram_noalloc(X_ptr, Y_ptr, rows, nb, ld, G_ptr, stream=None):
                                  ctypes.c_void_p(G_ptr), _stream(stream))
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
+
+
+def sweep_plan(A, fused_count=0):
+    """Host-only: (row levels, depth, bands) of the exact-order Kaczmarz
+    schedule of one sweep over the rows of A (fused_count 0) or of
+    fused_count fused minimal-SVD relaxations with B = C = I."""
+    c = _csr(A)
+    rows = c.m if fused_count == 0 else fused_count * (c.m + c.n)
+    lv = np.zeros(max(rows, 1), np.int32)
+    d, nb = ctypes.c_int(0), ctypes.c_int(0)
+    st = samg_sweep_plan(ctypes.byref(c), fused_count, _ptr(lv), lv.size, ctypes.byref(d),
+                         ctypes.byref(nb))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    return lv[:rows], d.value, nb.value

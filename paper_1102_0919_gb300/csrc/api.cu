@@ -570,6 +570,42 @@ samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double
     });
 }
 
+samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_level,
+                            int64_t capacity, int *depth, int *nbands) {
+    try {
+        SAMG_CHECK(A && A->row_ptr && A->m > 0 && A->n > 0 && fused_count >= 0 && depth && nbands,
+                   SAMG_E_INVALID, "sweep_plan: bad arguments");
+        SAMG_CHECK(A->nnz == 0 || (A->col && A->val), SAMG_E_INVALID, "sweep_plan: bad CSR");
+        HCsr h;
+        h.m = A->m;
+        h.n = A->n;
+        h.rp.assign(A->row_ptr, A->row_ptr + A->m + 1);
+        SAMG_CHECK(h.rp[0] == 0 && h.rp[A->m] == A->nnz, SAMG_E_INVALID, "sweep_plan: bad row_ptr");
+        for (int i = 0; i < A->m; ++i)
+            SAMG_CHECK(h.rp[i] <= h.rp[i + 1], SAMG_E_INVALID, "sweep_plan: bad row_ptr");
+        h.ci.assign(A->col, A->col + A->nnz);
+        h.v.assign(A->val, A->val + A->nnz);
+        for (int64_t e = 0; e < A->nnz; ++e)
+            SAMG_CHECK(h.ci[e] >= 0 && h.ci[e] < A->n, SAMG_E_INVALID, "sweep_plan: column out of range");
+        std::vector<int> lv;
+        plan_sweep(h, fused_count, lv, nbands);
+        int d = 0;
+        for (int x : lv) d = std::max(d, x + 1);
+        *depth = d;
+        if (row_level) {
+            SAMG_CHECK(capacity >= (int64_t)lv.size(), SAMG_E_INVALID,
+                       "sweep_plan: row_level holds fewer entries than the program has rows");
+            std::copy(lv.begin(), lv.end(), row_level);
+        }
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
 samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {

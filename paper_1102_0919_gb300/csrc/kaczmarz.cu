@@ -811,6 +811,33 @@ int write_image(std::vector<unsigned char> &img, bool shifted, const std::vector
 
 namespace {
 
+// Contiguous bands of rows, each grown (doubling) until it has about
+// TARGET_PAR rows per level, at most MAX_BAND_ROWS rows, and at most SLOT_CAP
+// columns live at once.  Returns the first row of every band, then p.rows.
+std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w) {
+    std::vector<int> bstart;
+    int slots = 0;
+    for (int r0 = 0; r0 < p.rows;) {
+        int R = std::min(256, p.rows - r0), good = 0;
+        for (;;) {
+            int nl = analyze_band(p, glv, r0, r0 + R, w, &slots);
+            if (slots > SLOT_CAP) {
+                if (good) break;
+                R = std::max(1, R / 2);
+                if (R == 1) { good = 1; break; }
+                continue;
+            }
+            good = R;
+            if (r0 + R >= p.rows || R >= MAX_BAND_ROWS || (R / std::max(nl, 1)) >= TARGET_PAR) break;
+            R = std::min(2 * R, p.rows - r0);
+        }
+        bstart.push_back(r0);
+        r0 += good;
+    }
+    bstart.push_back(p.rows);
+    return bstart;
+}
+
 // Schedule of one sweep program (rows in program order).  mode: 0 plain rows
 // of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
 // block Gauss-Seidel relaxations (b entries read the other unknown with
@@ -824,27 +851,9 @@ void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s) 
     BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
-    std::vector<int> bstart;
+    std::vector<int> bstart = form_bands(p, glv, w);
+    const int nb = (int)bstart.size() - 1;
     int slots = 0;
-    for (int r0 = 0; r0 < rows;) {
-        int R = std::min(256, rows - r0), good = 0;
-        for (;;) {
-            int nl = analyze_band(p, glv, r0, r0 + R, w, &slots);
-            if (slots > SLOT_CAP) {
-                if (good) break;
-                R = std::max(1, R / 2);
-                if (R == 1) { good = 1; break; }
-                continue;
-            }
-            good = R;
-            if (r0 + R >= rows || R >= MAX_BAND_ROWS || (R / std::max(nl, 1)) >= TARGET_PAR) break;
-            R = std::min(2 * R, rows - r0);
-        }
-        bstart.push_back(r0);
-        r0 += good;
-    }
-    const int nb = (int)bstart.size();
-    bstart.push_back(rows);
     ks.nbands = nb;
     // 2. per band: levels, window slots, sub-levels (<= chunk limits), chunks
     std::vector<int> band_chunk(nb + 1, 0);
@@ -1117,6 +1126,59 @@ void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const H
         }
     }
     build_from_pattern(p, 2, ks, s);
+}
+
+void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *nbands) {
+    Pattern p;
+    if (fused_count <= 0) {
+        p = merge_pattern(A, nullptr);
+    } else {
+        // the fused program of build_kschedule_fused with B = I, C = I
+        HCsr At, I_m, I_n;
+        At.m = A.n;
+        At.n = A.m;
+        At.rp.assign(A.n + 1, 0);
+        for (int64_t e = 0; e < A.nnz(); ++e) At.rp[A.ci[e] + 1]++;
+        for (int j = 0; j < A.n; ++j) At.rp[j + 1] += At.rp[j];
+        At.ci.resize(A.nnz());
+        At.v.resize(A.nnz());
+        std::vector<int64_t> fill(At.rp.begin(), At.rp.end() - 1);
+        for (int i = 0; i < A.m; ++i)
+            for (int64_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+                const int64_t f = fill[A.ci[e]]++;
+                At.ci[f] = i;
+                At.v[f] = A.v[e];
+            }
+        auto identity = [](int k, HCsr &h) {
+            h.m = h.n = k;
+            h.rp.resize(k + 1);
+            h.ci.resize(k);
+            h.v.assign(k, 1.0);
+            for (int i = 0; i <= k; ++i) h.rp[i] = i;
+            for (int i = 0; i < k; ++i) h.ci[i] = i;
+        };
+        identity(A.m, I_m);
+        identity(A.n, I_n);
+        const int m = A.m, n = A.n;
+        p.rows = fused_count * (m + n);
+        p.cols = n + m;
+        p.rp.assign(1, 0);
+        for (int k = 0; k < fused_count; ++k) {
+            for (int i = 0; i < m; ++i) {
+                append_row(p, A, i, 0, false);
+                append_row(p, I_m, i, n, true);
+                p.rp.push_back((int64_t)p.ci.size());
+            }
+            for (int j = 0; j < n; ++j) {
+                append_row(p, I_n, j, 0, true);
+                append_row(p, At, j, n, false);
+                p.rp.push_back((int64_t)p.ci.size());
+            }
+        }
+    }
+    levels = global_levels(p);
+    BandWork w(p.cols);
+    *nbands = (int)form_bands(p, levels, w).size() - 1;
 }
 
 template <typename T>

@@ -87,6 +87,13 @@ template <typename T>
 void launch_kaczmarz(const KSched &ks, int ld, const T *rhs, T *x, const double *shift,
                      cudaStream_t s);
 
+// Host-only analysis of a sweep program (no device work): the global
+// dependency level of every row and the number of bands.  fused_count = 0:
+// one sweep over the rows of A; >= 1: the fused program of that many
+// minimal-SVD relaxations with B = I, C = I (rows: per relaxation the m rows
+// of A, then the n rows of A^t).
+void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *nbands);
+
 // Test hook: the given band (-1: none) never publishes its progress, so later
 // bands that need it give up after their bounded wait.
 void kaczmarz_mute_band(KSched &ks, int band, cudaStream_t s);
