@@ -298,6 +298,71 @@ def test_spd_shifted_kaczmarz_fixes_exact_eigenpairs():
     assert np.allclose(lam, laplacian5_eigs(6)[:3], rtol=1e-12)
 
 
+# ---------------------------------------------------------------- setup readings
+
+def test_coarsest_triplets_are_normalized_generalized_triplets():
+    # Thm genSVD: A v = s B u, A^t u = s C v with u^t B u = v^t C v = 1, for
+    # random SPD B, C; the SVD of B^-1/2 A C^-1/2 (LAPACK, called) gives s
+    rng = np.random.default_rng(17)
+    m, n = 9, 6
+    A = rng.standard_normal((m, n))
+    Rb = rng.standard_normal((m, m))
+    Rc = rng.standard_normal((n, n))
+    B = Rb @ Rb.T + m * np.eye(m)
+    C = Rc @ Rc.T + n * np.eye(n)
+    L = oracle.Level(sp.csr_matrix(A), sp.csr_matrix(B), sp.csr_matrix(C))
+    for target in ("dominant", "minimal"):
+        s, U, V = oracle.coarsest_triplets(L, False, target, 3)
+        assert np.allclose(A @ V, B @ U * s, atol=1e-10)
+        assert np.allclose(A.T @ U, C @ V * s, atol=1e-10)
+        assert np.allclose(np.einsum("ij,ij->j", U, B @ U), 1.0, atol=1e-10)
+        assert np.allclose(np.einsum("ij,ij->j", V, C @ V), 1.0, atol=1e-10)
+        Bh = sla.sqrtm(np.linalg.inv(B)).real
+        Ch = sla.sqrtm(np.linalg.inv(C)).real
+        ref = np.sort(np.linalg.svd(Bh @ A @ Ch, compute_uv=False))
+        want = ref[::-1][:3] if target == "dominant" else ref[:3]
+        assert np.allclose(s, want, rtol=1e-10)
+
+
+def test_r14_jacobi_weight_never_amplifies():
+    # R14: the weight 2 omega / g (g the Gershgorin bound of D^-1 N) keeps
+    # every eigenvalue of I - w D^-1 N in [-1, 1] for omega <= 1, so repeated
+    # steps never grow the D-norm; the plain weight omega = 0.7 on A A^t of the
+    # gradient (g = 4) amplifies its high modes
+    A = W.gradient(6).to_scipy()
+    m, n = A.shape
+    L = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    N = (A @ A.T).toarray()
+    d = np.diag(N)
+    rng = np.random.default_rng(3)
+    Y0 = rng.standard_normal((m, 4))
+    Y = Y0.copy()
+    dnorm = lambda Z: np.sqrt(np.einsum("ij,i,ij->", Z, d, Z))
+    for _ in range(30):
+        Y = oracle.samg._jacobi_on_N(L, False, "u", Y, 0.7)
+    assert dnorm(Y) <= dnorm(Y0) * (1 + 1e-12)
+    Z = Y0.copy()
+    for _ in range(30):
+        Z = Z - 0.7 * (N @ Z) / d[:, None]
+    assert dnorm(Z) > 10 * dnorm(Y0)
+
+
+def test_r21_induced_interpolation_structure():
+    # minimal SVD kind with m >= n: P_0 = A Q_0 and P_l = Q_l below, so that
+    # A_1 = P_0^t A Q_0 = Q_0^t A^t A Q_0 equals B_1 = P_0^t P_0 (symmetric)
+    A = W.gradient(12).to_scipy()
+    H, s, U, V = oracle.setup(A, 4, "minimal", "svd",
+                              dict(W.GRAD_PARAMS, n_mult=1, seed=7, coarsest_max=40))
+    assert len(H.levels) >= 3
+    L0 = H.levels[0]
+    assert abs(L0.P - A @ L0.Q).max() < 1e-12
+    L1 = H.levels[1]
+    assert abs(L1.A - L1.B).max() < 1e-9 * abs(L1.A).max()
+    assert abs(L1.A - L1.A.T).max() < 1e-9 * abs(L1.A).max()
+    for L in H.levels[1:-1]:
+        assert abs(L.P - L.Q).max() == 0
+
+
 # ---------------------------------------------------------------- additive cycle
 
 def test_additive_equals_multiplicative_when_x_in_range_of_P():
