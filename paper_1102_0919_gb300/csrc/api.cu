@@ -359,6 +359,16 @@ samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_
                         ctx->L[l].kA.nbands, ctx->L[l].kA.nlevels, ctx->L[l].kA.nchunks,
                         (long long)ctx->L[l].kA.req.n, ctx->L[l].kA.max_slots, ctx->L[l].kAt.nbands,
                         ctx->L[l].kAt.nlevels, ctx->L[l].kAt.nchunks);
+        if (std::getenv("SAMG_PROFILE_LEVELS") && kernel_class == 0)
+            for (int l = 0; l < ctx->nlev(); ++l)
+                for (size_t k = 0; k < ctx->L[l].kF.size(); ++k) {
+                    const KSched &f = ctx->L[l].kF[k];
+                    if (f.rows)
+                        fprintf(stderr, "[samg] level %d fused program of %zu relaxations: rows %d"
+                                " bands %d levels %d chunks %d reqs %lld slots %d\n",
+                                l, k, f.rows, f.nbands, f.nlevels, f.nchunks, (long long)f.req.n,
+                                f.max_slots);
+                }
         if (launches) *launches = ctx->prof.launches[kernel_class];
         if (total_ms) *total_ms = ctx->prof.ms[kernel_class];
         if (alg_bytes) *alg_bytes = ctx->prof.bytes[kernel_class];
