@@ -168,7 +168,11 @@ samg_status samg_get_level_matrix(const samg_ctx *ctx, int level, int which, int
  * tau, Uc, Vc have m_l / n_l / m_{l+1} / n_{l+1} rows and n_b columns. */
 
 /* count block Gauss-Seidel relaxations of A v - s B u = kappa,
- * A^t u - s C v = tau (Eqs. genSVDresid1-2, add), in place on U, V. */
+ * A^t u - s C v = tau (Eqs. genSVDresid1-2, add), in place on U, V.  For the
+ * minimal target the count relaxations run as one exact-order sweep program
+ * (the same row updates in the same order as count sequential relaxations,
+ * up to the rounding order inside a row); the first call for a given count
+ * builds its schedule. */
 samg_status samg_relax(samg_ctx *ctx, int level, int count, const double *sigma, double *U,
                        double *V, const double *kappa, const double *tau);
 
