@@ -198,6 +198,25 @@ samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V
 /* Ritz step (Sec. 4.3) on host buffers: in/out sigma, U, V; resid = rho_j. */
 samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double *resid);
 
+/* Host-only steps of the setup phase (no GPU needed), as samg_setup runs
+ * them on each level:
+ *  - samg_host_coarsen: strength of connection on the square N (Eq. strength,
+ *    sums over all columns including the diagonal) and one-pass
+ *    Ruge-Stueben coarsening (Algorithm coarsening, ties to the lowest index);
+ *    cf[i] = 1 for C points, 0 for F points (n entries, host).
+ *  - samg_host_ls_interp: interpolation P (n x n_c, n_c = number of C points)
+ *    from that strength graph and cf: C rows carry a single 1 at the coarse
+ *    index (increasing fine index), F rows the weighted LS weights of Eq. LS
+ *    over the at most nf - 1 strongest C-point influences, fitting yF[i] by
+ *    the yC values of those points with weights w (w multiplies the squared
+ *    residuals).  yF, yC: n x nf row-major; w: nf.  Call with row_ptr = NULL
+ *    to get *nnz, then with row_ptr (n + 1), col and val (nnz) to fill P.
+ * Both return SAMG_E_INVALID for malformed input. */
+samg_status samg_host_coarsen(const samg_csr *N, double theta, int8_t *cf);
+samg_status samg_host_ls_interp(const samg_csr *N, double theta, const int8_t *cf, int nf,
+                                const double *yF, const double *yC, const double *w,
+                                int64_t *nnz, int64_t *row_ptr, int32_t *col, double *val);
+
 /* Host-only analysis of the exact-order Kaczmarz schedule (no GPU needed):
  * the dependency level of every row of a sweep program in natural order
  * (1 + the level of the latest earlier row sharing a column; rows of one

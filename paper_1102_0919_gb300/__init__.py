@@ -82,6 +82,9 @@ samg_vcycle = _sig("samg_vcycle", _I, _CTX, _P, _P, _P)
 samg_ritz = _sig("samg_ritz", _I, _CTX, _P, _P, _P, _P)
 samg_block_gram = _sig("samg_block_gram", _I, _P, _P, ctypes.c_int64, _I, _I, _P, _P)
 samg_debug_mute_band = _sig("samg_debug_mute_band", _I, _CTX, _I, _I, _I)
+samg_host_coarsen = _sig("samg_host_coarsen", _I, _P, ctypes.c_double, _P)
+samg_host_ls_interp = _sig("samg_host_ls_interp", _I, _P, ctypes.c_double, _P, _I, _P, _P, _P,
+                           ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
 samg_sweep_plan = _sig("samg_sweep_plan", _I, _P, _I, _P, ctypes.c_int64, ctypes.POINTER(_I),
                        ctypes.POINTER(_I))
 samg_block_gram_noalloc = _sig("samg_block_gram_noalloc", _I, _P, _P, ctypes.c_int64, _I, _I, _P,
@@ -98,7 +101,7 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
             "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band",
-            "samg_sweep_plan"]
+            "samg_sweep_plan", "samg_host_coarsen", "samg_host_ls_interp"]
 
 
 def _arr(x, dtype):
@@ -363,3 +366,37 @@ def sweep_plan(A, fused_count=0):
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
     return lv[:rows], d.value, nb.value
+
+
+def host_coarsen(N, theta):
+    """Host-only: C/F splitting (1 = C) of the strength graph of N."""
+    c = _csr(N)
+    cf = np.zeros(c.m, np.int8)
+    st = samg_host_coarsen(ctypes.byref(c), theta, _ptr(cf))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    return cf
+
+
+def host_ls_interp(N, theta, cf, Yf, Yc, w):
+    """Host-only: the setup's LS interpolation operator (scipy CSR)."""
+    import scipy.sparse as _sp
+
+    c = _csr(N)
+    nf = int(np.asarray(Yf).shape[1])
+    cf8 = np.ascontiguousarray(cf, dtype=np.int8)
+    f = _arr(Yf, np.float64)
+    g = _arr(Yc, np.float64)
+    ww = _arr(w, np.float64)
+    nnz = ctypes.c_int64(0)
+    args = (ctypes.byref(c), theta, _ptr(cf8), nf, _ptr(f), _ptr(g), _ptr(ww), ctypes.byref(nnz))
+    st = samg_host_ls_interp(*args, None, None, None)
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    rp = np.zeros(c.m + 1, np.int64)
+    ci = np.zeros(max(nnz.value, 1), np.int32)
+    v = np.zeros(max(nnz.value, 1), np.float64)
+    st = samg_host_ls_interp(*args, _ptr(rp), _ptr(ci), _ptr(v))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    return _sp.csr_matrix((v[:nnz.value], ci[:nnz.value], rp), shape=(c.m, int(cf8.sum())))

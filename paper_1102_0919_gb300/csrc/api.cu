@@ -580,6 +580,69 @@ samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double
     });
 }
 
+// Host copy of a caller's CSR, validated (host-only entry points).
+static HCsr host_copy(const samg_csr *A, bool square) {
+    SAMG_CHECK(A && A->row_ptr && A->m > 0 && A->n > 0 && A->nnz >= 0, SAMG_E_INVALID,
+               "bad CSR");
+    SAMG_CHECK(!square || A->m == A->n, SAMG_E_INVALID, "the matrix must be square");
+    SAMG_CHECK(A->nnz == 0 || (A->col && A->val), SAMG_E_INVALID, "bad CSR");
+    HCsr h;
+    h.m = A->m;
+    h.n = A->n;
+    h.rp.assign(A->row_ptr, A->row_ptr + A->m + 1);
+    SAMG_CHECK(h.rp[0] == 0 && h.rp[A->m] == A->nnz, SAMG_E_INVALID, "bad row_ptr");
+    for (int i = 0; i < A->m; ++i) SAMG_CHECK(h.rp[i] <= h.rp[i + 1], SAMG_E_INVALID, "bad row_ptr");
+    h.ci.assign(A->col, A->col + A->nnz);
+    h.v.assign(A->val, A->val + A->nnz);
+    for (int64_t e = 0; e < A->nnz; ++e)
+        SAMG_CHECK(h.ci[e] >= 0 && h.ci[e] < A->n, SAMG_E_INVALID, "column out of range");
+    return h;
+}
+
+samg_status samg_host_coarsen(const samg_csr *N, double theta, int8_t *cf) {
+    try {
+        SAMG_CHECK(cf && theta >= 0.0, SAMG_E_INVALID, "host_coarsen: bad arguments");
+        const HCsr h = host_copy(N, true);
+        std::vector<char> c;
+        host_coarsen(h, theta, c);
+        for (int i = 0; i < h.m; ++i) cf[i] = (int8_t)c[i];
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
+samg_status samg_host_ls_interp(const samg_csr *N, double theta, const int8_t *cf, int nf,
+                                const double *yF, const double *yC, const double *w,
+                                int64_t *nnz, int64_t *row_ptr, int32_t *col, double *val) {
+    try {
+        SAMG_CHECK(cf && nf >= 1 && yF && yC && w && nnz && theta >= 0.0, SAMG_E_INVALID,
+                   "host_ls_interp: bad arguments");
+        const HCsr h = host_copy(N, true);
+        std::vector<char> c(cf, cf + h.m);
+        std::vector<double> f(yF, yF + (size_t)h.m * nf), cc(yC, yC + (size_t)h.m * nf),
+            ww(w, w + nf);
+        HCsr P;
+        host_ls_interp(h, theta, c, f, cc, ww, nf, P);
+        *nnz = P.nnz();
+        if (row_ptr) {
+            SAMG_CHECK(col && val, SAMG_E_INVALID, "host_ls_interp: output arrays missing");
+            std::copy(P.rp.begin(), P.rp.end(), row_ptr);
+            std::copy(P.ci.begin(), P.ci.end(), col);
+            std::copy(P.v.begin(), P.v.end(), val);
+        }
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
 samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_level,
                             int64_t capacity, int *depth, int *nbands) {
     try {

@@ -157,5 +157,12 @@ template <typename T> void outer_vcycle(samg_ctx &c);   // defect form on (U, V)
 
 void ritz(samg_ctx &c, bool identity);  // identity: residuals of the current triplets only
 void host_setup(samg_ctx &c, const samg_csr &A);  // multiplicative phase (setup.cu)
+// The setup's host steps on their own (setup.cu): strength (Eq. strength) and
+// Ruge-Stueben coarsening of N; weighted LS interpolation (Eq. LS) from the
+// strong C-point influences, nf vectors per point (row-major yF, yC).
+void host_coarsen(const HCsr &N, double theta, std::vector<char> &cf);
+void host_ls_interp(const HCsr &N, double theta, const std::vector<char> &cf,
+                    const std::vector<double> &yF, const std::vector<double> &yC,
+                    const std::vector<double> &w, int nf, HCsr &P);
 
 }  // namespace samg

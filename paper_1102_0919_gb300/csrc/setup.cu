@@ -701,4 +701,18 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     SAMG_CUDA(cudaStreamSynchronize(s));
 }
 
+void host_coarsen(const HCsr &N, double theta, std::vector<char> &cf) {
+    HCsr S;
+    strength_of(N, theta, S);
+    cf = rs_split(S);
+}
+
+void host_ls_interp(const HCsr &N, double theta, const std::vector<char> &cf,
+                    const std::vector<double> &yF, const std::vector<double> &yC,
+                    const std::vector<double> &w, int nf, HCsr &P) {
+    HCsr S;
+    strength_of(N, theta, S);
+    ls_interp(S, cf, yF, yC, w, nf, P);
+}
+
 }  // namespace samg
