@@ -53,3 +53,33 @@ def test_default_params_and_null_handling(lib):
     # argument errors are reported without touching a GPU
     assert samg.samg_solve(None, 1e-8, 1, None) == samg.E_INVALID
     assert samg.samg_setup(None, 4, 1, 0, None, None, None) == samg.E_INVALID
+
+
+def test_header_serves_a_plain_c_client(lib, repo_root, tmp_path):
+    # the header compiles as C99 with warnings as errors, a client links
+    # against the library, and without a GPU the library says so (status
+    # SAMG_E_CUDA, exit 2) instead of computing anywhere else
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    so, path = lib
+    exe = str(tmp_path / "client")
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(repo_root, "include"),
+           os.path.join(repo_root, "tests", "c_abi_client.c"), "-o", exe,
+           "-L", os.path.dirname(path), "-l:" + os.path.basename(path),
+           "-Wl,-rpath," + os.path.dirname(path)]
+    out = subprocess.run(cmd, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if has_gpu:
+        assert run.returncode == 0, run.stderr
+    else:
+        assert run.returncode == 2, (run.returncode, run.stderr)
