@@ -52,6 +52,20 @@ def _env_rank():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of every rank's x (the replicas' timing rule); x itself
+    when no process group is up.  Collective on `device` (cuda under NCCL,
+    cpu under gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------- clocks
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -262,10 +276,7 @@ def run_gpu(args):
             s.profile(False)
             pr = s.profile_read()
         launches = samg.samg_launch_count() - launches0
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        results[prec] = dict(ms=float(t.item()), iters=iters, launches=launches, steps=steps,
+        results[prec] = dict(ms=max_over_ranks(ms, dev), iters=iters, launches=launches, steps=steps,
                              clocks=clk.summary(), prof=pr if prof else None)
         log("%s: %.1f ms/solve, iterations %s" % (prec, ms, iters))
         if prof:
