@@ -422,6 +422,21 @@ def test_fd_minimal_matches_paper_table_values():
     assert np.allclose(s, laplacian5_eigs(32)[:8] / 33.0 ** 2, rtol=1e-12)
 
 
+def test_fd_dominant_matches_paper_table_values():
+    # Sec. 6.2, dominant case: same setting, the 8 largest eigenpairs; the
+    # paper reports four levels and the Table's "FD lge" column, printed to
+    # 7 decimals (half a unit of the last place is 5e-8).
+    lge, sm = _table_fd()
+    A = W.laplacian5(32).to_scipy() / 33.0 ** 2
+    H, s, U, V = oracle.setup(A, 8, "dominant", "spd", dict(W.FD_PARAMS, seed=W.problem_seed(1)))
+    assert len(H.levels) == 4                           # "Four levels are used"
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-12, max_outer=150)
+    assert hist[-1].max() <= 1e-12
+    assert np.all(np.abs(s - lge) <= 5.01e-8)
+    assert np.allclose(s, laplacian5_eigs(32)[::-1][:8] / 33.0 ** 2, rtol=1e-12)
+    assert np.allclose(A @ U, U * s, atol=1e-11 * s.max())
+
+
 def test_laplacian_workload_minimal_closed_form():
     wl = W.workload(1)
     A = wl.build().to_scipy()
