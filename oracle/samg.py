@@ -48,6 +48,11 @@ silent the readings below are used (numbers as in the design notes):
   components of u in null(A^t) -- left there by rounding -- are invisible to
   every relaxation and correction and to the two-sided projection, and would
   otherwise stall the residual at the rounding level of the cycle.
+* R22 redo-P (Sec. 6.3): a triplet counts as converged once rho_j <=
+  redo_tol; each time that count grows (some still above), one downward
+  sweep of the multiplicative phase runs on copies of the boot triplets with
+  the LS weights of the test vectors and of the converged boot vectors
+  divided by 1000, replacing P, Q and the coarse operators.
 """
 from __future__ import annotations
 
@@ -230,6 +235,9 @@ class Hierarchy:
     target: str      # "minimal" | "dominant"
     levels: list
     params: dict
+    Ut: np.ndarray | None = None   # fine test vectors after the setup's last cycle
+    Vt: np.ndarray | None = None
+    redos: list = dataclasses.field(default_factory=list)  # outer iterations of redo sweeps
 
     @property
     def spd(self):
@@ -510,10 +518,104 @@ def _induced(spd: bool, target: str, shape) -> bool:
     return (not spd) and target == "minimal" and shape[0] >= shape[1]
 
 
+def _down_sweep(A, spd: bool, target: str, nb: int, p: dict, Ut, Vt, sigma, ub, vb,
+                wscale=None):
+    """Downward sweep of one multiplicative cycle (Sec. 3.3): on each level
+    coarsen, relax the test vectors (and the boot vectors, when there are
+    any, with Rayleigh-quotient updates), fit P and Q by weighted LS on
+    [test, boot], form the Galerkin operators and inject the vectors.  The
+    fine test vectors Ut, Vt and the fine boot vectors ub, vb are relaxed in
+    place.  wscale (optional, one factor per fitted vector) multiplies the LS
+    weights.  Returns (levels, sigma, ub, vb), the last three on the
+    coarsest level."""
+    m, n = A.shape
+    om = p["omega_J"]
+    induced = _induced(spd, target, A.shape)
+    boot = ub is not None
+    fine = Level(A, sp.identity(m, format="csr"),
+                 None if spd else sp.identity(n, format="csr"))
+    levels = [fine]
+    ut, vt = Ut, Vt                    # fine test vectors are relaxed in place
+    while True:
+        L = levels[-1]
+        lvl = len(levels) - 1
+        ml, nl = L.A.shape
+        if max(ml, nl) <= p["coarsest_max"] or len(levels) >= p["max_levels"]:
+            break
+        # coarsening (Sec. 3.7) depends on A_l only
+        if spd:
+            Su = strength(L.A, p["theta"])
+            cfu = rs_coarsen(Su)
+            mc = nc = int(cfu.sum())
+            total_f, total_c = ml, mc
+        elif induced:
+            Sv = strength(L.At @ L.A if lvl == 0 else L.A, p["theta"])
+            cfv = rs_coarsen(Sv)
+            mc = nc = int(cfv.sum())
+            total_f, total_c = ml + nl, 2 * nc
+        else:
+            Su = strength(L.A @ L.At, p["theta"])
+            Sv = strength(L.At @ L.A, p["theta"])
+            cfu, cfv = rs_coarsen(Su), rs_coarsen(Sv)
+            mc, nc = int(cfu.sum()), int(cfv.sum())
+            total_f, total_c = ml + nl, mc + nc
+        if total_c > 0.9 * total_f or min(mc, nc) < 2 * nb:
+            break
+        # relaxation of the test (and, after the first cycle, boot) vectors
+        if induced:
+            relax_test_v_only(L, vt, p["mu_t"])
+            ut = np.ascontiguousarray(L.A @ vt if lvl == 0 else vt)
+        else:
+            relax_test(L, spd, target, ut, vt, p["mu_t"], om)
+        if boot:
+            sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
+        # LS interpolation (Sec. 3.8) on [U_t, U_b]
+        Uf = ut if not boot else np.hstack([ut, ub])
+        Vf = None if spd else (vt if not boot else np.hstack([vt, vb]))
+        rq = rayleigh(L, spd, Uf, Vf if not spd else None)
+        w = _fit_weights(rq, target)
+        if wscale is not None:
+            w = w * wscale
+        if induced:
+            Yv = _jacobi_on_N(L, lvl > 0, "v", Vf, om)
+            L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
+            L.P = _csr(L.A @ L.Q) if lvl == 0 else L.Q
+        else:
+            if target == "minimal":
+                Yu = _jacobi_on_N(L, spd, "u", Uf, om)
+                Yv = None if spd else _jacobi_on_N(L, spd, "v", Vf, om)
+            else:
+                Yu, Yv = Uf, Vf
+            L.P = fit_interp(Su, cfu, Yu, Uf, w)
+            if not spd:
+                L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
+        levels.append(galerkin(L, spd))
+        # injection to the coarse level
+        if induced:
+            cv = np.flatnonzero(cfv)
+            vt = np.ascontiguousarray(vt[cv])
+            if boot:
+                # P_0 = A Q_0: u_b = A v_b / s is interpolated by v_b[C] / s
+                ub = np.ascontiguousarray(vb[cv] / sigma if lvl == 0 else ub[cv])
+                vb = np.ascontiguousarray(vb[cv])
+            continue
+        cu = np.flatnonzero(cfu)
+        ut = np.ascontiguousarray(ut[cu])
+        if boot:
+            ub = np.ascontiguousarray(ub[cu])
+        if not spd:
+            cv = np.flatnonzero(cfv)
+            vt = np.ascontiguousarray(vt[cv])
+            if boot:
+                vb = np.ascontiguousarray(vb[cv])
+    return levels, sigma, ub, vb
+
+
 def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
     """Multiplicative (setup) phase: n_mult bootstrap V-cycles (Sec. 3.3).
     Returns (Hierarchy of the last cycle, sigma_b, U_b, V_b) after the final
-    Ritz step."""
+    Ritz step.  The hierarchy keeps the fine test vectors for later
+    downward sweeps (redo_interpolation)."""
     p = dict(DEFAULTS)
     p.update(params or {})
     spd = kind == "spd"
@@ -528,81 +630,7 @@ def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
     sigma = Ub = Vb = None
     levels = []
     for cyc in range(p["n_mult"]):
-        fine = Level(A, sp.identity(m, format="csr"),
-                     None if spd else sp.identity(n, format="csr"))
-        levels = [fine]
-        ut, vt = Ut, Vt                    # fine test vectors are relaxed in place
-        ub, vb = Ub, Vb
-        while True:
-            L = levels[-1]
-            lvl = len(levels) - 1
-            ml, nl = L.A.shape
-            if max(ml, nl) <= p["coarsest_max"] or len(levels) >= p["max_levels"]:
-                break
-            # coarsening (Sec. 3.7) depends on A_l only
-            if spd:
-                Su = strength(L.A, p["theta"])
-                cfu = rs_coarsen(Su)
-                mc = nc = int(cfu.sum())
-                total_f, total_c = ml, mc
-            elif induced:
-                Sv = strength(L.At @ L.A if lvl == 0 else L.A, p["theta"])
-                cfv = rs_coarsen(Sv)
-                mc = nc = int(cfv.sum())
-                total_f, total_c = ml + nl, 2 * nc
-            else:
-                Su = strength(L.A @ L.At, p["theta"])
-                Sv = strength(L.At @ L.A, p["theta"])
-                cfu, cfv = rs_coarsen(Su), rs_coarsen(Sv)
-                mc, nc = int(cfu.sum()), int(cfv.sum())
-                total_f, total_c = ml + nl, mc + nc
-            if total_c > 0.9 * total_f or min(mc, nc) < 2 * nb:
-                break
-            # relaxation of the test (and, after the first cycle, boot) vectors
-            if induced:
-                relax_test_v_only(L, vt, p["mu_t"])
-                ut = np.ascontiguousarray(L.A @ vt if lvl == 0 else vt)
-            else:
-                relax_test(L, spd, target, ut, vt, p["mu_t"], om)
-            if cyc > 0:
-                sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
-            # LS interpolation (Sec. 3.8) on [U_t, U_b]
-            Uf = ut if cyc == 0 else np.hstack([ut, ub])
-            Vf = None if spd else (vt if cyc == 0 else np.hstack([vt, vb]))
-            rq = rayleigh(L, spd, Uf, Vf if not spd else None)
-            w = _fit_weights(rq, target)
-            if induced:
-                Yv = _jacobi_on_N(L, lvl > 0, "v", Vf, om)
-                L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
-                L.P = _csr(L.A @ L.Q) if lvl == 0 else L.Q
-            else:
-                if target == "minimal":
-                    Yu = _jacobi_on_N(L, spd, "u", Uf, om)
-                    Yv = None if spd else _jacobi_on_N(L, spd, "v", Vf, om)
-                else:
-                    Yu, Yv = Uf, Vf
-                L.P = fit_interp(Su, cfu, Yu, Uf, w)
-                if not spd:
-                    L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
-            levels.append(galerkin(L, spd))
-            # injection to the coarse level
-            if induced:
-                cv = np.flatnonzero(cfv)
-                vt = np.ascontiguousarray(vt[cv])
-                if cyc > 0:
-                    # P_0 = A Q_0: u_b = A v_b / s is interpolated by v_b[C] / s
-                    ub = np.ascontiguousarray(vb[cv] / sigma if lvl == 0 else ub[cv])
-                    vb = np.ascontiguousarray(vb[cv])
-                continue
-            cu = np.flatnonzero(cfu)
-            ut = np.ascontiguousarray(ut[cu])
-            if cyc > 0:
-                ub = np.ascontiguousarray(ub[cu])
-            if not spd:
-                cv = np.flatnonzero(cfv)
-                vt = np.ascontiguousarray(vt[cv])
-                if cyc > 0:
-                    vb = np.ascontiguousarray(vb[cv])
+        levels, sigma, ub, vb = _down_sweep(A, spd, target, nb, p, Ut, Vt, sigma, Ub, Vb)
         # coarsest level: new boot triplets by direct solve (Sec. 3.6)
         sigma, ub, vb = coarsest_triplets(levels[-1], spd, target, nb)
         # upward: interpolate (Eq. ranges), relax with RQ updates
@@ -613,14 +641,44 @@ def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
                 vb = np.ascontiguousarray(L.Q @ vb)
             sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
         sigma, Ub, Vb = ritz(A, spd, target, ub, vb)
-    H = Hierarchy(kind, target, levels, p)
+    H = Hierarchy(kind, target, levels, p, Ut, Vt)
     return H, sigma, Ub, Vb
 
 
-def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100):
+def redo_interpolation(H: Hierarchy, sigma, U, V, converged, factor: float = 1e-3) -> None:
+    """Sec. 6.3 remedy for lagging triplets: redetermine the interpolation
+    operators by one downward sweep of the multiplicative phase, with the LS
+    weights of the test vectors and of the converged boot vectors divided by
+    1/factor (1000 in the paper), so that P and Q preferentially fit the
+    unconverged triplets.  The sweep relaxes the hierarchy's fine test
+    vectors in place and works on copies of the current boot triplets: the
+    additive iterate (sigma, U, V) is not changed.  H.levels is replaced."""
+    if H.Ut is None:
+        raise ValueError("hierarchy without test vectors (not from setup)")
+    spd = H.spd
+    p = H.params
+    A = H.levels[0].A
+    nt = H.Ut.shape[1]
+    converged = np.asarray(converged, dtype=bool)
+    wscale = np.concatenate([np.full(nt, factor), np.where(converged, factor, 1.0)])
+    ub = np.array(U, dtype=np.float64, order="C")
+    vb = None if spd else np.array(V, dtype=np.float64, order="C")
+    levels, _, _, _ = _down_sweep(A, spd, H.target, len(sigma), p, H.Ut, H.Vt,
+                                  np.array(sigma, dtype=np.float64), ub, vb, wscale)
+    H.levels = levels
+
+
+def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
+          redo_tol: float | None = None):
     """Additive phase (Sec. 4): V-cycle per triplet with sigma_j fixed, then a
     Ritz step, until max_j rho_j <= tol.  Returns (sigma, U, V, history)
-    where history[i] = rho after i outer iterations."""
+    where history[i] = rho after i outer iterations.
+
+    redo_tol (optional; the Sec. 6.3 remedy): each time the number of
+    triplets with rho_j <= redo_tol grows while some are still above it, the
+    interpolation is redetermined (redo_interpolation, H.levels replaced)
+    with those triplets counted as converged, and the cycles go on with the
+    new hierarchy.  H.redos lists the outer iterations where that happened."""
     spd = H.spd
     A = H.levels[0].A
     U = np.array(U, dtype=np.float64, order="C")
@@ -628,11 +686,21 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100):
     sigma = np.array(sigma, dtype=np.float64)
     XY = dense_XY(H.levels[-1], spd)
     hist = [residual_norms(A, spd, sigma, U, V)]
-    for _ in range(max_outer):
+    H.redos.clear()
+    nconv = 0
+    for it in range(max_outer):
         if hist[-1].max() <= tol:
             break
         Z = np.zeros_like(U)
         vcycle(H, 0, sigma, U, V, Z, None if spd else np.zeros_like(V), XY)
         sigma, U, V = ritz(A, spd, H.target, U, V)
         hist.append(residual_norms(A, spd, sigma, U, V))
+        if redo_tol is not None:
+            conv = hist[-1] <= redo_tol
+            k = int(conv.sum())
+            if nconv < k < len(conv):
+                redo_interpolation(H, sigma, U, V, conv)
+                XY = dense_XY(H.levels[-1], spd)
+                H.redos.append(it + 1)
+            nconv = max(nconv, k)
     return sigma, U, V, hist
