@@ -92,7 +92,10 @@ void samg_default_params(samg_params *p);
  * the GPU, a direct generalized SVD on the coarsest level (Sec. 3.6) and a
  * Ritz step per cycle.  A is m x n (SVD) or n x n symmetric (SPD_EIG).
  * n_b in [1, 16], n_b <= min(m, n).  Returns SAMG_E_INVALID for malformed
- * input, SAMG_E_NT_TOO_SMALL if n_t + n_b < 2. */
+ * input (CSR: row_ptr from 0 to nnz and non-decreasing, columns in range and
+ * strictly increasing within a row, finite values), SAMG_E_NT_TOO_SMALL if
+ * n_t + n_b < 2; these checks run on the host before any device call, so
+ * they report the same status on a machine without a GPU. */
 samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind kind,
                        const samg_params *params, void *cuda_stream, samg_ctx **out);
 
@@ -102,7 +105,9 @@ samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind
  * ignored for SPD_EIG), and the boot triplets (sigma: n_b values, U: m x n_b,
  * V: n x n_b, V ignored for SPD_EIG).  The library forms the Galerkin
  * operators A_{l+1} = P^t A_l Q, B_{l+1} = P^t B_l P, C_{l+1} = Q^t C_l Q
- * (Eq. coarseOp; B_0 = I, C_0 = I) on the GPU. */
+ * (Eq. coarseOp; B_0 = I, C_0 = I) on the GPU.  Every matrix is checked as
+ * in samg_setup, and the row counts of P_l, Q_l against the level above,
+ * before any device call. */
 samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, const samg_csr *Q,
                         int n_b, samg_target target, samg_kind kind, const samg_params *params,
                         const double *sigma, const double *U, const double *V, void *cuda_stream,

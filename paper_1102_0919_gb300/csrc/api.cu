@@ -235,7 +235,7 @@ const char *samg_last_error(const samg_ctx *ctx) {
 
 void samg_destroy(samg_ctx *ctx) {
     if (!ctx) return;
-    if (ctx->stream == nullptr || true) cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     delete ctx;
 }
 
@@ -248,30 +248,38 @@ samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, cons
     samg_ctx *c = new (std::nothrow) samg_ctx();
     if (!c) return SAMG_E_NOMEM;
     samg_status st = guarded(c, [&] {
-        check_device();
+        // argument checks first: they need no device
         check_common(n_b, params);
         SAMG_CHECK(A != nullptr && n_levels >= 2 && P != nullptr, SAMG_E_INVALID,
                    "import needs A, P and at least two levels");
         SAMG_CHECK(kind == SAMG_SPD_EIG || Q != nullptr, SAMG_E_INVALID, "import: Q is NULL");
+        SAMG_CHECK(kind == SAMG_SVD || kind == SAMG_SPD_EIG, SAMG_E_INVALID, "bad kind");
+        SAMG_CHECK(target == SAMG_DOMINANT || target == SAMG_MINIMAL, SAMG_E_INVALID, "bad target");
+        validate_csr(*A);
+        SAMG_CHECK(kind != SAMG_SPD_EIG || A->m == A->n, SAMG_E_INVALID, "SPD_EIG needs square A");
+        SAMG_CHECK(n_b <= std::min(A->m, A->n), SAMG_E_INVALID, "n_b > min(m, n)");
+        for (int l = 0; l + 1 < n_levels; ++l) {
+            validate_csr(P[l]);
+            const int rows_u = l == 0 ? (kind == SAMG_SPD_EIG ? A->n : A->m) : P[l - 1].n;
+            SAMG_CHECK(P[l].m == rows_u, SAMG_E_INVALID, "P_l has the wrong number of rows");
+            if (kind != SAMG_SPD_EIG) {
+                validate_csr(Q[l]);
+                const int rows_v = l == 0 ? A->n : Q[l - 1].n;
+                SAMG_CHECK(Q[l].m == rows_v, SAMG_E_INVALID, "Q_l has the wrong number of rows");
+            }
+        }
+        check_device();
         c->stream = (cudaStream_t)cuda_stream;
         c->kind = kind;
         c->target = target;
         c->prm = *params;
         c->nb = n_b;
         c->ld = block_ld(n_b);
-        SAMG_CHECK(kind != SAMG_SPD_EIG || A->m == A->n, SAMG_E_INVALID, "SPD_EIG needs square A");
-        SAMG_CHECK(n_b <= std::min(A->m, A->n), SAMG_E_INVALID, "n_b > min(m, n)");
         c->L.resize(n_levels);
         upload_csr(*A, c->L[0].A, c->stream);
         for (int l = 0; l + 1 < n_levels; ++l) {
-            const int rows_u = l == 0 ? (kind == SAMG_SPD_EIG ? A->n : A->m) : P[l - 1].n;
-            SAMG_CHECK(P[l].m == rows_u, SAMG_E_INVALID, "P_l has the wrong number of rows");
             upload_csr(P[l], c->L[l].P, c->stream);
-            if (kind != SAMG_SPD_EIG) {
-                const int rows_v = l == 0 ? A->n : Q[l - 1].n;
-                SAMG_CHECK(Q[l].m == rows_v, SAMG_E_INVALID, "Q_l has the wrong number of rows");
-                upload_csr(Q[l], c->L[l].Q, c->stream);
-            }
+            if (kind != SAMG_SPD_EIG) upload_csr(Q[l], c->L[l].Q, c->stream);
         }
         build_galerkin(*c);
         finalize_hierarchy(*c);
@@ -295,13 +303,17 @@ samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind
     samg_ctx *c = new (std::nothrow) samg_ctx();
     if (!c) return SAMG_E_NOMEM;
     samg_status st = guarded(c, [&] {
-        check_device();
+        // argument checks first: they need no device
         check_common(n_b, params);
         SAMG_CHECK(A != nullptr, SAMG_E_INVALID, "A is NULL");
+        SAMG_CHECK(kind == SAMG_SVD || kind == SAMG_SPD_EIG, SAMG_E_INVALID, "bad kind");
+        SAMG_CHECK(target == SAMG_DOMINANT || target == SAMG_MINIMAL, SAMG_E_INVALID, "bad target");
+        validate_csr(*A);
         SAMG_CHECK(kind != SAMG_SPD_EIG || A->m == A->n, SAMG_E_INVALID, "SPD_EIG needs square A");
         SAMG_CHECK(n_b <= std::min(A->m, A->n), SAMG_E_INVALID, "n_b > min(m, n)");
         SAMG_CHECK(params->n_t + n_b >= 2, SAMG_E_NT_TOO_SMALL, "n_t + n_b < 2");
         SAMG_CHECK(params->n_t >= 1 && params->n_t <= 16, SAMG_E_INVALID, "n_t must be in [1, 16]");
+        check_device();
         c->stream = (cudaStream_t)cuda_stream;
         c->kind = kind;
         c->target = target;
@@ -582,20 +594,15 @@ samg_status samg_ritz(samg_ctx *ctx, double *sigma, double *U, double *V, double
 
 // Host copy of a caller's CSR, validated (host-only entry points).
 static HCsr host_copy(const samg_csr *A, bool square) {
-    SAMG_CHECK(A && A->row_ptr && A->m > 0 && A->n > 0 && A->nnz >= 0, SAMG_E_INVALID,
-               "bad CSR");
+    SAMG_CHECK(A && A->m > 0 && A->n > 0, SAMG_E_INVALID, "bad CSR");
     SAMG_CHECK(!square || A->m == A->n, SAMG_E_INVALID, "the matrix must be square");
-    SAMG_CHECK(A->nnz == 0 || (A->col && A->val), SAMG_E_INVALID, "bad CSR");
+    validate_csr(*A);
     HCsr h;
     h.m = A->m;
     h.n = A->n;
     h.rp.assign(A->row_ptr, A->row_ptr + A->m + 1);
-    SAMG_CHECK(h.rp[0] == 0 && h.rp[A->m] == A->nnz, SAMG_E_INVALID, "bad row_ptr");
-    for (int i = 0; i < A->m; ++i) SAMG_CHECK(h.rp[i] <= h.rp[i + 1], SAMG_E_INVALID, "bad row_ptr");
     h.ci.assign(A->col, A->col + A->nnz);
     h.v.assign(A->val, A->val + A->nnz);
-    for (int64_t e = 0; e < A->nnz; ++e)
-        SAMG_CHECK(h.ci[e] >= 0 && h.ci[e] < A->n, SAMG_E_INVALID, "column out of range");
     return h;
 }
 
@@ -755,12 +762,12 @@ samg_status samg_block_gram_noalloc(const double *X, const double *Y, int64_t ro
     try {
         SAMG_CHECK(X && Y && G && rows >= 0 && nb >= 1 && nb <= 16 && ld >= nb, SAMG_E_INVALID,
                    "block_gram_noalloc: bad arguments");
-        check_device();
         const size_t need = gram_workspace(rows, nb);
         SAMG_CHECK(need <= GRAM_STATIC_DOUBLES, SAMG_E_INVALID,
                    "block_gram_noalloc: ceil(rows / 4096) * nb * nb = " + std::to_string(need) +
                        " partial sums exceed the fixed scratch of " +
                        std::to_string(GRAM_STATIC_DOUBLES) + " doubles");
+        check_device();
         // Every partial sum the final pass reads is written by the partial
         // pass of the same call, so the scratch needs no clearing.
         launch_gram(X, Y, rows, nb, ld, G, gram_static_scratch(), (cudaStream_t)cuda_stream);

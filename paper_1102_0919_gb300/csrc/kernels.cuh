@@ -64,9 +64,13 @@ void launch_diagonal(const DCsr &a, DBuf<double> &outd, DBuf<float> &outf, cudaS
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s);
 // C = A^t on the device, rows sorted.
 void transpose(const DCsr &A, DCsr &C, cudaStream_t s);
-// C = A + alpha * I pattern union helper is not needed; refresh float copy:
+// refresh the float32 copy of the values
 void refresh_float(DCsr &A, cudaStream_t s);
-// upload / download a host CSR
+// host checks of a caller's CSR (SAMG_E_INVALID): sizes, row_ptr monotone
+// from 0 to nnz, columns in range and strictly increasing in a row, finite
+// values; no device call
+void validate_csr(const samg_csr &h);
+// upload / download a host CSR (upload validates first)
 void upload_csr(const HCsr &h, DCsr &d, cudaStream_t s);
 void upload_csr(const samg_csr &h, DCsr &d, cudaStream_t s);
 void download_csr(const DCsr &d, HCsr &h, cudaStream_t s);

@@ -97,14 +97,17 @@ void refresh_float(DCsr &A, cudaStream_t s) {
     launch_convert<double, float>((size_t)A.nnz, A.vd.p, A.vf.p, s);
 }
 
-void upload_csr(const samg_csr &h, DCsr &d, cudaStream_t s) {
+void validate_csr(const samg_csr &h) {
     SAMG_CHECK(h.m >= 0 && h.n >= 0 && h.nnz >= 0, SAMG_E_INVALID, "csr: negative size");
     SAMG_CHECK(h.nnz < ((int64_t)1 << 31), SAMG_E_INVALID, "csr: nnz >= 2^31");
     SAMG_CHECK(h.row_ptr != nullptr, SAMG_E_INVALID, "csr: null row_ptr");
+    SAMG_CHECK(h.nnz == 0 || (h.col != nullptr && h.val != nullptr), SAMG_E_INVALID,
+               "csr: null col or val");
     SAMG_CHECK(h.row_ptr[0] == 0 && h.row_ptr[h.m] == h.nnz, SAMG_E_INVALID,
                "csr: row_ptr[0] != 0 or row_ptr[m] != nnz");
     for (int i = 0; i < h.m; ++i) {
-        SAMG_CHECK(h.row_ptr[i + 1] >= h.row_ptr[i], SAMG_E_INVALID, "csr: row_ptr decreasing");
+        SAMG_CHECK(h.row_ptr[i + 1] >= h.row_ptr[i] && h.row_ptr[i + 1] <= h.nnz, SAMG_E_INVALID,
+                   "csr: row_ptr decreasing");
         for (int64_t e = h.row_ptr[i]; e < h.row_ptr[i + 1]; ++e) {
             SAMG_CHECK(h.col[e] >= 0 && h.col[e] < h.n, SAMG_E_INVALID, "csr: column out of range");
             SAMG_CHECK(e == h.row_ptr[i] || h.col[e] > h.col[e - 1], SAMG_E_INVALID,
@@ -112,6 +115,10 @@ void upload_csr(const samg_csr &h, DCsr &d, cudaStream_t s) {
             SAMG_CHECK(std::isfinite(h.val[e]), SAMG_E_INVALID, "csr: non-finite value");
         }
     }
+}
+
+void upload_csr(const samg_csr &h, DCsr &d, cudaStream_t s) {
+    validate_csr(h);
     d.m = h.m;
     d.n = h.n;
     d.nnz = h.nnz;
