@@ -222,6 +222,17 @@ samg_status samg_host_ls_interp(const samg_csr *N, double theta, const int8_t *c
                                 const double *yF, const double *yC, const double *w,
                                 int64_t *nnz, int64_t *row_ptr, int32_t *col, double *val);
 
+/* Host-only strength graph of a product (no GPU needed): the strong
+ * influences (Eq. strength, sums over all columns including the diagonal)
+ * of N = A A^t, computed row by row from A without forming N, as samg_setup
+ * does for A_l A_l^t and A_l^t A_l of the dominant SVD kind (pass A^t for
+ * A^t A).  Row i of the output S (m x m) holds the j != i with
+ * |n_ij| >= theta * sum_k |n_ik|, columns increasing, values |n_ij|.  Call
+ * with row_ptr = NULL to get *nnz, then with row_ptr (m + 1), col and val
+ * (nnz) to fill S.  Returns SAMG_E_INVALID for malformed input. */
+samg_status samg_host_strength_product(const samg_csr *A, double theta, int64_t *nnz,
+                                       int64_t *row_ptr, int32_t *col, double *val);
+
 /* Host-only analysis of the exact-order Kaczmarz schedule (no GPU needed):
  * the dependency level of every row of a sweep program in natural order
  * (1 + the level of the latest earlier row sharing a column; rows of one

@@ -85,6 +85,8 @@ samg_debug_mute_band = _sig("samg_debug_mute_band", _I, _CTX, _I, _I, _I)
 samg_host_coarsen = _sig("samg_host_coarsen", _I, _P, ctypes.c_double, _P)
 samg_host_ls_interp = _sig("samg_host_ls_interp", _I, _P, ctypes.c_double, _P, _I, _P, _P, _P,
                            ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
+samg_host_strength_product = _sig("samg_host_strength_product", _I, _P, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
 samg_sweep_plan = _sig("samg_sweep_plan", _I, _P, _I, _P, ctypes.c_int64, ctypes.POINTER(_I),
                        ctypes.POINTER(_I))
 samg_block_gram_noalloc = _sig("samg_block_gram_noalloc", _I, _P, _P, ctypes.c_int64, _I, _I, _P,
@@ -101,7 +103,8 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
             "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band",
-            "samg_sweep_plan", "samg_host_coarsen", "samg_host_ls_interp"]
+            "samg_sweep_plan", "samg_host_coarsen", "samg_host_ls_interp",
+            "samg_host_strength_product"]
 
 
 def _arr(x, dtype):
@@ -376,6 +379,26 @@ def host_coarsen(N, theta):
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
     return cf
+
+
+def host_strength_product(A, theta):
+    """Host-only: strong influences of A A^t (scipy CSR, values |n_ij|),
+    computed from A without forming the product."""
+    import scipy.sparse as _sp
+
+    c = _csr(A)
+    nnz = ctypes.c_int64(0)
+    st = samg_host_strength_product(ctypes.byref(c), theta, ctypes.byref(nnz), None, None, None)
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    rp = np.zeros(c.m + 1, np.int64)
+    ci = np.zeros(max(nnz.value, 1), np.int32)
+    v = np.zeros(max(nnz.value, 1), np.float64)
+    st = samg_host_strength_product(ctypes.byref(c), theta, ctypes.byref(nnz), _ptr(rp), _ptr(ci),
+                                    _ptr(v))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    return _sp.csr_matrix((v[:nnz.value], ci[:nnz.value], rp), shape=(c.m, c.m))
 
 
 def host_ls_interp(N, theta, cf, Yf, Yc, w):

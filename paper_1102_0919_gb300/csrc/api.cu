@@ -650,23 +650,34 @@ samg_status samg_host_ls_interp(const samg_csr *N, double theta, const int8_t *c
     }
 }
 
+samg_status samg_host_strength_product(const samg_csr *A, double theta, int64_t *nnz,
+                                       int64_t *row_ptr, int32_t *col, double *val) {
+    try {
+        SAMG_CHECK(nnz && theta >= 0.0, SAMG_E_INVALID, "host_strength_product: bad arguments");
+        const HCsr h = host_copy(A, false);
+        HCsr S;
+        host_strength_product(h, theta, S);
+        *nnz = S.nnz();
+        if (row_ptr) {
+            SAMG_CHECK(col && val, SAMG_E_INVALID, "host_strength_product: output arrays missing");
+            std::copy(S.rp.begin(), S.rp.end(), row_ptr);
+            std::copy(S.ci.begin(), S.ci.end(), col);
+            std::copy(S.v.begin(), S.v.end(), val);
+        }
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
 samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_level,
                             int64_t capacity, int *depth, int *nbands) {
     try {
-        SAMG_CHECK(A && A->row_ptr && A->m > 0 && A->n > 0 && fused_count >= 0 && depth && nbands,
-                   SAMG_E_INVALID, "sweep_plan: bad arguments");
-        SAMG_CHECK(A->nnz == 0 || (A->col && A->val), SAMG_E_INVALID, "sweep_plan: bad CSR");
-        HCsr h;
-        h.m = A->m;
-        h.n = A->n;
-        h.rp.assign(A->row_ptr, A->row_ptr + A->m + 1);
-        SAMG_CHECK(h.rp[0] == 0 && h.rp[A->m] == A->nnz, SAMG_E_INVALID, "sweep_plan: bad row_ptr");
-        for (int i = 0; i < A->m; ++i)
-            SAMG_CHECK(h.rp[i] <= h.rp[i + 1], SAMG_E_INVALID, "sweep_plan: bad row_ptr");
-        h.ci.assign(A->col, A->col + A->nnz);
-        h.v.assign(A->val, A->val + A->nnz);
-        for (int64_t e = 0; e < A->nnz; ++e)
-            SAMG_CHECK(h.ci[e] >= 0 && h.ci[e] < A->n, SAMG_E_INVALID, "sweep_plan: column out of range");
+        SAMG_CHECK(fused_count >= 0 && depth && nbands, SAMG_E_INVALID, "sweep_plan: bad arguments");
+        const HCsr h = host_copy(A, false);
         std::vector<int> lv;
         plan_sweep(h, fused_count, lv, nbands);
         int d = 0;

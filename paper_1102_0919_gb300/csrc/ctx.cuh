@@ -161,6 +161,8 @@ void host_setup(samg_ctx &c, const samg_csr &A);  // multiplicative phase (setup
 // Ruge-Stueben coarsening of N; weighted LS interpolation (Eq. LS) from the
 // strong C-point influences, nf vectors per point (row-major yF, yC).
 void host_coarsen(const HCsr &N, double theta, std::vector<char> &cf);
+// strong influences of N = A A^t from A itself, without forming N
+void host_strength_product(const HCsr &A, double theta, HCsr &S);
 void host_ls_interp(const HCsr &N, double theta, const std::vector<char> &cf,
                     const std::vector<double> &yF, const std::vector<double> &yC,
                     const std::vector<double> &w, int nf, HCsr &P);

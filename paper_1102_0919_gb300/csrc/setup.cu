@@ -72,6 +72,85 @@ void strength_of(const HCsr &N, double theta, HCsr &S) {
     }
 }
 
+// Strong influences (Eq. strength) of N = A A^t without forming N.  Row i of
+// N is the sum over the entries a_ic of row i of A of a_ic times row c of
+// A^t (entries accumulated in that order into a dense per-thread row); the
+// row sum of |n_ik| over every touched k (the diagonal included) sets the
+// threshold, and only the strong j != i are kept, sorted by column.  Memory
+// is that of S and one dense row per thread: the product of a
+// term-document matrix can hold ~1e10 entries while its strong graph holds
+// at most 1/theta per row.  The rows run on up to 16 host threads, each
+// writing its own block of rows.
+void strength_product(const HCsr &A, const HCsr &At, double theta, HCsr &S) {
+    const int m = A.m;
+    S.m = S.n = m;
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (m < 4096) nt = 1;
+    const int chunk = (m + (int)nt - 1) / (int)nt;
+    struct Part {
+        std::vector<int64_t> cnt;
+        std::vector<int> ci;
+        std::vector<double> v;
+    };
+    std::vector<Part> part(nt);
+    auto work = [&](unsigned t) {
+        const int a = (int)t * chunk, b = std::min(m, a + chunk);
+        if (a >= b) return;
+        Part &out = part[t];
+        out.cnt.assign(b - a, 0);
+        std::vector<double> acc(m, 0.0);
+        std::vector<int> mark(m, -1), touched;
+        std::vector<std::pair<int, double>> keep;
+        for (int i = a; i < b; ++i) {
+            touched.clear();
+            for (int64_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+                const int c = A.ci[e];
+                const double aic = A.v[e];
+                for (int64_t f = At.rp[c]; f < At.rp[c + 1]; ++f) {
+                    const int j = At.ci[f];
+                    if (mark[j] != i) {
+                        mark[j] = i;
+                        acc[j] = 0.0;
+                        touched.push_back(j);
+                    }
+                    acc[j] += aic * At.v[f];
+                }
+            }
+            double tot = 0.0;
+            for (int j : touched) tot += std::fabs(acc[j]);
+            const double thr = theta * tot;
+            keep.clear();
+            for (int j : touched) {
+                const double x = std::fabs(acc[j]);
+                if (j != i && x > 0.0 && x >= thr) keep.push_back({j, x});
+            }
+            std::sort(keep.begin(), keep.end());
+            out.cnt[i - a] = (int64_t)keep.size();
+            for (auto &kv : keep) {
+                out.ci.push_back(kv.first);
+                out.v.push_back(kv.second);
+            }
+        }
+    };
+    if (nt == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
+        for (auto &x : th) x.join();
+    }
+    S.rp.assign(m + 1, 0);
+    S.ci.clear();
+    S.v.clear();
+    for (unsigned t = 0; t < nt; ++t) {
+        const int a = (int)t * chunk;
+        for (size_t r = 0; r < part[t].cnt.size(); ++r) S.rp[a + r + 1] = part[t].cnt[r];
+        S.ci.insert(S.ci.end(), part[t].ci.begin(), part[t].ci.end());
+        S.v.insert(S.v.end(), part[t].v.begin(), part[t].v.end());
+    }
+    for (int i = 0; i < m; ++i) S.rp[i + 1] += S.rp[i];
+}
+
 // One-pass Ruge-Stueben coarsening (Algorithm "coarsening"): repeatedly take
 // the undecided point with the largest lambda (lowest index on ties), make it
 // C, make the undecided points it strongly influences F, and raise lambda of
@@ -525,18 +604,18 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                     spgemm(L.At, L.A, Nd, s);
                     download_csr(Nd, Nv, s);
                 } else {
-                    spgemm(L.A, L.At, Nd, s);
-                    download_csr(Nd, Nu, s);
-                    DCsr Nd2;
-                    spgemm(L.At, L.A, Nd2, s);
-                    download_csr(Nd2, Nv, s);
+                    // dominant SVD kind: the strength graphs of A A^t and
+                    // A^t A come from A and A^t directly (the LS fits need
+                    // no N here, R14 being a minimal-kind step)
+                    HCsr hA, hAt;
+                    download_csr(L.A, hA, s);
+                    download_csr(L.At, hAt, s);
+                    strength_product(hA, hAt, p.theta, Su);
+                    strength_product(hAt, hA, p.theta, Sv);
                 }
-                strength_of(Nv, p.theta, Sv);
+                if (spd || st.induced) strength_of(Nv, p.theta, Sv);
                 cfv = rs_split(Sv);
-                if (!spd && !st.induced) {
-                    strength_of(Nu, p.theta, Su);
-                    cfu = rs_split(Su);
-                }
+                if (!spd && !st.induced) cfu = rs_split(Su);
                 if (l == 0) {
                     st.have0 = true;
                     st.N0u = Nu; st.N0v = Nv; st.S0u = Su; st.S0v = Sv; st.cf0u = cfu; st.cf0v = cfv;
@@ -705,6 +784,24 @@ void host_coarsen(const HCsr &N, double theta, std::vector<char> &cf) {
     HCsr S;
     strength_of(N, theta, S);
     cf = rs_split(S);
+}
+
+void host_strength_product(const HCsr &A, double theta, HCsr &S) {
+    HCsr At;
+    At.m = A.n;
+    At.n = A.m;
+    At.rp.assign(A.n + 1, 0);
+    for (int64_t e = 0; e < A.nnz(); ++e) At.rp[A.ci[e] + 1]++;
+    for (int j = 0; j < A.n; ++j) At.rp[j + 1] += At.rp[j];
+    At.ci.resize(A.nnz());
+    At.v.resize(A.nnz());
+    std::vector<int64_t> f(At.rp.begin(), At.rp.end() - 1);
+    for (int i = 0; i < A.m; ++i)
+        for (int64_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+            At.ci[f[A.ci[e]]] = i;
+            At.v[f[A.ci[e]]++] = A.v[e];
+        }
+    strength_product(A, At, theta, S);
 }
 
 void host_ls_interp(const HCsr &N, double theta, const std::vector<char> &cf,

@@ -53,3 +53,45 @@ def test_ls_interpolation_matches_oracle(name):
     assert np.array_equal(P_lib.indptr, P_ref.indptr)
     assert np.array_equal(P_lib.indices, P_ref.indices)
     assert np.abs(P_lib.data - P_ref.data).max() <= 1e-10 * max(np.abs(P_ref.data).max(), 1.0)
+
+
+def _strength_cases():
+    G = W.gradient(12).to_scipy()
+    td = W.termdoc(6000, 1500, seed=77, kmax=300).to_scipy()      # > 4096 rows: threaded path
+    ti = td.copy()
+    ti.data = np.round(np.expm1(ti.data))                          # integer counts tf
+    return {"gradient": G, "laplacian": W.laplacian5(16).to_scipy(), "termdoc_counts": ti,
+            "termdoc": td}
+
+
+@pytest.mark.parametrize("name", ["gradient", "laplacian", "termdoc_counts", "termdoc"])
+@pytest.mark.parametrize("side", ["AAt", "AtA"])
+def test_strength_of_product_matches_oracle(name, side):
+    # the setup's strength graph of A A^t (or A^t A) formed from A alone
+    # equals the oracle's strength of the explicit product: bit for bit for
+    # integer entries (every sum exact), pattern exact and values to rounding
+    # otherwise
+    A = oracle.samg._csr(_strength_cases()[name])
+    if side == "AtA":
+        A = oracle.samg._csr(A.T)
+    theta = 0.03 if name.startswith("termdoc") else 0.06
+    S_lib = samg.host_strength_product(A, theta)
+    S_ref = oracle.strength(A @ A.T, theta)
+    S_lib.sort_indices()
+    S_ref.sort_indices()
+    assert np.array_equal(S_lib.indptr, S_ref.indptr)
+    assert np.array_equal(S_lib.indices, S_ref.indices)
+    if name == "termdoc":
+        assert np.allclose(S_lib.data, S_ref.data, rtol=1e-13, atol=0)
+    else:
+        assert np.array_equal(S_lib.data, S_ref.data)
+    # and the coarsening on it is the oracle's
+    assert np.array_equal(oracle.rs_coarsen(S_lib), oracle.rs_coarsen(S_ref))
+
+
+def test_strength_of_product_rejects_malformed_input():
+    bad = sp.csr_matrix(np.eye(3))
+    bad.indices = bad.indices.copy()
+    bad.indices[1] = 7
+    with pytest.raises(samg.SamgError):
+        samg.host_strength_product(bad, 0.06)
