@@ -113,6 +113,31 @@ samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, cons
                         const double *sigma, const double *U, const double *V, void *cuda_stream,
                         samg_ctx **out);
 
+/* A hierarchy and its boot triplets in one binary file.  The paper has no
+ * file format; the file keeps the solve phase's inputs.
+ *  - samg_export writes the context's finest A, its P_l and Q_l as the solve
+ *    uses them (minimal SVD kind: P_0 = A Q_0, P_l = Q_l below), and the
+ *    current boot triplets.
+ *  - samg_write_hierarchy writes the same file from host arrays given as to
+ *    samg_import (host only, no GPU needed).
+ *  - samg_import_file builds a context from such a file as samg_import does
+ *    (the Galerkin operators are rebuilt from P and Q).
+ * Layout, little-endian: "SAMGHIER", u32 version (1), u32 kind, u32 target,
+ * u32 n_b, u32 n_levels; csr A; for each level below the coarsest csr P_l,
+ * then csr Q_l (SVD kind only); f64 sigma[n_b], U[rows_u][n_b], V[n][n_b]
+ * (SVD kind only; rows_u = m, or n for SPD_EIG); u64 FNV-1a hash of every
+ * byte before it.  csr = i32 m, i32 n, i64 nnz, i64 row_ptr[m + 1],
+ * i32 col[nnz], f64 val[nnz].  A missing, truncated, corrupted or
+ * other-version file, or malformed matrices, give SAMG_E_INVALID before any
+ * device call. */
+samg_status samg_export(samg_ctx *ctx, const char *path);
+samg_status samg_write_hierarchy(const char *path, const samg_csr *A, int n_levels,
+                                 const samg_csr *P, const samg_csr *Q, int n_b, samg_target target,
+                                 samg_kind kind, const double *sigma, const double *U,
+                                 const double *V);
+samg_status samg_import_file(const char *path, const samg_params *params, void *cuda_stream,
+                             samg_ctx **out);
+
 void samg_destroy(samg_ctx *ctx);
 const char *samg_last_error(const samg_ctx *ctx);
 

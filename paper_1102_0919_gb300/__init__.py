@@ -85,6 +85,11 @@ samg_debug_mute_band = _sig("samg_debug_mute_band", _I, _CTX, _I, _I, _I)
 samg_host_coarsen = _sig("samg_host_coarsen", _I, _P, ctypes.c_double, _P)
 samg_host_ls_interp = _sig("samg_host_ls_interp", _I, _P, ctypes.c_double, _P, _I, _P, _P, _P,
                            ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
+samg_export = _sig("samg_export", _I, _CTX, ctypes.c_char_p)
+samg_write_hierarchy = _sig("samg_write_hierarchy", _I, ctypes.c_char_p, _P, _I, _P, _P, _I, _I, _I,
+                            _P, _P, _P)
+samg_import_file = _sig("samg_import_file", _I, ctypes.c_char_p, _P, ctypes.c_void_p,
+                        ctypes.POINTER(_CTX))
 samg_host_strength_product = _sig("samg_host_strength_product", _I, _P, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
 samg_sweep_plan = _sig("samg_sweep_plan", _I, _P, _I, _P, ctypes.c_int64, ctypes.POINTER(_I),
@@ -104,7 +109,8 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
             "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band",
             "samg_sweep_plan", "samg_host_coarsen", "samg_host_ls_interp",
-            "samg_host_strength_product"]
+            "samg_host_strength_product", "samg_export", "samg_write_hierarchy",
+            "samg_import_file"]
 
 
 def _arr(x, dtype):
@@ -195,6 +201,26 @@ class Solver:
         if st != OK:
             raise SamgError(st, samg_last_error(None).decode())
         return cls(ctx, nb, k, t, c.m, c.n)
+
+    @classmethod
+    def from_file(cls, path, stream=None, **params):
+        """Context from a hierarchy file (samg_import_file)."""
+        p = make_params(**params)
+        ctx = _CTX()
+        st = samg_import_file(os.fsencode(path), ctypes.byref(p), _stream(stream), ctypes.byref(ctx))
+        if st != OK:
+            raise SamgError(st, samg_last_error(None).decode())
+        # n_b, kind, target and the finest shape from the file's header (the
+        # library has just validated the whole file)
+        with open(path, "rb") as f:
+            head = f.read(36)
+        kind, target, nb = np.frombuffer(head[12:24], dtype="<u4")
+        m, n = np.frombuffer(head[28:36], dtype="<i4")
+        return cls(ctx, int(nb), int(kind), int(target), int(m), int(n))
+
+    def export(self, path):
+        """Write the hierarchy and the current boot triplets (samg_export)."""
+        self._check(samg_export(self._ctx, os.fsencode(path)))
 
     def close(self):
         if self._ctx:
@@ -379,6 +405,25 @@ def host_coarsen(N, theta):
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
     return cf
+
+
+def write_hierarchy(path, A, Ps, Qs, sigma, U, V, target="minimal", kind="svd"):
+    """Host-only: write a hierarchy file from host arrays (samg_write_hierarchy)."""
+    t = MINIMAL if target == "minimal" else DOMINANT
+    k = SPD_EIG if kind == "spd" else SVD
+    c = _csr(A)
+    Pl = [_csr(x) for x in Ps]
+    P = (_Csr * len(Pl))(*Pl)
+    Ql = [_csr(x) for x in Qs] if k == SVD else []
+    Q = (_Csr * len(Ql))(*Ql) if Ql else None
+    s = _arr(sigma, np.float64)
+    u = _arr(U, np.float64)
+    v = _arr(V, np.float64) if k == SVD else None
+    st = samg_write_hierarchy(os.fsencode(path), ctypes.byref(c), len(Ps) + 1, P, Q, len(s), t, k,
+                              _ptr(s), _ptr(u), _ptr(v))
+    del Pl, Ql
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
 
 
 def host_strength_product(A, theta):

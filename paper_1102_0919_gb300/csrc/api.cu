@@ -9,6 +9,7 @@
 #include <string>
 
 #include "ctx.cuh"
+#include "hierfile.cuh"
 
 using namespace samg;
 
@@ -648,6 +649,112 @@ samg_status samg_host_ls_interp(const samg_csr *N, double theta, const int8_t *c
     } catch (...) {
         return SAMG_E_INVALID;
     }
+}
+
+// host CSR -> caller-style view (arrays stay owned by h)
+static samg_csr view_of(const HCsr &h) {
+    return samg_csr{h.m, h.n, h.nnz(), h.rp.data(), h.ci.data(), h.v.data()};
+}
+
+samg_status samg_write_hierarchy(const char *path, const samg_csr *A, int n_levels,
+                                 const samg_csr *P, const samg_csr *Q, int n_b, samg_target target,
+                                 samg_kind kind, const double *sigma, const double *U,
+                                 const double *V) {
+    try {
+        SAMG_CHECK(path && A && P && n_levels >= 2 && n_levels <= 64 && n_b >= 1 && n_b <= 16,
+                   SAMG_E_INVALID, "write_hierarchy: bad arguments");
+        SAMG_CHECK(kind == SAMG_SVD || kind == SAMG_SPD_EIG, SAMG_E_INVALID, "bad kind");
+        SAMG_CHECK(target == SAMG_DOMINANT || target == SAMG_MINIMAL, SAMG_E_INVALID, "bad target");
+        const bool spd = kind == SAMG_SPD_EIG;
+        SAMG_CHECK(spd || Q, SAMG_E_INVALID, "write_hierarchy: Q is NULL");
+        SAMG_CHECK(sigma && U && (spd || V), SAMG_E_INVALID, "write_hierarchy: triplets missing");
+        HierFile h;
+        h.kind = kind;
+        h.target = target;
+        h.nb = n_b;
+        h.A = host_copy(A, spd);
+        for (int l = 0; l + 1 < n_levels; ++l) {
+            const int rows_u = l == 0 ? (spd ? A->n : A->m) : P[l - 1].n;
+            SAMG_CHECK(P[l].m == rows_u, SAMG_E_INVALID, "P_l has the wrong number of rows");
+            h.P.push_back(host_copy(&P[l], false));
+            if (!spd) {
+                const int rows_v = l == 0 ? A->n : Q[l - 1].n;
+                SAMG_CHECK(Q[l].m == rows_v, SAMG_E_INVALID, "Q_l has the wrong number of rows");
+                h.Q.push_back(host_copy(&Q[l], false));
+            }
+        }
+        const size_t ru = (size_t)(spd ? A->n : A->m);
+        h.sigma.assign(sigma, sigma + n_b);
+        h.U.assign(U, U + ru * n_b);
+        if (!spd) h.V.assign(V, V + (size_t)A->n * n_b);
+        write_hierarchy_file(path, h);
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "host allocation failed";
+        return SAMG_E_NOMEM;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
+samg_status samg_import_file(const char *path, const samg_params *params, void *cuda_stream,
+                             samg_ctx **out) {
+    if (!out) return SAMG_E_INVALID;
+    *out = nullptr;
+    HierFile h;
+    try {
+        SAMG_CHECK(path != nullptr, SAMG_E_INVALID, "import_file: path is NULL");
+        read_hierarchy_file(path, h);
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "host allocation failed";
+        return SAMG_E_NOMEM;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+    const samg_csr A = view_of(h.A);
+    std::vector<samg_csr> P, Q;
+    for (const HCsr &x : h.P) P.push_back(view_of(x));
+    for (const HCsr &x : h.Q) Q.push_back(view_of(x));
+    return samg_import(&A, (int)h.P.size() + 1, P.data(), Q.empty() ? nullptr : Q.data(), h.nb,
+                       h.target, h.kind, params, h.sigma.data(), h.U.data(),
+                       h.V.empty() ? nullptr : h.V.data(), cuda_stream, out);
+}
+
+samg_status samg_export(samg_ctx *ctx, const char *path) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        samg_ctx &c = *ctx;
+        SAMG_CHECK(path != nullptr, SAMG_E_INVALID, "export: path is NULL");
+        SAMG_CHECK(c.nlev() >= 2, SAMG_E_INVALID, "export: no hierarchy");
+        HierFile h;
+        h.kind = c.kind;
+        h.target = c.target;
+        h.nb = c.nb;
+        download_csr(c.L[0].A, h.A, c.stream);
+        h.P.resize(c.nlev() - 1);
+        if (!c.spd()) h.Q.resize(c.nlev() - 1);
+        for (int l = 0; l + 1 < c.nlev(); ++l) {
+            download_csr(c.L[l].P, h.P[l], c.stream);
+            if (!c.spd()) download_csr(c.L[l].Q, h.Q[l], c.stream);
+        }
+        std::vector<double> sg(c.ld);
+        c.sigma.download(sg.data(), c.ld, c.stream);
+        h.U.resize((size_t)urows(c, 0) * c.nb);
+        get_block(c, c.U, urows(c, 0), h.U.data());
+        if (!c.spd()) {
+            h.V.resize((size_t)c.L[0].n * c.nb);
+            get_block(c, c.V, c.L[0].n, h.V.data());
+        }
+        SAMG_CUDA(cudaStreamSynchronize(c.stream));
+        h.sigma.assign(sg.begin(), sg.begin() + c.nb);
+        write_hierarchy_file(path, h);
+    });
 }
 
 samg_status samg_host_strength_product(const samg_csr *A, double theta, int64_t *nnz,
