@@ -203,15 +203,15 @@ void check_kaczmarz(samg_ctx &c) {
 }  // namespace
 
 namespace samg {
-uint64_t &launch_counter() {
-    static uint64_t n = 0;
+std::atomic<uint64_t> &launch_counter() {
+    static std::atomic<uint64_t> n{0};
     return n;
 }
 }  // namespace samg
 
 extern "C" {
 
-uint64_t samg_launch_count(void) { return samg::launch_counter(); }
+uint64_t samg_launch_count(void) { return samg::launch_counter().load(); }
 
 void samg_default_params(samg_params *p) {
     if (!p) return;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -114,8 +115,9 @@ struct HCsr {
 
 inline int round_up(int x, int k) { return (x + k - 1) / k * k; }
 
-// Count of kernel launches issued by the library (samg_launch_count).
-uint64_t &launch_counter();
+// Count of kernel launches issued by the library (samg_launch_count); atomic,
+// since contexts may be driven from several host threads.
+std::atomic<uint64_t> &launch_counter();
 #define SAMG_COUNT_LAUNCH() (++::samg::launch_counter())
 
 // Columns of a device vector block: n_b padded to a multiple of 4 (16-byte rows

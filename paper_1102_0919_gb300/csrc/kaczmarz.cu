@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "kaczmarz.cuh"
 
@@ -747,18 +748,27 @@ void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaS
     const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + (size_t)KZ_NBUF * SG::stride;
     SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
                "kaczmarz: vector blocks must be 16-byte aligned");
-    // per kernel instance: the largest dynamic shared memory set so far, and
-    // the SM count; per schedule and instance: the resident CTA count
-    static size_t smem_set = 0;
-    static int nsm = 0;
-    if (smem > smem_set) {
-        SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = smem;
-    }
-    if (!nsm) {
-        int dev = 0;
-        SAMG_CUDA(cudaGetDevice(&dev));
-        SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // per kernel instance and device (a function attribute is set per
+    // device): the largest dynamic shared memory set so far and the SM
+    // count, under a lock since contexts may launch from several host
+    // threads; per schedule and instance: the resident CTA count
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static size_t smem_set[MAXDEV] = {};
+    static int nsm_of[MAXDEV] = {};
+    int dev = 0;
+    SAMG_CUDA(cudaGetDevice(&dev));
+    SAMG_CHECK(dev >= 0 && dev < MAXDEV, SAMG_E_CUDA, "kaczmarz: device ordinal out of range");
+    int nsm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem > smem_set[dev]) {
+            SAMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            smem_set[dev] = smem;
+        }
+        if (!nsm_of[dev])
+            SAMG_CUDA(cudaDeviceGetAttribute(&nsm_of[dev], cudaDevAttrMultiProcessorCount, dev));
+        nsm = nsm_of[dev];
     }
     const int key = (int)sizeof(T) * 64 + LD * 4 + MODE;
     int &grid = ks.grid_cache[key & 255];
