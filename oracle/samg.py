@@ -69,7 +69,7 @@ from . import build as _build
 _LIB = None
 
 DEFAULTS = dict(n_t=8, theta=0.06, mu_t=8, mu_b=4, mu_tJ=1, mu_bJ=1, omega_J=0.7,
-                n_mult=10, coarsest_max=100, max_levels=30, seed=20110204)
+                n_mult=10, coarsest_max=100, max_levels=30, seed=20110204, coarse_drop=1)
 
 
 def _lib():
@@ -389,16 +389,16 @@ def coarsest_triplets(L: Level, spd: bool, target: str, nb: int):
             np.ascontiguousarray(Z[m:, sel] * s))
 
 
-def coarsest_pinv_apply(XY, sigma, K, T, spd: bool):
+def coarsest_pinv_apply(XY, sigma, K, T, spd: bool, drop: int = 1):
     """[u; v] = (X - s_j Y)^+ [kappa; tau] per column j, with the SVD
     pseudo-inverse leaving out the single smallest singular value (Sec. 4.2,
-    R7)."""
+    R7).  drop > 1 leaves out that many (a variant, not the paper's)."""
     X, Y = XY
     rhs = K if spd else np.vstack([K, T])
     out = np.zeros_like(rhs)
     for j in range(rhs.shape[1]):
         Uu, s, Vt = np.linalg.svd(X - sigma[j] * Y)
-        k = len(s) - 1                    # s is descending: drop the last
+        k = len(s) - drop                 # s is descending: drop the last
         out[:, j] = Vt[:k].T @ ((Uu[:, :k].T @ rhs[:, j]) / s[:k])
     if spd:
         return out, None
@@ -466,7 +466,7 @@ def vcycle(H: Hierarchy, l: int, sigma, U, V, K, T, coarse_XY=None) -> None:
     L = H.levels[l]
     if l == len(H.levels) - 1:
         XY = coarse_XY if coarse_XY is not None else dense_XY(L, spd)
-        u, v = coarsest_pinv_apply(XY, sigma, K, T, spd)
+        u, v = coarsest_pinv_apply(XY, sigma, K, T, spd, p.get("coarse_drop", 1))
         U[:] = u
         if not spd:
             V[:] = v

@@ -220,6 +220,10 @@ def test_coarsest_pinv_drops_only_smallest_singular_value():
     expect = K[:, 0] / d
     expect[1] = 0.0
     assert np.allclose(out[:, 0], expect)
+    # the two-value variant also leaves out the next smallest |d| (2.0)
+    out, _ = oracle.coarsest_pinv_apply((X, Y), np.array([0.5]), K, None, True, drop=2)
+    expect[2] = 0.0
+    assert np.allclose(out[:, 0], expect)
 
 
 # ---------------------------------------------------------------- Ritz
