@@ -19,7 +19,8 @@ silent the readings below are used (numbers as in the design notes):
 * R6  coarsest level: max(m_l, n_l) <= coarsest_max, or the coarsening keeps
   more than 90% of the points, or min(m_c, n_c) < 2 n_b, or max_levels.
 * R7  coarsest additive solve: SVD pseudo-inverse of X - sigma_j Y with the
-  single smallest singular value left out.
+  single smallest singular value left out (params["coarse_drop"] > 1 leaves
+  out more: a variant, not the paper's).
 * R8  strength sums run over all columns including the diagonal.
 * R9  Ruge-Stueben ties go to the lowest index.
 * R10 coarse points are numbered in increasing fine index.
