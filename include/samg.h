@@ -272,6 +272,30 @@ samg_status samg_host_strength_product(const samg_csr *A, double theta, int64_t 
 samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_level,
                             int64_t capacity, int *depth, int *nbands);
 
+/* Host-only export of an exact-order sweep schedule, for tests that replay
+ * it on the CPU (the paper has no counterpart): the schedule the kernels
+ * receive for one sweep over the rows of A (fused_count = 0) or for the fused
+ * program of fused_count minimal-SVD relaxations with B = I, C = I, with
+ * float64 coefficients.  Call with buf = NULL (capacity 0) to get *size,
+ * then with a buffer of that many bytes.  Layout, little-endian:
+ *   i32 rows, cols, nbands, nlevels, nchunks, max_slots, mode, shifted;
+ *   i64 nreq, image_bytes;
+ *   i32 band_chunk[nbands + 1];
+ *   per chunk: i32 L0, nl, nr, ne, nx, bytes; i64 offset;
+ *   per level: i32 first requirement, requirement count, publish, 0;
+ *   per requirement: i32 band, levels that band must have completed;
+ *   the chunk images (float64 coefficients).
+ * A chunk image holds, at 16-byte aligned offsets: per level {first row,
+ * rows, lanes log2, has requirements} (4 x i32); per row {right-hand-side
+ * row, first entry | entries << 16} (2 x i32); per row 1 / |a_r|^2 (f64);
+ * per entry {column, flags} (2 x i32: 1 first touch in the band, 2 last
+ * touch, 4 staged, window slot + 1 in bits 3-14, staged index from bit 15);
+ * per entry a (f64); per entry b (f64, shifted programs only); per staged
+ * value its column (i32).  Returns SAMG_E_INVALID for a malformed CSR or a
+ * short buffer. */
+samg_status samg_sweep_schedule(const samg_csr *A, int fused_count, unsigned char *buf,
+                                int64_t capacity, int64_t *size);
+
 /* Test hook for the bounded device waits (the paper has no counterpart):
  * from now on band `band` of the Kaczmarz schedules of level `level`
  * (which: 0 the single sweep over the rows of A, 1 over the rows of A^t,

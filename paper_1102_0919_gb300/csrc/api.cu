@@ -804,6 +804,58 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
     }
 }
 
+samg_status samg_sweep_schedule(const samg_csr *A, int fused_count, unsigned char *buf,
+                                int64_t capacity, int64_t *size) {
+    try {
+        SAMG_CHECK(fused_count >= 0 && size && (capacity == 0 || buf), SAMG_E_INVALID,
+                   "sweep_schedule: bad arguments");
+        const HCsr h = host_copy(A, false);
+        HostSched hs;
+        host_schedule(h, fused_count, hs);
+        std::vector<unsigned char> out;
+        auto put32 = [&](int32_t v) {
+            const unsigned char *q = reinterpret_cast<const unsigned char *>(&v);
+            out.insert(out.end(), q, q + 4);
+        };
+        auto put64 = [&](int64_t v) {
+            const unsigned char *q = reinterpret_cast<const unsigned char *>(&v);
+            out.insert(out.end(), q, q + 8);
+        };
+        for (int32_t v : {hs.rows, hs.cols, hs.nbands, hs.nlevels, hs.nchunks, hs.max_slots,
+                          hs.mode, (int32_t)hs.shifted})
+            put32(v);
+        put64((int64_t)hs.req.size());
+        put64((int64_t)hs.img_d.size());
+        for (int v : hs.band_chunk) put32(v);
+        for (const KChunk &c : hs.chunk) {
+            for (int32_t v : {c.L0, c.nl, c.nr, c.ne, c.nx, c.bytes_d}) put32(v);
+            put64(c.off_d);
+        }
+        for (const int4 &l : hs.lvl)
+            for (int32_t v : {l.x, l.y, l.z, l.w}) put32(v);
+        for (const int2 &r : hs.req) {
+            put32(r.x);
+            put32(r.y);
+        }
+        out.insert(out.end(), hs.img_d.begin(), hs.img_d.end());
+        *size = (int64_t)out.size();
+        if (buf) {
+            SAMG_CHECK(capacity >= (int64_t)out.size(), SAMG_E_INVALID,
+                       "sweep_schedule: buffer smaller than the schedule");
+            std::copy(out.begin(), out.end(), buf);
+        }
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "host allocation failed";
+        return SAMG_E_NOMEM;
+    } catch (...) {
+        return SAMG_E_INVALID;
+    }
+}
+
 samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {

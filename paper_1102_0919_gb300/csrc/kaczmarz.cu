@@ -852,7 +852,7 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
 // of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
 // block Gauss-Seidel relaxations (b entries read the other unknown with
 // coefficient -s_j and are not updated; norms from a).
-void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s) {
+void build_host(const Pattern &p, int mode, HostSched &ks) {
     const int rows = p.rows, cols = p.cols;
     ks.rows = rows;
     ks.cols = cols;
@@ -1059,14 +1059,35 @@ void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s) 
     ks.max_slots = max_slots;
     ks.nent = nent;
     ks.nchunks = (int)chunk.size();
-    // 3. upload
-    ks.band_chunk.upload(band_chunk.data(), band_chunk.size(), s);
-    ks.chunk.upload(chunk.data(), chunk.size(), s);
-    ks.lvl.upload(lvl.data(), lvl.size(), s);
-    ks.img_f.upload(img_f.data(), img_f.size(), s);
-    ks.img_d.upload(img_d.data(), img_d.size(), s);
     if (req.empty()) req.push_back(make_int2(0, 0));
-    ks.req.upload(req.data(), req.size(), s);
+    ks.band_chunk = std::move(band_chunk);
+    ks.chunk = std::move(chunk);
+    ks.lvl = std::move(lvl);
+    ks.img_f = std::move(img_f);
+    ks.img_d = std::move(img_d);
+    ks.req = std::move(req);
+}
+
+void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s) {
+    HostSched h;
+    build_host(p, mode, h);
+    ks.rows = h.rows;
+    ks.cols = h.cols;
+    ks.shifted = h.shifted;
+    ks.mode = h.mode;
+    ks.nbands = h.nbands;
+    ks.nlevels = h.nlevels;
+    ks.max_slots = h.max_slots;
+    ks.nent = h.nent;
+    ks.nchunks = h.nchunks;
+    const int nb = h.nbands;
+    // upload
+    ks.band_chunk.upload(h.band_chunk.data(), h.band_chunk.size(), s);
+    ks.chunk.upload(h.chunk.data(), h.chunk.size(), s);
+    ks.lvl.upload(h.lvl.data(), h.lvl.size(), s);
+    ks.img_f.upload(h.img_f.data(), h.img_f.size(), s);
+    ks.img_d.upload(h.img_d.data(), h.img_d.size(), s);
+    ks.req.upload(h.req.data(), h.req.size(), s);
     ks.progress.alloc(std::max(nb, 1));
     ks.progress.zero(s);
     ks.ctl.alloc(1);
@@ -1138,7 +1159,12 @@ void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const H
     build_from_pattern(p, 2, ks, s);
 }
 
-void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *nbands) {
+namespace {
+
+// The program of one sweep over the rows of A (fused_count 0), or of
+// fused_count minimal-SVD relaxations with B = I, C = I, as
+// build_kschedule_fused forms it (right-hand-side rows i and m + j).
+Pattern sweep_pattern(const HCsr &A, int fused_count) {
     Pattern p;
     if (fused_count <= 0) {
         p = merge_pattern(A, nullptr);
@@ -1178,14 +1204,27 @@ void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *n
                 append_row(p, A, i, 0, false);
                 append_row(p, I_m, i, n, true);
                 p.rp.push_back((int64_t)p.ci.size());
+                p.rhs.push_back(i);
             }
             for (int j = 0; j < n; ++j) {
                 append_row(p, I_n, j, 0, true);
                 append_row(p, At, j, n, false);
                 p.rp.push_back((int64_t)p.ci.size());
+                p.rhs.push_back(m + j);
             }
         }
     }
+    return p;
+}
+
+}  // namespace
+
+void host_schedule(const HCsr &A, int fused_count, HostSched &h) {
+    build_host(sweep_pattern(A, fused_count), fused_count > 0 ? 2 : 0, h);
+}
+
+void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *nbands) {
+    const Pattern p = sweep_pattern(A, fused_count);
     levels = global_levels(p);
     BandWork w(p.cols);
     *nbands = (int)form_bands(p, levels, w).size() - 1;

@@ -21,6 +21,8 @@
 // ever waits for bands that are already running or finished.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace samg {
@@ -63,6 +65,24 @@ struct KSched {
     int *err = nullptr;        // error word shared by a context's schedules
                                // (null: the schedule's own ctl->err)
 };
+
+// The host side of a schedule, before upload (same arrays as KSched).
+struct HostSched {
+    int rows = 0, cols = 0, nbands = 0, nlevels = 0, nchunks = 0, max_slots = 0;
+    int64_t nent = 0;
+    bool shifted = false;
+    int mode = 0;
+    std::vector<int> band_chunk;
+    std::vector<KChunk> chunk;
+    std::vector<int4> lvl;
+    std::vector<unsigned char> img_f, img_d;
+    std::vector<int2> req;
+};
+
+// Host-only: the schedule of one sweep over the rows of A (fused_count 0,
+// mode 0) or of the fused program of fused_count minimal-SVD relaxations
+// with B = I, C = I (mode 2), as the kernels receive it.
+void host_schedule(const HCsr &A, int fused_count, HostSched &h);
 
 // Build the schedule of the rows of A (shift form when B != nullptr: rows of
 // A - s B over the union pattern).  Host CSR inputs.

@@ -1,0 +1,106 @@
+"""The exact-order sweep schedules the kernels receive, replayed on the CPU
+(tests/sweep_replay.py) against the oracle's sequential Kaczmarz sweeps:
+single sweeps and fused block Gauss-Seidel relaxation programs, on operators
+whose schedules span many bands, chunks and cross-band requirements.  The
+replay runs the bands in the most eager order the recorded requirements
+allow, so a missing requirement reads a stale value."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+import workloads as W
+from sweep_replay import parse, replay
+
+samg = pytest.importorskip("paper_1102_0919_gb300")
+
+
+def _rand_rect(m, n, seed, dens=0.02):
+    rng = np.random.default_rng(seed)
+    R = sp.random(m, n, density=dens, random_state=rng, format="csr")
+    # a few long rows (more than 32 entries) and no empty row
+    for i in rng.choice(m, 3, replace=False):
+        R[i, rng.choice(n, 40, replace=False)] = 1.0
+    R = R + sp.csr_matrix((np.ones(m), (np.arange(m), np.arange(m) % n)), shape=(m, n))
+    R = sp.csr_matrix(R)
+    R.sort_indices()
+    return R
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name", ["gradient48", "laplacian40", "random"])
+def test_single_sweep_schedule_replays_the_sequential_sweep(name):
+    A = {"gradient48": lambda: W.gradient(48).to_scipy(),
+         "laplacian40": lambda: W.laplacian5(40).to_scipy(),
+         "random": lambda: _rand_rect(3000, 1200, 5)}[name]()
+    A = oracle.samg._csr(A)
+    S = parse(samg.sweep_schedule(A, 0))
+    assert S["mode"] == 0 and S["rows"] == A.shape[0]
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((A.shape[1], 8))
+    rhs = rng.standard_normal((A.shape[0], 8))
+    got = replay(S, X.copy(), rhs)
+    ref = X.copy()
+    oracle.kaczmarz_sweep(A, ref, rhs)
+    assert rel(got, ref) < 1e-11, rel(got, ref)
+
+
+@pytest.mark.parametrize("N,count", [(32, 1), (32, 4), (96, 4)])
+def test_fused_relaxation_schedule_replays_block_gauss_seidel(N, count):
+    A = W.gradient(N).to_scipy()
+    m, n = A.shape
+    S = parse(samg.sweep_schedule(A, count))
+    assert S["mode"] == 2 and S["rows"] == count * (m + n)
+    if N == 96:
+        assert S["nbands"] >= 8 and len(S["req"]) >= 8     # many bands and requirements
+    rng = np.random.default_rng(N + count)
+    sig = np.linspace(3.0, 9.0, 8)
+    U = rng.standard_normal((m, 8))
+    V = rng.standard_normal((n, 8))
+    K = rng.standard_normal((m, 8))
+    T = rng.standard_normal((n, 8))
+    z = replay(S, np.vstack([V, U]), np.vstack([K, T]), sig)
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    Ur, Vr = U.copy(), V.copy()
+    for _ in range(count):
+        oracle.relax_boot(L0, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+    assert rel(z[:n], Vr) < 1e-10, rel(z[:n], Vr)
+    assert rel(z[n:], Ur) < 1e-10, rel(z[n:], Ur)
+
+
+def test_fused_schedule_of_a_random_operator():
+    A = _rand_rect(1500, 700, 9, dens=0.01)
+    m, n = A.shape
+    S = parse(samg.sweep_schedule(A, 2))
+    rng = np.random.default_rng(3)
+    sig = np.linspace(0.5, 2.0, 4)
+    U, V = rng.standard_normal((m, 4)), rng.standard_normal((n, 4))
+    K, T = rng.standard_normal((m, 4)), rng.standard_normal((n, 4))
+    z = replay(S, np.vstack([V, U]), np.vstack([K, T]), sig)
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    Ur, Vr = U.copy(), V.copy()
+    for _ in range(2):
+        oracle.relax_boot(L0, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+    assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10
+
+
+def test_replay_detects_a_dropped_requirement():
+    # the replay is only evidence if it can fail: remove every cross-band
+    # requirement of a multi-band schedule and the eager band order must
+    # produce a different (stale) result
+    A = W.gradient(96).to_scipy()
+    m, n = A.shape
+    S = parse(samg.sweep_schedule(A, 4))
+    lvl = S["lvl"].copy()
+    lvl[:, 1] = 0
+    S["lvl"] = lvl
+    rng = np.random.default_rng(2)
+    z0 = rng.standard_normal((n + m, 8))
+    rhs = rng.standard_normal((m + n, 8))
+    with pytest.raises(AssertionError):
+        z = replay(S, z0.copy(), rhs, np.linspace(3.0, 9.0, 8))
+        good = replay(parse(samg.sweep_schedule(A, 4)), z0.copy(), rhs, np.linspace(3.0, 9.0, 8))
+        assert rel(z, good) < 1e-12
