@@ -804,14 +804,14 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
     }
 }
 
-samg_status samg_sweep_schedule(const samg_csr *A, int fused_count, unsigned char *buf,
+samg_status samg_sweep_schedule(const samg_csr *A, int fused_count, int spd, unsigned char *buf,
                                 int64_t capacity, int64_t *size) {
     try {
         SAMG_CHECK(fused_count >= 0 && size && (capacity == 0 || buf), SAMG_E_INVALID,
                    "sweep_schedule: bad arguments");
-        const HCsr h = host_copy(A, false);
+        const HCsr h = host_copy(A, spd != 0);
         HostSched hs;
-        host_schedule(h, fused_count, hs);
+        host_schedule(h, fused_count, spd != 0, hs);
         std::vector<unsigned char> out;
         auto put32 = [&](int32_t v) {
             const unsigned char *q = reinterpret_cast<const unsigned char *>(&v);

@@ -1113,7 +1113,10 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     build_from_pattern(merge_pattern(A, B), B ? 1 : 0, ks, s);
 }
 
-void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s) {
+namespace {
+
+// count sweeps over the rows of A - s B in sequence, as one program
+Pattern stacked_pattern(const HCsr &A, const HCsr &B, int count) {
     const Pattern one = merge_pattern(A, &B);
     Pattern p;
     p.rows = one.rows * count;
@@ -1130,7 +1133,13 @@ void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks
             p.rhs.push_back(i);
         }
     }
-    build_from_pattern(p, 1, ks, s);
+    return p;
+}
+
+}  // namespace
+
+void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s) {
+    build_from_pattern(stacked_pattern(A, B, count), 1, ks, s);
 }
 
 void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
@@ -1219,8 +1228,19 @@ Pattern sweep_pattern(const HCsr &A, int fused_count) {
 
 }  // namespace
 
-void host_schedule(const HCsr &A, int fused_count, HostSched &h) {
-    build_host(sweep_pattern(A, fused_count), fused_count > 0 ? 2 : 0, h);
+void host_schedule(const HCsr &A, int fused_count, bool spd, HostSched &h) {
+    if (!spd) {
+        build_host(sweep_pattern(A, fused_count), fused_count > 0 ? 2 : 0, h);
+        return;
+    }
+    HCsr I;
+    I.m = I.n = A.m;
+    I.rp.resize(A.m + 1);
+    I.ci.resize(A.m);
+    I.v.assign(A.m, 1.0);
+    for (int i = 0; i <= A.m; ++i) I.rp[i] = i;
+    for (int i = 0; i < A.m; ++i) I.ci[i] = i;
+    build_host(stacked_pattern(A, I, std::max(1, fused_count)), 1, h);
 }
 
 void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *nbands) {

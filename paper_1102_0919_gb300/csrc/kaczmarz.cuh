@@ -79,10 +79,11 @@ struct HostSched {
     std::vector<int2> req;
 };
 
-// Host-only: the schedule of one sweep over the rows of A (fused_count 0,
-// mode 0) or of the fused program of fused_count minimal-SVD relaxations
-// with B = I, C = I (mode 2), as the kernels receive it.
-void host_schedule(const HCsr &A, int fused_count, HostSched &h);
+// Host-only: the schedule, as the kernels receive it, of one sweep over the
+// rows of A (fused_count 0, mode 0), of the fused program of fused_count
+// minimal-SVD relaxations with B = I, C = I (mode 2), or, with spd, of
+// max(1, fused_count) stacked sweeps over the rows of A - s I (mode 1).
+void host_schedule(const HCsr &A, int fused_count, bool spd, HostSched &h);
 
 // Build the schedule of the rows of A (shift form when B != nullptr: rows of
 // A - s B over the union pattern).  Host CSR inputs.

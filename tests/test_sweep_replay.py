@@ -87,6 +87,26 @@ def test_fused_schedule_of_a_random_operator():
     assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10
 
 
+@pytest.mark.parametrize("count", [1, 4])
+def test_stacked_spd_schedule_replays_shifted_sweeps(count):
+    # SPD kind: stacked sweeps over the rows of A - lambda_j I (norms per
+    # column), as the oracle's shifted Kaczmarz relaxation
+    A = oracle.samg._csr(W.laplacian5(40, 0.3).to_scipy())
+    n = A.shape[0]
+    S = parse(samg.sweep_schedule(A, count, spd=True))
+    assert S["mode"] == 1 and S["rows"] == count * n
+    rng = np.random.default_rng(count)
+    lam = np.linspace(5.0, 60.0, 8)
+    U = rng.standard_normal((n, 8))
+    K = rng.standard_normal((n, 8))
+    got = replay(S, U.copy(), K, lam)
+    L0 = oracle.Level(A, sp.identity(n, format="csr"))
+    ref = U.copy()
+    for _ in range(count):
+        oracle.relax_boot(L0, True, "minimal", lam, ref, None, K, None, 0.7)
+    assert rel(got, ref) < 1e-10, rel(got, ref)
+
+
 def test_replay_detects_a_dropped_requirement():
     # the replay is only evidence if it can fail: remove every cross-band
     # requirement of a multi-band schedule and the eager band order must
