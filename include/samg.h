@@ -276,9 +276,10 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
  * it on the CPU (the paper has no counterpart): the schedule the kernels
  * receive, with float64 coefficients, for one sweep over the rows of A
  * (fused_count = 0, spd = 0), for the fused program of fused_count
- * minimal-SVD relaxations with B = I, C = I (spd = 0), or for
- * max(1, fused_count) stacked sweeps over the rows of A - lambda_j I of the
- * SPD kind (spd = 1, A square; mode 1: norms formed per column).  Call with buf = NULL (capacity 0) to get *size,
+ * minimal-SVD relaxations with the level's B (m x m) and C (n x n)
+ * (spd = 0), or for max(1, fused_count) stacked sweeps over the rows of
+ * A - lambda_j B of the SPD kind (spd = 1, A square; mode 1: norms formed
+ * per column).  B, C may be NULL (identity, as on the finest level).  Call with buf = NULL (capacity 0) to get *size,
  * then with a buffer of that many bytes.  Layout, little-endian:
  *   i32 rows, cols, nbands, nlevels, nchunks, max_slots, mode, shifted;
  *   i64 nreq, image_bytes;
@@ -295,8 +296,9 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
  * per entry a (f64); per entry b (f64, shifted programs only); per staged
  * value its column (i32).  Returns SAMG_E_INVALID for a malformed CSR or a
  * short buffer. */
-samg_status samg_sweep_schedule(const samg_csr *A, int fused_count, int spd, unsigned char *buf,
-                                int64_t capacity, int64_t *size);
+samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
+                                int fused_count, int spd, unsigned char *buf, int64_t capacity,
+                                int64_t *size);
 
 /* Test hook for the bounded device waits (the paper has no counterpart):
  * from now on band `band` of the Kaczmarz schedules of level `level`

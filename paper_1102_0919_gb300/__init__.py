@@ -90,7 +90,7 @@ samg_write_hierarchy = _sig("samg_write_hierarchy", _I, ctypes.c_char_p, _P, _I,
                             _P, _P, _P)
 samg_import_file = _sig("samg_import_file", _I, ctypes.c_char_p, _P, ctypes.c_void_p,
                         ctypes.POINTER(_CTX))
-samg_sweep_schedule = _sig("samg_sweep_schedule", _I, _P, _I, _I, _P, ctypes.c_int64,
+samg_sweep_schedule = _sig("samg_sweep_schedule", _I, _P, _P, _P, _I, _I, _P, ctypes.c_int64,
                            ctypes.POINTER(ctypes.c_int64))
 samg_host_strength_product = _sig("samg_host_strength_product", _I, _P, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
@@ -399,16 +399,20 @@ def sweep_plan(A, fused_count=0):
     return lv[:rows], d.value, nb.value
 
 
-def sweep_schedule(A, fused_count=0, spd=False):
-    """Host-only: the serialized sweep schedule (bytes) the kernels receive."""
+def sweep_schedule(A, fused_count=0, spd=False, B=None, C=None):
+    """Host-only: the serialized sweep schedule (bytes) the kernels receive
+    (B, C: the level's operators; None = identity)."""
     c = _csr(A)
+    cb = None if B is None else _csr(B)
+    cc = None if C is None else _csr(C)
+    args = (ctypes.byref(c), None if cb is None else ctypes.byref(cb),
+            None if cc is None else ctypes.byref(cc), fused_count, int(spd))
     size = ctypes.c_int64(0)
-    st = samg_sweep_schedule(ctypes.byref(c), fused_count, int(spd), None, 0, ctypes.byref(size))
+    st = samg_sweep_schedule(*args, None, 0, ctypes.byref(size))
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
     buf = np.zeros(size.value, np.uint8)
-    st = samg_sweep_schedule(ctypes.byref(c), fused_count, int(spd), _ptr(buf), size.value,
-                             ctypes.byref(size))
+    st = samg_sweep_schedule(*args, _ptr(buf), size.value, ctypes.byref(size))
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
     return buf.tobytes()

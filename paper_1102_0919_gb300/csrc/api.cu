@@ -804,14 +804,24 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
     }
 }
 
-samg_status samg_sweep_schedule(const samg_csr *A, int fused_count, int spd, unsigned char *buf,
-                                int64_t capacity, int64_t *size) {
+samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
+                                int fused_count, int spd, unsigned char *buf, int64_t capacity,
+                                int64_t *size) {
     try {
         SAMG_CHECK(fused_count >= 0 && size && (capacity == 0 || buf), SAMG_E_INVALID,
                    "sweep_schedule: bad arguments");
         const HCsr h = host_copy(A, spd != 0);
+        HCsr hb, hc;
+        if (B) {
+            hb = host_copy(B, true);
+            SAMG_CHECK(hb.m == h.m, SAMG_E_INVALID, "sweep_schedule: B must be m x m");
+        }
+        if (C) {
+            hc = host_copy(C, true);
+            SAMG_CHECK(hc.m == h.n, SAMG_E_INVALID, "sweep_schedule: C must be n x n");
+        }
         HostSched hs;
-        host_schedule(h, fused_count, spd != 0, hs);
+        host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs);
         std::vector<unsigned char> out;
         auto put32 = [&](int32_t v) {
             const unsigned char *q = reinterpret_cast<const unsigned char *>(&v);

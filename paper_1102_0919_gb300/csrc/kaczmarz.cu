@@ -1142,8 +1142,11 @@ void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks
     build_from_pattern(stacked_pattern(A, B, count), 1, ks, s);
 }
 
-void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
-                           KSched &ks, cudaStream_t s) {
+namespace {
+
+// count block Gauss-Seidel relaxations of the minimal SVD kind as one
+// program over [v; u]
+Pattern fused_pattern(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count) {
     const int m = A.m, n = A.n;
     Pattern p;
     p.rows = count * (m + n);
@@ -1165,82 +1168,69 @@ void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const H
             p.rhs.push_back(m + j);
         }
     }
-    build_from_pattern(p, 2, ks, s);
+    return p;
+}
+
+HCsr identity_csr(int k) {
+    HCsr h;
+    h.m = h.n = k;
+    h.rp.resize(k + 1);
+    h.ci.resize(k);
+    h.v.assign(k, 1.0);
+    for (int i = 0; i <= k; ++i) h.rp[i] = i;
+    for (int i = 0; i < k; ++i) h.ci[i] = i;
+    return h;
+}
+
+HCsr transpose_csr(const HCsr &A) {
+    HCsr At;
+    At.m = A.n;
+    At.n = A.m;
+    At.rp.assign(A.n + 1, 0);
+    for (int64_t e = 0; e < A.nnz(); ++e) At.rp[A.ci[e] + 1]++;
+    for (int j = 0; j < A.n; ++j) At.rp[j + 1] += At.rp[j];
+    At.ci.resize(A.nnz());
+    At.v.resize(A.nnz());
+    std::vector<int64_t> fill(At.rp.begin(), At.rp.end() - 1);
+    for (int i = 0; i < A.m; ++i)
+        for (int64_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+            const int64_t f = fill[A.ci[e]]++;
+            At.ci[f] = i;
+            At.v[f] = A.v[e];
+        }
+    return At;
+}
+
+}  // namespace
+
+void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
+                           KSched &ks, cudaStream_t s) {
+    build_from_pattern(fused_pattern(A, At, B, C, count), 2, ks, s);
 }
 
 namespace {
 
 // The program of one sweep over the rows of A (fused_count 0), or of
-// fused_count minimal-SVD relaxations with B = I, C = I, as
-// build_kschedule_fused forms it (right-hand-side rows i and m + j).
+// fused_count minimal-SVD relaxations with B = I, C = I, as the solve
+// builds it with build_kschedule_fused.
 Pattern sweep_pattern(const HCsr &A, int fused_count) {
-    Pattern p;
-    if (fused_count <= 0) {
-        p = merge_pattern(A, nullptr);
-    } else {
-        // the fused program of build_kschedule_fused with B = I, C = I
-        HCsr At, I_m, I_n;
-        At.m = A.n;
-        At.n = A.m;
-        At.rp.assign(A.n + 1, 0);
-        for (int64_t e = 0; e < A.nnz(); ++e) At.rp[A.ci[e] + 1]++;
-        for (int j = 0; j < A.n; ++j) At.rp[j + 1] += At.rp[j];
-        At.ci.resize(A.nnz());
-        At.v.resize(A.nnz());
-        std::vector<int64_t> fill(At.rp.begin(), At.rp.end() - 1);
-        for (int i = 0; i < A.m; ++i)
-            for (int64_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
-                const int64_t f = fill[A.ci[e]]++;
-                At.ci[f] = i;
-                At.v[f] = A.v[e];
-            }
-        auto identity = [](int k, HCsr &h) {
-            h.m = h.n = k;
-            h.rp.resize(k + 1);
-            h.ci.resize(k);
-            h.v.assign(k, 1.0);
-            for (int i = 0; i <= k; ++i) h.rp[i] = i;
-            for (int i = 0; i < k; ++i) h.ci[i] = i;
-        };
-        identity(A.m, I_m);
-        identity(A.n, I_n);
-        const int m = A.m, n = A.n;
-        p.rows = fused_count * (m + n);
-        p.cols = n + m;
-        p.rp.assign(1, 0);
-        for (int k = 0; k < fused_count; ++k) {
-            for (int i = 0; i < m; ++i) {
-                append_row(p, A, i, 0, false);
-                append_row(p, I_m, i, n, true);
-                p.rp.push_back((int64_t)p.ci.size());
-                p.rhs.push_back(i);
-            }
-            for (int j = 0; j < n; ++j) {
-                append_row(p, I_n, j, 0, true);
-                append_row(p, At, j, n, false);
-                p.rp.push_back((int64_t)p.ci.size());
-                p.rhs.push_back(m + j);
-            }
-        }
-    }
-    return p;
+    if (fused_count <= 0) return merge_pattern(A, nullptr);
+    return fused_pattern(A, transpose_csr(A), identity_csr(A.m), identity_csr(A.n), fused_count);
 }
 
 }  // namespace
 
-void host_schedule(const HCsr &A, int fused_count, bool spd, HostSched &h) {
-    if (!spd) {
-        build_host(sweep_pattern(A, fused_count), fused_count > 0 ? 2 : 0, h);
-        return;
+void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
+                   HostSched &h) {
+    if (spd) {
+        const HCsr I = B ? HCsr() : identity_csr(A.m);
+        build_host(stacked_pattern(A, B ? *B : I, std::max(1, fused_count)), 1, h);
+    } else if (fused_count <= 0) {
+        build_host(merge_pattern(A, nullptr), 0, h);
+    } else {
+        const HCsr Im = B ? HCsr() : identity_csr(A.m), In = C ? HCsr() : identity_csr(A.n);
+        build_host(fused_pattern(A, transpose_csr(A), B ? *B : Im, C ? *C : In, fused_count), 2, h);
     }
-    HCsr I;
-    I.m = I.n = A.m;
-    I.rp.resize(A.m + 1);
-    I.ci.resize(A.m);
-    I.v.assign(A.m, 1.0);
-    for (int i = 0; i <= A.m; ++i) I.rp[i] = i;
-    for (int i = 0; i < A.m; ++i) I.ci[i] = i;
-    build_host(stacked_pattern(A, I, std::max(1, fused_count)), 1, h);
 }
 
 void plan_sweep(const HCsr &A, int fused_count, std::vector<int> &levels, int *nbands) {

@@ -81,9 +81,11 @@ struct HostSched {
 
 // Host-only: the schedule, as the kernels receive it, of one sweep over the
 // rows of A (fused_count 0, mode 0), of the fused program of fused_count
-// minimal-SVD relaxations with B = I, C = I (mode 2), or, with spd, of
-// max(1, fused_count) stacked sweeps over the rows of A - s I (mode 1).
-void host_schedule(const HCsr &A, int fused_count, bool spd, HostSched &h);
+// minimal-SVD relaxations with the level's B and C (mode 2), or, with spd,
+// of max(1, fused_count) stacked sweeps over the rows of A - s B (mode 1).
+// B, C null: identity.  The same pattern builders as the solve's.
+void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
+                   HostSched &h);
 
 // Build the schedule of the rows of A (shift form when B != nullptr: rows of
 // A - s B over the union pattern).  Host CSR inputs.

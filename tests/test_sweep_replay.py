@@ -124,3 +124,40 @@ def test_replay_detects_a_dropped_requirement():
         z = replay(S, z0.copy(), rhs, np.linspace(3.0, 9.0, 8))
         good = replay(parse(samg.sweep_schedule(A, 4)), z0.copy(), rhs, np.linspace(3.0, 9.0, 8))
         assert rel(z, good) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["svd", "spd"])
+def test_coarse_level_programs_with_galerkin_b_and_c(kind):
+    # the smoothing programs of coarse levels, where B and C are Galerkin
+    # products (not the identity): taken from an oracle hierarchy
+    if kind == "svd":
+        A = W.gradient(40).to_scipy()
+        H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(W.GRAD_PARAMS, seed=4, n_mult=2))
+    else:
+        A = W.laplacian5(48, 0.4).to_scipy()
+        H, s, U, V = oracle.setup(A, 4, "minimal", "spd", dict(W.FD_PARAMS, seed=4, n_mult=2))
+    assert len(H.levels) >= 3
+    L = H.levels[1]
+    nb = len(s)
+    rng = np.random.default_rng(6)
+    sig = np.abs(s) * (1 + 0.01 * rng.standard_normal(nb))
+    for count in (1, 3):
+        if kind == "svd":
+            m, n = L.A.shape
+            S = parse(samg.sweep_schedule(L.A, count, B=L.B, C=L.C))
+            Uc, Vc = rng.standard_normal((m, nb)), rng.standard_normal((n, nb))
+            K, T = rng.standard_normal((m, nb)), rng.standard_normal((n, nb))
+            z = replay(S, np.vstack([Vc, Uc]), np.vstack([K, T]), sig)
+            Ur, Vr = Uc.copy(), Vc.copy()
+            for _ in range(count):
+                oracle.relax_boot(L, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+            assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10, (rel(z[:n], Vr), rel(z[n:], Ur))
+        else:
+            n = L.A.shape[0]
+            S = parse(samg.sweep_schedule(L.A, count, spd=True, B=L.B))
+            Uc, K = rng.standard_normal((n, nb)), rng.standard_normal((n, nb))
+            got = replay(S, Uc.copy(), K, sig)
+            ref = Uc.copy()
+            for _ in range(count):
+                oracle.relax_boot(L, True, "minimal", sig, ref, None, K, None, 0.7)
+            assert rel(got, ref) < 1e-10, rel(got, ref)
