@@ -14,6 +14,10 @@ per solve (lower is better), mixed precision.  The plain float64 path is
 timed from the same boot triplets with max(1, W // 3) warm-up and
 max(1, K // 3) timed solves (it is the slower comparison arm).
 
+Beside the line ("other_workloads"), the default run also times the 32 x 32
+Laplacian's 4 minimal eigenpairs to residual 1e-8 in both precisions (a few
+seconds; --no-small skips it).
+
 --impl reference runs the FP64 CPU oracle on a bounded sample of the same
 workload instead (rank 0 only).
 """
@@ -348,8 +352,58 @@ def run_gpu(args):
                      if mixed["prof"]["block_spmm"]["ms"] > 0 else None),
         "cpu_baseline": cpu,
     }
+    if world == 1 and args.workload == 2 and not args.no_small:
+        line["other_workloads"] = {"laplacian5_N32_nb4_minimal": small_workload(1, dev, stream)}
     print(json.dumps(line))
     return 0
+
+
+def small_workload(i, dev, stream, warm=3, steps=5):
+    """Time to residual 1e-8 of a small workload (the 32 x 32 Laplacian's 4
+    minimal eigenpairs), float64 and mixed precision, from the same setup
+    output, with CUDA events on the library's stream; sigma against the
+    closed form.  Reported beside the main line; errors are reported, not
+    raised."""
+    try:
+        import numpy as np
+        import torch
+
+        import paper_1102_0919_gb300 as samg
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from closed_forms import laplacian5_eigs
+
+        wl, prm = workload(i)
+        A = wl.build()
+        s = samg.Solver.setup(A, wl.nb, wl.target, wl.kind, stream=stream, prec="fp32", **prm)
+        sig0, U0, V0, _ = s.triplets()
+        dsig = torch.tensor(sig0, device=dev, dtype=torch.float64)
+        dU = torch.tensor(U0, device=dev, dtype=torch.float64).contiguous()
+        exact = laplacian5_eigs(32)[:wl.nb]
+        out = {"levels": [[a, b] for a, b, _ in s.levels()], "unit": "s", "steps": steps}
+        for prec in ("fp64", "fp32"):
+            s.set_precision(prec)
+            for _ in range(warm):
+                s.set_triplets_device(dsig.data_ptr(), dU.data_ptr(), None)
+                s.solve(1e-8, 300)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            res = []
+            for _ in range(steps):
+                s.set_triplets_device(dsig.data_ptr(), dU.data_ptr(), None)
+                res.append(s.solve(1e-8, 300))
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            sg, _, _, rf = s.triplets()
+            out[prec] = {"value": ev0.elapsed_time(ev1) / steps / 1e3,
+                         "outer_iterations": res[-1][1], "converged": all(o for o, _ in res),
+                         "resid": float(rf.max()),
+                         "sigma_relerr_max": float(np.max(np.abs(sg - exact) / exact))}
+        s.close()
+        return out
+    except Exception as e:  # noqa: BLE001 -- the main line must still print
+        return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 def run_sweep_roofline(args):
@@ -423,6 +477,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-outer", type=int, default=300)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small 32 x 32 Laplacian measurement reported beside the line")
     ap.add_argument("--arms", default="fp64,fp32",
                     help="precision arms to time, in order (the JSON line needs both)")
     ap.add_argument("--ncu-range", action="store_true",
