@@ -9,7 +9,10 @@
  * solve phase -- V-cycles with fixed interpolation (Secs. 4.1-4.2) plus the
  * Ritz step (Sec. 4.3) -- on one GPU.  All arithmetic of the solve phase runs
  * in the library's CUDA kernels; there is no CPU fallback: every entry point
- * returns SAMG_E_CUDA when no usable sm_103a device is present.
+ * that computes returns SAMG_E_CUDA when no usable sm_103a device is present.
+ * Argument checks come first (SAMG_E_INVALID on any machine), and the entry
+ * points marked "host only" below (setup steps, schedule analysis, hierarchy
+ * files) need no GPU.
  *
  * Conventions for every entry point:
  *  - Host matrices are 0-based CSR with int64 row pointers, int32 sorted
