@@ -823,6 +823,8 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
         HostSched hs;
         host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs);
         std::vector<unsigned char> out;
+        out.reserve(64 + 4 * hs.band_chunk.size() + 32 * hs.chunk.size() + 16 * hs.lvl.size() +
+                    8 * hs.req.size() + hs.img_d.size());
         auto put32 = [&](int32_t v) {
             const unsigned char *q = reinterpret_cast<const unsigned char *>(&v);
             out.insert(out.end(), q, q + 4);
