@@ -47,3 +47,17 @@ def test_oracle_dominant_triplets_of_a_small_termdoc_match_lapack():
     assert hist[-1].max() <= 1e-10
     assert np.allclose(s, ref, rtol=1e-9)
     assert np.allclose(A @ V, U * s, atol=1e-8 * s.max())
+
+
+def test_oracle_on_the_first_batched_anisotropic_problem():
+    # problem 0 of the batched family (N = 64, its own epsilon): the oracle
+    # with the FD parameter set reaches the closed-form eigenvalues
+    from closed_forms import laplacian5_eigs
+
+    N, e = W.aniso_batch()[0]
+    A = W.laplacian5(N, e).to_scipy()
+    H, s, U, V = oracle.setup(A, 4, "minimal", "spd", dict(W.FD_PARAMS, seed=W.problem_seed(5, 0)))
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=60)
+    assert hist[-1].max() <= 1e-10
+    assert np.allclose(s, laplacian5_eigs(N, e)[:4], rtol=1e-12)
+    assert np.allclose(A @ U, U * s, atol=1e-9 * s.max())
