@@ -670,10 +670,14 @@ def redo_interpolation(H: Hierarchy, sigma, U, V, converged, factor: float = 1e-
 
 
 def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
-          redo_tol: float | None = None):
+          redo_tol: float | None = None, n_conv: int | None = None):
     """Additive phase (Sec. 4): V-cycle per triplet with sigma_j fixed, then a
     Ritz step, until max_j rho_j <= tol.  Returns (sigma, U, V, history)
     where history[i] = rho after i outer iterations.
+
+    n_conv (optional, not in the paper): only the first n_conv triplets must
+    meet tol; the rest are guards that keep the block complete past a small
+    gap.
 
     redo_tol (optional; the Sec. 6.3 remedy): each time the number of
     triplets with rho_j <= redo_tol grows while some are still above it, the
@@ -689,8 +693,9 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
     hist = [residual_norms(A, spd, sigma, U, V)]
     H.redos.clear()
     nconv = 0
+    k = len(sigma) if n_conv is None else int(n_conv)
     for it in range(max_outer):
-        if hist[-1].max() <= tol:
+        if hist[-1][:k].max() <= tol:
             break
         Z = np.zeros_like(U)
         vcycle(H, 0, sigma, U, V, Z, None if spd else np.zeros_like(V), XY)

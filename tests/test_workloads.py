@@ -61,3 +61,18 @@ def test_oracle_on_the_first_batched_anisotropic_problem():
     assert hist[-1].max() <= 1e-10
     assert np.allclose(s, laplacian5_eigs(N, e)[:4], rtol=1e-12)
     assert np.allclose(A @ U, U * s, atol=1e-9 * s.max())
+
+
+def test_oracle_guard_pairs_on_the_smallest_gap_batched_problem():
+    # problem 7 of the batched family has lambda_5 / lambda_4 = 1.0072; with
+    # two guard pairs (n_b = 6, n_conv = 4) the 4 wanted reach the closed form
+    from closed_forms import laplacian5_eigs
+
+    N, e = W.aniso_batch()[7]
+    A = W.laplacian5(N, e).to_scipy()
+    lam = laplacian5_eigs(N, e)
+    assert lam[4] / lam[3] < 1.01
+    H, s, U, V = oracle.setup(A, 6, "minimal", "spd", dict(W.FD_PARAMS, seed=W.problem_seed(5, 7)))
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=90, n_conv=4)
+    assert hist[-1][:4].max() <= 1e-10
+    assert np.allclose(s[:4], lam[:4], rtol=1e-12)
