@@ -79,11 +79,15 @@ typedef struct {
     int32_t max_levels;
     uint64_t seed;        /* SplitMix64 seed of the random test vectors */
     samg_precision prec;  /* arithmetic of the solve-phase V-cycle */
+    int32_t n_conv;       /* triplets that must meet samg_solve's tolerance:
+                             the first n_conv (0 = all n_b); the others are
+                             guards that keep the block complete past a small
+                             gap (not in the paper) */
 } samg_params;
 
 /* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
  * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
- * seed 20110204, prec SAMG_FP32. */
+ * seed 20110204, prec SAMG_FP32, n_conv 0 (all). */
 void samg_default_params(samg_params *p);
 
 /* ---------------------------------------------------------------- setup --

@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
                 ("mu_b", ctypes.c_int32), ("mu_tJ", ctypes.c_int32), ("mu_bJ", ctypes.c_int32),
                 ("omega_J", ctypes.c_double), ("n_mult", ctypes.c_int32),
                 ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32)]
 
 
 class _Csr(ctypes.Structure):

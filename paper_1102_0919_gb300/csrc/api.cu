@@ -228,6 +228,7 @@ void samg_default_params(samg_params *p) {
     p->max_levels = 30;
     p->seed = 20110204ull;
     p->prec = SAMG_FP32;
+    p->n_conv = 0;
 }
 
 const char *samg_last_error(const samg_ctx *ctx) {
@@ -432,6 +433,7 @@ samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done
     samg_status st = guarded(ctx, [&] {
         samg_ctx &c = *ctx;
         SAMG_CHECK(max_outer >= 0 && tol > 0.0, SAMG_E_INVALID, "bad tol or max_outer");
+        const int nconv = c.prm.n_conv > 0 && c.prm.n_conv < c.nb ? c.prm.n_conv : c.nb;
         std::vector<double> rs(c.ld);
         for (;;) {
             c.resid.download(rs.data(), c.ld, c.stream);
@@ -440,7 +442,7 @@ samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done
             bool finite = true;
             for (int j = 0; j < c.nb; ++j) {
                 finite = finite && std::isfinite(rs[j]);
-                mx = std::max(mx, rs[j]);
+                if (j < nconv) mx = std::max(mx, rs[j]);
             }
             if (!finite) check_kaczmarz(c);
             SAMG_CHECK(finite, SAMG_E_INVALID, "non-finite residual");

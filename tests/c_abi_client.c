@@ -2,6 +2,7 @@
  * eigenpairs of a small Dirichlet Laplacian, solves, reads the pairs and
  * destroys the context.  Exit status: 0 solved, 2 the library reported that
  * no usable GPU is present (SAMG_E_CUDA), 1 anything else. */
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -9,6 +10,9 @@
 
 int main(void) {
     enum { N = 12 };
+    /* the layout the bindings must mirror */
+    printf("sizeof(samg_params) %u offsetof(n_conv) %u\n", (unsigned)sizeof(samg_params),
+           (unsigned)offsetof(samg_params, n_conv));
     const int n = N * N;
     int64_t *rp = malloc(sizeof(int64_t) * (n + 1));
     int32_t *col = malloc(sizeof(int32_t) * 5 * n);

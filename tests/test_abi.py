@@ -49,7 +49,7 @@ def test_default_params_and_null_handling(lib):
 
     p = samg.make_params()
     assert p.n_t == 8 and abs(p.theta - 0.06) < 1e-15 and p.mu_b == 4
-    assert abs(p.omega_J - 0.7) < 1e-15 and p.prec == samg.FP32
+    assert abs(p.omega_J - 0.7) < 1e-15 and p.prec == samg.FP32 and p.n_conv == 0
     # argument errors are reported without touching a GPU
     assert samg.samg_solve(None, 1e-8, 1, None) == samg.E_INVALID
     assert samg.samg_setup(None, 4, 1, 0, None, None, None) == samg.E_INVALID
@@ -74,6 +74,13 @@ def test_header_serves_a_plain_c_client(lib, repo_root, tmp_path):
     out = subprocess.run(cmd, capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
     run = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+    # the binding's parameter struct has the header's layout
+    import paper_1102_0919_gb300 as samg
+
+    head = run.stdout.split()
+    assert head[:1] == ["sizeof(samg_params)"], run.stdout
+    assert int(head[1]) == ctypes.sizeof(samg.Params)
+    assert int(head[3]) == samg.Params.n_conv.offset
     try:
         import torch
         has_gpu = torch.cuda.is_available()
