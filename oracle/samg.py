@@ -693,9 +693,9 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
     hist = [residual_norms(A, spd, sigma, U, V)]
     H.redos.clear()
     nconv = 0
-    k = len(sigma) if n_conv is None else int(n_conv)
+    kc = len(sigma) if n_conv is None else int(n_conv)
     for it in range(max_outer):
-        if hist[-1][:k].max() <= tol:
+        if hist[-1][:kc].max() <= tol:
             break
         Z = np.zeros_like(U)
         vcycle(H, 0, sigma, U, V, Z, None if spd else np.zeros_like(V), XY)
