@@ -158,6 +158,66 @@ def test_ls_fit_recovers_exact_interpolation():
     assert np.allclose(P.toarray(), Pstar.toarray(), atol=1e-10)
 
 
+def test_ls_fit_weights_multiply_squared_residuals():
+    # R13: for data no interpolation fits exactly, each F row's weights are
+    # the minimiser of sum_k w_k (y_k(i) - sum_j p_j y_k(c_j))^2, i.e. the
+    # ordinary least-squares solution of the rows scaled by sqrt(w_k)
+    # (numpy's lstsq, called); weighting by w_k unsquared or by w_k^2 fails
+    A = W.laplacian5(9).to_scipy()
+    S = oracle.strength(A, 0.06)
+    cf = oracle.rs_coarsen(S)
+    rng = np.random.default_rng(13)
+    nf = 10
+    Y = rng.standard_normal((A.shape[0], nf))
+    w = rng.uniform(0.1, 5.0, nf)
+    P = oracle.fit_interp(S, cf, Y, Y, w).tocsr()
+    ptr, cols = oracle.interp_sets(S, cf, nf - 1)
+    alpha = np.cumsum(cf) - 1
+    checked = 0
+    for i in np.flatnonzero(cf == 0):
+        C = cols[ptr[i]:ptr[i + 1]]
+        if len(C) == 0:
+            continue
+        G = Y[C].T * np.sqrt(w)[:, None]           # nf x |C^i|
+        p_ref = np.linalg.lstsq(G, Y[i] * np.sqrt(w), rcond=None)[0]
+        row = dict(zip(P.indices[P.indptr[i]:P.indptr[i + 1]], P.data[P.indptr[i]:P.indptr[i + 1]]))
+        got = np.array([row[alpha[j]] for j in C])
+        assert np.allclose(got, p_ref, rtol=1e-9, atol=1e-12)
+        checked += 1
+    assert checked > 10
+
+
+def test_interpolatory_sets_keep_the_strongest_up_to_the_cap():
+    # R15: C^i holds the cap strongest strong C-point influences (ties to the
+    # lowest index), hand-built strength row
+    S = sp.csr_matrix(np.array([
+        [0, 3, 1, 3, 2, 5, 0],
+        [0, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 0, 0]], dtype=float))
+    cf = np.array([0, 1, 1, 1, 1, 1, 0])
+    ptr, cols = oracle.interp_sets(S, cf, 3)
+    assert list(cols[ptr[0]:ptr[1]]) == [5, 1, 3]      # 5 (5), then the tie 3/3 -> 1, 3
+    ptr, cols = oracle.interp_sets(S, cf, 10)
+    assert sorted(cols[ptr[0]:ptr[1]]) == [1, 2, 3, 4, 5]
+
+
+def test_minimal_test_vectors_have_unit_norm_after_relaxation():
+    # R16: minimal kind, test vectors scaled to unit B (C) norm after each
+    # block of mu_t relaxations, whatever their scale before
+    A = W.gradient(10).to_scipy()
+    m, n = A.shape
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    Ut = oracle.random_block(3, m, 4) * 7.0
+    Vt = oracle.random_block(4, n, 4) * 0.2
+    oracle.relax_test(L0, False, "minimal", Ut, Vt, 3, 0.7)
+    assert np.allclose(np.linalg.norm(Ut, axis=0), 1.0, atol=1e-12)
+    assert np.allclose(np.linalg.norm(Vt, axis=0), 1.0, atol=1e-12)
+
+
 # ---------------------------------------------------------------- Galerkin
 
 def test_galerkin_matches_dense_triple_product():
