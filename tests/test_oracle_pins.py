@@ -218,6 +218,36 @@ def test_minimal_test_vectors_have_unit_norm_after_relaxation():
     assert np.allclose(np.linalg.norm(Vt, axis=0), 1.0, atol=1e-12)
 
 
+def test_block_order_v_then_u():
+    # R1/R2: one minimal block Gauss-Seidel relaxation updates v from the rows
+    # of A, then u from the rows of A^t.  A Kaczmarz sweep leaves its last
+    # row satisfied exactly (P8), so afterwards the last row of
+    # A^t u - s C v = tau holds with the final v; the reverse order would
+    # leave the last row of A v - s B u = kappa exact instead.
+    A = W.gradient(9).to_scipy()
+    m, n = A.shape
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    rng = np.random.default_rng(21)
+    sig = np.array([2.0, 3.5, 5.0])
+    U, V = rng.standard_normal((m, 3)), rng.standard_normal((n, 3))
+    K, T = rng.standard_normal((m, 3)), rng.standard_normal((n, 3))
+    oracle.relax_boot(L0, False, "minimal", sig, U, V, K, T, 0.7)
+    last_t = (A.T @ U - sig * V)[-1] - T[-1]
+    last_k = (A @ V - sig * U)[-1] - K[-1]
+    assert np.allclose(last_t, 0.0, atol=1e-12)
+    assert np.abs(last_k).min() > 1e-6
+
+
+def test_coarsest_rule():
+    # R6: levels are added while max(m_l, n_l) > coarsest_max (and coarsening
+    # still reduces); the coarsest has max(m_L, n_L) <= coarsest_max here
+    A = W.gradient(24).to_scipy()
+    H, s, U, V = oracle.setup(A, 4, "minimal", "svd", dict(W.GRAD_PARAMS, seed=2, n_mult=2,
+                                                           coarsest_max=60))
+    sizes = [max(L.A.shape) for L in H.levels]
+    assert sizes[-1] <= 60 and all(x > 60 for x in sizes[:-1]), sizes
+
+
 # ---------------------------------------------------------------- Galerkin
 
 def test_galerkin_matches_dense_triple_product():
