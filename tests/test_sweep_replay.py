@@ -48,7 +48,8 @@ def test_single_sweep_schedule_replays_the_sequential_sweep(name):
     assert rel(got, ref) < 1e-11, rel(got, ref)
 
 
-@pytest.mark.parametrize("N,count", [(32, 1), (32, 4), (96, 4)])
+# (256, 4) is the bench workload's level-0 smoothing program (49 bands)
+@pytest.mark.parametrize("N,count", [(32, 1), (32, 4), (96, 4), (256, 4)])
 def test_fused_relaxation_schedule_replays_block_gauss_seidel(N, count):
     A = W.gradient(N).to_scipy()
     m, n = A.shape
