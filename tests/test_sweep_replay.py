@@ -162,3 +162,30 @@ def test_coarse_level_programs_with_galerkin_b_and_c(kind):
             for _ in range(count):
                 oracle.relax_boot(L, True, "minimal", sig, ref, None, K, None, 0.7)
             assert rel(got, ref) < 1e-10, rel(got, ref)
+
+
+def test_empty_rows_and_a_single_row():
+    # rows without entries leave x unchanged; a one-row program is one level
+    A = sp.csr_matrix(np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 0.0], [0.0, 0.0, 0.0],
+                                [0.0, 3.0, 1.0]]))
+    S = parse(samg.sweep_schedule(A, 0))
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((3, 4))
+    rhs = rng.standard_normal((4, 4))
+    got = replay(S, X.copy(), rhs)
+    ref = X.copy()
+    oracle.kaczmarz_sweep(oracle.samg._csr(A), ref, rhs)
+    assert rel(got, ref) < 1e-14
+    one = sp.csr_matrix(np.array([[2.0, 0.0, -1.0]]))
+    S1 = parse(samg.sweep_schedule(one, 0))
+    assert S1["nbands"] == 1 and len(S1["lvl"]) == 1
+
+
+def test_row_longer_than_a_staging_chunk_is_rejected():
+    # a chunk holds at most 1024 entries; a longer row is an input error,
+    # reported before any device work
+    n = 1100
+    A = sp.csr_matrix((np.ones(n), (np.zeros(n, dtype=int), np.arange(n))), shape=(1, n))
+    with pytest.raises(samg.SamgError) as e:
+        samg.sweep_schedule(A, 0)
+    assert e.value.status == samg.E_INVALID and "staging chunk" in str(e.value)
