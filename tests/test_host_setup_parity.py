@@ -60,11 +60,16 @@ def _strength_cases():
     td = W.termdoc(6000, 1500, seed=77, kmax=300).to_scipy()      # > 4096 rows: threaded path
     ti = td.copy()
     ti.data = np.round(np.expm1(ti.data))                          # integer counts tf
+    E = sp.lil_matrix((40, 30))                                    # empty rows and columns
+    rng = np.random.default_rng(2)
+    for i in range(0, 40, 3):
+        E[i, rng.choice(25, 4, replace=False)] = rng.integers(1, 5, 4)
     return {"gradient": G, "laplacian": W.laplacian5(16).to_scipy(), "termdoc_counts": ti,
-            "termdoc": td}
+            "termdoc": td, "empty_rows": sp.csr_matrix(E)}
 
 
-@pytest.mark.parametrize("name", ["gradient", "laplacian", "termdoc_counts", "termdoc"])
+@pytest.mark.parametrize("name", ["gradient", "laplacian", "termdoc_counts", "termdoc",
+                                  "empty_rows"])
 @pytest.mark.parametrize("side", ["AAt", "AtA"])
 def test_strength_of_product_matches_oracle(name, side):
     # the setup's strength graph of A A^t (or A^t A) formed from A alone
