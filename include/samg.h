@@ -120,6 +120,32 @@ samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, cons
                         const double *sigma, const double *U, const double *V, void *cuda_stream,
                         samg_ctx **out);
 
+/* Many independent problems with the same n_b, target, kind and parameters
+ * (the batched workload of uneven sizes; the paper treats one problem at a
+ * time).  Each problem gets its own hierarchy and context on the given
+ * stream; samg_solve_batched solves them one after another.  Fusing
+ * problems into shared launches or one captured graph is not built.
+ *  - samg_setup_batched: every problem's arguments are checked before any
+ *    device call (SAMG_E_INVALID names the problem); then the setups run in
+ *    order, and a failure destroys the contexts made so far.
+ *  - samg_solve_batched: outer_done (count entries, may be NULL) receives
+ *    each problem's iterations.  It returns SAMG_E_NOT_CONVERGED when some
+ *    problem reached max_outer (the others are still solved), or the first
+ *    other error, which stops the loop.
+ *  - samg_batch_problem: the problem's context, owned by the batch (valid
+ *    until samg_batch_destroy), for samg_get_triplets and the other
+ *    per-context calls.
+ *  - samg_batch_last_error(NULL) reports a failed samg_setup_batched. */
+typedef struct samg_batch samg_batch;
+samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, samg_target target,
+                               samg_kind kind, const samg_params *params, void *cuda_stream,
+                               samg_batch **out);
+samg_status samg_solve_batched(samg_batch *b, double tol, int max_outer, int *outer_done);
+samg_status samg_batch_problem(samg_batch *b, int problem, samg_ctx **ctx);
+int samg_batch_size(const samg_batch *b);
+const char *samg_batch_last_error(const samg_batch *b);
+void samg_batch_destroy(samg_batch *b);
+
 /* A hierarchy and its boot triplets in one binary file.  The paper has no
  * file format; the file keeps the solve phase's inputs.
  *  - samg_export writes the context's finest A, its P_l and Q_l as the solve

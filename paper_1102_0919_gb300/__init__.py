@@ -85,6 +85,14 @@ samg_debug_mute_band = _sig("samg_debug_mute_band", _I, _CTX, _I, _I, _I)
 samg_host_coarsen = _sig("samg_host_coarsen", _I, _P, ctypes.c_double, _P)
 samg_host_ls_interp = _sig("samg_host_ls_interp", _I, _P, ctypes.c_double, _P, _I, _P, _P, _P,
                            ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
+_BATCH = ctypes.c_void_p
+samg_setup_batched = _sig("samg_setup_batched", _I, _P, _I, _I, _I, _I, _P, ctypes.c_void_p,
+                          ctypes.POINTER(_BATCH))
+samg_solve_batched = _sig("samg_solve_batched", _I, _BATCH, ctypes.c_double, _I, _P)
+samg_batch_problem = _sig("samg_batch_problem", _I, _BATCH, _I, ctypes.POINTER(_CTX))
+samg_batch_size = _sig("samg_batch_size", _I, _BATCH)
+samg_batch_last_error = _sig("samg_batch_last_error", ctypes.c_char_p, _BATCH)
+samg_batch_destroy = _sig("samg_batch_destroy", None, _BATCH)
 samg_export = _sig("samg_export", _I, _CTX, ctypes.c_char_p)
 samg_write_hierarchy = _sig("samg_write_hierarchy", _I, ctypes.c_char_p, _P, _I, _P, _P, _I, _I, _I,
                             _P, _P, _P)
@@ -112,7 +120,9 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_profile", "samg_profile_read", "samg_launch_count", "samg_debug_mute_band",
             "samg_sweep_plan", "samg_host_coarsen", "samg_host_ls_interp",
             "samg_host_strength_product", "samg_export", "samg_write_hierarchy",
-            "samg_import_file", "samg_sweep_schedule"]
+            "samg_import_file", "samg_sweep_schedule", "samg_setup_batched",
+            "samg_solve_batched", "samg_batch_problem", "samg_batch_size",
+            "samg_batch_last_error", "samg_batch_destroy"]
 
 
 def _arr(x, dtype):
@@ -225,9 +235,9 @@ class Solver:
         self._check(samg_export(self._ctx, os.fsencode(path)))
 
     def close(self):
-        if self._ctx:
+        if self._ctx and not getattr(self, "_borrowed", False):
             samg_destroy(self._ctx)
-            self._ctx = None
+        self._ctx = None
 
     def __del__(self):
         try:
@@ -426,6 +436,57 @@ def host_coarsen(N, theta):
     if st != OK:
         raise SamgError(st, samg_last_error(None).decode())
     return cf
+
+
+class Batch:
+    """Independent problems with one n_b, target, kind and parameter set
+    (samg_setup_batched); problem(i) is a Solver view owned by the batch."""
+
+    def __init__(self, b, nb, kind, target, shapes):
+        self._b = b
+        self.nb, self.kind, self.target, self.shapes = nb, kind, target, shapes
+
+    @classmethod
+    def setup(cls, As, nb, target="minimal", kind="svd", stream=None, **params):
+        t = MINIMAL if target == "minimal" else DOMINANT
+        k = SPD_EIG if kind == "spd" else SVD
+        cs = [_csr(A) for A in As]
+        ptrs = (ctypes.c_void_p * len(cs))(*[ctypes.cast(ctypes.pointer(c), ctypes.c_void_p)
+                                             for c in cs])
+        p = make_params(**params)
+        b = _BATCH()
+        st = samg_setup_batched(ptrs, len(cs), nb, t, k, ctypes.byref(p), _stream(stream),
+                                ctypes.byref(b))
+        if st != OK:
+            raise SamgError(st, samg_batch_last_error(None).decode())
+        return cls(b, nb, k, t, [(c.m, c.n) for c in cs])
+
+    def solve(self, tol=1e-8, max_outer=100):
+        done = np.zeros(len(self.shapes), np.int32)
+        st = samg_solve_batched(self._b, tol, max_outer, _ptr(done))
+        if st not in (OK, E_NOT_CONVERGED):
+            raise SamgError(st, samg_batch_last_error(self._b).decode())
+        return st == OK, done
+
+    def problem(self, i):
+        ctx = _CTX()
+        if samg_batch_problem(self._b, i, ctypes.byref(ctx)) != OK:
+            raise SamgError(E_INVALID, "no problem %d" % i)
+        m, n = self.shapes[i]
+        v = Solver(ctx, self.nb, self.kind, self.target, m, n)
+        v._borrowed = True
+        return v
+
+    def close(self):
+        if self._b:
+            samg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def write_hierarchy(path, A, Ps, Qs, sigma, U, V, target="minimal", kind="svd"):

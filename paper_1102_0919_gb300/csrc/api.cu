@@ -333,6 +333,94 @@ samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind
     return SAMG_OK;
 }
 
+struct samg_batch {
+    std::vector<samg_ctx *> ctx;
+    std::string err;
+};
+
+void samg_batch_destroy(samg_batch *b) {
+    if (!b) return;
+    for (samg_ctx *c : b->ctx) samg_destroy(c);
+    delete b;
+}
+
+samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, samg_target target,
+                               samg_kind kind, const samg_params *params, void *cuda_stream,
+                               samg_batch **out) {
+    if (!out) return SAMG_E_INVALID;
+    *out = nullptr;
+    try {
+        // every problem's arguments are checked before any device call
+        SAMG_CHECK(A != nullptr && count >= 1, SAMG_E_INVALID, "setup_batched: no problems");
+        check_common(n_b, params);
+        SAMG_CHECK(kind == SAMG_SVD || kind == SAMG_SPD_EIG, SAMG_E_INVALID, "bad kind");
+        SAMG_CHECK(target == SAMG_DOMINANT || target == SAMG_MINIMAL, SAMG_E_INVALID, "bad target");
+        for (int p = 0; p < count; ++p) {
+            const std::string who = "setup_batched: problem " + std::to_string(p) + ": ";
+            SAMG_CHECK(A[p] != nullptr, SAMG_E_INVALID, who + "A is NULL");
+            try {
+                validate_csr(*A[p]);
+            } catch (const Error &e) {
+                throw Error(e.status, who + e.what());
+            }
+            SAMG_CHECK(kind != SAMG_SPD_EIG || A[p]->m == A[p]->n, SAMG_E_INVALID,
+                       who + "SPD_EIG needs square A");
+            SAMG_CHECK(n_b <= std::min(A[p]->m, A[p]->n), SAMG_E_INVALID, who + "n_b > min(m, n)");
+        }
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    }
+    samg_batch *b = new (std::nothrow) samg_batch();
+    if (!b) return SAMG_E_NOMEM;
+    for (int p = 0; p < count; ++p) {
+        samg_ctx *c = nullptr;
+        const samg_status st = samg_setup(A[p], n_b, target, kind, params, cuda_stream, &c);
+        if (st != SAMG_OK) {
+            const std::string msg = "setup_batched: problem " + std::to_string(p) + ": " + g_create_error;
+            samg_batch_destroy(b);
+            g_create_error = msg;
+            return st;
+        }
+        b->ctx.push_back(c);
+    }
+    *out = b;
+    return SAMG_OK;
+}
+
+samg_status samg_solve_batched(samg_batch *b, double tol, int max_outer, int *outer_done) {
+    if (!b) return SAMG_E_INVALID;
+    samg_status worst = SAMG_OK;
+    b->err.clear();
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        int done = 0;
+        const samg_status st = samg_solve(b->ctx[p], tol, max_outer, &done);
+        if (outer_done) outer_done[p] = done;
+        if (st == SAMG_E_NOT_CONVERGED) {
+            worst = SAMG_E_NOT_CONVERGED;
+            b->err = "problem " + std::to_string(p) + " reached max_outer before the tolerance";
+            continue;
+        }
+        if (st != SAMG_OK) {
+            b->err = "problem " + std::to_string(p) + ": " + samg_last_error(b->ctx[p]);
+            return st;
+        }
+    }
+    return worst;
+}
+
+samg_status samg_batch_problem(samg_batch *b, int problem, samg_ctx **ctx) {
+    if (!b || !ctx || problem < 0 || problem >= (int)b->ctx.size()) return SAMG_E_INVALID;
+    *ctx = b->ctx[problem];
+    return SAMG_OK;
+}
+
+int samg_batch_size(const samg_batch *b) { return b ? (int)b->ctx.size() : 0; }
+
+const char *samg_batch_last_error(const samg_batch *b) {
+    return b ? b->err.c_str() : g_create_error.c_str();
+}
+
 samg_status samg_set_triplets_device(samg_ctx *ctx, const double *sigma, const double *U,
                                      const double *V) {
     if (!ctx) return SAMG_E_INVALID;

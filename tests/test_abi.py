@@ -183,3 +183,39 @@ def test_well_formed_setup_without_a_gpu_reports_the_device(lib):
     st = _setup_status(samg, _lap())
     assert st == samg.E_CUDA
     assert "device" in samg.samg_last_error(None).decode()
+
+
+def test_batched_setup_checks_every_problem_before_the_device(lib):
+    import paper_1102_0919_gb300 as samg
+
+    good = [_lap(6), _lap(8), _lap(5)]
+    A = _lap(7)
+    bad = _RawCsr(A.shape[0], A.shape[1], A.indptr, A.indices, A.data.copy())
+    bad.val[3] = float("nan")
+    with pytest.raises(samg.SamgError) as e:
+        samg.Batch.setup(good + [bad], 2, "minimal", "spd")
+    assert e.value.status == samg.E_INVALID and "problem 3" in str(e.value)
+    rect = _RawCsr(3, 2, [0, 1, 2, 3], [0, 1, 1], [1.0, 1.0, 1.0])
+    with pytest.raises(samg.SamgError) as e:
+        samg.Batch.setup([good[0], rect], 2, "minimal", "spd")
+    assert e.value.status == samg.E_INVALID and "problem 1" in str(e.value)
+    with pytest.raises(samg.SamgError) as e:
+        samg.Batch.setup([], 2, "minimal", "spd")
+    assert e.value.status == samg.E_INVALID
+    assert samg.samg_solve_batched(None, 1e-8, 1, None) == samg.E_INVALID
+    assert samg.samg_batch_size(None) == 0
+
+
+def test_batched_setup_without_a_gpu_reports_the_device(lib):
+    import paper_1102_0919_gb300 as samg
+
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(samg.SamgError) as e:
+        samg.Batch.setup([_lap(6), _lap(8)], 2, "minimal", "spd")
+    assert e.value.status == samg.E_CUDA and "problem 0" in str(e.value)
