@@ -355,6 +355,10 @@ def relax_boot_rq(L, spd, target, sigma, U, V, mu_b, omega):
 
 def dense_XY(L: Level, spd: bool):
     """X = [[0, A], [A^t, 0]], Y = diag(B, C) of Eq. X (SPD kind: A, B)."""
+    size = L.A.shape[0] if spd else L.A.shape[0] + L.A.shape[1]
+    if size > 20000:
+        raise ValueError("coarsest level of %d unknowns is too large for a dense solve "
+                         "(the coarsening stopped early: check theta)" % size)
     if spd:
         return L.A.toarray(), L.B.toarray()
     m, n = L.A.shape
