@@ -312,7 +312,11 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
  * minimal-SVD relaxations with the level's B (m x m) and C (n x n)
  * (spd = 0), or for max(1, fused_count) stacked sweeps over the rows of
  * A - lambda_j B of the SPD kind (spd = 1, A square; mode 1: norms formed
- * per column).  B, C may be NULL (identity, as on the finest level).  Call with buf = NULL (capacity 0) to get *size,
+ * per column).  B, C may be NULL (identity, as on the finest level).
+ * resident_slots = 0 gives the solve's schedule.  resident_slots in
+ * [1, 4095] builds, when the program keeps at most that many columns live,
+ * one band with every column resident in the window (a mode the solve does
+ * not use yet).  Call with buf = NULL (capacity 0) to get *size,
  * then with a buffer of that many bytes.  Layout, little-endian:
  *   i32 rows, cols, nbands, nlevels, nchunks, max_slots, mode, shifted;
  *   i64 nreq, image_bytes;
@@ -330,8 +334,8 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
  * value its column (i32).  Returns SAMG_E_INVALID for a malformed CSR or a
  * short buffer. */
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
-                                int fused_count, int spd, unsigned char *buf, int64_t capacity,
-                                int64_t *size);
+                                int fused_count, int spd, int resident_slots, unsigned char *buf,
+                                int64_t capacity, int64_t *size);
 
 /* Test hook for the bounded device waits (the paper has no counterpart):
  * from now on band `band` of the Kaczmarz schedules of level `level`

@@ -895,8 +895,8 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
 }
 
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
-                                int fused_count, int spd, unsigned char *buf, int64_t capacity,
-                                int64_t *size) {
+                                int fused_count, int spd, int resident_slots, unsigned char *buf,
+                                int64_t capacity, int64_t *size) {
     try {
         SAMG_CHECK(fused_count >= 0 && size && (capacity == 0 || buf), SAMG_E_INVALID,
                    "sweep_schedule: bad arguments");
@@ -911,7 +911,8 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
             SAMG_CHECK(hc.m == h.n, SAMG_E_INVALID, "sweep_schedule: C must be n x n");
         }
         HostSched hs;
-        host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs);
+        host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs,
+                      resident_slots);
         std::vector<unsigned char> out;
         out.reserve(64 + 4 * hs.band_chunk.size() + 32 * hs.chunk.size() + 16 * hs.lvl.size() +
                     8 * hs.req.size() + hs.img_d.size());

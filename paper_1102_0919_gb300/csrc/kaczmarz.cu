@@ -824,9 +824,17 @@ namespace {
 // Contiguous bands of rows, each grown (doubling) until it has about
 // TARGET_PAR rows per level, at most MAX_BAND_ROWS rows, and at most SLOT_CAP
 // columns live at once.  Returns the first row of every band, then p.rows.
-std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w) {
+// resident_cap > 0: when the whole program keeps at most that many columns
+// live, it is one band (every column resident in the window; no cross-band
+// requirement and no first touch written by another band).
+std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w,
+                            int resident_cap = 0) {
     std::vector<int> bstart;
     int slots = 0;
+    if (resident_cap > 0 && p.rows > 0) {
+        analyze_band(p, glv, 0, p.rows, w, &slots);
+        if (slots <= resident_cap) return {0, p.rows};
+    }
     for (int r0 = 0; r0 < p.rows;) {
         int R = std::min(256, p.rows - r0), good = 0;
         for (;;) {
@@ -852,7 +860,7 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
 // of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
 // block Gauss-Seidel relaxations (b entries read the other unknown with
 // coefficient -s_j and are not updated; norms from a).
-void build_host(const Pattern &p, int mode, HostSched &ks) {
+void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0) {
     const int rows = p.rows, cols = p.cols;
     ks.rows = rows;
     ks.cols = cols;
@@ -861,7 +869,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks) {
     BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
-    std::vector<int> bstart = form_bands(p, glv, w);
+    std::vector<int> bstart = form_bands(p, glv, w, resident_cap);
     const int nb = (int)bstart.size() - 1;
     int slots = 0;
     ks.nbands = nb;
@@ -1221,15 +1229,18 @@ Pattern sweep_pattern(const HCsr &A, int fused_count) {
 }  // namespace
 
 void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
-                   HostSched &h) {
+                   HostSched &h, int resident_cap) {
+    SAMG_CHECK(resident_cap >= 0 && resident_cap <= 4095, SAMG_E_INVALID,
+               "kaczmarz: resident window larger than the slot field (4095)");
     if (spd) {
         const HCsr I = B ? HCsr() : identity_csr(A.m);
-        build_host(stacked_pattern(A, B ? *B : I, std::max(1, fused_count)), 1, h);
+        build_host(stacked_pattern(A, B ? *B : I, std::max(1, fused_count)), 1, h, resident_cap);
     } else if (fused_count <= 0) {
-        build_host(merge_pattern(A, nullptr), 0, h);
+        build_host(merge_pattern(A, nullptr), 0, h, resident_cap);
     } else {
         const HCsr Im = B ? HCsr() : identity_csr(A.m), In = C ? HCsr() : identity_csr(A.n);
-        build_host(fused_pattern(A, transpose_csr(A), B ? *B : Im, C ? *C : In, fused_count), 2, h);
+        build_host(fused_pattern(A, transpose_csr(A), B ? *B : Im, C ? *C : In, fused_count), 2, h,
+                   resident_cap);
     }
 }
 

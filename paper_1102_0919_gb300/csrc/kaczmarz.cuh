@@ -84,8 +84,11 @@ struct HostSched {
 // minimal-SVD relaxations with the level's B and C (mode 2), or, with spd,
 // of max(1, fused_count) stacked sweeps over the rows of A - s B (mode 1).
 // B, C null: identity.  The same pattern builders as the solve's.
+// resident_cap > 0 (at most 4095): a program that keeps at most that many
+// columns live is built as one band with every column resident (a mode the
+// solve does not use yet).
 void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
-                   HostSched &h);
+                   HostSched &h, int resident_cap = 0);
 
 // Build the schedule of the rows of A (shift form when B != nullptr: rows of
 // A - s B over the union pattern).  Host CSR inputs.

@@ -189,3 +189,35 @@ def test_row_longer_than_a_staging_chunk_is_rejected():
     with pytest.raises(samg.SamgError) as e:
         samg.sweep_schedule(A, 0)
     assert e.value.status == samg.E_INVALID and "staging chunk" in str(e.value)
+
+
+def test_resident_band_mode_on_coarse_levels():
+    # optional mode: a coarse level whose program keeps at most 4095 columns
+    # live is one band with every column resident; all first touches are
+    # then staged ahead (no global reads at compute time, no requirements),
+    # and the replay still matches the oracle's relaxations
+    A = W.gradient(64).to_scipy()
+    H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(W.GRAD_PARAMS, seed=4, n_mult=2))
+    L = H.levels[3]
+    m, n = L.A.shape
+    assert m + n <= 4095
+    base = parse(samg.sweep_schedule(L.A, 4, B=L.B, C=L.C))
+    S = parse(samg.sweep_schedule(L.A, 4, B=L.B, C=L.C, resident_slots=4095))
+    assert base["nbands"] > 1 and S["nbands"] == 1
+    assert S["lvl"][:, 1].sum() == 0                      # no cross-band requirement
+    from sweep_replay import _image
+    for c in range(len(S["chunks"])):
+        fl = _image(S, c)["ent"][:, 1]
+        assert not np.any(((fl & 1) != 0) & ((fl & 4) == 0))   # every first touch staged
+    rng = np.random.default_rng(8)
+    sig = np.abs(s) * 1.01
+    Uc, Vc = rng.standard_normal((m, 8)), rng.standard_normal((n, 8))
+    K, T = rng.standard_normal((m, 8)), rng.standard_normal((n, 8))
+    z = replay(S, np.vstack([Vc, Uc]), np.vstack([K, T]), sig)
+    Ur, Vr = Uc.copy(), Vc.copy()
+    for _ in range(4):
+        oracle.relax_boot(L, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+    assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10
+    # a program with more live columns than the cap keeps the usual bands
+    big = parse(samg.sweep_schedule(A, 4, resident_slots=64))
+    assert big["nbands"] == parse(samg.sweep_schedule(A, 4))["nbands"]
