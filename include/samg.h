@@ -83,11 +83,23 @@ typedef struct {
                              the first n_conv (0 = all n_b); the others are
                              guards that keep the block complete past a small
                              gap (not in the paper) */
+    int32_t coarse_pinv;  /* coarsest additive solve (Sec. 4.2):
+                             0 = the paper's form, the SVD pseudo-inverse of
+                               X_L - s_j Y_L without its smallest singular
+                               value;
+                             1 = a variant (not in the paper): with the
+                               generalized eigenpairs X_L w_k = lam_k Y_L w_k,
+                               W^t Y_L W = I (once per hierarchy),
+                               z = sum over k != k* of w_k (w_k^t r) /
+                               (lam_k - s_j), k* the lam_k nearest s_j (ties:
+                               the lowest k).  It equals form 0 when Y_L = I
+                               and costs two passes over W per cycle, so it
+                               suits large coarsest levels. */
 } samg_params;
 
 /* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
  * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
- * seed 20110204, prec SAMG_FP32, n_conv 0 (all). */
+ * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0. */
 void samg_default_params(samg_params *p);
 
 /* ---------------------------------------------------------------- setup --
@@ -199,6 +211,12 @@ samg_status samg_set_triplets_device(samg_ctx *ctx, const double *sigma, const d
                                      const double *V);
 
 samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec);
+
+/* Selects the form of the coarsest additive solve of this context, as
+ * samg_params.coarse_pinv (0 the paper's SVD pseudo-inverse, 1 the
+ * generalized-eigen variant); SAMG_E_INVALID for any other value.  The
+ * hierarchy is unchanged. */
+samg_status samg_set_coarse_pinv(samg_ctx *ctx, int form);
 
 /* Kernel timing: with profiling on, every launch of the solve phase is
  * bracketed by CUDA events on the context's stream.  samg_profile_read
@@ -371,9 +389,11 @@ samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int 
  * 1,048,576 at nb = 16).  The array is shared by all callers in the process
  * on a device: calls whose GPU work overlaps (other streams, other host
  * threads) race on it and give wrong results; serialize them.  The first
- * call on each device looks the array's address up with
- * cudaGetSymbolAddress (that device current) and caches it; make that first
- * call before any stream capture begins on that device.  Arguments as for
+ * call in each CUDA context (each device's primary context, and again after
+ * a cudaDeviceReset has replaced it) looks the array's address up with
+ * cudaGetSymbolAddress (that device current) and caches it under the
+ * context's unique id; make that first call before any stream capture
+ * begins on that device.  Arguments as for
  * samg_block_gram; X, Y and G are device pointers, stream NULL = legacy
  * default stream; the call returns when the work is enqueued. */
 samg_status samg_block_gram_noalloc(const double *X, const double *Y, int64_t rows, int nb,

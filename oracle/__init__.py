@@ -20,7 +20,8 @@ Parity unpinned: the per-cycle convergence rates of the figures (the
 figures are not in the available text) and the setup constants the paper
 leaves open (R5-R10, R13-R16 in samg.py) beyond the invariants above.
 """
-from .samg import (DEFAULTS, Hierarchy, Level, coarsest_pinv_apply, coarsest_triplets,  # noqa: F401
+from .samg import (DEFAULTS, Hierarchy, Level, coarse_geneig, coarsest_pinv_apply,  # noqa: F401
+                   coarsest_triplets,
                    dense_XY, fit_interp, galerkin, interp_sets, kaczmarz_sweep,
                    level_residual, random_block, rayleigh, relax_boot, relax_test, residual_norms,
                    ritz, rs_coarsen, setup, solve, strength, vcycle)

@@ -20,7 +20,11 @@ silent the readings below are used (numbers as in the design notes):
   more than 90% of the points, or min(m_c, n_c) < 2 n_b, or max_levels.
 * R7  coarsest additive solve: SVD pseudo-inverse of X - sigma_j Y with the
   single smallest singular value left out (params["coarse_drop"] > 1 leaves
-  out more: a variant, not the paper's).
+  out more: a variant, not the paper's).  params["coarse_pinv"] = "geneig"
+  selects a variant (not the paper's): with the generalized eigenpairs
+  X w_k = lam_k Y w_k, W^t Y W = I, z = sum over k != k* of
+  w_k (w_k^t r) / (lam_k - sigma_j), k* the lam_k nearest sigma_j (lowest
+  k on ties); it equals the paper's form when Y = I.
 * R8  strength sums run over all columns including the diagonal.
 * R9  Ruge-Stueben ties go to the lowest index.
 * R10 coarse points are numbered in increasing fine index.
@@ -70,7 +74,8 @@ from . import build as _build
 _LIB = None
 
 DEFAULTS = dict(n_t=8, theta=0.06, mu_t=8, mu_b=4, mu_tJ=1, mu_bJ=1, omega_J=0.7,
-                n_mult=10, coarsest_max=100, max_levels=30, seed=20110204, coarse_drop=1)
+                n_mult=10, coarsest_max=100, max_levels=30, seed=20110204, coarse_drop=1,
+                coarse_pinv="svd")
 
 
 def _lib():
@@ -394,17 +399,41 @@ def coarsest_triplets(L: Level, spd: bool, target: str, nb: int):
             np.ascontiguousarray(Z[m:, sel] * s))
 
 
-def coarsest_pinv_apply(XY, sigma, K, T, spd: bool, drop: int = 1):
+def coarse_geneig(XY):
+    """Generalized eigenpairs of the coarsest pencil: X W = Y W diag(lam),
+    W^t Y W = I, lam ascending (dense LAPACK, called once per hierarchy by
+    the "geneig" variant of the coarsest solve)."""
+    X, Y = XY[0], XY[1]
+    return sla.eigh(X, Y)
+
+
+def coarsest_pinv_apply(XY, sigma, K, T, spd: bool, drop: int = 1, form: str = "svd"):
     """[u; v] = (X - s_j Y)^+ [kappa; tau] per column j, with the SVD
     pseudo-inverse leaving out the single smallest singular value (Sec. 4.2,
-    R7).  drop > 1 leaves out that many (a variant, not the paper's)."""
-    X, Y = XY
+    R7).  drop > 1 leaves out that many (a variant, not the paper's).
+
+    form = "geneig" (a variant, not the paper's): with X w_k = lam_k Y w_k,
+    W^t Y W = I, the inverse of X - s_j Y is W (Lam - s_j)^-1 W^t; the
+    `drop` generalized eigenpairs nearest s_j (lowest k on ties) are left
+    out.  XY may carry coarse_geneig(XY) as a third item."""
+    X, Y = XY[0], XY[1]
     rhs = K if spd else np.vstack([K, T])
     out = np.zeros_like(rhs)
-    for j in range(rhs.shape[1]):
-        Uu, s, Vt = np.linalg.svd(X - sigma[j] * Y)
-        k = len(s) - drop                 # s is descending: drop the last
-        out[:, j] = Vt[:k].T @ ((Uu[:, :k].T @ rhs[:, j]) / s[:k])
+    if form == "geneig":
+        lam, Wm = XY[2] if len(XY) > 2 else coarse_geneig(XY)
+        for j in range(rhs.shape[1]):
+            d = lam - sigma[j]
+            near = np.lexsort((np.arange(len(d)), np.abs(d)))[:drop]
+            inv = np.zeros_like(d)
+            keep = np.ones(len(d), dtype=bool)
+            keep[near] = False
+            inv[keep] = 1.0 / d[keep]
+            out[:, j] = Wm @ (inv * (Wm.T @ rhs[:, j]))
+    else:
+        for j in range(rhs.shape[1]):
+            Uu, s, Vt = np.linalg.svd(X - sigma[j] * Y)
+            k = len(s) - drop                 # s is descending: drop the last
+            out[:, j] = Vt[:k].T @ ((Uu[:, :k].T @ rhs[:, j]) / s[:k])
     if spd:
         return out, None
     m = K.shape[0]
@@ -471,7 +500,8 @@ def vcycle(H: Hierarchy, l: int, sigma, U, V, K, T, coarse_XY=None) -> None:
     L = H.levels[l]
     if l == len(H.levels) - 1:
         XY = coarse_XY if coarse_XY is not None else dense_XY(L, spd)
-        u, v = coarsest_pinv_apply(XY, sigma, K, T, spd, p.get("coarse_drop", 1))
+        u, v = coarsest_pinv_apply(XY, sigma, K, T, spd, p.get("coarse_drop", 1),
+                                   p.get("coarse_pinv", "svd"))
         U[:] = u
         if not spd:
             V[:] = v
@@ -673,6 +703,15 @@ def redo_interpolation(H: Hierarchy, sigma, U, V, converged, factor: float = 1e-
     H.levels = levels
 
 
+def _solve_XY(H: Hierarchy):
+    """The coarsest pencil (X, Y), with its generalized eigenpairs for the
+    "geneig" form of the coarsest solve."""
+    XY = dense_XY(H.levels[-1], H.spd)
+    if H.params.get("coarse_pinv", "svd") == "geneig":
+        XY = (XY[0], XY[1], coarse_geneig(XY))
+    return XY
+
+
 def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
           redo_tol: float | None = None, n_conv: int | None = None):
     """Additive phase (Sec. 4): V-cycle per triplet with sigma_j fixed, then a
@@ -693,7 +732,7 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
     U = np.array(U, dtype=np.float64, order="C")
     V = None if spd else np.array(V, dtype=np.float64, order="C")
     sigma = np.array(sigma, dtype=np.float64)
-    XY = dense_XY(H.levels[-1], spd)
+    XY = _solve_XY(H)
     hist = [residual_norms(A, spd, sigma, U, V)]
     H.redos.clear()
     nconv = 0
@@ -710,7 +749,7 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
             k = int(conv.sum())
             if nconv < k < len(conv):
                 redo_interpolation(H, sigma, U, V, conv)
-                XY = dense_XY(H.levels[-1], spd)
+                XY = _solve_XY(H)
                 H.redos.append(it + 1)
             nconv = max(nconv, k)
     return sigma, U, V, hist

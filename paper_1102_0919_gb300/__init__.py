@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
                 ("mu_b", ctypes.c_int32), ("mu_tJ", ctypes.c_int32), ("mu_bJ", ctypes.c_int32),
                 ("omega_J", ctypes.c_double), ("n_mult", ctypes.c_int32),
                 ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32),
+                ("coarse_pinv", ctypes.c_int32)]
 
 
 class _Csr(ctypes.Structure):
@@ -71,6 +72,7 @@ samg_solve = _sig("samg_solve", _I, _CTX, ctypes.c_double, _I, ctypes.POINTER(_I
 samg_set_triplets = _sig("samg_set_triplets", _I, _CTX, _P, _P, _P)
 samg_get_triplets = _sig("samg_get_triplets", _I, _CTX, _P, _P, _P, _P)
 samg_set_precision = _sig("samg_set_precision", _I, _CTX, _I)
+samg_set_coarse_pinv = _sig("samg_set_coarse_pinv", _I, _CTX, _I)
 samg_get_hierarchy_info = _sig("samg_get_hierarchy_info", _I, _CTX, ctypes.POINTER(_I), _P, _P, _P)
 samg_get_level_matrix = _sig("samg_get_level_matrix", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
@@ -114,6 +116,7 @@ samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(c
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
             "samg_solve", "samg_set_triplets", "samg_get_triplets", "samg_set_precision",
+            "samg_set_coarse_pinv",
             "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
@@ -282,6 +285,11 @@ class Solver:
 
     def set_precision(self, prec):
         self._check(samg_set_precision(self._ctx, {"fp64": FP64, "fp32": FP32}.get(prec, prec)))
+
+    def set_coarse_pinv(self, form):
+        """0: the paper's SVD pseudo-inverse on the coarsest level; 1: the
+        generalized-eigen variant."""
+        self._check(samg_set_coarse_pinv(self._ctx, int(form)))
 
     # ---------------------------------------------------------- solve
     def solve(self, tol=1e-8, max_outer=100):

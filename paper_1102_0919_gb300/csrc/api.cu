@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <dlfcn.h>
 #include <mutex>
 #include <string>
 
@@ -57,6 +58,8 @@ void check_common(int n_b, const samg_params *prm) {
     SAMG_CHECK(prm != nullptr, SAMG_E_INVALID, "params is NULL");
     SAMG_CHECK(prm->mu_b >= 0 && prm->mu_t >= 0, SAMG_E_INVALID, "negative relaxation count");
     SAMG_CHECK(prm->prec == SAMG_FP64 || prm->prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
+    SAMG_CHECK(prm->coarse_pinv == 0 || prm->coarse_pinv == 1, SAMG_E_INVALID,
+               "coarse_pinv must be 0 (SVD pseudo-inverse) or 1 (generalized-eigen variant)");
 }
 
 template <typename T>
@@ -229,6 +232,7 @@ void samg_default_params(samg_params *p) {
     p->seed = 20110204ull;
     p->prec = SAMG_FP32;
     p->n_conv = 0;
+    p->coarse_pinv = 0;
 }
 
 const char *samg_last_error(const samg_ctx *ctx) {
@@ -370,19 +374,29 @@ samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, sam
     } catch (const Error &e) {
         g_create_error = e.what();
         return e.status;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "setup_batched: host allocation failed";
+        return SAMG_E_NOMEM;
     }
     samg_batch *b = new (std::nothrow) samg_batch();
     if (!b) return SAMG_E_NOMEM;
-    for (int p = 0; p < count; ++p) {
-        samg_ctx *c = nullptr;
-        const samg_status st = samg_setup(A[p], n_b, target, kind, params, cuda_stream, &c);
-        if (st != SAMG_OK) {
-            const std::string msg = "setup_batched: problem " + std::to_string(p) + ": " + g_create_error;
-            samg_batch_destroy(b);
-            g_create_error = msg;
-            return st;
+    try {
+        b->ctx.reserve(count);  // push_back below cannot throw after this
+        for (int p = 0; p < count; ++p) {
+            samg_ctx *c = nullptr;
+            const samg_status st = samg_setup(A[p], n_b, target, kind, params, cuda_stream, &c);
+            if (st != SAMG_OK) {
+                const std::string msg = "setup_batched: problem " + std::to_string(p) + ": " + g_create_error;
+                samg_batch_destroy(b);
+                g_create_error = msg;
+                return st;
+            }
+            b->ctx.push_back(c);
         }
-        b->ctx.push_back(c);
+    } catch (const std::bad_alloc &) {
+        samg_batch_destroy(b);
+        g_create_error = "setup_batched: host allocation failed";
+        return SAMG_E_NOMEM;
     }
     *out = b;
     return SAMG_OK;
@@ -489,6 +503,15 @@ samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec) {
     return guarded(ctx, [&] {
         SAMG_CHECK(prec == SAMG_FP64 || prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
         ctx->prm.prec = prec;
+    });
+}
+
+samg_status samg_set_coarse_pinv(samg_ctx *ctx, int form) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(form == 0 || form == 1, SAMG_E_INVALID,
+                   "coarse_pinv must be 0 (SVD pseudo-inverse) or 1 (generalized-eigen variant)");
+        ctx->prm.coarse_pinv = form;
     });
 }
 
@@ -1004,26 +1027,61 @@ namespace {
 constexpr size_t GRAM_STATIC_DOUBLES = 65536;  // 512 KiB of partial sums
 __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
 
-constexpr int GRAM_STATIC_MAX_DEVICES = 64;
-double *g_gram_static_addr[GRAM_STATIC_MAX_DEVICES];  // per device, looked up once
+// The scratch's device address belongs to a CUDA context: a device reset or a
+// new primary context loads the module again, possibly elsewhere.  The cache
+// is therefore keyed on the current context's process-unique id
+// (cuCtxGetId), which a new context never repeats, unlike its handle.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    double *addr;
+};
+std::vector<ScratchAddr> g_gram_static_addr;  // one entry per context seen
 std::mutex g_gram_static_mu;
 
-// Device address of g_gram_static for the current device.  The first call on
-// a device asks the runtime once (cudaGetSymbolAddress, with that device
-// current) and caches the answer; later calls only read the cache.
-double *gram_static_scratch() {
-    int dev = 0;
-    SAMG_CUDA(cudaGetDevice(&dev));
-    SAMG_CHECK(dev >= 0 && dev < GRAM_STATIC_MAX_DEVICES, SAMG_E_INVALID,
-               "block_gram_noalloc: device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_gram_static_mu);
-    if (!g_gram_static_addr[dev]) {
-        void *p = nullptr;
-        SAMG_CUDA(cudaGetSymbolAddress(&p, g_gram_static));
-        SAMG_CHECK(p != nullptr, SAMG_E_CUDA, "block_gram_noalloc: no address for the scratch");
-        g_gram_static_addr[dev] = static_cast<double *>(p);
+// Current context's unique id from the driver API, through the driver
+// library the runtime has already loaded (the library links only the
+// runtime).  0 when no context is current yet.
+unsigned long long current_context_id() {
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
+        if (h) {
+            get_current = reinterpret_cast<GetCurrent>(dlsym(h, "cuCtxGetCurrent"));
+            get_id = reinterpret_cast<GetId>(dlsym(h, "cuCtxGetId"));
+        }
     }
-    return g_gram_static_addr[dev];
+    SAMG_CHECK(get_current && get_id, SAMG_E_CUDA,
+               "block_gram_noalloc: the CUDA driver's context functions are unavailable");
+    void *ctx = nullptr;
+    SAMG_CHECK(get_current(&ctx) == 0, SAMG_E_CUDA, "block_gram_noalloc: cuCtxGetCurrent failed");
+    if (!ctx) return 0;
+    unsigned long long id = 0;
+    SAMG_CHECK(get_id(ctx, &id) == 0, SAMG_E_CUDA, "block_gram_noalloc: cuCtxGetId failed");
+    return id;
+}
+
+// Device address of g_gram_static in the current context.  The first call
+// in a context asks the runtime once (cudaGetSymbolAddress, which also makes
+// the device's primary context current) and caches the answer under the
+// context's id; later calls in that context only read the cache.
+double *gram_static_scratch() {
+    std::lock_guard<std::mutex> lock(g_gram_static_mu);
+    unsigned long long id = current_context_id();
+    if (id != 0)
+        for (const ScratchAddr &e : g_gram_static_addr)
+            if (e.ctx_id == id) return e.addr;
+    void *p = nullptr;
+    SAMG_CUDA(cudaGetSymbolAddress(&p, g_gram_static));
+    SAMG_CHECK(p != nullptr, SAMG_E_CUDA, "block_gram_noalloc: no address for the scratch");
+    id = current_context_id();
+    SAMG_CHECK(id != 0, SAMG_E_CUDA, "block_gram_noalloc: no current CUDA context");
+    g_gram_static_addr.push_back({id, static_cast<double *>(p)});
+    return static_cast<double *>(p);
 }
 
 }  // namespace

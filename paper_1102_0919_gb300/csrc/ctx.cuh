@@ -104,6 +104,7 @@ struct Coarse {
     DBuf<double> X, Y, lam, W, Wt, work;
     DBuf<int> status;
     DBuf<double> qwarm;  // per column: the pseudo-inverse's subspace basis of the last call
+    DBuf<double> cbuf;   // generalized-eigen variant: coefficients W^t r (M x ld)
     bool warm = false;
 };
 

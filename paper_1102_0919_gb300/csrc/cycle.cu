@@ -216,6 +216,13 @@ void coarse_solve(samg_ctx &c) {
     Level &L = c.L.back();
     Work<T> &w = work<T>(L);
     Prof pr(c.prof, c.stream, 3, 2.0 * (double)c.co.M * c.co.M * 8.0);
+    if (c.prm.coarse_pinv == 1) {
+        if (c.co.cbuf.n < (size_t)c.co.M * c.ld) c.co.cbuf.alloc((size_t)c.co.M * c.ld);
+        launch_coarse_apply_geneig<T>(c.co.M, c.co.m1, c.ld, c.nb, c.co.lam.p, c.co.W.p, c.co.Wt.p,
+                                      c.sigma.p, w.k.p, c.spd() ? w.k.p : w.t.p, w.u.p,
+                                      c.spd() ? w.u.p : w.v.p, c.co.cbuf.p, c.stream);
+        return;
+    }
     const size_t nq = coarse_warm_size(c.co.M, c.nb);
     if (c.co.qwarm.n != nq) {
         c.co.qwarm.alloc(nq);

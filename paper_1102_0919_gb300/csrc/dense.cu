@@ -753,6 +753,130 @@ void launch_coarse_apply(int M, int m1, int ld, int nb, const double *lam, const
     SAMG_CUDA(cudaGetLastError());
 }
 size_t coarse_warm_size(int M, int nb) { return (size_t)nb * 2 * M; }
+
+// Pass 1 of the generalized-eigen coarsest solve: warp w of the CTA owns
+// row k of W^t; its lanes split the M-long dot products for all nb columns,
+// then c[k, j] = (W^t r_j)_k / (lam_k - s_j), zero at k = k*_j.  Every CTA
+// finds k*_j itself (an argmin over M values per column).
+constexpr int CG_WARPS = 8;
+template <typename T>
+__global__ void __launch_bounds__(CG_WARPS * 32)
+    k_coarse_geneig_c(int M, int m1, int ld, int nb, const double *__restrict__ lam,
+                      const double *__restrict__ Wt, const double *__restrict__ sigma,
+                      const T *__restrict__ k1, const T *__restrict__ k2, double *__restrict__ cbuf) {
+    __shared__ int s_kstar[16];
+    __shared__ double s_best[CG_WARPS][16];
+    __shared__ int s_bidx[CG_WARPS][16];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // k*_j: nearest lam_k to s_j, lowest k on ties
+    for (int j = 0; j < nb; ++j) {
+        const double sj = sigma[j];
+        double best = INFINITY;
+        int bi = 0x7fffffff;
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            const double d = fabs(lam[k] - sj);
+            if (d < best || (d == best && k < bi)) { best = d; bi = k; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_best[warp][j] = best; s_bidx[warp][j] = bi; }
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+        const int j = threadIdx.x;
+        double best = s_best[0][j];
+        int bi = s_bidx[0][j];
+        for (int w = 1; w < CG_WARPS; ++w)
+            if (s_best[w][j] < best || (s_best[w][j] == best && s_bidx[w][j] < bi)) {
+                best = s_best[w][j];
+                bi = s_bidx[w][j];
+            }
+        s_kstar[j] = bi;
+    }
+    __syncthreads();
+    const int k = blockIdx.x * CG_WARPS + warp;
+    if (k >= M) return;
+    double acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    const double *wrow = Wt + (size_t)k * M;
+    for (int i = lane; i < M; i += 32) {
+        const double w = wrow[i];
+        const T *r = i < m1 ? k1 + (size_t)i * ld : k2 + (size_t)(i - m1) * ld;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nb) acc[j] = fma(w, (double)r[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        for (int o = 16; o; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    if (lane < nb) {
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j == lane) v = acc[j];
+        const double den = lam[k] - sigma[lane];
+        cbuf[(size_t)k * ld + lane] = (k == s_kstar[lane] || den == 0.0) ? 0.0 : v / den;
+    }
+}
+
+// Pass 2: z = W c, warp w of the CTA owns row i of W.
+template <typename T>
+__global__ void __launch_bounds__(CG_WARPS * 32)
+    k_coarse_geneig_z(int M, int m1, int ld, int nb, const double *__restrict__ W,
+                      const double *__restrict__ cbuf, T *__restrict__ o1, T *__restrict__ o2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * CG_WARPS + warp;
+    if (i >= M) return;
+    double acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    const double *wrow = W + (size_t)i * M;
+    for (int k = lane; k < M; k += 32) {
+        const double w = wrow[k];
+        const double *c = cbuf + (size_t)k * ld;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nb) acc[j] = fma(w, c[j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        for (int o = 16; o; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    if (lane < nb) {
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j == lane) v = acc[j];
+        if (i < m1) o1[(size_t)i * ld + lane] = (T)v;
+        else o2[(size_t)(i - m1) * ld + lane] = (T)v;
+    }
+}
+
+template <typename T>
+void launch_coarse_apply_geneig(int M, int m1, int ld, int nb, const double *lam,
+                                const double *W, const double *Wt, const double *sigma,
+                                const T *k1, const T *k2, T *o1, T *o2, double *cbuf,
+                                cudaStream_t s) {
+    SAMG_CHECK(nb >= 1 && nb <= 16 && ld >= nb, SAMG_E_INVALID, "coarse geneig: bad block width");
+    const unsigned grid = (unsigned)((M + CG_WARPS - 1) / CG_WARPS);
+    SAMG_COUNT_LAUNCH();
+    k_coarse_geneig_c<T><<<grid, CG_WARPS * 32, 0, s>>>(M, m1, ld, nb, lam, Wt, sigma, k1, k2, cbuf);
+    SAMG_CUDA(cudaGetLastError());
+    SAMG_COUNT_LAUNCH();
+    k_coarse_geneig_z<T><<<grid, CG_WARPS * 32, 0, s>>>(M, m1, ld, nb, W, cbuf, o1, o2);
+    SAMG_CUDA(cudaGetLastError());
+}
+template void launch_coarse_apply_geneig<float>(int, int, int, int, const double *,
+                                                const double *, const double *, const double *,
+                                                const float *, const float *, float *, float *,
+                                                double *, cudaStream_t);
+template void launch_coarse_apply_geneig<double>(int, int, int, int, const double *,
+                                                 const double *, const double *, const double *,
+                                                 const double *, const double *, double *,
+                                                 double *, double *, cudaStream_t);
 template void launch_coarse_apply<float>(int, int, int, int, const double *, const double *,
                                          const double *, const double *, const float *,
                                          const float *, float *, float *, double *, int,

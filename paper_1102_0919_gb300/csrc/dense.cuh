@@ -38,4 +38,14 @@ void launch_coarse_apply(int M, int m1, int ld, int nb, const double *lam, const
                          T *o2, double *qwarm, int warm, cudaStream_t s);
 size_t coarse_warm_size(int M, int nb);
 
+// The generalized-eigen variant of the coarsest solve (coarse_pinv = 1):
+// z_j = sum over k != k*_j of w_k (w_k^t r_j) / (lam_k - s_j), k*_j the lam_k
+// nearest s_j (ties: lowest k).  Two passes, each one warp per output row
+// over all columns: c = D_j W^t r (into cbuf, M x ld float64), z = W c.
+template <typename T>
+void launch_coarse_apply_geneig(int M, int m1, int ld, int nb, const double *lam,
+                                const double *W, const double *Wt, const double *sigma,
+                                const T *k1, const T *k2, T *o1, T *o2, double *cbuf,
+                                cudaStream_t s);
+
 }  // namespace samg

@@ -574,9 +574,16 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                             // requirements of this level: wait for the producer,
                             // which releases every wait when it gives up
                             const unsigned long long t0 = gtimer();
+                            bool late = false;
                             while (ld_acq_cta(&s_ready) <= lb)
-                                if (gtimer() - t0 > 2 * WAIT_NS) break;
-                            aborted = __any_sync(FULL, *((volatile int *)&s_abort) != 0);
+                                if (gtimer() - t0 > 2 * WAIT_NS) { late = true; break; }
+                            if (late) {
+                                // the producer never released this level: give up
+                                // like a timed-out wait (error word, CTA abort)
+                                atomicExch(kv.err, 1);
+                                *((volatile int *)&s_abort) = 1;
+                            }
+                            aborted = __any_sync(FULL, late || *((volatile int *)&s_abort) != 0);
                         }
                         if (!aborted) {
                             // G = 2^lgG lanes per row (the smallest power of two
@@ -748,6 +755,11 @@ void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaS
     const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + (size_t)KZ_NBUF * SG::stride;
     SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
                "kaczmarz: vector blocks must be 16-byte aligned");
+    // a window of more slots than a CTA's shared memory holds (a resident
+    // schedule built for a narrower block or precision) is refused here
+    SAMG_CHECK(smem <= 227u * 1024u, SAMG_E_INVALID,
+               "kaczmarz: the schedule's window and staging buffers exceed 227 KB of shared memory "
+               "at this block width and precision");
     // per kernel instance and device (a function attribute is set per
     // device): the largest dynamic shared memory set so far and the SM
     // count, under a lock since contexts may launch from several host

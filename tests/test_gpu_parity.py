@@ -144,6 +144,26 @@ def test_coarsest_pseudo_inverse(case):
         assert rel(vg, vr) < 1e-9
 
 
+def test_coarsest_geneig_variant(case):
+    """coarse_pinv = 1 (the generalized-eigen variant of the Sec. 4.2 coarsest
+    solve) against the oracle's definition of the same variant."""
+    H, g = case["H"], case["g"]
+    spd = case["kind"] == "spd"
+    l = len(H.levels) - 1
+    sig, U, V, K, T = _vecs(case, l, 401)
+    mL, nL = H.levels[l].A.shape
+    g.set_coarse_pinv(1)
+    try:
+        ug, vg = g.coarsest_solve(sig, K, T, nL if spd else mL, nL)
+    finally:
+        g.set_coarse_pinv(0)
+    XY = oracle.dense_XY(H.levels[l], spd)
+    ur, vr = oracle.coarsest_pinv_apply(XY, sig, K, T, spd, form="geneig")
+    assert rel(ug, ur) < 1e-9
+    if not spd:
+        assert rel(vg, vr) < 1e-9
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 5e-4)])
 def test_one_vcycle(case, prec, tol):
     H, g = case["H"], case["g"]

@@ -566,3 +566,87 @@ def test_dominant_svd_lapack():
     assert hist[-1].max() <= 1e-9
     ref = np.sort(np.linalg.svd(A.toarray(), compute_uv=False))[::-1][:4]
     assert np.allclose(s, ref, rtol=1e-10)
+
+
+def test_residual_norms_hand_built_triplets():
+    """R11 pinned on triplets whose residuals are worked out by hand.
+
+    A = [[3, 0], [0, 1], [0, 0]], sigma = 3, u = e1, v = (e1 + e2)/sqrt(2):
+      A v - sigma u   = (3/r - 3, 1/r, 0)      with r = sqrt(2)
+      A^t u - sigma v = (3 - 3/r, -3/r)
+    so |A v - s u|^2 + |A^t u - s v|^2 = 2 (3 - 3/r)^2 + 1/2 + 9/2 and
+    rho = sqrt(2 (3 - 3/r)^2 + 5) / 3.  Dropping either term, using the
+    wrong sign of sigma, dividing by sigma^2 or skipping the unit scaling of
+    u and v changes the value.  The SPD form: A = diag(2, 5), lam = 2,
+    x = (1, 1)/sqrt(2): A x - lam x = (0, 3/r), rho = (3/r)/2."""
+    r = np.sqrt(2.0)
+    A = sp.csr_matrix(np.array([[3.0, 0.0], [0.0, 1.0], [0.0, 0.0]]))
+    U = np.array([[1.0], [0.0], [0.0]])
+    V = np.array([[1.0], [1.0]]) / r
+    want = np.sqrt(2.0 * (3.0 - 3.0 / r) ** 2 + 5.0) / 3.0
+    got = oracle.residual_norms(A, False, np.array([3.0]), U, V)
+    assert abs(got[0] - want) < 1e-15 * want
+    # the scale of u and v does not matter (R11 takes unit vectors)
+    got2 = oracle.residual_norms(A, False, np.array([3.0]), 7.0 * U, 0.25 * V)
+    assert abs(got2[0] - want) < 1e-15 * want
+    # (3, e1, e1) is an exact triplet: both terms vanish
+    got3 = oracle.residual_norms(A, False, np.array([3.0]), U, np.array([[1.0], [0.0]]))
+    assert got3[0] < 1e-16
+    # one side nonzero: u = e2, v = e2, sigma = 1 is exact; sigma = 2 gives
+    # A v - s u = (0, -1, 0), A^t u - s v = (0, -1): rho = sqrt(2)/2
+    e2u = np.array([[0.0], [1.0], [0.0]])
+    e2v = np.array([[0.0], [1.0]])
+    assert oracle.residual_norms(A, False, np.array([1.0]), e2u, e2v)[0] < 1e-16
+    assert abs(oracle.residual_norms(A, False, np.array([2.0]), e2u, e2v)[0] - r / 2.0) < 1e-15
+    # u with a component in null(A^t) = span(e3): A^t u is unchanged but
+    # A v - s u gains -s e3/|u|.  u = (e2 + e3)/r, v = e2, s = 1:
+    # A v - s u = (0, 1 - 1/r, -1/r), A^t u - s v = (0, 1/r - 1)
+    u = np.array([[0.0], [1.0], [1.0]]) / r
+    want4 = np.sqrt(2.0 * (1.0 - 1.0 / r) ** 2 + 0.5)
+    assert abs(oracle.residual_norms(A, False, np.array([1.0]), u, e2v)[0] - want4) < 1e-15
+    # SPD form
+    D = sp.csr_matrix(np.diag([2.0, 5.0]))
+    x = np.array([[1.0], [1.0]]) / r
+    assert abs(oracle.residual_norms(D, True, np.array([2.0]), x, None)[0] - (3.0 / r) / 2.0) < 1e-15
+    # several columns at once are independent
+    got5 = oracle.residual_norms(A, False, np.array([3.0, 2.0]), np.hstack([U, e2u]),
+                                 np.hstack([V, e2v]))
+    assert abs(got5[0] - want) < 1e-15 * want and abs(got5[1] - r / 2.0) < 1e-15
+
+
+def test_coarse_geneig_variant_pins():
+    """The generalized-eigen form of the coarsest solve (a variant of R7).
+
+    * With Y = I the generalized eigenpairs are the eigenpairs of the
+      symmetric X, the singular values of X - s I are |lam_k - s|, and the
+      mode nearest s is the smallest singular value: the variant equals the
+      paper's SVD pseudo-inverse.
+    * For any SPD Y: X - s Y = Y W (Lam - s) W^t Y and W W^t = Y^-1, so the
+      variant's z satisfies (X - s Y) z = r - Y w* (w*^t r), w* the dropped
+      generalized eigenvector; and w*^t Y z = 0."""
+    rng = np.random.default_rng(31)
+    n = 9
+    X = rng.standard_normal((n, n))
+    X = X + X.T
+    I = np.eye(n)
+    K = rng.standard_normal((n, 3))
+    s = np.array([0.3, -1.1, 2.0])
+    zs, _ = oracle.coarsest_pinv_apply((X, I), s, K, None, True)
+    zg, _ = oracle.coarsest_pinv_apply((X, I), s, K, None, True, form="geneig")
+    assert np.abs(zs - zg).max() < 1e-11 * np.abs(zs).max()
+    G = rng.standard_normal((n, n))
+    Y = G @ G.T + n * I
+    lam, Wm = oracle.coarse_geneig((X, Y))
+    zg, _ = oracle.coarsest_pinv_apply((X, Y), s, K, None, True, form="geneig")
+    for j in range(3):
+        k = int(np.argmin(np.abs(lam - s[j])))
+        w = Wm[:, k]
+        lhs = (X - s[j] * Y) @ zg[:, j]
+        rhs = K[:, j] - Y @ w * (w @ K[:, j])
+        assert np.abs(lhs - rhs).max() < 1e-10 * np.abs(K).max()
+        assert abs(w @ Y @ zg[:, j]) < 1e-10 * np.abs(zg).max()
+    # the SVD kind splits [kappa; tau] into the two blocks in order
+    m1 = 4
+    zu, zv = oracle.coarsest_pinv_apply((X, Y), s, K[:m1], K[m1:], False, form="geneig")
+    full, _ = oracle.coarsest_pinv_apply((X, Y), s, K, None, True, form="geneig")
+    assert np.array_equal(np.vstack([zu, zv]), full)
