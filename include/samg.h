@@ -95,11 +95,22 @@ typedef struct {
                                the lowest k).  It equals form 0 when Y_L = I
                                and costs two passes over W per cycle, so it
                                suits large coarsest levels. */
+    int32_t row_form;     /* minimal SVD kind with m >= n (Sec. 3.7):
+                             0 = rows coarsened directly from A (a reading of
+                               the option Sec. 3.7 leaves open): P_0 = A Q_0,
+                               P_l = Q_l below level 0, and the Ritz step of
+                               Sec. 4.3 takes the left basis A V_b;
+                             1 = the paper's form: rows coarsened on A A^t
+                               with their own LS-fitted P, two-sided Ritz
+                               on span(U_b) x span(V_b).  On the gradient
+                               workloads form 1 collapses onto the
+                               null(A^t) zero modes of Thm genSVD.
+                             Ignored by the other kinds. */
 } samg_params;
 
 /* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
  * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
- * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0. */
+ * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0, row_form 0. */
 void samg_default_params(samg_params *p);
 
 /* ---------------------------------------------------------------- setup --

@@ -75,7 +75,7 @@ _LIB = None
 
 DEFAULTS = dict(n_t=8, theta=0.06, mu_t=8, mu_b=4, mu_tJ=1, mu_bJ=1, omega_J=0.7,
                 n_mult=10, coarsest_max=100, max_levels=30, seed=20110204, coarse_drop=1,
-                coarse_pinv="svd")
+                coarse_pinv="svd", row_form="induced")
 
 
 def _lib():
@@ -444,18 +444,21 @@ def coarsest_pinv_apply(XY, sigma, K, T, spd: bool, drop: int = 1, form: str = "
 # Ritz step (Sec. 4.3) and residuals (R11)
 # --------------------------------------------------------------------------
 
-def ritz(A: sp.csr_matrix, spd: bool, target: str, U, V):
+def ritz(A: sp.csr_matrix, spd: bool, target: str, U, V, row_form: str = "induced"):
     """Ritz projection on the finest level (B = I, C = I): orthonormalise the
     boot blocks by Householder QR, form M = U^t A V and take its SVD, which is
     the 2n_b generalized eigenproblem of Eq. genSVDRitz by Thm genSVD.  SPD:
-    eigh(X^t A X).  sigma sorted descending (dominant) / ascending (minimal)."""
+    eigh(X^t A X).  sigma sorted descending (dominant) / ascending (minimal).
+    row_form = "paper" keeps the two-sided projection on span(U_b) x span(V_b)
+    for every kind; "induced" (R21) takes the left basis A V_b for the minimal
+    SVD kind with m >= n."""
     if spd:
         Xh, _ = np.linalg.qr(U)
         M = Xh.T @ (A @ Xh)
         w, Yv = np.linalg.eigh(M)
         order = np.arange(len(w)) if target == "minimal" else np.arange(len(w))[::-1]
         return w[order].copy(), np.ascontiguousarray(Xh @ Yv[:, order]), None
-    if target == "minimal" and A.shape[0] >= A.shape[1]:
+    if row_form == "induced" and target == "minimal" and A.shape[0] >= A.shape[1]:
         # R21: the left basis is A V_b, which excludes the null(A^t) modes
         # (the spurious zero modes of Thm genSVD) from the projection
         U = np.ascontiguousarray(A @ V)
@@ -546,11 +549,14 @@ def _jacobi_on_N(L: Level, spd: bool, side: str, Y: np.ndarray, omega: float) ->
     return Y - (omega * 2.0 / g) * (N @ Y) / d[:, None]
 
 
-def _induced(spd: bool, target: str, shape) -> bool:
+def _induced(spd: bool, target: str, shape, row_form: str = "induced") -> bool:
     """R21: the minimal SVD kind with m >= n takes its row (u) interpolation
     from the column interpolation, P_0 = A Q_0 on the finest level and
-    P_l = Q_l below it (where A_l = B_l by construction)."""
-    return (not spd) and target == "minimal" and shape[0] >= shape[1]
+    P_l = Q_l below it (where A_l = B_l by construction).  row_form =
+    "paper" keeps Sec. 3.7's form: the rows coarsened on A A^t with their own
+    LS-fitted P."""
+    return (row_form == "induced" and (not spd) and target == "minimal"
+            and shape[0] >= shape[1])
 
 
 def _down_sweep(A, spd: bool, target: str, nb: int, p: dict, Ut, Vt, sigma, ub, vb,
@@ -565,7 +571,7 @@ def _down_sweep(A, spd: bool, target: str, nb: int, p: dict, Ut, Vt, sigma, ub, 
     coarsest level."""
     m, n = A.shape
     om = p["omega_J"]
-    induced = _induced(spd, target, A.shape)
+    induced = _induced(spd, target, A.shape, p.get("row_form", "induced"))
     boot = ub is not None
     fine = Level(A, sp.identity(m, format="csr"),
                  None if spd else sp.identity(n, format="csr"))
@@ -657,7 +663,7 @@ def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
     A = _csr(A)
     m, n = A.shape
     om = p["omega_J"]
-    induced = _induced(spd, target, A.shape)
+    induced = _induced(spd, target, A.shape, p.get("row_form", "induced"))
     Ut = random_block(p["seed"], m, p["n_t"])
     Vt = None if spd else random_block(p["seed"] ^ (1 << 63), n, p["n_t"])
     if induced:
@@ -675,7 +681,7 @@ def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
             if not spd:
                 vb = np.ascontiguousarray(L.Q @ vb)
             sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
-        sigma, Ub, Vb = ritz(A, spd, target, ub, vb)
+        sigma, Ub, Vb = ritz(A, spd, target, ub, vb, p.get("row_form", "induced"))
     H = Hierarchy(kind, target, levels, p, Ut, Vt)
     return H, sigma, Ub, Vb
 
@@ -742,7 +748,7 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
             break
         Z = np.zeros_like(U)
         vcycle(H, 0, sigma, U, V, Z, None if spd else np.zeros_like(V), XY)
-        sigma, U, V = ritz(A, spd, H.target, U, V)
+        sigma, U, V = ritz(A, spd, H.target, U, V, H.params.get("row_form", "induced"))
         hist.append(residual_norms(A, spd, sigma, U, V))
         if redo_tol is not None:
             conv = hist[-1] <= redo_tol

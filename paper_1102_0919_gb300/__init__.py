@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("omega_J", ctypes.c_double), ("n_mult", ctypes.c_int32),
                 ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32),
-                ("coarse_pinv", ctypes.c_int32)]
+                ("coarse_pinv", ctypes.c_int32), ("row_form", ctypes.c_int32)]
 
 
 class _Csr(ctypes.Structure):
@@ -158,6 +158,10 @@ def make_params(**kw) -> Params:
     for k, v in kw.items():
         if k == "prec":
             v = {"fp64": FP64, "fp32": FP32}.get(v, v)
+        elif k == "coarse_pinv":
+            v = {"svd": 0, "geneig": 1}.get(v, v)
+        elif k == "row_form":
+            v = {"induced": 0, "paper": 1}.get(v, v)
         setattr(p, k, v)
     return p
 

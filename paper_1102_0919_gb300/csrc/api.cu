@@ -60,6 +60,8 @@ void check_common(int n_b, const samg_params *prm) {
     SAMG_CHECK(prm->prec == SAMG_FP64 || prm->prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
     SAMG_CHECK(prm->coarse_pinv == 0 || prm->coarse_pinv == 1, SAMG_E_INVALID,
                "coarse_pinv must be 0 (SVD pseudo-inverse) or 1 (generalized-eigen variant)");
+    SAMG_CHECK(prm->row_form == 0 || prm->row_form == 1, SAMG_E_INVALID,
+               "row_form must be 0 (rows from A) or 1 (the paper's A A^t coarsening)");
 }
 
 template <typename T>
@@ -233,6 +235,7 @@ void samg_default_params(samg_params *p) {
     p->prec = SAMG_FP32;
     p->n_conv = 0;
     p->coarse_pinv = 0;
+    p->row_form = 0;
 }
 
 const char *samg_last_error(const samg_ctx *ctx) {

@@ -556,7 +556,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     SetupState st(c);
     st.nt = p.n_t;
     st.ldt = block_ld(p.n_t);
-    st.induced = !spd && c.minimal();
+    st.induced = !spd && c.minimal() && p.row_form == 0;
     const int m = Ah.m, n = Ah.n, ldt = st.ldt;
     st.ones.alloc(16);
     // random test vectors (Sec. 3.3)
@@ -603,6 +603,17 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                 } else if (st.induced) {
                     spgemm(L.At, L.A, Nd, s);
                     download_csr(Nd, Nv, s);
+                } else if (c.minimal()) {
+                    // minimal SVD kind in the paper's form (Sec. 3.7): rows
+                    // coarsened on N_u = A A^t, columns on N_v = A^t A; both
+                    // products are formed, since R14's Jacobi step needs them
+                    spgemm(L.A, L.At, Nd, s);
+                    download_csr(Nd, Nu, s);
+                    DCsr Nd2;
+                    spgemm(L.At, L.A, Nd2, s);
+                    download_csr(Nd2, Nv, s);
+                    strength_of(Nu, p.theta, Su);
+                    strength_of(Nv, p.theta, Sv);
                 } else {
                     // dominant SVD kind: the strength graphs of A A^t and
                     // A^t A come from A and A^t directly (the LS fits need

@@ -650,3 +650,29 @@ def test_coarse_geneig_variant_pins():
     zu, zv = oracle.coarsest_pinv_apply((X, Y), s, K[:m1], K[m1:], False, form="geneig")
     full, _ = oracle.coarsest_pinv_apply((X, Y), s, K, None, True, form="geneig")
     assert np.array_equal(np.vstack([zu, zv]), full)
+
+
+def test_paper_row_form_collapses_onto_null_At_on_the_gradient():
+    """Why R21 replaces the paper's row coarsening for the minimal SVD kind.
+
+    With the rows coarsened on A A^t and a two-sided Ritz step (Secs. 3.7,
+    4.3), the setup's left boot vectors of the 16 x 16 gradient end up almost
+    entirely in null(A^t) -- the |m - n| zero modes of Thm genSVD -- and the
+    Ritz values fall far below the true smallest singular value.  R21 (rows
+    from A, left basis A V_b) keeps u in range(A) and finds the closed-form
+    values."""
+    A = W.gradient(16).to_scipy()
+    exact = gradient_singular_values(16)[:8]
+    Q, _ = np.linalg.qr(A.toarray())          # orthonormal basis of range(A)
+    prm = dict(W.GRAD_PARAMS, seed=14, coarsest_max=40, n_mult=5)
+    H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(prm, row_form="paper"))
+    Un = U / np.linalg.norm(U, axis=0)
+    outside = np.linalg.norm(Un - Q @ (Q.T @ Un), axis=0)
+    assert outside.min() > 0.99, outside
+    assert s.max() < 0.2 * exact[0], s
+    H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(prm, row_form="induced"))
+    Un = U / np.linalg.norm(U, axis=0)
+    assert np.linalg.norm(Un - Q @ (Q.T @ Un), axis=0).max() < 1e-10
+    s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=60)
+    assert hist[-1].max() <= 1e-10
+    assert np.abs(s - exact).max() < 1e-10 * exact.max()
