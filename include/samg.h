@@ -350,18 +350,22 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
  *   i32 rows, cols, nbands, nlevels, nchunks, max_slots, mode, shifted;
  *   i64 nreq, image_bytes;
  *   i32 band_chunk[nbands + 1];
- *   per chunk: i32 L0, nl, nr, ne, nx, bytes; i64 offset;
+ *   per chunk: i32 L0, nl, nr, ne, nx, nq, bytes, 0; i64 offset;
  *   per level: i32 first requirement, requirement count, publish, 0;
  *   per requirement: i32 band, levels that band must have completed;
  *   the chunk images (float64 coefficients).
  * A chunk image holds, at 16-byte aligned offsets: per level {first row,
- * rows, lanes log2, has requirements} (4 x i32); per row {right-hand-side
- * row, first entry | entries << 16} (2 x i32); per row 1 / |a_r|^2 (f64);
- * per entry {column, flags} (2 x i32: 1 first touch in the band, 2 last
- * touch, 4 staged, window slot + 1 in bits 3-14, staged index from bit 15);
- * per entry a (f64); per entry b (f64, shifted programs only); per staged
- * value its column (i32).  Returns SAMG_E_INVALID for a malformed CSR or a
- * short buffer. */
+ * rows, lanes log2, flags: 1 has requirements | 2 publish after it}
+ * (4 x i32); per level {first requirement in the image's list, count}
+ * (2 x i32; a count c < 0 means the level's -c - 1 requirements are read
+ * from the global list at that first index); per row {right-hand-side row,
+ * first entry | entries << 16} (2 x i32); per row 1 / |a_r|^2 (f64); per
+ * entry {column, flags} (2 x i32: 1 first touch in the band, 2 last touch,
+ * 4 staged, window slot + 1 in bits 3-14, staged index from bit 15); per
+ * entry a (f64); per entry b (f64, shifted programs only); per staged value
+ * its column (i32); per carried requirement {band, levels that band must
+ * have completed} (2 x i32, nq of them).  Returns SAMG_E_INVALID for a
+ * malformed CSR or a short buffer. */
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
                                 int fused_count, int spd, int resident_slots, unsigned char *buf,
                                 int64_t capacity, int64_t *size);
@@ -380,7 +384,7 @@ samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band);
 /* ------------------------------------------- device-level building blocks --
  * G = X^t Y for two row-major device blocks X, Y (rows x ld, first nb
  * columns used), G row-major nb x nb on the device; float64.  Uses a
- * device workspace of (ceil(rows / 4096) * nb * nb) doubles that it
+ * device workspace of (ceil(rows / 2048) * nb * nb) doubles that it
  * allocates and frees.  stream: CUDA stream or NULL. */
 samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
                             double *G, void *cuda_stream);
@@ -394,8 +398,8 @@ samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int 
  * stream that cannot afford cudaFree, which waits for all work on the
  * device.  It also does not synchronize the stream.
  *
- * The partial sums live in one fixed device array of 65536 doubles
- * (512 KiB): calls with ceil(rows / 4096) * nb * nb > 65536 are rejected with
+ * The partial sums live in one fixed device array of 131072 doubles
+ * (1 MiB): calls with ceil(rows / 2048) * nb * nb > 131072 are rejected with
  * SAMG_E_INVALID and a message (e.g. rows <= 4,194,304 at nb = 8, rows <=
  * 1,048,576 at nb = 16).  The array is shared by all callers in the process
  * on a device: calls whose GPU work overlaps (other streams, other host

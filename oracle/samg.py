@@ -250,6 +250,25 @@ class Hierarchy:
         return self.kind == "spd"
 
 
+def hierarchy_from_interp(A, Ps, Qs, kind: str, target: str, params: dict | None = None):
+    """A hierarchy with given interpolation operators (P_l, Q_l for l = 0 ..
+    L-1; Qs ignored for the SPD kind): the finest level has B = I, C = I and
+    every coarser level the Galerkin operators of Eq. coarseOp."""
+    p = dict(DEFAULTS)
+    p.update(params or {})
+    spd = kind == "spd"
+    A = _csr(A)
+    m, n = A.shape
+    levels = [Level(A, sp.identity(m, format="csr"), None if spd else sp.identity(n, format="csr"))]
+    for l, P in enumerate(Ps):
+        L = levels[-1]
+        L.P = _csr(P)
+        if not spd:
+            L.Q = _csr(Qs[l])
+        levels.append(galerkin(L, spd))
+    return Hierarchy(kind, target, levels, p)
+
+
 def galerkin(L: Level, spd: bool) -> Level:
     """Coarse operators of Eq. coarseOp: A_c = P^t A Q, B_c = P^t B P,
     C_c = Q^t C Q (SPD kind: P^t A P, P^t B P)."""

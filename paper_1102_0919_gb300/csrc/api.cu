@@ -940,7 +940,7 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
         host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs,
                       resident_slots);
         std::vector<unsigned char> out;
-        out.reserve(64 + 4 * hs.band_chunk.size() + 32 * hs.chunk.size() + 16 * hs.lvl.size() +
+        out.reserve(64 + 4 * hs.band_chunk.size() + 40 * hs.chunk.size() + 16 * hs.lvl.size() +
                     8 * hs.req.size() + hs.img_d.size());
         auto put32 = [&](int32_t v) {
             const unsigned char *q = reinterpret_cast<const unsigned char *>(&v);
@@ -957,7 +957,7 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
         put64((int64_t)hs.img_d.size());
         for (int v : hs.band_chunk) put32(v);
         for (const KChunk &c : hs.chunk) {
-            for (int32_t v : {c.L0, c.nl, c.nr, c.ne, c.nx, c.bytes_d}) put32(v);
+            for (int32_t v : {c.L0, c.nl, c.nr, c.ne, c.nx, c.nq, c.bytes_d, 0}) put32(v);
             put64(c.off_d);
         }
         for (const int4 &l : hs.lvl)
@@ -1027,7 +1027,7 @@ samg_status samg_block_gram(const double *X, const double *Y, int64_t rows, int 
 // in one fixed device array instead of a cudaMalloc'd workspace.
 namespace {
 
-constexpr size_t GRAM_STATIC_DOUBLES = 65536;  // 512 KiB of partial sums
+constexpr size_t GRAM_STATIC_DOUBLES = 131072;  // 1 MiB of partial sums
 __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
 
 // The scratch's device address belongs to a CUDA context: a device reset or a

@@ -8,8 +8,14 @@
 namespace samg {
 
 // ====================================================================== Gram
-static constexpr int GRAM_ROWS = 4096;  // rows per CTA partial
-static constexpr int GRAM_TILE = 64;
+// One CTA per GRAM_ROWS rows writes the partial sums of its rows; the final
+// pass adds the partials in chunk order (a fixed order: the result is
+// reproducible).  FP64 FMA latency on this part is long, so a thread keeps
+// GRAM_ACC independent accumulators and the CTA's threads split the rows
+// into groups, one group per (g, h) pair copy.
+static constexpr int GRAM_ROWS = 2048;  // rows per CTA partial
+static constexpr int GRAM_TILE = 64;    // rows staged in shared memory at a time
+static constexpr int GRAM_ACC = 4;
 
 size_t gram_workspace(int64_t rows, int nb) {
     int64_t chunks = (rows + GRAM_ROWS - 1) / GRAM_ROWS;
@@ -17,40 +23,68 @@ size_t gram_workspace(int64_t rows, int nb) {
 }
 
 // partial[c][g][h] = sum over the chunk's rows of X[i][g] * Y[i][h]
-__global__ void k_gram_partial(const double *__restrict__ X, const double *__restrict__ Y,
-                               int64_t rows, int nb, int ld, double *__restrict__ part) {
-    __shared__ double sx[GRAM_TILE][16], sy[GRAM_TILE][16];
+__global__ void __launch_bounds__(256)
+    k_gram_partial(const double *__restrict__ X, const double *__restrict__ Y, int64_t rows,
+                   int nb, int ld, double *__restrict__ part) {
+    __shared__ double sx[GRAM_TILE][17], sy[GRAM_TILE][17];
+    __shared__ double red[256];
     const int t = threadIdx.x;
-    const int g = t / 16, h = t % 16;
-    const bool act = (g < nb && h < nb);
-    double acc = 0.0;
+    const int pairs = nb * nb;
+    const int groups = 256 / pairs;  // row groups (nb <= 16: at least 1)
+    const int pr = t % pairs, grp = t / pairs;
+    const int g = pr / nb, h = pr % nb;
+    const bool act = grp < groups;
+    double acc[GRAM_ACC];
+#pragma unroll
+    for (int a = 0; a < GRAM_ACC; ++a) acc[a] = 0.0;
     const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
     const int64_t r1 = min(rows, r0 + GRAM_ROWS);
     for (int64_t rt = r0; rt < r1; rt += GRAM_TILE) {
         __syncthreads();
         for (int q = t; q < GRAM_TILE * 16; q += blockDim.x) {
-            int rr = q / 16, cc = q % 16;
-            int64_t row = rt + rr;
-            bool ok = row < r1 && cc < nb;
+            const int rr = q / 16, cc = q % 16;
+            const int64_t row = rt + rr;
+            const bool ok = row < r1 && cc < nb;
             sx[rr][cc] = ok ? X[row * ld + cc] : 0.0;
             sy[rr][cc] = ok ? Y[row * ld + cc] : 0.0;
         }
         __syncthreads();
         if (act) {
-#pragma unroll 8
-            for (int rr = 0; rr < GRAM_TILE; ++rr) acc = fma(sx[rr][g], sy[rr][h], acc);
+            // rows grp, grp + groups, ...; GRAM_ACC chains over them
+            int k = 0;
+            for (int rr = grp; rr < GRAM_TILE; rr += groups, ++k)
+                acc[k % GRAM_ACC] = fma(sx[rr][g], sy[rr][h], acc[k % GRAM_ACC]);
         }
     }
-    if (act) part[(size_t)blockIdx.x * nb * nb + g * nb + h] = acc;
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < GRAM_ACC; ++a) v += acc[a];
+    red[t] = act ? v : 0.0;
+    __syncthreads();
+    if (t < pairs) {
+        double sum = 0.0;
+        for (int q = 0; q < groups; ++q) sum += red[q * pairs + t];
+        part[(size_t)blockIdx.x * pairs + t] = sum;
+    }
 }
 
+// G[e] = sum over chunks of partial[c][e], one warp per entry e (lanes
+// stride over the chunks, then a fixed shuffle tree)
 __global__ void k_gram_final(const double *__restrict__ part, int chunks, int nb,
                              double *__restrict__ G) {
-    const int e = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     if (e >= nb * nb) return;
-    double s = 0.0;
-    for (int c = 0; c < chunks; ++c) s += part[(size_t)c * nb * nb + e];
-    G[e] = s;
+    double a0 = 0.0, a1 = 0.0;
+    int c = lane;
+    for (; c + 32 < chunks; c += 64) {
+        a0 += part[(size_t)c * nb * nb + e];
+        a1 += part[(size_t)(c + 32) * nb * nb + e];
+    }
+    if (c < chunks) a0 += part[(size_t)c * nb * nb + e];
+    double sum = a0 + a1;
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) G[e] = sum;
 }
 
 void launch_gram(const double *X, const double *Y, int64_t rows, int nb, int ld, double *G,
@@ -63,7 +97,7 @@ void launch_gram(const double *X, const double *Y, int64_t rows, int nb, int ld,
     SAMG_COUNT_LAUNCH();
     k_gram_partial<<<chunks, 256, 0, s>>>(X, Y, rows, nb, ld, work);
     SAMG_COUNT_LAUNCH();
-    k_gram_final<<<1, 256, 0, s>>>(work, chunks, nb, G);
+    k_gram_final<<<(nb * nb + 7) / 8, 256, 0, s>>>(work, chunks, nb, G);
     SAMG_CUDA(cudaGetLastError());
 }
 
@@ -276,25 +310,29 @@ void launch_ritz_small(const double *GU, const double *GV, const double *H, int 
 }
 
 // Ritz update of one side: Xn = X T, AXn = W T2 (W = A x old other side),
-// res[c][j] partial of |AXn_j - s_j Xn_j|^2 (deterministic per chunk).
-__global__ void k_ritz_update(const double *__restrict__ X, const double *__restrict__ W,
-                              const double *__restrict__ T, const double *__restrict__ T2,
-                              const double *__restrict__ sigma, int64_t rows, int nb, int ld,
-                              double *__restrict__ Xn, double *__restrict__ part) {
+// res[c][j] partial of |AXn_j - s_j Xn_j|^2 (deterministic per chunk).  The
+// CTA's threads are ld columns x (256 / ld) row lanes.
+__global__ void __launch_bounds__(256)
+    k_ritz_update(const double *__restrict__ X, const double *__restrict__ W,
+                  const double *__restrict__ T, const double *__restrict__ T2,
+                  const double *__restrict__ sigma, int64_t rows, int nb, int ld,
+                  double *__restrict__ Xn, double *__restrict__ part) {
     __shared__ double sT[256], sT2[256];
-    __shared__ double red[16][16];  // [warp-ish group][column]
+    __shared__ double red[256];
     for (int q = threadIdx.x; q < ld * ld && q < 256; q += blockDim.x) {
         sT[q] = T[q];
         sT2[q] = T2[q];
     }
     __syncthreads();
-    const int j = threadIdx.x % 16;
-    const int rsub = threadIdx.x / 16;  // 16 row lanes
-    double acc = 0.0;
+    const int lanes = 256 / ld;  // row lanes
+    const int j = threadIdx.x % ld;
+    const int rsub = threadIdx.x / ld;
+    double acc0 = 0.0, acc1 = 0.0;
     const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
     const int64_t r1 = min(rows, r0 + GRAM_ROWS);
-    if (j < ld) {
-        for (int64_t i = r0 + rsub; i < r1; i += 16) {
+    if (rsub < lanes) {
+        int k = 0;
+        for (int64_t i = r0 + rsub; i < r1; i += lanes, ++k) {
             double xn = 0.0, axn = 0.0;
             for (int l = 0; l < nb; ++l) {
                 xn = fma(X[i * ld + l], sT[l * ld + j], xn);
@@ -302,17 +340,18 @@ __global__ void k_ritz_update(const double *__restrict__ X, const double *__rest
             }
             Xn[i * ld + j] = xn;
             if (j < nb) {
-                double r = axn - sigma[j] * xn;
-                acc = fma(r, r, acc);
+                const double r = axn - sigma[j] * xn;
+                if (k & 1) acc1 = fma(r, r, acc1);
+                else acc0 = fma(r, r, acc0);
             }
         }
     }
-    red[rsub][j] = acc;
+    red[threadIdx.x] = rsub < lanes ? acc0 + acc1 : 0.0;
     __syncthreads();
-    if (threadIdx.x < 16) {
+    if (threadIdx.x < nb) {
         double s = 0.0;
-        for (int q = 0; q < 16; ++q) s += red[q][threadIdx.x];
-        if (threadIdx.x < nb) part[(size_t)blockIdx.x * nb + threadIdx.x] = s;
+        for (int q = 0; q < lanes; ++q) s += red[q * ld + threadIdx.x];
+        part[(size_t)blockIdx.x * nb + threadIdx.x] = s;
     }
 }
 

@@ -17,32 +17,40 @@ constexpr int KZ_NBUF = 3;          // staging buffers (the producer runs up to 
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
 constexpr int MAX_BAND_ROWS = 1 << 17;
 constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
-// staging chunk limits: levels, rows, entries, staged first values
-constexpr int KZ_CHL = 32, KZ_CHR = 256, KZ_CHE = 1024, KZ_CHX = 256;
+// staging chunk limits: levels, rows, entries, staged first values,
+// cross-band requirements carried in the image
+constexpr int KZ_CHL = 32, KZ_CHR = 256, KZ_CHE = 1024, KZ_CHX = 256, KZ_CHQ = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on any wait
 constexpr unsigned FULL = 0xffffffffu;
 
 // Byte layout of one chunk image: the schedule of up to KZ_CHL levels, copied
 // to shared memory by one bulk copy.  Every array starts on 16 bytes.
-//   lv  int4 per level {first row, rows, log2 lanes per row, has requirements}
+//   lv  int4 per level {first row, rows, log2 lanes per row,
+//                       flags: 1 has requirements | 2 publish after it}
+//   lq  int2 per level {first requirement in rq, count}; count < 0: the
+//                      level's -count - 1 requirements are read from the
+//                      schedule's global list at the first index instead
 //   ri  int2 per row   {original row, first entry | entries << 16}
 //   inv T per row      1 / ||a_i||^2 (unshifted form)
 //   ent int2 per entry {column, 1 first | 2 last | 4 staged | (slot + 1) << 3 | xs << 15}
 //   a, b T per entry   coefficients (b: shifted form only)
 //   xc  int per staged first value: its column
+//   rq  int2 per requirement {band, levels that band must have completed}
 struct ImgLayout {
-    unsigned lv, ri, inv, ent, a, b, xc, bytes;
+    unsigned lv, lq, ri, inv, ent, a, b, xc, rq, bytes;
 };
 __host__ __device__ constexpr unsigned al16u(unsigned v) { return (v + 15u) & ~15u; }
-__host__ __device__ constexpr ImgLayout img_layout(int nl, int nr, int ne, int nx, int tsz,
+__host__ __device__ constexpr ImgLayout img_layout(int nl, int nr, int ne, int nx, int nq, int tsz,
                                                    bool shifted) {
-    const unsigned ri = al16u(16u * nl);
+    const unsigned lq = al16u(16u * nl);
+    const unsigned ri = al16u(lq + 8u * nl);
     const unsigned inv = al16u(ri + 8u * nr);
     const unsigned ent = al16u(inv + (unsigned)tsz * nr);
     const unsigned a = al16u(ent + 8u * ne);
     const unsigned b = al16u(a + (unsigned)tsz * ne);
     const unsigned xc = al16u(b + (shifted ? (unsigned)tsz * ne : 0u));
-    return ImgLayout{0u, ri, inv, ent, a, b, xc, al16u(xc + 4u * nx)};
+    const unsigned rq = al16u(xc + 4u * nx);
+    return ImgLayout{0u, lq, ri, inv, ent, a, b, xc, rq, al16u(rq + 8u * nq)};
 }
 
 struct Pattern {                      // rows of a sweep program: a (and b) coefficients
@@ -331,6 +339,14 @@ __device__ __forceinline__ int ld_acq_cta(const int *p) {
     asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_acq_cta64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.cta.shared.u64 %0, [%1];" : "=l"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel_cta64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.cta.shared.u64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "l"(v) : "memory");
+}
 __device__ __forceinline__ void st_rel_cta(int *p, int v) {
     asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
@@ -355,7 +371,7 @@ template <typename T, int LD, bool SHIFT>
 struct Stage {
     static constexpr int VB = LD * (int)sizeof(T);  // bytes of one vector row
     static constexpr bool VALS = VB <= 64;
-    static constexpr unsigned IMG = img_layout(KZ_CHL, KZ_CHR, KZ_CHE, KZ_CHX, (int)sizeof(T), SHIFT).bytes;
+    static constexpr unsigned IMG = img_layout(KZ_CHL, KZ_CHR, KZ_CHE, KZ_CHX, KZ_CHQ, (int)sizeof(T), SHIFT).bytes;
     static constexpr unsigned o_rhs = IMG;
     static constexpr unsigned o_xs = o_rhs + (VALS ? (unsigned)VB * KZ_CHR : 0u);
     static constexpr unsigned bytes = o_xs + (VALS ? (unsigned)VB * KZ_CHX : 0u);
@@ -364,10 +380,12 @@ struct Stage {
 
 // Warps 0 .. KZ_COMPUTE/32 - 1 compute.  The last warp is the producer: it
 // stages chunk images (bulk copies) and gathered values (cp.async) up to
-// KZ_NBUF chunks ahead, polls (acquire) the progress that upcoming levels
-// require from earlier bands, and publishes (release) this band's progress
-// when it crosses a level that a later band waits for, and at the band's
-// end.  The compute warps touch only shared memory for synchronization.
+// KZ_NBUF chunks ahead, and publishes (release) this band's progress when the
+// compute warps complete a level that the image flags as waited for by a
+// later band, and at the band's end.  Before a level with cross-band
+// requirements, every compute warp that holds rows of it polls (acquire) the
+// progress words of the bands the image lists, so a handoff between bands
+// passes through one release and one acquire and no relay.
 // MODE 0: rows of A (norms given).  MODE 1: rows of A - s_j B (entries carry
 // b; norms formed per column).  MODE 2: fused relaxations (entries carry b;
 // the accumulation uses a - s_j b, the update only a; norms given).
@@ -385,8 +403,10 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
     __shared__ int s_band;
     __shared__ int s_abort;
     __shared__ int s_done;   // band-local levels completed by the compute warps
-    __shared__ int s_ready;  // band-local levels whose requirements are met
-    __shared__ unsigned long long s_pc[64];  // producer: band << 32 | observed level
+    // progress seen by this CTA: band << 32 | completed levels (slot band % 64)
+    __shared__ unsigned long long s_pc[64];
+    // producer: band-local first level and level count of the chunk in each buffer
+    __shared__ int s_cl0[KZ_NBUF], s_cnl[KZ_NBUF];
     const bool comm = threadIdx.x >= KZ_COMPUTE;
     T sh[SHIFT ? LD : 1];
 #pragma unroll
@@ -409,7 +429,10 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
         if (threadIdx.x == 0) {
             s_band = (int)atomicAdd(&kv.ctl->ticket, 1u);
             s_done = 0;
-            s_ready = 0;
+            for (int q = 0; q < KZ_NBUF; ++q) {  // no chunk of this band staged yet
+                s_cl0[q] = -(1 << 30);
+                s_cnl[q] = 0;
+            }
         }
         __syncthreads();
         const int b = s_band;
@@ -420,17 +443,25 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
         if (comm) {
             // ------------------------------------------------------ producer warp
             const int lane = threadIdx.x & 31;
-            int sn = cb, vn = cb, ready = 0, published = 0;
+            int sn = cb, vn = cb, published = 0;
             bool aborted = false;
             const bool mute = *((volatile int *)&kv.ctl->mute) == b;
             unsigned long long t0 = gtimer();  // re-armed whenever something advances
+            int idle = 0;
             for (;;) {
-                if (*((volatile int *)&s_abort) || *((volatile int *)kv.err)) {
-                    // another CTA gave up: release this CTA's compute warps too
+                // this CTA's abort flag every pass; the launch's error word (an
+                // L2 read) only once the loop has idled for a while
+                bool ab = *((volatile int *)&s_abort) != 0;
+                if (!ab && idle >= 32) {
+                    idle = 0;
+                    ab = *((volatile int *)kv.err) != 0;
+                }
+                if (ab) {
+                    // another warp or CTA gave up: stop staging
                     if (lane == 0) *((volatile int *)&s_abort) = 1;
                     aborted = true;
                 }
-                if (!aborted && gtimer() - t0 > WAIT_NS) {
+                if (!aborted && gtimer() - t0 > 2 * WAIT_NS) {
                     if (lane == 0) {
                         atomicExch(kv.err, 1);
                         *((volatile int *)&s_abort) = 1;
@@ -443,6 +474,27 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                 }
                 bool adv = false;
                 const int done = __shfl_sync(FULL, ld_acq_cta(&s_done), 0);
+                // publish first: the release covers the compute warps' stores,
+                // which precede thread 0's release of s_done (acquired above).
+                // The flags of the levels below done are read from their
+                // chunks' images, which stay in place until this step has seen
+                // them completed (a buffer is refilled only below).
+                if (done > published) {
+                    bool f = done == nlev;
+                    for (int l = published + lane; l < done; l += 32) {
+                        for (int q = 0; q < KZ_NBUF; ++q) {
+                            const int l0 = s_cl0[q];
+                            if (l >= l0 && l < l0 + s_cnl[q]) {
+                                const int4 *lvq = reinterpret_cast<const int4 *>(bufs + (size_t)q * SG::stride);
+                                f = f || (lvq[l - l0].w & 2) != 0;
+                            }
+                        }
+                    }
+                    if (__any_sync(FULL, f) && lane == 0 && !mute)
+                        st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
+                    published = done;
+                    adv = true;
+                }
                 // a. image of chunk sn, once the chunk that used its buffer is done
                 if (sn < ce) {
                     const int old = sn - KZ_NBUF;
@@ -453,12 +505,15 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                             const KChunk ck = kv.chunk[sn];
                             const unsigned bytes = sizeof(T) == 4 ? ck.bytes_f : ck.bytes_d;
                             const long long off = sizeof(T) == 4 ? ck.off_f : ck.off_d;
+                            s_cl0[bi] = ck.L0 - Lband;
+                            s_cnl[bi] = ck.nl;
                             // the compute warps' reads of the old chunk precede
                             // the asynchronous overwrite
                             fence_proxy_async();
                             mbar_expect_tx(&mb_sched[bi], bytes);
                             bulk_g2s(bufs + (size_t)bi * SG::stride, kv.img + off, bytes, &mb_sched[bi]);
                         }
+                        __syncwarp();
                         ++sn;
                         adv = true;
                     }
@@ -472,7 +527,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                     if (landed) {
                         const KChunk ck = kv.chunk[vn];
                         unsigned char *B = bufs + (size_t)bi * SG::stride;
-                        const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, (int)sizeof(T), SHIFT);
+                        const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, ck.nq, (int)sizeof(T), SHIFT);
                         const int2 *ri = reinterpret_cast<const int2 *>(B + IL.ri);
                         const int *xc = reinterpret_cast<const int *>(B + IL.xc);
                         constexpr int P = SG::VB / 16;
@@ -492,44 +547,16 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                         adv = true;
                     }
                 }
-                // c. requirements of the next levels, a few at a time
-                int nready = 0;
-                while (ready < nlev && nready < 8) {
-                    const int4 lq = kv.lvl[Lband + ready];
-                    bool ok = true;
-                    for (int q = lq.x + lane; q < lq.x + lq.y; q += 32) {
-                        const int2 rq = kv.req[q];
-                        const unsigned long long key = s_pc[rq.x & 63];
-                        if ((int)(key >> 32) == rq.x && (unsigned)key >= (unsigned)rq.y) continue;
-                        const unsigned long long v = ld_acquire(&kv.progress[rq.x]);
-                        if ((v >> 32) == epoch)
-                            s_pc[rq.x & 63] = ((unsigned long long)(unsigned)rq.x << 32) | (v & 0xffffffffull);
-                        ok = ok && (v >= ((epoch << 32) | (unsigned)rq.y));
-                    }
-                    if (!__all_sync(FULL, ok)) break;
-                    ++ready;
-                    ++nready;
-                }
-                if (nready) {
-                    if (lane == 0) st_rel_cta(&s_ready, ready);
-                    adv = true;
-                }
-                // d. publish: the release covers the compute warps' stores, which
-                // precede thread 0's release of s_done (acquired above)
-                if (done > published) {
-                    bool f = false;
-                    for (int l = published + lane; l < done; l += 32) f = f || kv.lvl[Lband + l].z != 0;
-                    if ((__any_sync(FULL, f) || done == nlev) && lane == 0 && !mute)
-                        st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
-                    published = done;
-                    adv = true;
-                }
                 if (published >= nlev) break;
-                if (adv) t0 = gtimer();
-                else __nanosleep(32);
+                if (adv) {
+                    t0 = gtimer();
+                    idle = 0;
+                } else {
+                    ++idle;
+                    __nanosleep(20);
+                }
             }
             if (aborted) {
-                if (lane == 0) st_rel_cta(&s_ready, nlev);  // release the compute warps
                 // copies issued by this warp land before the CTA moves on
                 cp_async_wait_all();
                 if (lane == 0)
@@ -557,8 +584,10 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                     aborted = __any_sync(FULL, !ok);
                 }
                 unsigned char *B = bufs + (size_t)bi * SG::stride;
-                const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, (int)sizeof(T), SHIFT);
+                const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, ck.nq, (int)sizeof(T), SHIFT);
                 const int4 *lv = reinterpret_cast<const int4 *>(B + IL.lv);
+                const int2 *lq = reinterpret_cast<const int2 *>(B + IL.lq);
+                const int2 *srq = reinterpret_cast<const int2 *>(B + IL.rq);
                 const int2 *ri = reinterpret_cast<const int2 *>(B + IL.ri);
                 const T *sinv = reinterpret_cast<const T *>(B + IL.inv);
                 const int2 *se = reinterpret_cast<const int2 *>(B + IL.ent);
@@ -570,42 +599,68 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                     const int lb = ck.L0 + L - Lband;  // band-local level
                     if (!aborted) {
                         const int4 lr = lv[L];
-                        if (lr.w) {
-                            // requirements of this level: wait for the producer,
-                            // which releases every wait when it gives up
-                            const unsigned long long t0 = gtimer();
-                            bool late = false;
-                            while (ld_acq_cta(&s_ready) <= lb)
-                                if (gtimer() - t0 > 2 * WAIT_NS) { late = true; break; }
-                            if (late) {
-                                // the producer never released this level: give up
-                                // like a timed-out wait (error word, CTA abort)
-                                atomicExch(kv.err, 1);
-                                *((volatile int *)&s_abort) = 1;
+                        // G = 2^lgG lanes per row (the smallest power of two
+                        // not below the level's longest row, at most 32);
+                        // lane lg takes entries lg, lg + G, ... for all LD
+                        // columns.  Rows of more than 16 entries (float32) or
+                        // 32 entries (float64) take G = 2^(lr.z - 1) lanes, each
+                        // loading its second entry together with its first,
+                        // which keeps the row sums one shuffle step shorter.  A
+                        // warp holding no row of the level goes straight to
+                        // the barrier.
+                        // (float64 keeps G = 32 for rows of 17-32 entries: the
+                        // setup phase runs in float64, and its hierarchy
+                        // should not depend on how float32 sweeps are tuned)
+                        constexpr int TWO_FROM = sizeof(T) == 4 ? 5 : 6;
+                        const bool two = lr.z >= TWO_FROM;
+                        const int lgG = two ? lr.z - 1 : lr.z;
+                        const int G = 1 << lgG;
+                        const int nrow = lr.y;
+                        const int lane = threadIdx.x & 31;
+                        const int wrow = (threadIdx.x & ~31) >> lgG;
+                        if ((lr.w & 1) && wrow < nrow) {
+                            // cross-band requirements: the warp's lanes poll
+                            // (acquire) the listed bands' progress words; a
+                            // progress this CTA has already seen (s_pc, written
+                            // with release after an acquire) needs no poll
+                            const int2 q = lq[L];
+                            const int cnt = q.y >= 0 ? q.y : -q.y - 1;
+                            const int2 *rl = q.y >= 0 ? srq + q.x : kv.req + q.x;
+                            bool bad = false;
+                            for (int i = lane; i < cnt && !bad; i += 32) {
+                                const int2 r = rl[i];
+                                const unsigned long long key = ld_acq_cta64(&s_pc[r.x & 63]);
+                                if ((int)(key >> 32) == r.x && (unsigned)key >= (unsigned)r.y) continue;
+                                const unsigned long long want = (epoch << 32) | (unsigned)r.y;
+                                unsigned long long v = ld_acquire(&kv.progress[r.x]);
+                                if (v < want) {
+                                    const unsigned long long t0 = gtimer();
+                                    int k = 0;
+                                    do {
+                                        if ((++k & 15) == 0 && (*((volatile int *)&s_abort) ||
+                                                                *((volatile int *)kv.err))) {
+                                            bad = true;
+                                            break;
+                                        }
+                                        if (gtimer() - t0 > WAIT_NS) {
+                                            atomicExch(kv.err, 1);
+                                            *((volatile int *)&s_abort) = 1;
+                                            bad = true;
+                                            break;
+                                        }
+                                        v = ld_acquire(&kv.progress[r.x]);
+                                    } while (v < want);
+                                }
+                                if (!bad)
+                                    st_rel_cta64(&s_pc[r.x & 63],
+                                                 ((unsigned long long)(unsigned)r.x << 32) | (v & 0xffffffffull));
                             }
-                            aborted = __any_sync(FULL, late || *((volatile int *)&s_abort) != 0);
+                            // the other lanes' loads follow the pollers' acquires
+                            __syncwarp();
+                            aborted = __any_sync(FULL, bad || *((volatile int *)&s_abort) != 0);
                         }
                         if (!aborted) {
-                            // G = 2^lgG lanes per row (the smallest power of two
-                            // not below the level's longest row, at most 32);
-                            // lane lg takes entries lg, lg + G, ... for all LD
-                            // columns.  Rows of more than 16 entries (float32) or
-                            // 32 entries (float64) take G = 2^(lr.z - 1) lanes, each
-                            // loading its second entry together with its first,
-                            // which keeps the row sums one shuffle step shorter.  A
-                            // warp holding no row of the level goes straight to
-                            // the barrier.
-                            // (float64 keeps G = 32 for rows of 17-32 entries: the
-                            // setup phase runs in float64, and its hierarchy
-                            // should not depend on how float32 sweeps are tuned)
-                            constexpr int TWO_FROM = sizeof(T) == 4 ? 5 : 6;
-                            const bool two = lr.z >= TWO_FROM;
-                            const int lgG = two ? lr.z - 1 : lr.z;
-                            const int G = 1 << lgG;
-                            const int nrow = lr.y;
-                            const int lane = threadIdx.x & 31;
                             const int lg = threadIdx.x & (G - 1);
-                            const int wrow = (threadIdx.x & ~31) >> lgG;
                             for (int pr = 0; pr + wrow < nrow; pr += KZ_COMPUTE >> lgG) {
                                 const int r = pr + (threadIdx.x >> lgG);
                                 const bool act = r < nrow;
@@ -801,15 +856,18 @@ void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaS
 // Appends the image of one chunk with coefficients of type T; returns its size.
 template <typename T>
 int write_image(std::vector<unsigned char> &img, bool shifted, const std::vector<int4> &lrec,
-                const std::vector<int2> &rrec, const std::vector<double> &rinv,
-                const std::vector<int2> &erec, const std::vector<double> &ca,
-                const std::vector<double> &cb, const std::vector<int> &xc) {
+                const std::vector<int2> &qrec, const std::vector<int2> &rrec,
+                const std::vector<double> &rinv, const std::vector<int2> &erec,
+                const std::vector<double> &ca, const std::vector<double> &cb,
+                const std::vector<int> &xc, const std::vector<int2> &rq) {
     const ImgLayout L = img_layout((int)lrec.size(), (int)rrec.size(), (int)erec.size(),
-                                   (int)xc.size(), (int)sizeof(T), shifted);
+                                   (int)xc.size(), (int)rq.size(), (int)sizeof(T), shifted);
     const size_t base = img.size();
     img.resize(base + L.bytes, 0);
     unsigned char *p = img.data() + base;
     std::memcpy(p + L.lv, lrec.data(), 16 * lrec.size());
+    std::memcpy(p + L.lq, qrec.data(), 8 * qrec.size());
+    std::memcpy(p + L.rq, rq.data(), 8 * rq.size());
     std::memcpy(p + L.ri, rrec.data(), 8 * rrec.size());
     for (size_t i = 0; i < rinv.size(); ++i) {
         const T v = (T)rinv[i];
@@ -897,6 +955,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
     int max_slots = 0;
     std::vector<std::vector<int>> pub(nb);  // per band: band-local sub-levels to publish
     std::vector<int> band_lvl0(nb + 1, 0);
+    std::vector<int> lvl_chunk;  // per (global) level: its chunk
     struct PendReq { int sub, band, need; };
     struct RowRec { int row, sub; };
     for (int b = 0; b < nb; ++b) {
@@ -960,20 +1019,6 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
             }
         }
         const int nsub = (int)sub_rows.size();
-        // chunks of consecutive sub-levels
-        std::vector<int> sub_chunk(nsub), chunk_first_sub;
-        {
-            int cl = 0, cr = 0, ce = 0, cx = 0;
-            for (int q = 0; q < nsub; ++q) {
-                if (q == 0 || cl + 1 > KZ_CHL || cr + sub_rows[q] > KZ_CHR ||
-                    ce + sub_ents[q] > KZ_CHE || cx + sub_xs[q] > KZ_CHX) {
-                    chunk_first_sub.push_back(q);
-                    cl = cr = ce = cx = 0;
-                }
-                cl += 1; cr += sub_rows[q]; ce += sub_ents[q]; cx += sub_xs[q];
-                sub_chunk[q] = (int)chunk_first_sub.size() - 1;
-            }
-        }
         for (const RowRec &x : rr)
             for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e)
                 if (w.lastlv[p.ci[e]] == w.rowlv[x.row - r0]) last_sub[p.ci[e]] = x.sub;
@@ -1011,16 +1056,34 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
             }
             lvl[L0 + l].y = (int)req.size() - lvl[L0 + l].x;
         }
+        // chunks of consecutive sub-levels; a sub-level's requirements travel
+        // in its chunk's image unless they alone exceed KZ_CHQ (then the
+        // kernel reads them from the global list)
+        auto img_reqs = [&](int l) { return lvl[L0 + l].y <= KZ_CHQ ? lvl[L0 + l].y : 0; };
+        std::vector<int> chunk_first_sub;
+        {
+            int cl = 0, cr = 0, ce = 0, cx = 0, cq = 0;
+            for (int q = 0; q < nsub; ++q) {
+                if (q == 0 || cl + 1 > KZ_CHL || cr + sub_rows[q] > KZ_CHR ||
+                    ce + sub_ents[q] > KZ_CHE || cx + sub_xs[q] > KZ_CHX ||
+                    cq + img_reqs(q) > KZ_CHQ) {
+                    chunk_first_sub.push_back(q);
+                    cl = cr = ce = cx = cq = 0;
+                }
+                cl += 1; cr += sub_rows[q]; ce += sub_ents[q]; cx += sub_xs[q]; cq += img_reqs(q);
+            }
+        }
         // one image per chunk (chunk-local row and entry numbers)
         size_t ri = 0;
         const int nch = (int)chunk_first_sub.size();
         std::vector<int4> lrec;
-        std::vector<int2> rrec, erec;
+        std::vector<int2> qrec, rrec, erec, rqrec;
         std::vector<double> rinv, ca, cbv;
         std::vector<int> xc;
         for (int ch = 0; ch < nch; ++ch) {
             const int q0 = chunk_first_sub[ch], q1 = ch + 1 < nch ? chunk_first_sub[ch + 1] : nsub;
-            lrec.clear(); rrec.clear(); erec.clear(); rinv.clear(); ca.clear(); cbv.clear(); xc.clear();
+            lrec.clear(); qrec.clear(); rrec.clear(); erec.clear(); rinv.clear(); ca.clear();
+            cbv.clear(); xc.clear(); rqrec.clear();
             for (int qq = q0; qq < q1; ++qq) {
                 // lanes per row: a power of two >= the longest row of the level
                 // (at most 32; 6 marks rows of more than 32 entries, whose lanes
@@ -1052,7 +1115,17 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
                     rrec.push_back(make_int2(p.rhs.empty() ? r : p.rhs[r], e0 | (((int)erec.size() - e0) << 16)));
                     rinv.push_back(n2 > 0.0 ? 1.0 / n2 : 0.0);
                 }
-                lrec.push_back(make_int4(row0, (int)rrec.size() - row0, lg, lvl[L0 + qq].y > 0 ? 1 : 0));
+                // flags: 1 requirements (the publish flag 2 is set once every
+                // band's requirements are known)
+                const int4 g = lvl[L0 + qq];
+                lrec.push_back(make_int4(row0, (int)rrec.size() - row0, lg, g.y > 0 ? 1 : 0));
+                if (g.y <= KZ_CHQ) {
+                    qrec.push_back(make_int2((int)rqrec.size(), g.y));
+                    for (int k = 0; k < g.y; ++k) rqrec.push_back(req[g.x + k]);
+                } else {
+                    qrec.push_back(make_int2(g.x, -g.y - 1));
+                }
+                lvl_chunk.push_back((int)chunk.size());
             }
             KChunk ck{};
             ck.L0 = L0 + q0;
@@ -1060,10 +1133,11 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
             ck.nr = (int)rrec.size();
             ck.ne = (int)erec.size();
             ck.nx = (int)xc.size();
+            ck.nq = (int)rqrec.size();
             ck.off_f = (long long)img_f.size();
             ck.off_d = (long long)img_d.size();
-            ck.bytes_f = write_image<float>(img_f, ks.shifted, lrec, rrec, rinv, erec, ca, cbv, xc);
-            ck.bytes_d = write_image<double>(img_d, ks.shifted, lrec, rrec, rinv, erec, ca, cbv, xc);
+            ck.bytes_f = write_image<float>(img_f, ks.shifted, lrec, qrec, rrec, rinv, erec, ca, cbv, xc, rqrec);
+            ck.bytes_d = write_image<double>(img_d, ks.shifted, lrec, qrec, rrec, rinv, erec, ca, cbv, xc, rqrec);
             chunk.push_back(ck);
             nent += ck.ne;
         }
@@ -1073,8 +1147,26 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
         }
     }
     band_chunk[nb] = (int)chunk.size();
-    for (int b = 0; b < nb; ++b)
-        for (int l : pub[b]) lvl[band_lvl0[b] + l].z = 1;
+    // publish flags: levels a later band waits for, and every band's last
+    // level; set in the global records and in both images (flag 2 of the
+    // level record, which sits at the image's offset 0)
+    auto set_publish = [&](int L) {
+        lvl[L].z = 1;
+        const KChunk &ck = chunk[lvl_chunk[L]];
+        const size_t at = 16u * (size_t)(L - ck.L0) + 12u;
+        int f = 0;
+        std::memcpy(&f, img_f.data() + ck.off_f + at, 4);
+        f |= 2;
+        std::memcpy(img_f.data() + ck.off_f + at, &f, 4);
+        std::memcpy(&f, img_d.data() + ck.off_d + at, 4);
+        f |= 2;
+        std::memcpy(img_d.data() + ck.off_d + at, &f, 4);
+    };
+    band_lvl0[nb] = (int)lvl.size();
+    for (int b = 0; b < nb; ++b) {
+        for (int l : pub[b]) set_publish(band_lvl0[b] + l);
+        set_publish(band_lvl0[b + 1] - 1);
+    }
     ks.nlevels = (int)lvl.size();
     ks.max_slots = max_slots;
     ks.nent = nent;

@@ -44,7 +44,7 @@ struct KChunk {
     int L0, nl;                // first (global) level, levels
     int nr, ne, nx;            // rows, entries, staged first values
     int bytes_f, bytes_d;      // image sizes (multiples of 16)
-    int pad;
+    int nq;                    // cross-band requirements carried in the image
     long long off_f, off_d;    // image byte offsets (multiples of 16)
 };
 

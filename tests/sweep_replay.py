@@ -24,10 +24,10 @@ def parse(blob):
     at += 4 * (nbands + 1)
     chunks = []
     for _ in range(nchunks):
-        L0, nl, nr, ne, nx, nbytes = (int(v) for v in np.frombuffer(b[at:at + 24], "<i4"))
-        off = int(np.frombuffer(b[at + 24:at + 32], "<i8")[0])
-        chunks.append(dict(L0=L0, nl=nl, nr=nr, ne=ne, nx=nx, bytes=nbytes, off=off))
-        at += 32
+        L0, nl, nr, ne, nx, nq, nbytes, _pad = (int(v) for v in np.frombuffer(b[at:at + 32], "<i4"))
+        off = int(np.frombuffer(b[at + 32:at + 40], "<i8")[0])
+        chunks.append(dict(L0=L0, nl=nl, nr=nr, ne=ne, nx=nx, nq=nq, bytes=nbytes, off=off))
+        at += 40
     lvl = np.frombuffer(b[at:at + 16 * nlevels], "<i4").reshape(nlevels, 4)
     at += 16 * nlevels
     req = np.frombuffer(b[at:at + 8 * nreq], "<i4").reshape(nreq, 2)
@@ -41,18 +41,22 @@ def parse(blob):
 
 def _image(S, c):
     ck = S["chunks"][c]
-    nl, nr, ne, nx = ck["nl"], ck["nr"], ck["ne"], ck["nx"]
-    ri = _al16(16 * nl)
+    nl, nr, ne, nx, nq = ck["nl"], ck["nr"], ck["ne"], ck["nx"], ck["nq"]
+    lq = _al16(16 * nl)
+    ri = _al16(lq + 8 * nl)
     inv = _al16(ri + 8 * nr)
     ent = _al16(inv + 8 * nr)
     a = _al16(ent + 8 * ne)
     bo = _al16(a + 8 * ne)
     xc = _al16(bo + (8 * ne if S["shifted"] else 0))
-    total = _al16(xc + 4 * nx)
+    rq = _al16(xc + 4 * nx)
+    total = _al16(rq + 8 * nq)
     assert total == ck["bytes"]
     m = S["img"][ck["off"]:ck["off"] + total]
     return dict(
         lv=np.frombuffer(m[:16 * nl], "<i4").reshape(nl, 4),
+        lq=np.frombuffer(m[lq:lq + 8 * nl], "<i4").reshape(nl, 2),
+        rq=np.frombuffer(m[rq:rq + 8 * nq], "<i4").reshape(nq, 2),
         ri=np.frombuffer(m[ri:ri + 8 * nr], "<i4").reshape(nr, 2),
         inv=np.frombuffer(m[inv:inv + 8 * nr], "<f8"),
         ent=np.frombuffer(m[ent:ent + 8 * ne], "<i4").reshape(ne, 2),
@@ -83,11 +87,25 @@ def replay(S, x, rhs=None, shift=None):
     staged = [None] * nb
     images = {}
 
-    def ready(b):
-        c, li = steps[b][nxt[b]]
+    def level_reqs(c, li):
+        """The requirements a level's kernel reads: the image's own list, or
+        the global list where the image says so; checked against the
+        global records."""
+        I = images.get(c)
+        if I is None:
+            I = images[c] = _image(S, c)
         L = S["chunks"][c]["L0"] + li
         q0, nq = lvl[L, 0], lvl[L, 1]
-        return all(progress[req[q, 0]] >= req[q, 1] for q in range(q0, q0 + nq))
+        glob = req[q0:q0 + nq]
+        assert bool(I["lv"][li, 3] & 1) == (nq > 0), "requirement flag disagrees"
+        f, k = I["lq"][li]
+        own = I["rq"][f:f + k] if k >= 0 else req[f:f + (-k - 1)]
+        assert np.array_equal(own, glob), "image requirement list differs"
+        return own
+
+    def ready(b):
+        c, li = steps[b][nxt[b]]
+        return all(progress[r[0]] >= r[1] for r in level_reqs(c, li))
 
     left = sum(len(s) for s in steps)
     while left:
@@ -148,6 +166,9 @@ def replay(S, x, rhs=None, shift=None):
         nxt[b] += 1
         left -= 1
         L = S["chunks"][c]["L0"] + li
-        if lvl[L, 2] or nxt[b] == len(steps[b]):
+        publish = bool(I["lv"][li, 3] & 2)
+        assert publish == bool(lvl[L, 2]), "publish flag disagrees"
+        assert publish or nxt[b] < len(steps[b]), "a band's last level must publish"
+        if publish:
             progress[b] = nxt[b]
     return x

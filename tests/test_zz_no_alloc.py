@@ -37,14 +37,14 @@ def test_noalloc_gram_rejects_more_rows_than_its_scratch():
 
     import paper_1102_0919_gb300 as samg
 
-    # ceil(rows / 4096) * 16 * 16 = 257 * 256 > 65536 partial sums; real
+    # ceil(rows / 2048) * 16 * 16 = 514 * 256 > 131072 partial sums; real
     # buffers of that size are passed, so nothing outside them is touched
     rows, nb = 4096 * 257, 16
     X, Y = _blocks(torch, rows, nb, seed=5)
     G = torch.zeros(nb, nb, dtype=torch.float64, device="cuda")
     with pytest.raises(samg.SamgError, match="fixed scratch"):
         samg.block_gram_noalloc(X.data_ptr(), Y.data_ptr(), rows, nb, nb, G.data_ptr())
-    # the largest accepted size still works
+    # the largest accepted size (512 chunks of 2048 rows) still works
     rows = 4096 * 256
     samg.block_gram_noalloc(X.data_ptr(), Y.data_ptr(), rows, nb, nb, G.data_ptr())
     torch.cuda.synchronize()
