@@ -202,7 +202,8 @@ def test_ritz_step(case):
     U = case["U"] + 1e-2 * rng.standard_normal(case["U"].shape)
     V = None if spd else case["V"] + 1e-2 * rng.standard_normal(case["V"].shape)
     sg, Ug, Vg, rg = g.ritz(U, V)
-    sr, Ur, Vr = oracle.ritz(H.levels[0].A, spd, H.target, U, V)
+    sr, Ur, Vr = oracle.ritz(H.levels[0].A, spd, H.target, U, V,
+                             H.params.get("row_form", "induced"))
     rr = oracle.residual_norms(H.levels[0].A, spd, sr, Ur, Vr)
     assert rel(sg, sr) < 1e-12
     assert rel(rg, rr) < 1e-7
