@@ -106,11 +106,24 @@ typedef struct {
                                workloads form 1 collapses onto the
                                null(A^t) zero modes of Thm genSVD.
                              Ignored by the other kinds. */
+    int32_t relax_order;  /* order of the solve phase's Kaczmarz sweeps
+                             (minimal target; Sec. 5.3, R3):
+                             0 = the paper's natural row order, run exactly
+                               (dependency levels, bands, cross-band waits);
+                             1 = a coloured variant (not in the paper): each
+                               sweep's rows greedily coloured in natural
+                               order (rows of one colour share no updated
+                               column) and visited colour by colour, one
+                               fully parallel pass per colour.  It changes
+                               the iteration, so its cycle convergence
+                               factor differs from form 0's.
+                             The setup phase always sweeps in natural order. */
 } samg_params;
 
 /* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
  * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
- * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0, row_form 0. */
+ * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0, row_form 0,
+ * relax_order 0. */
 void samg_default_params(samg_params *p);
 
 /* ---------------------------------------------------------------- setup --
@@ -229,6 +242,12 @@ samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec);
  * hierarchy is unchanged. */
 samg_status samg_set_coarse_pinv(samg_ctx *ctx, int form);
 
+/* Selects the order of this context's solve-phase sweeps, as
+ * samg_params.relax_order (0 the paper's natural order, 1 the coloured
+ * variant); SAMG_E_INVALID for any other value.  The hierarchy is
+ * unchanged; each order's sweep programs are built on first use. */
+samg_status samg_set_relax_order(samg_ctx *ctx, int order);
+
 /* Kernel timing: with profiling on, every launch of the solve phase is
  * bracketed by CUDA events on the context's stream.  samg_profile_read
  * returns, for one kernel class (0 Kaczmarz sweep, 1 block SpMM pass
@@ -333,6 +352,14 @@ samg_status samg_host_strength_product(const samg_csr *A, double theta, int64_t 
  * short row_level. */
 samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_level,
                             int64_t capacity, int *depth, int *nbands);
+
+/* Host only: the greedy row colouring the coloured sweep variant
+ * (relax_order = 1) uses, for tests that compare it with a reference (the
+ * paper has no counterpart).  Rows are taken in natural order; row i gets the
+ * smallest colour that no earlier row sharing a column with it has.
+ * colour: m entries; *ncolour: the number of colours.  SAMG_E_INVALID for a
+ * malformed CSR. */
+samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolour);
 
 /* Host-only export of an exact-order sweep schedule, for tests that replay
  * it on the CPU (the paper has no counterpart): the schedule the kernels

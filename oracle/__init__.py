@@ -23,5 +23,6 @@ leaves open (R5-R10, R13-R16 in samg.py) beyond the invariants above.
 from .samg import (DEFAULTS, Hierarchy, Level, coarse_geneig, coarsest_pinv_apply,  # noqa: F401
                    coarsest_triplets,
                    dense_XY, fit_interp, galerkin, hierarchy_from_interp, interp_sets, kaczmarz_sweep,
+                   kaczmarz_sweep_coloured, colour_order, row_colours,
                    level_residual, random_block, rayleigh, relax_boot, relax_test, residual_norms,
                    ritz, rs_coarsen, setup, solve, strength, vcycle)

@@ -309,3 +309,43 @@ int64_t oracle_ls_fit(int32_t n, int32_t nf, const int64_t *ci_ptr, const int32_
     free(N);
     return dropped;
 }
+
+/* ------------------------------------------------------------------------
+ * Greedy row colouring for the coloured-order Kaczmarz variant (not the
+ * paper's order, which is the natural one, Sec. 5.3).  Rows are taken in
+ * natural order; row i gets the smallest colour c such that no earlier row
+ * sharing a column with row i has colour c.  Rows of one colour then share
+ * no column, so their Kaczmarz projections commute.  used[] keeps, per
+ * column, the colours of the earlier rows touching it (bit c of word
+ * c / 64).  Returns the number of colours, or -1 if more than 128 are
+ * needed or memory runs out.
+ * ---------------------------------------------------------------------- */
+int32_t oracle_row_colours(int64_t nrows, int32_t ncols, const int64_t *rp, const int32_t *ci,
+                           int32_t *colour)
+{
+    uint64_t *used = (uint64_t *)calloc((size_t)ncols * 2 + 1, sizeof(uint64_t));
+    if (!used)
+        return -1;
+    int32_t ncolour = 0;
+    for (int64_t i = 0; i < nrows; ++i) {
+        uint64_t forbid[2] = {0, 0};
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            forbid[0] |= used[2 * (int64_t)ci[e]];
+            forbid[1] |= used[2 * (int64_t)ci[e] + 1];
+        }
+        int32_t c = 0;
+        while (c < 128 && ((forbid[c / 64] >> (c % 64)) & 1u))
+            ++c;
+        if (c == 128) {
+            free(used);
+            return -1;
+        }
+        colour[i] = c;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+            used[2 * (int64_t)ci[e] + c / 64] |= (uint64_t)1 << (c % 64);
+        if (c + 1 > ncolour)
+            ncolour = c + 1;
+    }
+    free(used);
+    return ncolour;
+}

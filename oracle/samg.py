@@ -13,7 +13,11 @@ silent the readings below are used (numbers as in the design notes):
 * R1/R2  minimal relaxation: block Gauss-Seidel, first Kaczmarz over the rows
   of A for v (Eq. genSVDresid1), then over the rows of A^t for u
   (Eq. genSVDresid2); SPD kind: one Kaczmarz sweep over the rows of A-lam*B.
-* R3  sweeps in natural row order of the stored matrix.
+* R3  sweeps in natural row order of the stored matrix.  params["relax_order"]
+  = "coloured" selects a variant (not the paper's) for the solve phase's
+  relaxations only: rows greedily coloured in natural order (rows of one
+  colour share no column) and swept colour by colour, natural order inside a
+  colour; the setup phase keeps the natural order.
 * R4  V(mu_b, mu_b) cycles in the additive phase.
 * R5  random test vectors from SplitMix64 (see oracle.c).
 * R6  coarsest level: max(m_l, n_l) <= coarsest_max, or the coarsening keeps
@@ -75,7 +79,7 @@ _LIB = None
 
 DEFAULTS = dict(n_t=8, theta=0.06, mu_t=8, mu_b=4, mu_tJ=1, mu_bJ=1, omega_J=0.7,
                 n_mult=10, coarsest_max=100, max_levels=30, seed=20110204, coarse_drop=1,
-                coarse_pinv="svd", row_form="induced")
+                coarse_pinv="svd", row_form="induced", relax_order="natural")
 
 
 def _lib():
@@ -93,6 +97,8 @@ def _lib():
         L.oracle_rs_coarsen.restype = ctypes.c_int
         L.oracle_ls_fit.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, P]
         L.oracle_ls_fit.restype = ctypes.c_int64
+        L.oracle_row_colours.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P, P]
+        L.oracle_row_colours.restype = ctypes.c_int32
         _LIB = L
     return _LIB
 
@@ -142,6 +148,37 @@ def kaczmarz_sweep(R: sp.csr_matrix, X: np.ndarray, rhs: np.ndarray,
         bp = bc = bv = sh = None
     _lib().oracle_kaczmarz_sweep(R.shape[0], nb, _ptr(rp), _ptr(rc), _ptr(rv), _ptr(bp),
                                  _ptr(bc), _ptr(bv), _ptr(sh), _ptr(rhs), _ptr(X))
+
+
+def row_colours(R: sp.csr_matrix) -> np.ndarray:
+    """Greedy colouring of the rows of R in natural order (oracle.c): rows of
+    one colour share no column.  Used by the coloured-order variant only."""
+    R = _csr(R)
+    rp, rc, _ = _arrs(R)
+    col = np.zeros(R.shape[0], dtype=np.int32)
+    k = _lib().oracle_row_colours(R.shape[0], R.shape[1], _ptr(rp), _ptr(rc), _ptr(col))
+    if k < 0:
+        raise ValueError("row colouring needs more than 128 colours")
+    return col
+
+
+def colour_order(R: sp.csr_matrix) -> np.ndarray:
+    """The coloured sweep order (a variant of R3, not the paper's): rows by
+    colour, natural order inside a colour."""
+    return np.argsort(row_colours(R), kind="stable")
+
+
+def kaczmarz_sweep_coloured(R: sp.csr_matrix, X: np.ndarray, rhs: np.ndarray,
+                            B: sp.csr_matrix | None = None, shift: np.ndarray | None = None,
+                            order: np.ndarray | None = None) -> None:
+    """One Kaczmarz sweep over the rows of R - shift_j B in the coloured order
+    (the colouring of R's pattern, merged with B's for the shifted form):
+    the natural-order sweep of the rows permuted into that order."""
+    R = _csr(R)
+    if order is None:
+        order = colour_order(R if B is None else _csr(abs(R) + abs(B)))
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)[order]
+    kaczmarz_sweep(R[order], X, rhs, None if B is None else _csr(B)[order], shift)
 
 
 def strength(N: sp.csr_matrix, theta: float) -> sp.csr_matrix:
@@ -287,7 +324,8 @@ def _cols_norm(M: sp.csr_matrix, X: np.ndarray) -> np.ndarray:
     return np.sqrt(np.einsum("ij,ij->j", X, M @ X))
 
 
-def relax_boot(L: Level, spd: bool, target: str, sigma, U, V, K, T, omega: float) -> None:
+def relax_boot(L: Level, spd: bool, target: str, sigma, U, V, K, T, omega: float,
+               relax_order: str = "natural") -> None:
     """One block Gauss-Seidel relaxation of the boot vectors on
     A v - s B u = kappa, A^t u - s C v = tau (Eqs. genSVDresid1-2, add) with
     sigma fixed, in place.  Dominant: one weighted-Jacobi step for u, then
@@ -295,11 +333,12 @@ def relax_boot(L: Level, spd: bool, target: str, sigma, U, V, K, T, omega: float
     from the rows of A^t (Sec. 5.3, R1/R2); SPD: rows of A - lam B."""
     sigma = np.asarray(sigma, dtype=np.float64)
     if target == "minimal":
+        sweep = kaczmarz_sweep if relax_order == "natural" else kaczmarz_sweep_coloured
         if spd:
-            kaczmarz_sweep(L.A, U, K, B=L.B, shift=sigma)
+            sweep(L.A, U, K, B=L.B, shift=sigma)
             return
-        kaczmarz_sweep(L.A, V, sigma * (L.B @ U) + K)
-        kaczmarz_sweep(L.At, U, sigma * (L.C @ V) + T)
+        sweep(L.A, V, sigma * (L.B @ U) + K)
+        sweep(L.At, U, sigma * (L.C @ V) + T)
         return
     dB = L.B.diagonal()[:, None]
     if spd:
@@ -528,8 +567,9 @@ def vcycle(H: Hierarchy, l: int, sigma, U, V, K, T, coarse_XY=None) -> None:
         if not spd:
             V[:] = v
         return
+    order = p.get("relax_order", "natural")
     for _ in range(p["mu_b"]):
-        relax_boot(L, spd, H.target, sigma, U, V, K, T, p["omega_J"])
+        relax_boot(L, spd, H.target, sigma, U, V, K, T, p["omega_J"], order)
     r, s = level_residual(L, spd, sigma, U, V, K, T)
     Kc = L.P.T @ r
     Tc = None if spd else L.Q.T @ s
@@ -540,7 +580,7 @@ def vcycle(H: Hierarchy, l: int, sigma, U, V, K, T, coarse_XY=None) -> None:
     if not spd:
         V += L.Q @ Vc
     for _ in range(p["mu_b"]):
-        relax_boot(L, spd, H.target, sigma, U, V, K, T, p["omega_J"])
+        relax_boot(L, spd, H.target, sigma, U, V, K, T, p["omega_J"], order)
 
 
 # --------------------------------------------------------------------------

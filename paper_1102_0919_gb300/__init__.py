@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
                 ("omega_J", ctypes.c_double), ("n_mult", ctypes.c_int32),
                 ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32),
-                ("coarse_pinv", ctypes.c_int32), ("row_form", ctypes.c_int32)]
+                ("coarse_pinv", ctypes.c_int32), ("row_form", ctypes.c_int32),
+                ("relax_order", ctypes.c_int32)]
 
 
 class _Csr(ctypes.Structure):
@@ -73,6 +74,7 @@ samg_set_triplets = _sig("samg_set_triplets", _I, _CTX, _P, _P, _P)
 samg_get_triplets = _sig("samg_get_triplets", _I, _CTX, _P, _P, _P, _P)
 samg_set_precision = _sig("samg_set_precision", _I, _CTX, _I)
 samg_set_coarse_pinv = _sig("samg_set_coarse_pinv", _I, _CTX, _I)
+samg_set_relax_order = _sig("samg_set_relax_order", _I, _CTX, _I)
 samg_get_hierarchy_info = _sig("samg_get_hierarchy_info", _I, _CTX, ctypes.POINTER(_I), _P, _P, _P)
 samg_get_level_matrix = _sig("samg_get_level_matrix", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
@@ -109,6 +111,7 @@ samg_sweep_plan = _sig("samg_sweep_plan", _I, _P, _I, _P, ctypes.c_int64, ctypes
 samg_block_gram_noalloc = _sig("samg_block_gram_noalloc", _I, _P, _P, ctypes.c_int64, _I, _I, _P,
                                _P)
 samg_set_triplets_device = _sig("samg_set_triplets_device", _I, _CTX, _P, _P, _P)
+samg_row_colours = _sig("samg_row_colours", _I, _P, _P, ctypes.POINTER(ctypes.c_int32))
 samg_profile = _sig("samg_profile", _I, _CTX, _I)
 samg_launch_count = _sig("samg_launch_count", ctypes.c_uint64)
 samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int64),
@@ -116,7 +119,7 @@ samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(c
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
             "samg_solve", "samg_set_triplets", "samg_get_triplets", "samg_set_precision",
-            "samg_set_coarse_pinv",
+            "samg_set_coarse_pinv", "samg_set_relax_order",
             "samg_get_hierarchy_info", "samg_get_level_matrix", "samg_relax",
             "samg_residual_restrict", "samg_interpolate", "samg_coarsest_solve", "samg_vcycle",
             "samg_ritz", "samg_block_gram", "samg_block_gram_noalloc", "samg_set_triplets_device",
@@ -125,7 +128,7 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_host_strength_product", "samg_export", "samg_write_hierarchy",
             "samg_import_file", "samg_sweep_schedule", "samg_setup_batched",
             "samg_solve_batched", "samg_batch_problem", "samg_batch_size",
-            "samg_batch_last_error", "samg_batch_destroy"]
+            "samg_batch_last_error", "samg_batch_destroy", "samg_row_colours"]
 
 
 def _arr(x, dtype):
@@ -152,6 +155,17 @@ def _csr(A):
     return c
 
 
+def row_colours(A):
+    """The library's greedy row colouring of A (host only): (colours, count)."""
+    c = _csr(A)
+    out = np.zeros(max(c.m, 1), np.int32)
+    k = ctypes.c_int32(0)
+    st = samg_row_colours(ctypes.byref(c), _ptr(out), ctypes.byref(k))
+    if st != OK:
+        raise SamgError(st, samg_last_error(None).decode())
+    return out[:c.m], k.value
+
+
 def make_params(**kw) -> Params:
     p = Params()
     samg_default_params(ctypes.byref(p))
@@ -162,6 +176,8 @@ def make_params(**kw) -> Params:
             v = {"svd": 0, "geneig": 1}.get(v, v)
         elif k == "row_form":
             v = {"induced": 0, "paper": 1}.get(v, v)
+        elif k == "relax_order":
+            v = {"natural": 0, "coloured": 1}.get(v, v)
         setattr(p, k, v)
     return p
 
@@ -294,6 +310,10 @@ class Solver:
         """0: the paper's SVD pseudo-inverse on the coarsest level; 1: the
         generalized-eigen variant."""
         self._check(samg_set_coarse_pinv(self._ctx, int(form)))
+
+    def set_relax_order(self, order):
+        """"natural" (0, the paper's) or "coloured" (1, the variant)."""
+        self._check(samg_set_relax_order(self._ctx, {"natural": 0, "coloured": 1}.get(order, order)))
 
     # ---------------------------------------------------------- solve
     def solve(self, tol=1e-8, max_outer=100):

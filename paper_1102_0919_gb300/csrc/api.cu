@@ -62,6 +62,8 @@ void check_common(int n_b, const samg_params *prm) {
                "coarse_pinv must be 0 (SVD pseudo-inverse) or 1 (generalized-eigen variant)");
     SAMG_CHECK(prm->row_form == 0 || prm->row_form == 1, SAMG_E_INVALID,
                "row_form must be 0 (rows from A) or 1 (the paper's A A^t coarsening)");
+    SAMG_CHECK(prm->relax_order == 0 || prm->relax_order == 1, SAMG_E_INVALID,
+               "relax_order must be 0 (natural, the paper's) or 1 (coloured variant)");
 }
 
 template <typename T>
@@ -236,6 +238,7 @@ void samg_default_params(samg_params *p) {
     p->n_conv = 0;
     p->coarse_pinv = 0;
     p->row_form = 0;
+    p->relax_order = 0;
 }
 
 const char *samg_last_error(const samg_ctx *ctx) {
@@ -506,6 +509,15 @@ samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec) {
     return guarded(ctx, [&] {
         SAMG_CHECK(prec == SAMG_FP64 || prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
         ctx->prm.prec = prec;
+    });
+}
+
+samg_status samg_set_relax_order(samg_ctx *ctx, int order) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(order == 0 || order == 1, SAMG_E_INVALID,
+                   "relax_order must be 0 (natural, the paper's) or 1 (coloured variant)");
+        ctx->prm.relax_order = order;
     });
 }
 
@@ -917,6 +929,25 @@ samg_status samg_sweep_plan(const samg_csr *A, int fused_count, int32_t *row_lev
         return e.status;
     } catch (...) {
         return SAMG_E_INVALID;
+    }
+}
+
+samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolour) {
+    try {
+        SAMG_CHECK(A && colour && ncolour, SAMG_E_INVALID, "row_colours: NULL argument");
+        validate_csr(*A);
+        std::vector<int64_t> rp(A->row_ptr, A->row_ptr + A->m + 1);
+        std::vector<int> ci(A->col, A->col + A->nnz);
+        std::vector<int> col;
+        *ncolour = greedy_row_colours(A->m, A->n, rp, ci, col);
+        std::copy(col.begin(), col.end(), colour);
+        return SAMG_OK;
+    } catch (const Error &e) {
+        g_create_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "row_colours: host allocation failed";
+        return SAMG_E_NOMEM;
     }
 }
 

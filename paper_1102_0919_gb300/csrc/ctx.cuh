@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "coloured.cuh"
 #include "common.cuh"
 #include "dense.cuh"
 #include "kaczmarz.cuh"
@@ -28,6 +29,7 @@ struct Level {
     DCsr P, Pt, Q, Qt;          // empty on the coarsest level
     KSched kA, kAt;             // Kaczmarz schedules (minimal target)
     std::vector<KSched> kF;     // fused programs of `count` relaxations, by count
+    std::vector<CSched> kC;     // their coloured-order variants, by count
     DBuf<double> dBd, dCd;      // diagonals of B, C (dominant target)
     DBuf<float> dBf, dCf;
     Work<float> wf;

@@ -95,6 +95,56 @@ void relax(samg_ctx &c, int l) {
     std::swap(w.v, w.tv);
 }
 
+// The coloured-order variant of a smoothing phase (not the paper's order):
+// the same relaxations with every sweep's rows visited colour by colour
+// (coloured.cuh), on the same unknown [v; u] and right-hand side [kappa; tau]
+// as the exact-order program.  The program is built on first use.
+template <typename T>
+static void relax_phase_coloured(samg_ctx &c, int l, int count) {
+    Level &L = c.L[l];
+    Work<T> &w = work<T>(L);
+    cudaStream_t s = c.stream;
+    const int ld = c.ld;
+    if ((int)L.kC.size() <= count) L.kC.resize(count + 1);
+    CSched &cs = L.kC[count];
+    if (cs.rows == 0) {
+        HCsr hA, hB;
+        download_csr(L.A, hA, s);
+        if (L.B.empty()) csr_identity(c.spd() ? L.n : L.m, hB);
+        else download_csr(L.B, hB, s);
+        if (c.spd()) {
+            build_cschedule_stacked(hA, hB, count, cs, s);
+        } else {
+            HCsr hAt, hC;
+            download_csr(L.At, hAt, s);
+            if (L.C.empty()) csr_identity(L.n, hC);
+            else download_csr(L.C, hC, s);
+            build_cschedule_fused(hA, hAt, hB, hC, count, cs, s);
+        }
+    }
+    const size_t sz = sizeof(T);
+    const double bytes = (double)cs.nent * ((cs.mode == 1 ? 2.0 : 1.0) * sz + 4.0) +
+                         4.0 * (cs.rows + 1.0) + (double)cs.rows * c.nb * sz +
+                         2.0 * count * (double)(c.spd() ? L.n : L.m + L.n) * c.nb * sz;
+    Prof pr(c.prof, s, 0, bytes);
+    if (c.spd()) {
+        launch_coloured<T>(cs, ld, w.k.p, w.u.p, c.sigma.p, s);
+        return;
+    }
+    const size_t nv = (size_t)L.n * ld, nu = (size_t)L.m * ld;
+    if (w.z.n != nu + nv) {
+        w.z.alloc(nu + nv);
+        w.kt.alloc(nu + nv);
+    }
+    SAMG_CUDA(cudaMemcpyAsync(w.z.p, w.v.p, nv * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.z.p + nv, w.u.p, nu * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.kt.p, w.k.p, nu * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.kt.p + nu, w.t.p, nv * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    launch_coloured<T>(cs, ld, w.kt.p, w.z.p, c.sigma.p, s);
+    SAMG_CUDA(cudaMemcpyAsync(w.v.p, w.z.p, nv * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    SAMG_CUDA(cudaMemcpyAsync(w.u.p, w.z.p + nv, nu * sizeof(T), cudaMemcpyDeviceToDevice, s));
+}
+
 // count relaxations of the minimal kind as one fused sweep program (the
 // schedule is built on first use for each count); other kinds relax one at a
 // time.  The result is that of count calls of relax() up to the rounding
@@ -110,6 +160,10 @@ void relax_phase(samg_ctx &c, int l, int count) {
     Work<T> &w = work<T>(L);
     cudaStream_t s = c.stream;
     const int ld = c.ld;
+    if (c.prm.relax_order == 1) {
+        relax_phase_coloured<T>(c, l, count);
+        return;
+    }
     if ((int)L.kF.size() <= count) L.kF.resize(count + 1);
     KSched &ks = L.kF[count];
     if (ks.rows == 0) {

@@ -114,6 +114,32 @@ def test_relaxation_each_level(case, prec, tol):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_relaxation_coloured_each_level(case, prec, tol):
+    """relax_order = 1 (the coloured variant): every level's smoothing phase
+    against the oracle's coloured sweeps (the same greedy colouring)."""
+    H, g = case["H"], case["g"]
+    if H.target != "minimal":
+        pytest.skip("the coloured order applies to the Kaczmarz (minimal) relaxation")
+    g.set_precision(prec)
+    g.set_relax_order("coloured")
+    spd = case["kind"] == "spd"
+    try:
+        for l in range(len(H.levels) - 1):
+            sig, U, V, K, T = _vecs(case, l, 150 + l)
+            Ug, Vg = g.relax(l, sig, U, V, K, T, count=3)
+            Ur, Vr = U.copy(), None if spd else V.copy()
+            for _ in range(3):
+                oracle.relax_boot(H.levels[l], spd, H.target, sig, Ur, Vr, K, T,
+                                  H.params["omega_J"], "coloured")
+            assert rel(Ug, Ur) < tol, (l, rel(Ug, Ur))
+            if not spd:
+                assert rel(Vg, Vr) < tol, (l, rel(Vg, Vr))
+    finally:
+        g.set_relax_order("natural")
+        g.set_precision("fp64")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
 def test_residual_restrict_and_interpolate(case, prec, tol):
     H, g = case["H"], case["g"]
     g.set_precision(prec)
@@ -237,6 +263,30 @@ def test_solve_matches_oracle(case, prec):
         # the defect form equals the paper form to rounding: same iteration counts
         assert abs(it - (len(hist) - 1)) <= 1
     g.set_precision("fp64")
+
+
+def test_solve_coloured_matches_oracle(case):
+    """The solve with the coloured variant reaches the oracle's triplets, and
+    the FP64 path takes the oracle's coloured iteration count to within 1."""
+    H, g = case["H"], case["g"]
+    if H.target != "minimal" or case["name"] == "svd_min_paper":
+        pytest.skip("coloured order: minimal target, converging form")
+    g.set_precision("fp64")
+    g.set_relax_order("coloured")
+    try:
+        g.set_triplets(case["s"], case["U"], case["V"])
+        ok, it = g.solve(1e-10, 200)
+        sg, Ug, Vg, rg = g.triplets()
+        Hc = oracle.hierarchy_from_interp(H.levels[0].A, [L.P for L in H.levels[:-1]],
+                                          None if case["kind"] == "spd" else
+                                          [L.Q for L in H.levels[:-1]],
+                                          case["kind"], H.target, dict(H.params, relax_order="coloured"))
+        so, Uo, Vo, hist = oracle.solve(Hc, case["s"], case["U"], case["V"], tol=1e-10, max_outer=200)
+        assert ok and rg.max() <= 1e-10
+        assert rel(sg, so) < 1e-10
+        assert abs(it - (len(hist) - 1)) <= 1
+    finally:
+        g.set_relax_order("natural")
 
 
 # ----------------------------------------------------------- Kaczmarz stress

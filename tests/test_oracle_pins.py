@@ -676,3 +676,54 @@ def test_paper_row_form_collapses_onto_null_At_on_the_gradient():
     s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=60)
     assert hist[-1].max() <= 1e-10
     assert np.abs(s - exact).max() < 1e-10 * exact.max()
+
+
+def test_coloured_order_pins():
+    """The coloured-order variant of the sweep (not the paper's order).
+
+    * The greedy colouring is proper (rows of one colour share no column)
+      and greedy: a row of colour c > 0 has, for every c' < c, an earlier
+      row of colour c' sharing a column with it.
+    * On the N x N gradient it is worked out by hand: the x-edge rows
+      alternate colours 0, 1 along a grid row; a y-edge row meets up to two
+      x-edges at each end, which hold both 0 and 1, so y-edges take 2 and 3:
+      4 colours for the rows of A.  The rows of A^t (nodes) conflict when
+      adjacent, and the natural order gives the checkerboard: 2 colours.
+    * A coloured sweep is the natural-order sweep of the rows permuted by
+      colour, and reordering rows inside a colour does not change it (they
+      commute); after it the rows of the last colour hold exactly."""
+    A = W.gradient(12).to_scipy()
+    for R, want in ((A, 4), (sp.csr_matrix(A.T), 2)):
+        col = oracle.row_colours(R)
+        assert col.max() + 1 == want
+        S = (abs(R) @ abs(R).T).tocsr()       # rows sharing a column
+        for i in range(R.shape[0]):
+            nbr = S.indices[S.indptr[i]:S.indptr[i + 1]]
+            nbr = nbr[nbr != i]
+            assert not np.any(col[nbr] == col[i])
+            earlier = set(col[nbr[nbr < i]].tolist())
+            assert all(c in earlier for c in range(col[i]))
+    rng = np.random.default_rng(3)
+    R = sp.random(60, 40, density=0.08, random_state=4, format="csr") + sp.eye(60, 40, format="csr")
+    R = oracle.samg._csr(R)
+    X0 = rng.standard_normal((40, 3))
+    rhs = rng.standard_normal((60, 3))
+    col = oracle.row_colours(R)
+    order = np.argsort(col, kind="stable")
+    X1 = X0.copy()
+    oracle.kaczmarz_sweep_coloured(R, X1, rhs)
+    # plain projections in the permuted order
+    X2 = X0.copy()
+    D = R.toarray()
+    for i in order:
+        a = D[i]
+        if a @ a > 0:                        # an empty row projects nothing
+            X2 += np.outer(a, (rhs[i] - a @ X2) / (a @ a))
+    assert np.abs(X1 - X2).max() < 1e-12
+    # rows shuffled inside each colour
+    shuf = np.concatenate([rng.permutation(np.flatnonzero(col == c)) for c in range(col.max() + 1)])
+    X3 = X0.copy()
+    oracle.kaczmarz_sweep_coloured(R, X3, rhs, order=shuf)
+    assert np.abs(X1 - X3).max() < 1e-12
+    last = np.flatnonzero((col == col.max()) & (np.abs(D).sum(axis=1) > 0))
+    assert last.size and np.abs(D[last] @ X1 - rhs[last]).max() < 1e-12
