@@ -3,28 +3,36 @@
 self-learning AMG triplet method, mixed precision (float32 V-cycle, float64
 residual/Ritz) vs plain float64, on one GB300.
 
-Workload (default): 8 minimal singular triplets of the 256 x 256
-forward-difference gradient (m = 131,584, n = 65,536, nnz = 262,144), seeded
-synthetic input (--workload 3 selects the 1024 x 1024 member of the family).
-One step = one solve from the same post-setup boot triplets (already resident
-in HBM) to max_j rho_j <= 1e-8: every outer iteration runs the whole hot path
-(V-cycle with Kaczmarz block Gauss-Seidel, residual + restriction, coarsest
-pseudo-inverse, interpolation, Ritz step, residual norms).  value = seconds
-per solve (lower is better), mixed precision.  The plain float64 path is
-timed from the same boot triplets with max(1, W // 3) warm-up and
-max(1, K // 3) timed solves (it is the slower comparison arm).
+Workload (default, --workload 3): 8 minimal singular triplets of the
+1024 x 1024 forward-difference gradient (m = 2,099,200, n = 1,048,576,
+nnz = 4,194,304), seeded synthetic input; --workload 2 selects the 256 x 256
+member.  Both precision arms start from the same post-setup boot triplets,
+resident in HBM.
 
-Beside the line ("other_workloads"), the default run also times the 32 x 32
-Laplacian's 4 minimal eigenpairs to residual 1e-8 in both precisions, and
-("variants") the main workload with two guard triplets (n_b = 10, the first
-8 converged); --no-small skips both.
+* A step is one outer iteration: one pass of the whole hot path (V-cycle
+  with Kaczmarz block Gauss-Seidel smoothing in the paper's natural order,
+  residual + restriction, coarsest pseudo-inverse, interpolation, Ritz
+  step, residual norms).  W warm-up steps, then K timed steps (CUDA events
+  on the library's stream) give ms_per_step.
+* value (the metric) is one solve from the boot triplets to
+  max_j rho_j <= 1e-8, timed directly with CUDA events, mixed precision.
+  The float64 arm is timed the same way (fewer steps).
+* e2e: the same solve through the C ABI with host buffers (the boot
+  triplets copied in, the triplets and residuals copied out).
+* variants: the coloured-order smoothing variant (not the paper's order):
+  its solve time, iterations and convergence factor beside the paper
+  order's, and its sweep kernel's algorithmic GB/s.
+* cpu_baseline: the FP64 oracle on the GPU's own hierarchy and boot
+  triplets (interpolation operators read back through the C ABI), a sample
+  of outer iterations timed on the host cores and scaled by the GPU's
+  iteration count.
 
---impl reference runs the FP64 CPU oracle on a bounded sample of the same
-workload instead (rank 0 only).
+--impl reference runs the FP64 CPU oracle alone (rank 0 only).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -37,6 +45,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "kaczmarz_dram_traffic.json")
+KZ_SOURCE = os.path.join(ROOT, "paper_1102_0919_gb300", "csrc", "kaczmarz.cu")
 
 
 def _peaks():
@@ -128,74 +138,122 @@ class Clocks:
 
 # --------------------------------------------------------------- workload
 def workload(i):
+    """The workload, its setup parameters (seeded) and the triplets that must
+    reach the tolerance (the first n_conv; the others are guards)."""
     import workloads as W
 
     wl = W.workload(i)
-    return wl, dict(wl.params, seed=W.problem_seed(i))
+    prm = dict(wl.params, seed=W.problem_seed(i))
+    return wl, prm
 
 
-# --------------------------------------------------------------- CPU oracle sample
-def oracle_sample(i: int, gpu_iters: int | None):
-    """Oracle per-outer-iteration time on the 256 x 256 member of the same
-    gradient family (the oracle's setup of the full workload takes tens of
-    minutes), scaled linearly in m + n (the paper's cost model, Sec. 6.1) to
-    the benchmarked size and multiplied by the iteration count."""
+def traffic_record():
+    """DRAM bytes per sweep launch from the committed ncu summary, when it was
+    taken on the current sweep kernel source (else None)."""
+    try:
+        with open(TRAFFIC) as f:
+            rec = json.load(f)
+        with open(KZ_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    return rec if rec.get("kernel_source_sha256") == sha else None
+
+
+# --------------------------------------------------------------- CPU oracle
+def _oracle_params(prm, n_conv):
+    keys = ("mu_b", "omega_J", "coarse_drop", "coarse_pinv", "row_form", "relax_order")
+    p = {k: prm[k] for k in keys if k in prm}
+    for k, names in (("coarse_pinv", ("svd", "geneig")), ("row_form", ("induced", "paper")),
+                     ("relax_order", ("natural", "coloured"))):
+        if isinstance(p.get(k), int):
+            p[k] = names[p[k]]
+    return p
+
+
+def oracle_same_hierarchy(s, wl, prm, sig0, U0, V0, n_it, sample_iters=1):
+    """The FP64 oracle on the library's own hierarchy (its P_l and Q_l read
+    back through the C ABI, Galerkin operators formed by the oracle) from the
+    same boot triplets: sample_iters outer iterations timed on the host
+    cores, scaled by the iteration count n_it of the GPU solve."""
+    import numpy as np
+    import scipy.sparse as sp
+
+    import oracle
+
+    A = wl.build().to_scipy()
+    nl = len(s.levels())
+
+    def mat(l, which):
+        rp, ci, v, shape = s.level_matrix(l, which)
+        return sp.csr_matrix((v, ci, rp), shape=shape)
+
+    t0 = time.perf_counter()
+    Ps = [mat(l, "P") for l in range(nl - 1)]
+    Qs = None if wl.kind == "spd" else [mat(l, "Q") for l in range(nl - 1)]
+    H = oracle.hierarchy_from_interp(A, Ps, Qs, wl.kind, wl.target,
+                                     _oracle_params(prm, prm.get("n_conv", 0)))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.solve(H, sig0, U0, V0, tol=1e-300, max_outer=sample_iters)
+    per_it = (time.perf_counter() - t0) / sample_iters
+    cores = os.cpu_count() or 1
+    return {
+        "value": per_it * n_it, "unit": "s", "cores": cores, "kind": "oracle",
+        "sample": ("%d outer iteration(s) of the FP64 oracle (V-cycle + Ritz + residual norms) on "
+                   "the library's own hierarchy of this workload (%d levels, operators formed by "
+                   "the oracle in %.1f s, untimed) from the same boot triplets: %.2f s per "
+                   "iteration, scaled by the %d outer iterations of the GPU solve.  Sweeps and "
+                   "sparse products run on one thread, dense LAPACK on up to %d" %
+                   (sample_iters, nl, t_build, per_it, n_it, n_it, cores)),
+        "s_per_iteration": per_it,
+    }
+
+
+def run_reference(args):
+    """The oracle alone on the host cores (no GPU): per step, one outer
+    iteration of the oracle's solve on the 256 x 256 member of the gradient
+    family (its own 1-cycle hierarchy, built untimed), scaled to the
+    benchmarked size by m + n (the paper's cost model, Sec. 6.1) and by the
+    outer iterations the GPU solve of the benchmarked workload takes."""
     import numpy as np
 
     import oracle
     import workloads as W
 
-    wl, prm = workload(i)
-    full = wl.build()
-    if wl.kind == "svd" and wl.target == "minimal" and i in (2, 3):
-        small = W.gradient(256)
-    else:
-        small = full
-    A = small.to_scipy()
-    t0 = time.perf_counter()
-    H, s, U, V = oracle.setup(A, wl.nb, wl.target, wl.kind, dict(prm, n_mult=1))
-    t_setup = time.perf_counter() - t0
-    iters = 2
-    XY = oracle.dense_XY(H.levels[-1], H.spd)
-    t0 = time.perf_counter()
-    for _ in range(iters):
-        oracle.vcycle(H, 0, s, U, V, np.zeros_like(U), None if H.spd else np.zeros_like(V), XY)
-        s, U, V = oracle.ritz(H.levels[0].A, H.spd, H.target, U, V)
-        oracle.residual_norms(H.levels[0].A, H.spd, s, U, V)
-    per_it = (time.perf_counter() - t0) / iters
-    scale = (full.m + full.n) / float(A.shape[0] + A.shape[1])
-    # without a GPU count (the reference arm): the outer iterations the GPU
-    # solve needs on the 256 x 256 gradient from its 20-cycle setup (103;
-    # the oracle's own 1-cycle hierarchy does not reach 1e-8), else 30
-    n_it = gpu_iters if gpu_iters else (103 if i == 2 else 30)
-    return {
-        "value": per_it * scale * n_it, "unit": "s", "cores": 1, "kind": "oracle",
-        "sample": ("%d oracle outer iterations (V-cycle + Ritz + residual norms, float64, one "
-                   "thread) on the %dx%d gradient of the same family with a 1-cycle oracle "
-                   "hierarchy (setup %.1f s, untimed): %.3f s/iteration, scaled by (m+n) x%.1f "
-                   "to the benchmarked size and by %d iterations" %
-                   (iters, A.shape[0], A.shape[1], t_setup, per_it, scale, n_it)),
-    }
-
-
-def run_reference(args):
     rank, _, world = _env_rank()
     if rank != 0:
         return 0
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    wl, _ = workload(args.workload)
-    vals = []
-    cb = None
-    for _ in range(args.warmup + args.steps):
-        cb = oracle_sample(args.workload, None)
-        vals.append(cb["value"])
-    v = statistics.median(vals[args.warmup:])
+    wl, prm = workload(args.workload)
+    full = wl.build()
+    small = W.gradient(256).to_scipy() if args.workload in (2, 3) else full.to_scipy()
+    p = dict(_oracle_params(prm, 0), n_t=prm.get("n_t", 8), theta=prm.get("theta", 0.06),
+             mu_t=prm.get("mu_t", 8), n_mult=1, seed=prm["seed"])
+    t0 = time.perf_counter()
+    H, s, U, V = oracle.setup(small, wl.nb, wl.target, wl.kind, p)
+    t_setup = time.perf_counter() - t0
+    scale = (full.m + full.n) / float(small.shape[0] + small.shape[1])
+    n_it = W.SOLVE_ITERATIONS.get(args.workload, 30)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s, U, V, _ = oracle.solve(H, s, U, V, tol=1e-300, max_outer=1)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per_it = statistics.median(times)
+    v = per_it * scale * n_it
+    sample = ("per step one FP64 oracle outer iteration on the 256 x 256 gradient of the same "
+              "family (1-cycle oracle hierarchy, setup %.1f s untimed): %.3f s, scaled by "
+              "(m + n) x%.1f to the benchmarked size and by %d outer iterations (the GPU "
+              "solve's count for this workload); the value is a projection, the steps are "
+              "what was timed" % (t_setup, per_it, scale, n_it))
     line = {
         "impl": "reference", "metric": "time to residual 1e-8 (s)", "value": v, "unit": "s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wl.name},
-        "cpu_baseline": dict(cb, value=v),
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_it * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name}, "projected": True,
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -215,9 +273,13 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     import paper_1102_0919_gb300 as samg
 
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from closed_forms import gradient_singular_values, laplacian5_eigs
+
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     wl, prm = workload(args.workload)
+    n_conv = prm.get("n_conv", 0) or wl.nb
     A = wl.build()
     m, n = A.m, A.n
     mu = n if wl.kind == "spd" else m
@@ -228,10 +290,14 @@ def run_gpu(args):
     levels = s.levels()
     log("setup %.1f s, levels %s" % (t_setup, levels))
     sig0, U0, V0, res0 = s.triplets()
-    # initial boot triplets resident in HBM (torch owns the memory)
+    # boot triplets resident in HBM (torch owns the memory)
     dsig = torch.tensor(sig0, device=dev, dtype=torch.float64)
     dU = torch.tensor(U0, device=dev, dtype=torch.float64).contiguous()
     dV = None if V0 is None else torch.tensor(V0, device=dev, dtype=torch.float64).contiguous()
+    if wl.kind == "spd":
+        exact = laplacian5_eigs(int(round(n ** 0.5)))[:n_conv]
+    else:
+        exact = gradient_singular_values(int(round(n ** 0.5)))[:n_conv]
 
     def reset():
         s.set_triplets_device(dsig.data_ptr(), dU.data_ptr(),
@@ -242,164 +308,167 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def steps(k):
+        """k outer iterations (each one pass of the hot path) in a row."""
+        for _ in range(k):
+            s.solve(1e-300, 1)
+
+    def timed(fn):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1), out
+
+    def solve_record():
+        sg, _, _, rf = s.triplets()
+        return {"resid": float(rf[:n_conv].max()),
+                "sigma_relerr_max": float(np.max(np.abs(sg[:n_conv] - exact) / exact))}
+
     results = {}
     log("launches after setup: %d" % samg.samg_launch_count())
     for prec in args.arms.split(","):
         s.set_precision(prec)
-        warm = args.warmup if prec == "fp32" else max(1, args.warmup // 3)
-        steps = args.steps if prec == "fp32" else max(1, args.steps // 3)
-        for _ in range(warm):
-            reset()
-            tw = time.perf_counter()
-            ok, it = s.solve(args.tol, args.max_outer)
-            log("%s warm-up solve: %d iterations, converged %s, %.2f s" %
-                (prec, it, ok, time.perf_counter() - tw))
-        iters = []
-        barrier()
-        launches0 = samg.samg_launch_count()
-        log("%s: launches before the timed region: %d" % (prec, launches0))
-        rng = args.ncu_range and prec == "fp32"
-        if rng:
-            torch.cuda.profiler.start()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        prof = prec == "fp32"
-        if prof:
+        k_steps = args.steps if prec == "fp32" else max(1, args.steps // 4)
+        # warm-up: W steps (the first builds every level's sweep programs)
+        reset()
+        steps(max(args.warmup, 3))
+        reset()
+        ms_k, _ = timed(lambda: steps(k_steps))
+        rec = {"ms_per_step": ms_k / k_steps, "steps": k_steps}
+        if prec == "fp32":
+            # kernel classes over K more steps with per-launch CUDA events
             s.profile(True)
-        with Clocks(local) as clk:
-            ev0.record(stream)
-            for _ in range(steps):
-                reset()
-                ok, it = s.solve(args.tol, args.max_outer)
-                iters.append((ok, it))
-            ev1.record(stream)
-            barrier()
-        if rng:
-            torch.cuda.profiler.stop()
-        ms = ev0.elapsed_time(ev1) / steps
-        if prof:
+            s.profile_read(reset=True)
+            reset()
+            if args.ncu_range:
+                torch.cuda.profiler.start()
+            steps(k_steps)
+            if args.ncu_range:
+                torch.cuda.profiler.stop()
+            rec["prof"] = s.profile_read()
             s.profile(False)
-            pr = s.profile_read()
-        launches = samg.samg_launch_count() - launches0
-        results[prec] = dict(ms=max_over_ranks(ms, dev), iters=iters, launches=launches, steps=steps,
-                             clocks=clk.summary(), prof=pr if prof else None)
-        log("%s: %.1f ms/solve, iterations %s" % (prec, ms, iters))
-        if prof:
-            log("kernels: %s" % json.dumps(pr))
-        _, _, _, rf = s.triplets()
-        results[prec]["resid"] = float(rf.max())
+            launches0 = samg.samg_launch_count()
+        reset()
+        with Clocks(local) as clk:
+            ms_solve, (ok, it) = timed(lambda: s.solve(args.tol, args.max_outer))
+        rec.update(solve_ms=max_over_ranks(ms_solve, dev), converged=bool(ok), iterations=it,
+                   clocks=clk.summary(), **solve_record())
+        if prec == "fp32":
+            rec["launches"] = samg.samg_launch_count() - launches0
+        log("%s: %.2f ms/step, solve %.1f ms, %d iterations, converged %s, resid %.2e" %
+            (prec, rec["ms_per_step"], ms_solve, it, ok, rec["resid"]))
+        results[prec] = rec
+    mixed = results["fp32"]
     # end to end through the C ABI with host buffers (mixed precision)
     s.set_precision("fp32")
-    e2e = []
-    for k in range(max(args.steps, 1) + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s.set_triplets(sig0, U0, V0)
-        ok, it = s.solve(args.tol, args.max_outer)
-        sg, Uh, Vh, rh = s.triplets()
-        t1 = time.perf_counter()
-        if k:
-            e2e.append(t1 - t0)
+    barrier()
+    t0 = time.perf_counter()
+    s.set_triplets(sig0, U0, V0)
+    ok_e, it_e = s.solve(args.tol, args.max_outer)
+    sg, Uh, Vh, rh = s.triplets()
+    e2e_s = time.perf_counter() - t0
     h2d = 8 * (wl.nb + mu * wl.nb + (0 if V0 is None else n * wl.nb))
     d2h = h2d + 8 * wl.nb
+    # the coloured-order smoothing variant (not the paper's order)
+    variants = {}
+    if not args.no_variant and wl.target == "minimal":
+        s.set_relax_order("coloured")
+        try:
+            reset()
+            steps(3)
+            reset()
+            s.profile(True)
+            s.profile_read(reset=True)
+            ms_c, (okc, itc) = timed(lambda: s.solve(args.tol, args.max_outer))
+            prc = s.profile_read()
+            s.profile(False)
+            kz = prc["kaczmarz_sweep"]
+            peaks, how = _peaks()
+            gbs = kz["bytes"] / (kz["ms"] * 1e-3) / 1e9 if kz["ms"] > 0 else 0.0
+            variants["coloured_order"] = dict(
+                value=ms_c / 1e3, unit="s", outer_iterations=itc, converged=bool(okc),
+                precision="fp32", **solve_record(),
+                sweep_gbs=gbs, sweep_frac=gbs / peaks["hbm_gbs"], sweep_launches=kz["launches"],
+                sweep_ms_per_solve=kz["ms"],
+                note="rows of each sweep visited colour by colour (relax_order = 1); the "
+                     "paper's natural order is the headline")
+        finally:
+            s.set_relax_order("natural")
+    cpu = None
+    if world == 1 and not args.no_cpu and rank == 0:
+        try:
+            cpu = oracle_same_hierarchy(s, wl, prm, sig0, U0, V0, mixed["iterations"])
+        except Exception as e:  # noqa: BLE001 -- the main line must still print
+            cpu = {"error": "%s: %s" % (type(e).__name__, e)}
     s.close()
     if rank != 0:
         return 0
     peaks, how = _peaks()
-    mixed = results["fp32"]
-    f64 = results.get("fp64", {"ms": float("nan"), "steps": 0, "iters": [(False, 0)], "resid": float("nan")})
+    f64 = results.get("fp64", {"solve_ms": float("nan"), "iterations": 0, "converged": False,
+                               "resid": float("nan"), "ms_per_step": float("nan"), "steps": 0})
     kz = mixed["prof"]["kaczmarz_sweep"]
+    spm = mixed["prof"]["block_spmm"]
     achieved = kz["bytes"] / (kz["ms"] * 1e-3) / 1e9 if kz["ms"] > 0 else 0.0
-    cpu = oracle_sample(args.workload, mixed["iters"][-1][1]) if world == 1 and not args.no_cpu else None
-    value = mixed["ms"] / 1e3
+    tr = traffic_record()
+    value = mixed["solve_ms"] / 1e3
+    vec_bytes = (m + n) * wl.nb * 4 * 10 + A.nnz * 8 * 4
     line = {
         "metric": "time to residual 1e-8 (s)",
         "value": value,
         "unit": "s",
         "n_gpus": world,
-        "steps": args.steps,
+        "steps": mixed["steps"],
         "warmup": args.warmup,
-        "ms_per_step": mixed["ms"],
+        "ms_per_step": mixed["ms_per_step"],
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl.name, "m": m, "n": n, "nnz": A.nnz, "n_b": wl.nb,
-                   "tol": args.tol, "levels": [[a, b] for a, b, _ in levels],
+                   "n_conv": n_conv, "tol": args.tol,
+                   "levels": [[a, b] for a, b, _ in levels],
+                   "setup": {k: prm[k] for k in sorted(prm) if k != "seed"},
+                   "step": "one outer iteration (V-cycle + Ritz + residual norms)",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (vectors + operators > 129 MB); no flush",
+                   "l2": ("inputs larger than L2: the finest operators and vector blocks alone "
+                          "are about %.0f MB, above the 129 MB L2; no flush" % (vec_bytes / 1e6))
+                   if vec_bytes > 129e6 else
+                   ("working set of about %.0f MB fits the 129 MB L2; no flush between "
+                    "steps (latency-bound sweeps)" % (vec_bytes / 1e6)),
                    "setup_s": round(t_setup, 3)},
-        "fp64": {"value": f64["ms"] / 1e3, "unit": "s", "steps": f64["steps"],
-                 "outer_iterations": f64["iters"][-1][1],
-                 "converged": all(o for o, _ in f64["iters"]), "resid": f64["resid"]},
-        "mixed": {"outer_iterations": mixed["iters"][-1][1],
-                  "converged": all(o for o, _ in mixed["iters"]), "resid": mixed["resid"]},
-        "speedup_mixed_vs_fp64": f64["ms"] / mixed["ms"] if mixed["ms"] else None,
-        "e2e": {"value": statistics.median(e2e), "unit": "s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "solve": {"outer_iterations": mixed["iterations"], "converged": mixed["converged"],
+                  "resid": mixed["resid"], "sigma_relerr_max": mixed["sigma_relerr_max"]},
+        "fp64": {"value": f64["solve_ms"] / 1e3, "unit": "s", "ms_per_step": f64["ms_per_step"],
+                 "steps": f64["steps"], "outer_iterations": f64["iterations"],
+                 "converged": f64["converged"], "resid": f64["resid"],
+                 "sigma_relerr_max": f64.get("sigma_relerr_max")},
+        "speedup_mixed_vs_fp64": f64["solve_ms"] / mixed["solve_ms"] if mixed["solve_ms"] else None,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "outer_iterations": it_e, "converged": bool(ok_e)},
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
-        "roofline": {"bound": "hbm", "kernel": "kaczmarz_sweep (float32)",
+        "roofline": {"bound": "hbm", "kernel": "k_kaczmarz (float32, exact natural order)",
                      "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": None if tr is None else tr["bytes_per_launch"],
+                     "traffic_source": None if tr is None else tr["how"],
                      "peak_source": how, "launches": kz["launches"],
                      "avg_launch_us": 1e3 * kz["ms"] / max(kz["launches"], 1),
                      "alg_bytes_per_launch": kz["bytes"] / max(kz["launches"], 1)},
-        "kernel_time_ms_per_solve": {k: v["ms"] / mixed["steps"] for k, v in mixed["prof"].items()},
-        # the V-cycle's sparse products (residual, restriction, interpolation,
-        # right-hand sides): algorithmic GB/s over their CUDA-event time
-        "spmm_gbs": (mixed["prof"]["block_spmm"]["bytes"] / (mixed["prof"]["block_spmm"]["ms"] * 1e-3) / 1e9
-                     if mixed["prof"]["block_spmm"]["ms"] > 0 else None),
+        "kernel_ms_per_step": {k: v["ms"] / mixed["steps"] for k, v in mixed["prof"].items()},
+        "spmm_gbs": spm["bytes"] / (spm["ms"] * 1e-3) / 1e9 if spm["ms"] > 0 else None,
+        "variants": variants,
         "cpu_baseline": cpu,
     }
-    if world == 1 and args.workload == 2 and not args.no_small:
+    if world == 1 and args.workload in (2, 3) and not args.no_small:
         line["other_workloads"] = {"laplacian5_N32_nb4_minimal": small_workload(1, dev, stream)}
-        line["variants"] = {"guard_nb10_nconv8": guard_variant(args, dev, stream)}
     print(json.dumps(line))
     return 0
-
-
-def guard_variant(args, dev, stream):
-    """The main workload with two guard triplets (n_b = 10, of which the
-    first 8 must reach the tolerance; not the paper's form): setup, then one
-    warm-up and one timed solve per precision.  Errors are reported, not
-    raised."""
-    try:
-        import torch
-
-        import paper_1102_0919_gb300 as samg
-
-        wl, prm = workload(args.workload)
-        A = wl.build()
-        t0 = time.perf_counter()
-        s = samg.Solver.setup(A, 10, wl.target, wl.kind, stream=stream, prec="fp32", n_conv=8, **prm)
-        torch.cuda.synchronize()
-        out = {"setup_s": round(time.perf_counter() - t0, 3), "unit": "s",
-               "levels": [[a, b] for a, b, _ in s.levels()]}
-        sig0, U0, V0, _ = s.triplets()
-        dsig = torch.tensor(sig0, device=dev, dtype=torch.float64)
-        dU = torch.tensor(U0, device=dev, dtype=torch.float64).contiguous()
-        dV = torch.tensor(V0, device=dev, dtype=torch.float64).contiguous()
-        for prec in ("fp64", "fp32"):
-            s.set_precision(prec)
-            s.set_triplets_device(dsig.data_ptr(), dU.data_ptr(), dV.data_ptr())
-            s.solve(args.tol, args.max_outer)
-            torch.cuda.synchronize()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            s.set_triplets_device(dsig.data_ptr(), dU.data_ptr(), dV.data_ptr())
-            ev0.record(stream)
-            ok, it = s.solve(args.tol, args.max_outer)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            _, _, _, rf = s.triplets()
-            out[prec] = {"value": ev0.elapsed_time(ev1) / 1e3, "outer_iterations": it,
-                         "converged": ok, "resid_first8": float(rf[:8].max())}
-        s.close()
-        return out
-    except Exception as e:  # noqa: BLE001 -- the main line must still print
-        return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 def small_workload(i, dev, stream, warm=3, steps=5):
@@ -514,19 +583,21 @@ def run_sweep_roofline(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="samg", choices=["samg", "reference"])
-    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--max-outer", type=int, default=300)
+    ap.add_argument("--max-outer", type=int, default=400)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the small 32 x 32 Laplacian measurement reported beside the line")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="skip the coloured-order variant reported beside the line")
     ap.add_argument("--arms", default="fp64,fp32",
-                    help="precision arms to time, in order (the JSON line needs both)")
+                    help="precision arms to time, in order (the JSON line needs fp32)")
     ap.add_argument("--ncu-range", action="store_true",
-                    help="bracket the timed mixed-precision solves with cudaProfilerStart/Stop "
+                    help="bracket the profiled mixed-precision steps with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
     ap.add_argument("--sweep-roofline", action="store_true",
                     help="time only level-0 relaxations at full size on a two-level "

@@ -380,12 +380,12 @@ struct Stage {
 
 // Warps 0 .. KZ_COMPUTE/32 - 1 compute.  The last warp is the producer: it
 // stages chunk images (bulk copies) and gathered values (cp.async) up to
-// KZ_NBUF chunks ahead, and publishes (release) this band's progress when the
-// compute warps complete a level that the image flags as waited for by a
-// later band, and at the band's end.  Before a level with cross-band
-// requirements, every compute warp that holds rows of it polls (acquire) the
-// progress words of the bands the image lists, so a handoff between bands
-// passes through one release and one acquire and no relay.
+// KZ_NBUF chunks ahead.  Cross-band handoffs involve no relay: after the
+// barrier of a level the image flags as waited for by a later band (and
+// after the band's last level), the last compute warp publishes (release)
+// the band's progress; before a level with cross-band requirements, every
+// compute warp that holds rows of it polls (acquire) the progress words of
+// the bands the image lists.
 // MODE 0: rows of A (norms given).  MODE 1: rows of A - s_j B (entries carry
 // b; norms formed per column).  MODE 2: fused relaxations (entries carry b;
 // the accumulation uses a - s_j b, the update only a; norms given).
@@ -439,13 +439,11 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
         if (b >= kv.nbands || s_abort) break;
         const int cb = kv.band_chunk[b], ce = kv.band_chunk[b + 1];
         const int Lband = kv.chunk[cb].L0;
-        const int nlev = kv.chunk[ce - 1].L0 + kv.chunk[ce - 1].nl - Lband;
         if (comm) {
             // ------------------------------------------------------ producer warp
             const int lane = threadIdx.x & 31;
-            int sn = cb, vn = cb, published = 0;
+            int sn = cb, vn = cb;
             bool aborted = false;
-            const bool mute = *((volatile int *)&kv.ctl->mute) == b;
             unsigned long long t0 = gtimer();  // re-armed whenever something advances
             int idle = 0;
             for (;;) {
@@ -474,33 +472,13 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                 }
                 bool adv = false;
                 const int done = __shfl_sync(FULL, ld_acq_cta(&s_done), 0);
-                // publish first: the release covers the compute warps' stores,
-                // which precede thread 0's release of s_done (acquired above).
-                // The flags of the levels below done are read from their
-                // chunks' images, which stay in place until this step has seen
-                // them completed (a buffer is refilled only below).
-                if (done > published) {
-                    bool f = done == nlev;
-                    for (int l = published + lane; l < done; l += 32) {
-                        for (int q = 0; q < KZ_NBUF; ++q) {
-                            const int l0 = s_cl0[q];
-                            if (l >= l0 && l < l0 + s_cnl[q]) {
-                                const int4 *lvq = reinterpret_cast<const int4 *>(bufs + (size_t)q * SG::stride);
-                                f = f || (lvq[l - l0].w & 2) != 0;
-                            }
-                        }
-                    }
-                    if (__any_sync(FULL, f) && lane == 0 && !mute)
-                        st_release(&kv.progress[b], (epoch << 32) | (unsigned)done);
-                    published = done;
-                    adv = true;
-                }
-                // a. image of chunk sn, once the chunk that used its buffer is done
+                // a. image of chunk sn, once the chunk that used its buffer
+                // (its level range is kept in s_cl0 / s_cnl) is done
                 if (sn < ce) {
-                    const int old = sn - KZ_NBUF;
-                    if (old < cb || done >= kv.chunk[old].L0 + kv.chunk[old].nl - Lband) {
-                        const int j = base + (sn - cb);
-                        const int bi = j % KZ_NBUF;
+                    const int j = base + (sn - cb);
+                    const int bi = j % KZ_NBUF;
+                    if (done >= s_cl0[bi] + s_cnl[bi]) {
+                        __syncwarp();
                         if (lane == 0) {
                             const KChunk ck = kv.chunk[sn];
                             const unsigned bytes = sizeof(T) == 4 ? ck.bytes_f : ck.bytes_d;
@@ -547,7 +525,9 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                         adv = true;
                     }
                 }
-                if (published >= nlev) break;
+                // every chunk staged and its values requested: the compute
+                // warps finish the band on their own
+                if (sn >= ce && (!SG::VALS || vn >= ce)) break;
                 if (adv) {
                     t0 = gtimer();
                     idle = 0;
@@ -568,6 +548,11 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
         } else {
             // ------------------------------------------------------ compute warps
             bool aborted = false;
+            // the last compute warp publishes (release) the band's progress after
+            // the levels the image flags; its rows are the fewest, so its wait
+            // for the release delays the next level the least
+            const bool publisher = threadIdx.x == KZ_COMPUTE - 32;
+            const bool mute = publisher && *((volatile int *)&kv.ctl->mute) == b;
             for (int c = cb; c < ce; ++c) {
                 const int j = base + (c - cb);
                 const int bi = j % KZ_NBUF;
@@ -597,8 +582,8 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                 const T *sxs = reinterpret_cast<const T *>(B + SG::o_xs);
                 for (int L = 0; L < ck.nl; ++L) {
                     const int lb = ck.L0 + L - Lband;  // band-local level
+                    const int4 lr = lv[L];
                     if (!aborted) {
-                        const int4 lr = lv[L];
                         // G = 2^lgG lanes per row (the smallest power of two
                         // not below the level's longest row, at most 32);
                         // lane lg takes entries lg, lg + G, ... for all LD
@@ -784,6 +769,11 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                     // every compute warp reaches every barrier, aborted or not
                     bar_compute();
                     if (threadIdx.x == 0) st_rel_cta(&s_done, lb + 1);
+                    // the release covers every compute warp's stores, which
+                    // precede the barrier
+                    if (publisher && (lr.w & 2) && !mute && !aborted &&
+                        !*((volatile int *)&s_abort))
+                        st_release(&kv.progress[b], (epoch << 32) | (unsigned)(lb + 1));
                 }
             }
         }

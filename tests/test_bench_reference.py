@@ -24,4 +24,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["config"]["workload"] == "gradient_N256_nb8_minimal"
+    assert d["config"]["workload"] == "gradient_N1024_nb8_minimal"
+    # the timed steps are what the line says was timed: one oracle outer
+    # iteration each; the value is marked as a projection from them
+    assert d["projected"] is True and 0 < d["ms_per_step"] < 600e3
+    assert "projection" in d["cpu_baseline"]["sample"]
