@@ -85,6 +85,12 @@ void upload(const CRows &P, int cols, int mode, CSched &cs, cudaStream_t s) {
     cs.class_off = P.class_off;
     cs.class_lg = P.class_lg;
     cs.ncolour_max = P.ncolour_max;
+    cs.max_class_threads = 0;
+    for (size_t k = 0; k + 1 < P.class_off.size(); ++k)
+        cs.max_class_threads = std::max(cs.max_class_threads,
+                                        (P.class_off[k + 1] - P.class_off[k]) << P.class_lg[k]);
+    cs.d_class_off.upload(P.class_off.data(), P.class_off.size(), s);
+    cs.d_class_lg.upload(P.class_lg.data(), P.class_lg.size(), s);
     SAMG_CHECK(cs.nent < (int64_t)1 << 31, SAMG_E_INVALID, "coloured sweep: too many entries");
     std::vector<int> rp32(P.rp.begin(), P.rp.end());
     cs.rp.upload(rp32.data(), rp32.size(), s);
@@ -188,25 +194,22 @@ __device__ __forceinline__ void cst(T *p, const T (&v)[LD]) {
     }
 }
 
-// One colour class: rows [r0, r1) of the program, G = 2^lg lanes per row
-// (aligned groups inside a warp; a lane takes entries lg, lg + G, ...).
+// The rows [r0, r1) of one colour class, G = 2^lg lanes per row (aligned
+// groups inside a warp; a lane takes entries lg, lg + G, ...), rows handed
+// out to groups from `first` in steps of `groups`.  Every lane of a warp
+// calls (the row sums shuffle within the group).
 // MODE 1: coefficients a - s_j b for the row sums, the norms and the update.
 // MODE 2: a - s_j b for the row sums, a for the update (b entries belong to
 // the other unknown and are not written), norms given.
 template <typename T, int LD, int MODE>
-__global__ void __launch_bounds__(256)
-    k_kz_class(int r0, int r1, int lg, const int *__restrict__ rp, const int *__restrict__ ci,
-               const int *__restrict__ rrow, const T *__restrict__ av, const T *__restrict__ bv,
-               const T *__restrict__ inv, const T *__restrict__ rhs, T *x,
-               const double *__restrict__ shift) {
+__device__ __forceinline__ void class_rows(int r0, int r1, int lg, long long first, long long groups,
+                                           const int *__restrict__ rp, const int *__restrict__ ci,
+                                           const int *__restrict__ rrow, const T *__restrict__ av,
+                                           const T *__restrict__ bv, const T *__restrict__ inv,
+                                           const T *__restrict__ rhs, T *x, const T (&sh)[LD]) {
     const int G = 1 << lg;
-    const int lane = threadIdx.x & 31;
-    const int lgi = lane & (G - 1);
-    const long long groups = (long long)gridDim.x * (blockDim.x >> lg);
-    T sh[LD];
-#pragma unroll
-    for (int q = 0; q < LD; ++q) sh[q] = MODE != 0 ? (T)shift[q] : T(0);
-    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg;; g += groups) {
+    const int lgi = (threadIdx.x & 31) & (G - 1);
+    for (long long g = first;; g += groups) {
         const long long r = r0 + g;
         const bool act = r < r1;
         if (!__any_sync(0xffffffffu, act)) break;
@@ -276,6 +279,44 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// One colour class on a grid.
+template <typename T, int LD, int MODE>
+__global__ void __launch_bounds__(256)
+    k_kz_class(int r0, int r1, int lg, const int *__restrict__ rp, const int *__restrict__ ci,
+               const int *__restrict__ rrow, const T *__restrict__ av, const T *__restrict__ bv,
+               const T *__restrict__ inv, const T *__restrict__ rhs, T *x,
+               const double *__restrict__ shift) {
+    T sh[LD];
+#pragma unroll
+    for (int q = 0; q < LD; ++q) sh[q] = MODE != 0 ? (T)shift[q] : T(0);
+    class_rows<T, LD, MODE>(r0, r1, lg, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg,
+                            (long long)gridDim.x * (blockDim.x >> lg), rp, ci, rrow, av, bv, inv,
+                            rhs, x, sh);
+}
+
+// A whole program of small classes in one CTA: the classes in order, a CTA
+// barrier between them (it orders the global stores of one class before the
+// loads of the next for every thread of the CTA).
+constexpr int COLOURED_CTA = 512;
+constexpr int COLOURED_CTA_ROWS = 32 * COLOURED_CTA;
+template <typename T, int LD, int MODE>
+__global__ void __launch_bounds__(COLOURED_CTA)
+    k_kz_classes_cta(int nclass, const int *__restrict__ class_off, const int *__restrict__ class_lg,
+                     const int *__restrict__ rp, const int *__restrict__ ci,
+                     const int *__restrict__ rrow, const T *__restrict__ av,
+                     const T *__restrict__ bv, const T *__restrict__ inv,
+                     const T *__restrict__ rhs, T *x, const double *__restrict__ shift) {
+    T sh[LD];
+#pragma unroll
+    for (int q = 0; q < LD; ++q) sh[q] = MODE != 0 ? (T)shift[q] : T(0);
+    for (int k = 0; k < nclass; ++k) {
+        const int lg = class_lg[k];
+        class_rows<T, LD, MODE>(class_off[k], class_off[k + 1], lg, (long long)threadIdx.x >> lg,
+                                (long long)(blockDim.x >> lg), rp, ci, rrow, av, bv, inv, rhs, x, sh);
+        __syncthreads();
+    }
+}
+
 template <typename T> const T *pick(const DBuf<double> &d, const DBuf<float> &f);
 template <> const double *pick<double>(const DBuf<double> &d, const DBuf<float> &) { return d.p; }
 template <> const float *pick<float>(const DBuf<double> &, const DBuf<float> &f) { return f.p; }
@@ -289,7 +330,16 @@ void run(const CSched &cs, const T *rhs, T *x, const double *shift, cudaStream_t
         SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     }
     const T *a = pick<T>(cs.ad, cs.af), *b = pick<T>(cs.bd, cs.bf), *inv = pick<T>(cs.invd, cs.invf);
-    for (size_t k = 0; k + 1 < cs.class_off.size(); ++k) {
+    const int nclass = (int)cs.class_off.size() - 1;
+    if (cs.max_class_threads <= COLOURED_CTA_ROWS) {
+        SAMG_COUNT_LAUNCH();
+        k_kz_classes_cta<T, LD, MODE><<<1, COLOURED_CTA, 0, s>>>(
+            nclass, cs.d_class_off.p, cs.d_class_lg.p, cs.rp.p, cs.ci.p, cs.rrow.p, a, b, inv, rhs,
+            x, shift);
+        SAMG_CUDA(cudaGetLastError());
+        return;
+    }
+    for (int k = 0; k < nclass; ++k) {
         const int r0 = cs.class_off[k], r1 = cs.class_off[k + 1];
         const int lg = cs.class_lg[k];
         const long long threads = (long long)(r1 - r0) << lg;

@@ -22,6 +22,8 @@ struct CSched {
     std::vector<int> class_off;        // classes in program order: row ranges
     std::vector<int> class_lg;         // log2 lanes per row of each class
     int ncolour_max = 0;               // colours of the most coloured sweep
+    int max_class_threads = 0;         // largest rows x lanes of one class
+    DBuf<int> d_class_off, d_class_lg; // the classes on the device (one-CTA path)
     DBuf<int> rp, ci, rrow;            // permuted rows: entries, right-hand-side row
     DBuf<double> ad, bd, invd;         // coefficients (b: modes 1 and 2), 1/|a|^2
     DBuf<float> af, bf, invf;
@@ -42,7 +44,10 @@ void build_cschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const H
 void build_cschedule_stacked(const HCsr &A, const HCsr &B, int count, CSched &cs, cudaStream_t s);
 
 // Runs the program on x (cols x ld); rhs (program right-hand-side rows x ld);
-// shift: ld device values.
+// shift: ld device values.  A program whose every class fits COLOURED_CTA_ROWS
+// row-lane slots runs as one launch of one CTA that steps through the
+// classes with a CTA barrier between them; larger ones launch a grid per
+// class.
 template <typename T>
 void launch_coloured(const CSched &cs, int ld, const T *rhs, T *x, const double *shift,
                      cudaStream_t s);
