@@ -57,8 +57,12 @@ typedef enum { SAMG_SVD = 0, SAMG_SPD_EIG = 1 } samg_kind;
 /* Arithmetic of the V-cycle.  FP64: everything in float64.  FP32: relaxation,
  * residual, transfers and coarse levels in float32 on the defect (error)
  * equation, with the finest-level residual, the correction, the coarsest
- * solve and the Ritz step in float64. */
-typedef enum { SAMG_FP64 = 0, SAMG_FP32 = 1 } samg_precision;
+ * solve and the Ritz step in float64.  BF16_STORE (a variant, not in the
+ * paper): as FP32, but the V-cycle's vector blocks are stored in HBM as
+ * bfloat16 (8-bit mantissa) and converted to float32 on load; matrix
+ * coefficients and all arithmetic stay float32, and the float64 residual and
+ * Ritz step of every outer iteration recover the accuracy. */
+typedef enum { SAMG_FP64 = 0, SAMG_FP32 = 1, SAMG_BF16_STORE = 2 } samg_precision;
 
 typedef struct {
     int32_t m, n;            /* rows, columns */

@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "NT_TOO_SMALL", 5: "N
           6: "TIMEOUT"}
 DOMINANT, MINIMAL = 0, 1
 SVD, SPD_EIG = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
 
 
 class SamgError(RuntimeError):
@@ -171,7 +171,7 @@ def make_params(**kw) -> Params:
     samg_default_params(ctypes.byref(p))
     for k, v in kw.items():
         if k == "prec":
-            v = {"fp64": FP64, "fp32": FP32}.get(v, v)
+            v = {"fp64": FP64, "fp32": FP32, "bf16": BF16}.get(v, v)
         elif k == "coarse_pinv":
             v = {"svd": 0, "geneig": 1}.get(v, v)
         elif k == "row_form":
@@ -304,7 +304,7 @@ class Solver:
         return rp, ci[:z.value], v[:z.value], (r.value, c.value)
 
     def set_precision(self, prec):
-        self._check(samg_set_precision(self._ctx, {"fp64": FP64, "fp32": FP32}.get(prec, prec)))
+        self._check(samg_set_precision(self._ctx, {"fp64": FP64, "fp32": FP32, "bf16": BF16}.get(prec, prec)))
 
     def set_coarse_pinv(self, form):
         """0: the paper's SVD pseudo-inverse on the coarsest level; 1: the

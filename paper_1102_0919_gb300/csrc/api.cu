@@ -57,7 +57,8 @@ void check_common(int n_b, const samg_params *prm) {
     SAMG_CHECK(n_b >= 1 && n_b <= 16, SAMG_E_INVALID, "n_b must be in [1, 16]");
     SAMG_CHECK(prm != nullptr, SAMG_E_INVALID, "params is NULL");
     SAMG_CHECK(prm->mu_b >= 0 && prm->mu_t >= 0, SAMG_E_INVALID, "negative relaxation count");
-    SAMG_CHECK(prm->prec == SAMG_FP64 || prm->prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
+    SAMG_CHECK(prm->prec == SAMG_FP64 || prm->prec == SAMG_FP32 || prm->prec == SAMG_BF16_STORE,
+               SAMG_E_INVALID, "bad precision");
     SAMG_CHECK(prm->coarse_pinv == 0 || prm->coarse_pinv == 1, SAMG_E_INVALID,
                "coarse_pinv must be 0 (SVD pseudo-inverse) or 1 (generalized-eigen variant)");
     SAMG_CHECK(prm->row_form == 0 || prm->row_form == 1, SAMG_E_INVALID,
@@ -73,14 +74,22 @@ void put_level<double>(samg_ctx &c, const double *h, int rows, DBuf<double> &d) 
     if (h) put_block(c, h, rows, d);
     else d.zero(c.stream);
 }
-template <>
-void put_level<float>(samg_ctx &c, const double *h, int rows, DBuf<float> &d) {
+template <typename S>
+void put_level_conv(samg_ctx &c, const double *h, int rows, DBuf<S> &d) {
     if (!h) { d.zero(c.stream); return; }
     DBuf<double> tmp((size_t)std::max(rows, 1) * c.ld);
     tmp.zero(c.stream);
     put_block(c, h, rows, tmp);
-    launch_convert<double, float>((size_t)rows * c.ld, tmp.p, d.p, c.stream);
+    launch_convert<double, S>((size_t)rows * c.ld, tmp.p, d.p, c.stream);
     SAMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+template <>
+void put_level<float>(samg_ctx &c, const double *h, int rows, DBuf<float> &d) {
+    put_level_conv<float>(c, h, rows, d);
+}
+template <>
+void put_level<bf16>(samg_ctx &c, const double *h, int rows, DBuf<bf16> &d) {
+    put_level_conv<bf16>(c, h, rows, d);
 }
 template <typename T>
 void get_level(samg_ctx &c, const DBuf<T> &d, int rows, double *h);
@@ -90,13 +99,21 @@ void get_level<double>(samg_ctx &c, const DBuf<double> &d, int rows, double *h) 
     get_block(c, d, rows, h);
     SAMG_CUDA(cudaStreamSynchronize(c.stream));
 }
-template <>
-void get_level<float>(samg_ctx &c, const DBuf<float> &d, int rows, double *h) {
+template <typename S>
+void get_level_conv(samg_ctx &c, const DBuf<S> &d, int rows, double *h) {
     if (!h) return;
     DBuf<double> tmp((size_t)std::max(rows, 1) * c.ld);
-    launch_convert<float, double>((size_t)rows * c.ld, d.p, tmp.p, c.stream);
+    launch_convert<S, double>((size_t)rows * c.ld, d.p, tmp.p, c.stream);
     get_block(c, tmp, rows, h);
     SAMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+template <>
+void get_level<float>(samg_ctx &c, const DBuf<float> &d, int rows, double *h) {
+    get_level_conv<float>(c, d, rows, h);
+}
+template <>
+void get_level<bf16>(samg_ctx &c, const DBuf<bf16> &d, int rows, double *h) {
+    get_level_conv<bf16>(c, d, rows, h);
 }
 
 void set_sigma(samg_ctx &c, const double *sigma) {
@@ -111,6 +128,18 @@ int urows(const samg_ctx &c, int l) { return c.spd() ? c.L[l].n : c.L[l].m; }
 void check_level(const samg_ctx &c, int l, bool need_coarser) {
     SAMG_CHECK(l >= 0 && l < c.nlev(), SAMG_E_INVALID, "level out of range");
     SAMG_CHECK(!need_coarser || l + 1 < c.nlev(), SAMG_E_INVALID, "level has no coarser level");
+}
+
+// Calls f with a value of the context's vector storage type (float64,
+// float32 or bfloat16), after making sure every level has its work vectors
+// in that type.
+template <typename F>
+void by_prec(samg_ctx &c, F f) {
+    switch (c.prm.prec) {
+        case SAMG_FP32: ensure_work<float>(c); f(float{}); break;
+        case SAMG_BF16_STORE: ensure_work<bf16>(c); f(bf16{}); break;
+        default: ensure_work<double>(c); f(double{}); break;
+    }
 }
 
 template <typename T>
@@ -507,7 +536,8 @@ samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_
 samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {
-        SAMG_CHECK(prec == SAMG_FP64 || prec == SAMG_FP32, SAMG_E_INVALID, "bad precision");
+        SAMG_CHECK(prec == SAMG_FP64 || prec == SAMG_FP32 || prec == SAMG_BF16_STORE,
+                   SAMG_E_INVALID, "bad precision");
         ctx->prm.prec = prec;
     });
 }
@@ -574,8 +604,7 @@ samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done
             SAMG_CHECK(finite, SAMG_E_INVALID, "non-finite residual");
             if (mx <= tol) { converged = true; break; }
             if (done >= max_outer) break;
-            if (c.prm.prec == SAMG_FP32) outer_vcycle<float>(c);
-            else outer_vcycle<double>(c);
+            by_prec(c, [&](auto tag) { outer_vcycle<decltype(tag)>(c); });
             ritz(c, false);
             ++done;
         }
@@ -637,8 +666,9 @@ samg_status samg_relax(samg_ctx *ctx, int level, int count, const double *sigma,
     return guarded(ctx, [&] {
         check_level(*ctx, level, false);
         set_sigma(*ctx, sigma);
-        if (ctx->prm.prec == SAMG_FP32) step_relax<float>(*ctx, level, count, U, V, kappa, tau);
-        else step_relax<double>(*ctx, level, count, U, V, kappa, tau);
+        by_prec(*ctx, [&](auto tag) {
+            step_relax<decltype(tag)>(*ctx, level, count, U, V, kappa, tau);
+        });
         check_kaczmarz(*ctx);
     });
 }
@@ -650,10 +680,9 @@ samg_status samg_residual_restrict(samg_ctx *ctx, int level, const double *sigma
     return guarded(ctx, [&] {
         check_level(*ctx, level, true);
         set_sigma(*ctx, sigma);
-        if (ctx->prm.prec == SAMG_FP32)
-            step_restrict<float>(*ctx, level, U, V, kappa, tau, kappa_c, tau_c);
-        else
-            step_restrict<double>(*ctx, level, U, V, kappa, tau, kappa_c, tau_c);
+        by_prec(*ctx, [&](auto tag) {
+            step_restrict<decltype(tag)>(*ctx, level, U, V, kappa, tau, kappa_c, tau_c);
+        });
     });
 }
 
@@ -662,8 +691,7 @@ samg_status samg_interpolate(samg_ctx *ctx, int level, double *U, double *V, con
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {
         check_level(*ctx, level, true);
-        if (ctx->prm.prec == SAMG_FP32) step_interp<float>(*ctx, level, U, V, Uc, Vc);
-        else step_interp<double>(*ctx, level, U, V, Uc, Vc);
+        by_prec(*ctx, [&](auto tag) { step_interp<decltype(tag)>(*ctx, level, U, V, Uc, Vc); });
     });
 }
 
@@ -672,8 +700,7 @@ samg_status samg_coarsest_solve(samg_ctx *ctx, const double *sigma, const double
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {
         set_sigma(*ctx, sigma);
-        if (ctx->prm.prec == SAMG_FP32) step_coarse<float>(*ctx, kappa, tau, U, V);
-        else step_coarse<double>(*ctx, kappa, tau, U, V);
+        by_prec(*ctx, [&](auto tag) { step_coarse<decltype(tag)>(*ctx, kappa, tau, U, V); });
     });
 }
 
@@ -688,8 +715,7 @@ samg_status samg_vcycle(samg_ctx *ctx, const double *sigma, double *U, double *V
             c.V.zero(c.stream);
             put_block(c, V, c.L[0].n, c.V);
         }
-        if (c.prm.prec == SAMG_FP32) outer_vcycle<float>(c);
-        else outer_vcycle<double>(c);
+        by_prec(c, [&](auto tag) { outer_vcycle<decltype(tag)>(c); });
         get_block(c, c.U, urows(c, 0), U);
         if (!c.spd()) get_block(c, c.V, c.L[0].n, V);
         SAMG_CUDA(cudaStreamSynchronize(c.stream));

@@ -165,32 +165,52 @@ void build_cschedule_stacked(const HCsr &A, const HCsr &B, int count, CSched &cs
 
 namespace {
 
-template <typename T, int LD>
-__device__ __forceinline__ void cld(T (&v)[LD], const T *p) {
-    if constexpr (sizeof(T) == 4) {
+// A row of LD stored values S read into / written from the arithmetic type
+// T (bfloat16 storage: 8-byte pieces of 4 values, converted to float32).
+template <typename T, typename S, int LD>
+__device__ __forceinline__ void cld(T (&v)[LD], const S *p) {
+    if constexpr (sizeof(S) == 4 && sizeof(T) == 4) {
 #pragma unroll
         for (int i = 0; i < LD / 4; ++i) {
             const float4 t = reinterpret_cast<const float4 *>(p)[i];
             v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
         }
-    } else {
+    } else if constexpr (sizeof(S) == 8) {
 #pragma unroll
         for (int i = 0; i < LD / 2; ++i) {
             const double2 t = reinterpret_cast<const double2 *>(p)[i];
             v[2 * i] = t.x; v[2 * i + 1] = t.y;
         }
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i) {
+            const uint2 w = reinterpret_cast<const uint2 *>(p)[i];
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.y));
+            v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = b.x; v[4 * i + 3] = b.y;
+        }
     }
 }
-template <typename T, int LD>
-__device__ __forceinline__ void cst(T *p, const T (&v)[LD]) {
-    if constexpr (sizeof(T) == 4) {
+template <typename T, typename S, int LD>
+__device__ __forceinline__ void cst(S *p, const T (&v)[LD]) {
+    if constexpr (sizeof(S) == 4 && sizeof(T) == 4) {
 #pragma unroll
         for (int i = 0; i < LD / 4; ++i)
             reinterpret_cast<float4 *>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-    } else {
+    } else if constexpr (sizeof(S) == 8) {
 #pragma unroll
         for (int i = 0; i < LD / 2; ++i)
             reinterpret_cast<double2 *>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i) {
+            const __nv_bfloat162 a = __floats2bfloat162_rn(v[4 * i], v[4 * i + 1]);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(v[4 * i + 2], v[4 * i + 3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const unsigned *>(&a);
+            w.y = *reinterpret_cast<const unsigned *>(&b);
+            reinterpret_cast<uint2 *>(p)[i] = w;
+        }
     }
 }
 
@@ -201,12 +221,12 @@ __device__ __forceinline__ void cst(T *p, const T (&v)[LD]) {
 // MODE 1: coefficients a - s_j b for the row sums, the norms and the update.
 // MODE 2: a - s_j b for the row sums, a for the update (b entries belong to
 // the other unknown and are not written), norms given.
-template <typename T, int LD, int MODE>
+template <typename T, typename S, int LD, int MODE>
 __device__ __forceinline__ void class_rows(int r0, int r1, int lg, long long first, long long groups,
                                            const int *__restrict__ rp, const int *__restrict__ ci,
                                            const int *__restrict__ rrow, const T *__restrict__ av,
                                            const T *__restrict__ bv, const T *__restrict__ inv,
-                                           const T *__restrict__ rhs, T *x, const T (&sh)[LD]) {
+                                           const S *__restrict__ rhs, S *x, const T (&sh)[LD]) {
     const int G = 1 << lg;
     const int lgi = (threadIdx.x & 31) & (G - 1);
     for (long long g = first;; g += groups) {
@@ -225,7 +245,7 @@ __device__ __forceinline__ void class_rows(int r0, int r1, int lg, long long fir
                 const int col = ci[e];
                 const T a = av[e], b = MODE != 0 ? bv[e] : T(0);
                 T val[LD];
-                cld<T, LD>(val, x + (size_t)col * LD);
+                cld<T, S, LD>(val, x + (size_t)col * LD);
                 if (e == e0 + lgi) {  // the lane's first entry stays in registers
                     fcol = col; fa = a; fb = b;
 #pragma unroll
@@ -248,11 +268,11 @@ __device__ __forceinline__ void class_rows(int r0, int r1, int lg, long long fir
         }
         if (!act) continue;
         T d[LD];
-        const T *bq = rhs ? rhs + (size_t)rrow[r] * LD : nullptr;
+        const S *bq = rhs ? rhs + (size_t)rrow[r] * LD : nullptr;
         const T iv = MODE == 1 ? T(0) : inv[r];
 #pragma unroll
         for (int q = 0; q < LD; ++q) {
-            const T bi = bq ? bq[q] : T(0);
+            const T bi = bq ? (T)to_acc(bq[q]) : T(0);
             d[q] = MODE == 1 ? (nrm[q] > T(0) ? (bi - acc[q]) / nrm[q] : T(0)) : (bi - acc[q]) * iv;
         }
         for (int e = e0 + lgi; e < e1; e += G) {
@@ -266,7 +286,7 @@ __device__ __forceinline__ void class_rows(int r0, int r1, int lg, long long fir
                 col = ci[e];
                 a = av[e];
                 b = MODE != 0 ? bv[e] : T(0);
-                cld<T, LD>(val, x + (size_t)col * LD);
+                cld<T, S, LD>(val, x + (size_t)col * LD);
             }
             if (MODE == 2 && a == T(0)) continue;  // an entry of the other unknown
 #pragma unroll
@@ -274,22 +294,22 @@ __device__ __forceinline__ void class_rows(int r0, int r1, int lg, long long fir
                 const T coef = MODE == 1 ? a - sh[q] * b : a;
                 val[q] = fma(d[q], coef, val[q]);
             }
-            cst<T, LD>(x + (size_t)col * LD, val);
+            cst<T, S, LD>(x + (size_t)col * LD, val);
         }
     }
 }
 
 // One colour class on a grid.
-template <typename T, int LD, int MODE>
+template <typename T, typename S, int LD, int MODE>
 __global__ void __launch_bounds__(256)
     k_kz_class(int r0, int r1, int lg, const int *__restrict__ rp, const int *__restrict__ ci,
                const int *__restrict__ rrow, const T *__restrict__ av, const T *__restrict__ bv,
-               const T *__restrict__ inv, const T *__restrict__ rhs, T *x,
+               const T *__restrict__ inv, const S *__restrict__ rhs, S *x,
                const double *__restrict__ shift) {
     T sh[LD];
 #pragma unroll
     for (int q = 0; q < LD; ++q) sh[q] = MODE != 0 ? (T)shift[q] : T(0);
-    class_rows<T, LD, MODE>(r0, r1, lg, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg,
+    class_rows<T, S, LD, MODE>(r0, r1, lg, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> lg,
                             (long long)gridDim.x * (blockDim.x >> lg), rp, ci, rrow, av, bv, inv,
                             rhs, x, sh);
 }
@@ -299,19 +319,19 @@ __global__ void __launch_bounds__(256)
 // loads of the next for every thread of the CTA).
 constexpr int COLOURED_CTA = 512;
 constexpr int COLOURED_CTA_ROWS = 32 * COLOURED_CTA;
-template <typename T, int LD, int MODE>
+template <typename T, typename S, int LD, int MODE>
 __global__ void __launch_bounds__(COLOURED_CTA)
     k_kz_classes_cta(int nclass, const int *__restrict__ class_off, const int *__restrict__ class_lg,
                      const int *__restrict__ rp, const int *__restrict__ ci,
                      const int *__restrict__ rrow, const T *__restrict__ av,
                      const T *__restrict__ bv, const T *__restrict__ inv,
-                     const T *__restrict__ rhs, T *x, const double *__restrict__ shift) {
+                     const S *__restrict__ rhs, S *x, const double *__restrict__ shift) {
     T sh[LD];
 #pragma unroll
     for (int q = 0; q < LD; ++q) sh[q] = MODE != 0 ? (T)shift[q] : T(0);
     for (int k = 0; k < nclass; ++k) {
         const int lg = class_lg[k];
-        class_rows<T, LD, MODE>(class_off[k], class_off[k + 1], lg, (long long)threadIdx.x >> lg,
+        class_rows<T, S, LD, MODE>(class_off[k], class_off[k + 1], lg, (long long)threadIdx.x >> lg,
                                 (long long)(blockDim.x >> lg), rp, ci, rrow, av, bv, inv, rhs, x, sh);
         __syncthreads();
     }
@@ -321,8 +341,9 @@ template <typename T> const T *pick(const DBuf<double> &d, const DBuf<float> &f)
 template <> const double *pick<double>(const DBuf<double> &d, const DBuf<float> &) { return d.p; }
 template <> const float *pick<float>(const DBuf<double> &, const DBuf<float> &f) { return f.p; }
 
-template <typename T, int LD, int MODE>
-void run(const CSched &cs, const T *rhs, T *x, const double *shift, cudaStream_t s) {
+template <typename S, int LD, int MODE>
+void run(const CSched &cs, const S *rhs, S *x, const double *shift, cudaStream_t s) {
+    using T = typename Acc<S>::T;
     static int nsm = 0;
     if (!nsm) {
         int dev = 0;
@@ -333,7 +354,7 @@ void run(const CSched &cs, const T *rhs, T *x, const double *shift, cudaStream_t
     const int nclass = (int)cs.class_off.size() - 1;
     if (cs.max_class_threads <= COLOURED_CTA_ROWS) {
         SAMG_COUNT_LAUNCH();
-        k_kz_classes_cta<T, LD, MODE><<<1, COLOURED_CTA, 0, s>>>(
+        k_kz_classes_cta<T, S, LD, MODE><<<1, COLOURED_CTA, 0, s>>>(
             nclass, cs.d_class_off.p, cs.d_class_lg.p, cs.rp.p, cs.ci.p, cs.rrow.p, a, b, inv, rhs,
             x, shift);
         SAMG_CUDA(cudaGetLastError());
@@ -345,7 +366,7 @@ void run(const CSched &cs, const T *rhs, T *x, const double *shift, cudaStream_t
         const long long threads = (long long)(r1 - r0) << lg;
         const int grid = (int)std::min<long long>((threads + 255) / 256, (long long)nsm * 8);
         SAMG_COUNT_LAUNCH();
-        k_kz_class<T, LD, MODE><<<std::max(grid, 1), 256, 0, s>>>(
+        k_kz_class<T, S, LD, MODE><<<std::max(grid, 1), 256, 0, s>>>(
             r0, r1, lg, cs.rp.p, cs.ci.p, cs.rrow.p, a, b, inv, rhs, x, shift);
     }
     SAMG_CUDA(cudaGetLastError());
@@ -354,8 +375,9 @@ void run(const CSched &cs, const T *rhs, T *x, const double *shift, cudaStream_t
 template <typename T>
 void dispatch(const CSched &cs, int ld, const T *rhs, T *x, const double *shift, cudaStream_t s) {
     SAMG_CHECK(cs.mode == 1 || cs.mode == 2, SAMG_E_INVALID, "coloured sweep: bad mode");
-    SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
-               "coloured sweep: vector blocks must be 16-byte aligned");
+    const uintptr_t al = ((size_t)ld * sizeof(T)) % 16 == 0 ? 16 : 8;
+    SAMG_CHECK(((uintptr_t)x % al) == 0 && ((uintptr_t)rhs % al) == 0, SAMG_E_INVALID,
+               "coloured sweep: vector blocks must be aligned to their row pieces");
 #define CZ_CASE(L)                                                       \
     case L:                                                              \
         if (cs.mode == 1) run<T, L, 1>(cs, rhs, x, shift, s);            \
@@ -383,6 +405,11 @@ template <>
 void launch_coloured<double>(const CSched &cs, int ld, const double *rhs, double *x,
                              const double *shift, cudaStream_t s) {
     if (cs.rows) dispatch<double>(cs, ld, rhs, x, shift, s);
+}
+template <>
+void launch_coloured<bf16>(const CSched &cs, int ld, const bf16 *rhs, bf16 *x, const double *shift,
+                           cudaStream_t s) {
+    if (cs.rows) dispatch<bf16>(cs, ld, rhs, x, shift, s);
 }
 
 }  // namespace samg

@@ -1,6 +1,7 @@
 // common.cuh -- shared device/host helpers of the GB300 SAMG library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,6 +34,19 @@ struct Error : public std::runtime_error {
     do {                                                       \
         if (!(cond)) throw ::samg::Error((status), (msg));     \
     } while (0)
+
+// Vector storage types of the V-cycle and the arithmetic each computes in:
+// float64 and float32 compute in themselves; bfloat16 storage (16-bit
+// vectors in HBM) computes in float32, with float32 matrix coefficients.
+using bf16 = __nv_bfloat16;
+template <typename S> struct Acc { using T = S; };
+template <> struct Acc<bf16> { using T = float; };
+
+__host__ __device__ inline float to_acc(bf16 v) { return __bfloat162float(v); }
+__host__ __device__ inline float to_acc(float v) { return v; }
+__host__ __device__ inline double to_acc(double v) { return v; }
+template <typename S> __host__ __device__ inline S from_acc(typename Acc<S>::T v) { return (S)v; }
+template <> __host__ __device__ inline bf16 from_acc<bf16>(float v) { return __float2bfloat16_rn(v); }
 
 // Device buffer owned by value (move-only).
 template <typename T>

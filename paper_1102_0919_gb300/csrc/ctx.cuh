@@ -34,6 +34,7 @@ struct Level {
     DBuf<float> dBf, dCf;
     Work<float> wf;
     Work<double> wd;
+    Work<bf16> wb;              // bfloat16 storage (allocated on first use)
 };
 
 // Launch timing with CUDA events on the context's stream (samg_profile).
@@ -150,6 +151,8 @@ void get_block(samg_ctx &c, const DBuf<double> &d, int rows, double *h);
 
 // V-cycle pieces in precision T on level l (vectors in L[l].w*)
 template <typename T> Work<T> &work(Level &L);
+// every level's work vectors in storage type T (allocated when missing)
+template <typename T> void ensure_work(samg_ctx &c);
 template <typename T> void relax(samg_ctx &c, int l);
 template <typename T> void relax_phase(samg_ctx &c, int l, int count);
 template <typename T> void residual_restrict(samg_ctx &c, int l);

@@ -9,17 +9,24 @@ namespace samg {
 
 template <> Work<float> &work<float>(Level &L) { return L.wf; }
 template <> Work<double> &work<double>(Level &L) { return L.wd; }
+template <> Work<bf16> &work<bf16>(Level &L) { return L.wb; }
 
-template <typename T> static const T *dgB(const Level &L);
+// diagonals and matrix views in the arithmetic type of storage type T
+template <typename T> static const typename Acc<T>::T *dgB(const Level &L);
 template <> const float *dgB<float>(const Level &L) { return L.dBf.p; }
+template <> const float *dgB<bf16>(const Level &L) { return L.dBf.p; }
 template <> const double *dgB<double>(const Level &L) { return L.dBd.p; }
-template <typename T> static const T *dgC(const Level &L);
+template <typename T> static const typename Acc<T>::T *dgC(const Level &L);
 template <> const float *dgC<float>(const Level &L) { return L.dCf.p; }
+template <> const float *dgC<bf16>(const Level &L) { return L.dCf.p; }
 template <> const double *dgC<double>(const Level &L) { return L.dCd.p; }
 
-template <typename T> static CsrView<T> opt_view(const DCsr &a) {
-    if (a.empty()) return CsrView<T>{0, 0, nullptr, nullptr, nullptr};
-    return view<T>(a);
+template <typename T> static CsrView<typename Acc<T>::T> mview(const DCsr &a) {
+    return view<typename Acc<T>::T>(a);
+}
+template <typename T> static CsrView<typename Acc<T>::T> opt_view(const DCsr &a) {
+    if (a.empty()) return CsrView<typename Acc<T>::T>{0, 0, nullptr, nullptr, nullptr};
+    return mview<T>(a);
 }
 
 // Algorithmic bytes of one pass (what the method must move, no credit for
@@ -82,15 +89,15 @@ void relax(samg_ctx &c, int l) {
     Prof pr(c.prof, s, 2,
             2.0 * (spmv_bytes(L.A, c.nb, sizeof(T)) + spmv_bytes(L.B, c.nb, sizeof(T))));
     if (c.spd()) {
-        launch_jacobi<T>(L.n, ld, view<T>(L.A), w.u.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p,
+        launch_jacobi<T>(L.n, ld, mview<T>(L.A), w.u.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p,
                          sig, om, w.tu.p, s);
         std::swap(w.u, w.tu);
         return;
     }
-    launch_jacobi<T>(L.m, ld, view<T>(L.A), w.v.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p, sig,
+    launch_jacobi<T>(L.m, ld, mview<T>(L.A), w.v.p, opt_view<T>(L.B), dgB<T>(L), w.u.p, w.k.p, sig,
                      om, w.tu.p, s);
     std::swap(w.u, w.tu);
-    launch_jacobi<T>(L.n, ld, view<T>(L.At), w.u.p, opt_view<T>(L.C), dgC<T>(L), w.v.p, w.t.p,
+    launch_jacobi<T>(L.n, ld, mview<T>(L.At), w.u.p, opt_view<T>(L.C), dgC<T>(L), w.v.p, w.t.p,
                      sig, om, w.tv.p, s);
     std::swap(w.v, w.tv);
 }
@@ -203,6 +210,7 @@ void relax_phase(samg_ctx &c, int l, int count) {
 }
 template void relax_phase<float>(samg_ctx &, int, int);
 template void relax_phase<double>(samg_ctx &, int, int);
+template void relax_phase<bf16>(samg_ctx &, int, int);
 
 // r = kappa - (A v - s B u), s = tau - (A^t u - s C v); kappa_c = P^t r,
 // tau_c = Q^t s into level l+1 (Eqs. add, addCoarse).
@@ -222,23 +230,23 @@ void residual_restrict(samg_ctx &c, int l) {
                 (c.spd() ? 0.0 : spmv_bytes(L.At, nb, sz) + spmv_bytes(L.C, nb, sz) +
                                      spmv_bytes(L.Qt, nb, sz)));
     if (c.spd()) {
-        Term<T> ta{view<T>(L.A), w.u.p, -1.0, false};
+        Term<T> ta{mview<T>(L.A), w.u.p, -1.0, false};
         Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
         launch_combine<T, T>(L.n, ld, w.k.p, 1.0, ta, tb, sig, w.r.p, s);
         launch_combine<T, T>(Lc.n, ld, (const T *)nullptr, 0.0,
-                             Term<T>{view<T>(L.Pt), w.r.p, 1.0, false}, Term<T>{}, sig, wc.k.p, s);
+                             Term<T>{mview<T>(L.Pt), w.r.p, 1.0, false}, Term<T>{}, sig, wc.k.p, s);
         return;
     }
-    Term<T> ta{view<T>(L.A), w.v.p, -1.0, false};
+    Term<T> ta{mview<T>(L.A), w.v.p, -1.0, false};
     Term<T> tb{opt_view<T>(L.B), w.u.p, 1.0, true};
     launch_combine<T, T>(L.m, ld, w.k.p, 1.0, ta, tb, sig, w.r.p, s);
-    Term<T> tat{view<T>(L.At), w.u.p, -1.0, false};
+    Term<T> tat{mview<T>(L.At), w.u.p, -1.0, false};
     Term<T> tc{opt_view<T>(L.C), w.v.p, 1.0, true};
     launch_combine<T, T>(L.n, ld, w.t.p, 1.0, tat, tc, sig, w.s.p, s);
     launch_combine<T, T>(Lc.m, ld, (const T *)nullptr, 0.0,
-                         Term<T>{view<T>(L.Pt), w.r.p, 1.0, false}, Term<T>{}, sig, wc.k.p, s);
+                         Term<T>{mview<T>(L.Pt), w.r.p, 1.0, false}, Term<T>{}, sig, wc.k.p, s);
     launch_combine<T, T>(Lc.n, ld, (const T *)nullptr, 0.0,
-                         Term<T>{view<T>(L.Qt), w.s.p, 1.0, false}, Term<T>{}, sig, wc.t.p, s);
+                         Term<T>{mview<T>(L.Qt), w.s.p, 1.0, false}, Term<T>{}, sig, wc.t.p, s);
 }
 
 // u += P u_c, v += Q v_c (Eq. corrAdd)
@@ -254,13 +262,13 @@ void interpolate(samg_ctx &c, int l) {
             spmv_bytes(L.P, c.nb, sizeof(T)) + (double)L.P.m * c.nb * sizeof(T) +
                 (c.spd() ? 0.0 : spmv_bytes(L.Q, c.nb, sizeof(T)) + (double)L.Q.m * c.nb * sizeof(T)));
     if (c.spd()) {
-        launch_combine<T, T>(L.n, ld, w.u.p, 1.0, Term<T>{view<T>(L.P), wc.u.p, 1.0, false},
+        launch_combine<T, T>(L.n, ld, w.u.p, 1.0, Term<T>{mview<T>(L.P), wc.u.p, 1.0, false},
                              Term<T>{}, sig, w.u.p, s);
         return;
     }
-    launch_combine<T, T>(L.m, ld, w.u.p, 1.0, Term<T>{view<T>(L.P), wc.u.p, 1.0, false},
+    launch_combine<T, T>(L.m, ld, w.u.p, 1.0, Term<T>{mview<T>(L.P), wc.u.p, 1.0, false},
                          Term<T>{}, sig, w.u.p, s);
-    launch_combine<T, T>(L.n, ld, w.v.p, 1.0, Term<T>{view<T>(L.Q), wc.v.p, 1.0, false},
+    launch_combine<T, T>(L.n, ld, w.v.p, 1.0, Term<T>{mview<T>(L.Q), wc.v.p, 1.0, false},
                          Term<T>{}, sig, w.v.p, s);
 }
 
@@ -338,6 +346,22 @@ void outer_vcycle(samg_ctx &c) {
     launch_add_to<T>((size_t)L0.n * ld, c.V.p, w.v.p, s);
 }
 
+template <typename T>
+static void alloc_work(Work<T> &w, int m, int n, int ld, bool spd, cudaStream_t s);
+
+template <typename T>
+void ensure_work(samg_ctx &c) {
+    for (int l = 0; l < c.nlev(); ++l) {
+        Level &L = c.L[l];
+        Work<T> &w = work<T>(L);
+        const size_t want = (size_t)(c.spd() ? L.n : L.m) * c.ld;
+        if (w.u.n != want) alloc_work(w, L.m, L.n, c.ld, c.spd(), c.stream);
+    }
+}
+template void ensure_work<float>(samg_ctx &);
+template void ensure_work<double>(samg_ctx &);
+template void ensure_work<bf16>(samg_ctx &);
+
 template void relax<float>(samg_ctx &, int);
 template void relax<double>(samg_ctx &, int);
 template void residual_restrict<float>(samg_ctx &, int);
@@ -350,6 +374,12 @@ template void vcycle<float>(samg_ctx &, int);
 template void vcycle<double>(samg_ctx &, int);
 template void outer_vcycle<float>(samg_ctx &);
 template void outer_vcycle<double>(samg_ctx &);
+template void relax<bf16>(samg_ctx &, int);
+template void residual_restrict<bf16>(samg_ctx &, int);
+template void interpolate<bf16>(samg_ctx &, int);
+template void coarse_solve<bf16>(samg_ctx &);
+template void vcycle<bf16>(samg_ctx &, int);
+template void outer_vcycle<bf16>(samg_ctx &);
 
 // ------------------------------------------------------------------ Ritz
 // Sec. 4.3 on the finest level (B = I, C = I): Gram matrices, M = U^t A V

@@ -702,7 +702,8 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
     for (int i = t; i < M; i += nt) {
         for (int b = 0; b < kb; ++b)
             Q[b * M + i] = b < nwarm ? qwarm[((size_t)j * 2 + b) * M + i] : W[(size_t)i * M + s_sel[b - nwarm]];
-        r[i] = (i < m1) ? (double)k1[(size_t)i * ld + j] : (double)k2[(size_t)(i - m1) * ld + j];
+        r[i] = (i < m1) ? (double)to_acc(k1[(size_t)i * ld + j])
+                        : (double)to_acc(k2[(size_t)(i - m1) * ld + j]);
     }
     __syncthreads();
     orthonormalize(Q, kb);
@@ -774,8 +775,8 @@ __global__ void k_coarse_apply(int M, int m1, int ld, const double *__restrict__
     double wz = dot(w, Z);
     for (int i = t; i < M; i += nt) {
         double z = Z[i] - wz * w[i];
-        if (i < m1) o1[(size_t)i * ld + j] = (T)z;
-        else o2[(size_t)(i - m1) * ld + j] = (T)z;
+        if (i < m1) o1[(size_t)i * ld + j] = from_acc<T>((typename Acc<T>::T)z);
+        else o2[(size_t)(i - m1) * ld + j] = from_acc<T>((typename Acc<T>::T)z);
     }
 }
 
@@ -847,7 +848,7 @@ __global__ void __launch_bounds__(CG_WARPS * 32)
         const T *r = i < m1 ? k1 + (size_t)i * ld : k2 + (size_t)(i - m1) * ld;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-            if (j < nb) acc[j] = fma(w, (double)r[j], acc[j]);
+            if (j < nb) acc[j] = fma(w, (double)to_acc(r[j]), acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < 16; ++j)
@@ -889,8 +890,8 @@ __global__ void __launch_bounds__(CG_WARPS * 32)
 #pragma unroll
         for (int j = 0; j < 16; ++j)
             if (j == lane) v = acc[j];
-        if (i < m1) o1[(size_t)i * ld + lane] = (T)v;
-        else o2[(size_t)(i - m1) * ld + lane] = (T)v;
+        if (i < m1) o1[(size_t)i * ld + lane] = from_acc<T>((typename Acc<T>::T)v);
+        else o2[(size_t)(i - m1) * ld + lane] = from_acc<T>((typename Acc<T>::T)v);
     }
 }
 
@@ -916,6 +917,10 @@ template void launch_coarse_apply_geneig<double>(int, int, int, int, const doubl
                                                  const double *, const double *, const double *,
                                                  const double *, const double *, double *,
                                                  double *, double *, cudaStream_t);
+template void launch_coarse_apply_geneig<bf16>(int, int, int, int, const double *, const double *,
+                                               const double *, const double *, const bf16 *,
+                                               const bf16 *, bf16 *, bf16 *, double *,
+                                               cudaStream_t);
 template void launch_coarse_apply<float>(int, int, int, int, const double *, const double *,
                                          const double *, const double *, const float *,
                                          const float *, float *, float *, double *, int,
@@ -924,5 +929,8 @@ template void launch_coarse_apply<double>(int, int, int, int, const double *, co
                                           const double *, const double *, const double *,
                                           const double *, double *, double *, double *, int,
                                           cudaStream_t);
+template void launch_coarse_apply<bf16>(int, int, int, int, const double *, const double *,
+                                        const double *, const double *, const bf16 *, const bf16 *,
+                                        bf16 *, bf16 *, double *, int, cudaStream_t);
 
 }  // namespace samg

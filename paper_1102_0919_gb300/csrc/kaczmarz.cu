@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "kaczmarz.cuh"
 
@@ -294,6 +295,50 @@ __device__ __forceinline__ void vst_cg(T *p, const T (&v)[LD]) {
     }
 }
 
+// Rows of LD stored values S read into / written from LD values of the
+// arithmetic type T (bfloat16 storage: 8-byte pieces of 4 values, converted
+// to and from float32).  cg: global memory through L2 only.
+template <typename T, typename S, int LD, bool CG>
+__device__ __forceinline__ void sld(T (&v)[LD], const S *p) {
+    if constexpr (std::is_same<S, T>::value) {
+        if constexpr (CG) vld_cg<T, LD>(v, p);
+        else vld<T, LD>(v, p);
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i) {
+            const uint2 w = CG ? __ldcg(reinterpret_cast<const uint2 *>(p) + i)
+                               : reinterpret_cast<const uint2 *>(p)[i];
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.y));
+            v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = b.x; v[4 * i + 3] = b.y;
+        }
+    }
+}
+template <typename T, typename S, int LD>
+__device__ __forceinline__ void sst_cg(S *p, const T (&v)[LD]) {
+    if constexpr (std::is_same<S, T>::value) {
+        vst_cg<T, LD>(p, v);
+    } else {
+#pragma unroll
+        for (int i = 0; i < LD / 4; ++i) {
+            const __nv_bfloat162 a = __floats2bfloat162_rn(v[4 * i], v[4 * i + 1]);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(v[4 * i + 2], v[4 * i + 3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const unsigned *>(&a);
+            w.y = *reinterpret_cast<const unsigned *>(&b);
+            __stcg(reinterpret_cast<uint2 *>(p) + i, w);
+        }
+    }
+}
+template <typename S>
+__device__ __forceinline__ typename Acc<S>::T sval(const S *p) { return to_acc(*p); }
+
+// asynchronous 8-byte global -> shared copy (bfloat16 rows of 4 or 12 values)
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 __host__ __device__ constexpr bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 __device__ __forceinline__ int brev_low(int v, int nbits) {  // reverse the low nbits
@@ -367,9 +412,9 @@ struct KView {
 // One staging buffer: the chunk image (capacity of a full chunk), then the
 // gathered right-hand-side rows and staged first values (when a row of LD
 // values is at most 64 bytes; wider rows are read from global memory).
-template <typename T, int LD, bool SHIFT>
+template <typename T, typename S, int LD, bool SHIFT>
 struct Stage {
-    static constexpr int VB = LD * (int)sizeof(T);  // bytes of one vector row
+    static constexpr int VB = LD * (int)sizeof(S);  // bytes of one stored vector row
     static constexpr bool VALS = VB <= 64;
     static constexpr unsigned IMG = img_layout(KZ_CHL, KZ_CHR, KZ_CHE, KZ_CHX, KZ_CHQ, (int)sizeof(T), SHIFT).bytes;
     static constexpr unsigned o_rhs = IMG;
@@ -389,13 +434,14 @@ struct Stage {
 // MODE 0: rows of A (norms given).  MODE 1: rows of A - s_j B (entries carry
 // b; norms formed per column).  MODE 2: fused relaxations (entries carry b;
 // the accumulation uses a - s_j b, the update only a; norms given).
-template <typename T, int LD, int MODE>
+template <typename S, int LD, int MODE>
 __global__ void __launch_bounds__(KZ_THREADS, 1)
-    k_kaczmarz(KView kv, const T *__restrict__ rhs, T *x, const double *__restrict__ shift,
+    k_kaczmarz(KView kv, const S *__restrict__ rhs, S *x, const double *__restrict__ shift,
                int window_slots) {
+    using T = typename Acc<S>::T;      // arithmetic (and window) type
     constexpr bool SHIFT = MODE != 0;  // entries carry b
     constexpr bool NRM = MODE == 1;    // row norms formed per column
-    using SG = Stage<T, LD, SHIFT>;
+    using SG = Stage<T, S, LD, SHIFT>;
     extern __shared__ __align__(128) unsigned char smraw[];
     T *win = reinterpret_cast<T *>(smraw);
     unsigned char *bufs = smraw + ((size_t)window_slots * LD * sizeof(T) + 127) / 128 * 128;
@@ -508,17 +554,23 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                         const ImgLayout IL = img_layout(ck.nl, ck.nr, ck.ne, ck.nx, ck.nq, (int)sizeof(T), SHIFT);
                         const int2 *ri = reinterpret_cast<const int2 *>(B + IL.ri);
                         const int *xc = reinterpret_cast<const int *>(B + IL.xc);
-                        constexpr int P = SG::VB / 16;
+                        // 16-byte pieces, or 8-byte ones for rows of 8 or 24 bytes
+                        constexpr int PB = SG::VB % 16 == 0 ? 16 : 8;
+                        constexpr int P = SG::VB / PB;
+                        auto piece = [&](unsigned char *d, const unsigned char *g) {
+                            if constexpr (PB == 16) cp_async16(d, g);
+                            else cp_async8(d, g);
+                        };
                         if (rhs)
                             for (int q = lane; q < ck.nr * P; q += 32) {
                                 const int r = q / P, p = q % P;
-                                cp_async16(B + SG::o_rhs + (size_t)SG::VB * r + 16 * p,
-                                           reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + 16 * p);
+                                piece(B + SG::o_rhs + (size_t)SG::VB * r + PB * p,
+                                      reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + PB * p);
                             }
                         for (int q = lane; q < ck.nx * P; q += 32) {
                             const int r = q / P, p = q % P;
-                            cp_async16(B + SG::o_xs + (size_t)SG::VB * r + 16 * p,
-                                       reinterpret_cast<const unsigned char *>(x + (size_t)xc[r] * LD) + 16 * p);
+                            piece(B + SG::o_xs + (size_t)SG::VB * r + PB * p,
+                                  reinterpret_cast<const unsigned char *>(x + (size_t)xc[r] * LD) + PB * p);
                         }
                         cp_async_arrive(&mb_vals[bi]);
                         ++vn;
@@ -578,8 +630,8 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                 const int2 *se = reinterpret_cast<const int2 *>(B + IL.ent);
                 const T *sa = reinterpret_cast<const T *>(B + IL.a);
                 const T *sb = reinterpret_cast<const T *>(B + IL.b);
-                const T *srhs = reinterpret_cast<const T *>(B + SG::o_rhs);
-                const T *sxs = reinterpret_cast<const T *>(B + SG::o_xs);
+                const S *srhs = reinterpret_cast<const S *>(B + SG::o_rhs);
+                const S *sxs = reinterpret_cast<const S *>(B + SG::o_xs);
                 for (int L = 0; L < ck.nl; ++L) {
                     const int lb = ck.L0 + L - Lband;  // band-local level
                     const int4 lr = lv[L];
@@ -667,9 +719,11 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                     // first touches not staged come from global memory, the
                                     // rest from the staged values or the window
                                     if ((fl & 1) && !(SG::VALS && (fl & 4)))
-                                        vld_cg<T, LD>(val, x + (size_t)en.x * LD);
+                                        sld<T, S, LD, true>(val, x + (size_t)en.x * LD);
+                                    else if (fl & 1)
+                                        sld<T, S, LD, false>(val, sxs + (fl >> 15) * LD);
                                     else
-                                        vld<T, LD>(val, (fl & 1) ? sxs + (fl >> 15) * LD : win + ((fl >> 3) & 0xfff) * LD);
+                                        vld<T, LD>(val, win + ((fl >> 3) & 0xfff) * LD);
                                 };
                                 auto accumulate = [&](T a, T bq, const T (&val)[LD]) {
 #pragma unroll
@@ -718,7 +772,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                     const int c = brev_low(lane & (LD - 1), ilog2(LD));
                                     T dc = T(0);
                                     if (act) {
-                                        const T bi = rhs ? (SG::VALS ? srhs[k * LD + c] : rhs[(size_t)rk.x * LD + c]) : T(0);
+                                        const T bi = rhs ? (SG::VALS ? sval(srhs + k * LD + c) : sval(rhs + (size_t)rk.x * LD + c)) : T(0);
                                         dc = NRM ? (sn_c > T(0) ? (bi - sa_c) / sn_c : T(0)) : (bi - sa_c) * sinv[k];
                                     }
                                     const int gb = lane & ~(G - 1);
@@ -733,7 +787,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                     if (act) {
 #pragma unroll
                                         for (int q = 0; q < LD; ++q) {
-                                            const T bi = rhs ? (SG::VALS ? srhs[k * LD + q] : rhs[(size_t)rk.x * LD + q]) : T(0);
+                                            const T bi = rhs ? (SG::VALS ? sval(srhs + k * LD + q) : sval(rhs + (size_t)rk.x * LD + q)) : T(0);
                                             const T nq = NRM ? nrm[q] : T(1);
                                             d[q] = NRM ? (nq > T(0) ? (bi - acc[q]) / nq : T(0)) : (bi - acc[q]) * sinv[k];
                                         }
@@ -751,7 +805,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                                         val[q] = fma(d[q], coef, val[q]);
                                     }
                                     vst<T, LD>(win + ((en.y >> 3) & 0xfff) * LD, val);
-                                    if (en.y & 2) vst_cg<T, LD>(x + (size_t)en.x * LD, val);
+                                    if (en.y & 2) sst_cg<T, S, LD>(x + (size_t)en.x * LD, val);
                                 };
                                 if (own) {
                                     update(fen, fa, fb, fv);
@@ -792,14 +846,18 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
     }
 }
 
-template <typename T, int LD, int MODE>
-void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaStream_t s) {
-    using SG = Stage<T, LD, MODE != 0>;
-    auto kern = k_kaczmarz<T, LD, MODE>;
+template <typename S, int LD, int MODE>
+void launch_one(const KSched &ks, const S *rhs, S *x, const double *shift, cudaStream_t s) {
+    using T = typename Acc<S>::T;
+    using SG = Stage<T, S, LD, MODE != 0>;
+    auto kern = k_kaczmarz<S, LD, MODE>;
     const int slots = ks.max_slots + 1;  // slot 0: scratch
     const size_t smem = ((size_t)slots * LD * sizeof(T) + 127) / 128 * 128 + (size_t)KZ_NBUF * SG::stride;
-    SAMG_CHECK(((uintptr_t)x & 15) == 0 && ((uintptr_t)rhs & 15) == 0, SAMG_E_INVALID,
-               "kaczmarz: vector blocks must be 16-byte aligned");
+    // rows of 8 or 24 bytes (bfloat16, LD 4 or 12) move in 8-byte pieces
+    constexpr uintptr_t AL = (LD * sizeof(S)) % 16 == 0 ? 16 : 8;
+    SAMG_CHECK(((uintptr_t)x % AL) == 0 && ((uintptr_t)rhs % AL) == 0, SAMG_E_INVALID,
+               "kaczmarz: vector blocks must be aligned to their row pieces");
+    static_assert(LD % 4 == 0, "vector rows of a multiple of 4 values");
     // a window of more slots than a CTA's shared memory holds (a resident
     // schedule built for a narrower block or precision) is refused here
     SAMG_CHECK(smem <= 227u * 1024u, SAMG_E_INVALID,
@@ -827,8 +885,8 @@ void launch_one(const KSched &ks, const T *rhs, T *x, const double *shift, cudaS
             SAMG_CUDA(cudaDeviceGetAttribute(&nsm_of[dev], cudaDevAttrMultiProcessorCount, dev));
         nsm = nsm_of[dev];
     }
-    const int key = (int)sizeof(T) * 64 + LD * 4 + MODE;
-    int &grid = ks.grid_cache[key & 255];
+    const int key = (sizeof(S) == 2 ? 0 : sizeof(S) == 4 ? 1 : 2) * 64 + LD * 3 + MODE;
+    int &grid = ks.grid_cache[key];
     if (!grid) {
         int bps = 0;
         SAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, KZ_THREADS, smem));
@@ -1375,6 +1433,11 @@ template <>
 void launch_kaczmarz<float>(const KSched &ks, int ld, const float *rhs, float *x,
                             const double *shift, cudaStream_t s) {
     dispatch<float>(ks, ld, rhs, x, shift, s);
+}
+template <>
+void launch_kaczmarz<bf16>(const KSched &ks, int ld, const bf16 *rhs, bf16 *x,
+                           const double *shift, cudaStream_t s) {
+    dispatch<bf16>(ks, ld, rhs, x, shift, s);
 }
 
 void kaczmarz_mute_band(KSched &ks, int band, cudaStream_t s) {

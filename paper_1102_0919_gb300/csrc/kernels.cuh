@@ -11,9 +11,11 @@ namespace samg {
 // where s_t[j] = sigma[j] when sig_t is set (else 1), M_t == identity when
 // its row pointer is null, and o is the column-wise product.  TI is the
 // arithmetic and input type, TO the output type.
+// TI is the storage type of the vectors; the matrix coefficients and the
+// arithmetic are Acc<TI>::T (float32 for bfloat16 storage).
 template <typename TI>
 struct Term {
-    CsrView<TI> M{0, 0, nullptr, nullptr, nullptr};
+    CsrView<typename Acc<TI>::T> M{0, 0, nullptr, nullptr, nullptr};
     const TI *x = nullptr;
     double c = 0.0;
     bool sig = false;
@@ -27,9 +29,9 @@ void launch_combine(int rows, int ld, const TI *in0, double a0, const Term<TI> &
 //   out_i = x_i - (omega / d_i) ((B x)_i - ((A y)_i - kappa_i) / sigma)
 // B == identity (d = 1) when its row pointer is null; kappa may be null.
 template <typename T>
-void launch_jacobi(int rows, int ld, CsrView<T> A, const T *y, CsrView<T> B, const T *dB,
-                   const T *x, const T *kappa, const double *sigma, double omega, T *out,
-                   cudaStream_t s);
+void launch_jacobi(int rows, int ld, CsrView<typename Acc<T>::T> A, const T *y,
+                   CsrView<typename Acc<T>::T> B, const typename Acc<T>::T *dB, const T *x,
+                   const T *kappa, const double *sigma, double omega, T *out, cudaStream_t s);
 
 template <typename TA, typename TB>
 void launch_convert(size_t count, const TA *a, TB *b, cudaStream_t s);

@@ -28,10 +28,32 @@ __device__ __forceinline__ void st4(double *p, const V4<double> &v) {
     reinterpret_cast<double2 *>(p)[0] = make_double2(v.a[0], v.a[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(v.a[2], v.a[3]);
 }
+// bfloat16 storage: 4 values in 8 bytes, arithmetic in float32
+__device__ __forceinline__ V4<float> ld4(const bf16 *p) {
+    const uint2 w = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w.y));
+    return V4<float>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(bf16 *p, const V4<float> &v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.a[0], v.a[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.a[2], v.a[3]);
+    uint2 w;
+    w.x = *reinterpret_cast<const unsigned *>(&a);
+    w.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = w;
+}
+template <typename TO, typename C> __device__ __forceinline__ V4<typename Acc<TO>::T> cvt4(const V4<C> &v) {
+    V4<typename Acc<TO>::T> o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o.a[k] = (typename Acc<TO>::T)v.a[k];
+    return o;
+}
 
-// (M x)_i for 4 columns; identity when M.rp is null
-template <typename T>
-__device__ __forceinline__ V4<T> row_apply(const CsrView<T> &M, const T *x, int i, int ld,
+// (M x)_i for 4 columns; identity when M.rp is null.  S: storage type of x,
+// T: arithmetic and coefficient type.
+template <typename T, typename S>
+__device__ __forceinline__ V4<T> row_apply(const CsrView<T> &M, const S *x, int i, int ld,
                                            int c0) {
     V4<T> r{{T(0), T(0), T(0), T(0)}};
     if (M.rp == nullptr) return ld4(x + (size_t)i * ld + c0);
@@ -47,58 +69,58 @@ __device__ __forceinline__ V4<T> row_apply(const CsrView<T> &M, const T *x, int 
 
 template <typename TI>
 struct TermD {
-    CsrView<TI> M;
+    CsrView<typename Acc<TI>::T> M;
     const TI *x;
-    TI c;
+    typename Acc<TI>::T c;
     int sig;
 };
 
 template <typename TI, typename TO>
-__global__ void k_combine(int rows, int ld, const TI *__restrict__ in0, TI a0, TermD<TI> t1,
-                          TermD<TI> t2, const double *__restrict__ sigma, TO *__restrict__ out) {
+__global__ void k_combine(int rows, int ld, const TI *__restrict__ in0, typename Acc<TI>::T a0,
+                          TermD<TI> t1, TermD<TI> t2, const double *__restrict__ sigma,
+                          TO *__restrict__ out) {
+    using C = typename Acc<TI>::T;
     const int q4 = ld >> 2;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (int64_t)rows * q4) return;
     int i = (int)(tid / q4);
     int c0 = (int)(tid % q4) * 4;
-    V4<TI> acc{{TI(0), TI(0), TI(0), TI(0)}};
+    V4<C> acc{{C(0), C(0), C(0), C(0)}};
     if (in0) {
-        V4<TI> a = ld4(in0 + (size_t)i * ld + c0);
+        V4<C> a = ld4(in0 + (size_t)i * ld + c0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc.a[k] = a0 * a.a[k];
     }
     if (t1.x) {
-        V4<TI> r = row_apply(t1.M, t1.x, i, ld, c0);
+        V4<C> r = row_apply(t1.M, t1.x, i, ld, c0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            TI sc = t1.sig ? t1.c * (TI)sigma[c0 + k] : t1.c;
+            C sc = t1.sig ? t1.c * (C)sigma[c0 + k] : t1.c;
             acc.a[k] = fma(sc, r.a[k], acc.a[k]);
         }
     }
     if (t2.x) {
-        V4<TI> r = row_apply(t2.M, t2.x, i, ld, c0);
+        V4<C> r = row_apply(t2.M, t2.x, i, ld, c0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            TI sc = t2.sig ? t2.c * (TI)sigma[c0 + k] : t2.c;
+            C sc = t2.sig ? t2.c * (C)sigma[c0 + k] : t2.c;
             acc.a[k] = fma(sc, r.a[k], acc.a[k]);
         }
     }
-    V4<TO> o;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o.a[k] = (TO)acc.a[k];
-    st4(out + (size_t)i * ld + c0, o);
+    st4(out + (size_t)i * ld + c0, cvt4<TO>(acc));
 }
 
 template <typename TI, typename TO>
 void launch_combine(int rows, int ld, const TI *in0, double a0, const Term<TI> &t1,
                     const Term<TI> &t2, const double *sigma, TO *out, cudaStream_t s) {
     if (rows == 0) return;
-    TermD<TI> d1{t1.M, t1.x, (TI)t1.c, t1.sig ? 1 : 0};
-    TermD<TI> d2{t2.M, t2.x, (TI)t2.c, t2.sig ? 1 : 0};
+    using C = typename Acc<TI>::T;
+    TermD<TI> d1{t1.M, t1.x, (C)t1.c, t1.sig ? 1 : 0};
+    TermD<TI> d2{t2.M, t2.x, (C)t2.c, t2.sig ? 1 : 0};
     int64_t n = (int64_t)rows * (ld / 4);
     int bs = 256;
     SAMG_COUNT_LAUNCH();
-    k_combine<TI, TO><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rows, ld, in0, (TI)a0, d1, d2,
+    k_combine<TI, TO><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rows, ld, in0, (C)a0, d1, d2,
                                                                     sigma, out);
     SAMG_CUDA(cudaGetLastError());
 }
@@ -112,13 +134,20 @@ template void launch_combine<double, double>(int, int, const double *, double,
 template void launch_combine<double, float>(int, int, const double *, double,
                                             const Term<double> &, const Term<double> &,
                                             const double *, float *, cudaStream_t);
+template void launch_combine<bf16, bf16>(int, int, const bf16 *, double, const Term<bf16> &,
+                                         const Term<bf16> &, const double *, bf16 *, cudaStream_t);
+template void launch_combine<double, bf16>(int, int, const double *, double,
+                                           const Term<double> &, const Term<double> &,
+                                           const double *, bf16 *, cudaStream_t);
 
 // ------------------------------------------------------------------ Jacobi
-template <typename T>
-__global__ void k_jacobi(int rows, int ld, CsrView<T> A, const T *__restrict__ y, CsrView<T> B,
-                         const T *__restrict__ dB, const T *__restrict__ x,
-                         const T *__restrict__ kappa, const double *__restrict__ sigma, T omega,
-                         T *__restrict__ out) {
+template <typename S>
+__global__ void k_jacobi(int rows, int ld, CsrView<typename Acc<S>::T> A, const S *__restrict__ y,
+                         CsrView<typename Acc<S>::T> B, const typename Acc<S>::T *__restrict__ dB,
+                         const S *__restrict__ x, const S *__restrict__ kappa,
+                         const double *__restrict__ sigma, typename Acc<S>::T omega,
+                         S *__restrict__ out) {
+    using T = typename Acc<S>::T;
     const int q4 = ld >> 2;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (int64_t)rows * q4) return;
@@ -136,19 +165,19 @@ __global__ void k_jacobi(int rows, int ld, CsrView<T> A, const T *__restrict__ y
         T inv_s = T(1) / (T)sigma[c0 + k];
         o.a[k] = xi.a[k] - w * (bx.a[k] - (ay.a[k] - ki.a[k]) * inv_s);
     }
-    st4(out + (size_t)i * ld + c0, o);
+    st4(out + (size_t)i * ld + c0, cvt4<S>(o));
 }
 
 template <typename T>
-void launch_jacobi(int rows, int ld, CsrView<T> A, const T *y, CsrView<T> B, const T *dB,
-                   const T *x, const T *kappa, const double *sigma, double omega, T *out,
-                   cudaStream_t s) {
+void launch_jacobi(int rows, int ld, CsrView<typename Acc<T>::T> A, const T *y,
+                   CsrView<typename Acc<T>::T> B, const typename Acc<T>::T *dB, const T *x,
+                   const T *kappa, const double *sigma, double omega, T *out, cudaStream_t s) {
     if (rows == 0) return;
     int64_t n = (int64_t)rows * (ld / 4);
     int bs = 256;
     SAMG_COUNT_LAUNCH();
     k_jacobi<T><<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(rows, ld, A, y, B, dB, x, kappa,
-                                                             sigma, (T)omega, out);
+                                                             sigma, (typename Acc<T>::T)omega, out);
     SAMG_CUDA(cudaGetLastError());
 }
 template void launch_jacobi<float>(int, int, CsrView<float>, const float *, CsrView<float>,
@@ -157,12 +186,15 @@ template void launch_jacobi<float>(int, int, CsrView<float>, const float *, CsrV
 template void launch_jacobi<double>(int, int, CsrView<double>, const double *, CsrView<double>,
                                     const double *, const double *, const double *,
                                     const double *, double, double *, cudaStream_t);
+template void launch_jacobi<bf16>(int, int, CsrView<float>, const bf16 *, CsrView<float>,
+                                  const float *, const bf16 *, const bf16 *, const double *, double,
+                                  bf16 *, cudaStream_t);
 
 // ------------------------------------------------------------- elementwise
 template <typename TA, typename TB>
 __global__ void k_convert(size_t n, const TA *__restrict__ a, TB *__restrict__ b) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (TB)a[i];
+    if (i < n) b[i] = from_acc<TB>((typename Acc<TB>::T)to_acc(a[i]));
 }
 template <typename TA, typename TB>
 void launch_convert(size_t count, const TA *a, TB *b, cudaStream_t s) {
@@ -173,11 +205,13 @@ void launch_convert(size_t count, const TA *a, TB *b, cudaStream_t s) {
 }
 template void launch_convert<double, float>(size_t, const double *, float *, cudaStream_t);
 template void launch_convert<float, double>(size_t, const float *, double *, cudaStream_t);
+template void launch_convert<double, bf16>(size_t, const double *, bf16 *, cudaStream_t);
+template void launch_convert<bf16, double>(size_t, const bf16 *, double *, cudaStream_t);
 
 template <typename TY>
 __global__ void k_add_to(size_t n, double *__restrict__ x, const TY *__restrict__ y) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] += (double)y[i];
+    if (i < n) x[i] += (double)to_acc(y[i]);
 }
 template <typename TY>
 void launch_add_to(size_t count, double *x, const TY *y, cudaStream_t s) {
@@ -188,6 +222,7 @@ void launch_add_to(size_t count, double *x, const TY *y, cudaStream_t s) {
 }
 template void launch_add_to<float>(size_t, double *, const float *, cudaStream_t);
 template void launch_add_to<double>(size_t, double *, const double *, cudaStream_t);
+template void launch_add_to<bf16>(size_t, double *, const bf16 *, cudaStream_t);
 
 // ----------------------------------------------------------- column dots
 // Column-wise x_j^t (M y)_j: per-block partial sums in a fixed order, then one

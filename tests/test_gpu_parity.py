@@ -1,4 +1,5 @@
-"""GPU path vs the FP64 CPU oracle, through the C ABI.
+"""GPU path vs the FP64 CPU oracle, through the C ABI (float64, float32 and
+bfloat16-storage arithmetic).
 
 Each step of the additive cycle (Sec. 4) -- Galerkin operators, block
 Gauss-Seidel relaxation (Kaczmarz or Jacobi blocks), residual + restriction,
@@ -24,6 +25,11 @@ samg = pytest.importorskip("paper_1102_0919_gb300")
 
 TOL64 = 1e-10
 TOL32 = 2e-4
+# bfloat16 vector storage: unit roundoff u = 2^-8 = 3.9e-3 per stored value; a
+# relaxation, transfer or V-cycle step stores an entry up to about 8 times
+# (every row update that touches it, then the output), so its error relative
+# to the largest entry stays within 8u = 3.1e-2
+TOLB16 = 3.2e-2
 
 
 def rel(a, b):
@@ -96,7 +102,7 @@ def test_galerkin_operators(case):
             assert d <= TOL64 * abs(ref).max(), (l, which, d)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32), ("bf16", TOLB16)])
 def test_relaxation_each_level(case, prec, tol):
     H, g = case["H"], case["g"]
     g.set_precision(prec)
@@ -113,7 +119,7 @@ def test_relaxation_each_level(case, prec, tol):
     g.set_precision("fp64")
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32), ("bf16", TOLB16)])
 def test_relaxation_coloured_each_level(case, prec, tol):
     """relax_order = 1 (the coloured variant): every level's smoothing phase
     against the oracle's coloured sweeps (the same greedy colouring)."""
@@ -139,7 +145,7 @@ def test_relaxation_coloured_each_level(case, prec, tol):
         g.set_precision("fp64")
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32), ("bf16", TOLB16)])
 def test_residual_restrict_and_interpolate(case, prec, tol):
     H, g = case["H"], case["g"]
     g.set_precision(prec)
@@ -196,7 +202,7 @@ def test_coarsest_geneig_variant(case):
         assert rel(vg, vr) < 1e-9
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 5e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 5e-4), ("bf16", 2 * TOLB16)])
 def test_one_vcycle(case, prec, tol):
     H, g = case["H"], case["g"]
     g.set_precision(prec)
@@ -239,7 +245,7 @@ def test_ritz_step(case):
         assert rel(_match_up_to_sign(Ug, Ur), Ur) < 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_solve_matches_oracle(case, prec):
     if case["name"] == "svd_min_paper":
         pytest.skip("the paper's row form collapses onto the null(A^t) zero modes of the "
