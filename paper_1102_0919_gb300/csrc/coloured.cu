@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256)
 // barrier between them (it orders the global stores of one class before the
 // loads of the next for every thread of the CTA).
 constexpr int COLOURED_CTA = 512;
-constexpr int COLOURED_CTA_ROWS = 32 * COLOURED_CTA;
+constexpr int COLOURED_CTA_ROWS = 4 * COLOURED_CTA;
 template <typename T, typename S, int LD, int MODE>
 __global__ void __launch_bounds__(COLOURED_CTA)
     k_kz_classes_cta(int nclass, const int *__restrict__ class_off, const int *__restrict__ class_lg,
