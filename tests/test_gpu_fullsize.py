@@ -43,9 +43,42 @@ def big():
     g.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-3)])
-def test_relaxation_full_size(big, prec, tol):
+def _fp32_bound(A, count):
+    """Max-norm bound of a float32 relaxation program relative to its largest
+    entry: every row update rounds its correction and each updated value
+    (3 roundings of u = 2^-24), the projections do not amplify earlier
+    errors, and a value's error collects at most one update per level along
+    the longest chain of dependent rows -- the program's dependency depth D
+    (from the schedule builder's plan).  Twice 3 u D."""
+    _, depth, _ = samg.sweep_plan(A, count)
+    return 2.0 * 3.0 * 2.0 ** -24 * depth
+
+
+@pytest.mark.parametrize("count", [4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fused_relaxations_full_size(big, prec, count):
+    """The fused program of four block Gauss-Seidel relaxations (12.6 M rows
+    over about 190 bands at this size) against four sequential relaxations
+    of the oracle, element by element."""
     g, L0, sig, U, V = big["g"], big["L0"], big["sig"], big["U"], big["V"]
+    tol = 1e-10 if prec == "fp64" else _fp32_bound(big["A"], count)
+    rng = np.random.default_rng(9)
+    K = rng.standard_normal(U.shape)
+    T = rng.standard_normal(V.shape)
+    g.set_precision(prec)
+    Ug, Vg = g.relax(0, sig, U, V, K, T, count=count)
+    Ur, Vr = U.copy(), V.copy()
+    for _ in range(count):
+        oracle.relax_boot(L0, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+    assert rel(Vg, Vr) < tol, (rel(Vg, Vr), tol)
+    assert rel(Ug, Ur) < tol, (rel(Ug, Ur), tol)
+    g.set_precision("fp64")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_relaxation_full_size(big, prec):
+    g, L0, sig, U, V = big["g"], big["L0"], big["sig"], big["U"], big["V"]
+    tol = 1e-10 if prec == "fp64" else _fp32_bound(big["A"], 1)
     rng = np.random.default_rng(7)
     K = rng.standard_normal(U.shape)
     T = rng.standard_normal(V.shape)
