@@ -179,13 +179,13 @@ void relax_phase(samg_ctx &c, int l, int count) {
         if (L.B.empty()) csr_identity(c.spd() ? L.n : L.m, hB);
         else download_csr(L.B, hB, s);
         if (c.spd()) {
-            build_kschedule_stacked(hA, hB, count, ks, s);
+            build_kschedule_stacked(hA, hB, count, ks, s, ld);
         } else {
             HCsr hAt, hC;
             download_csr(L.At, hAt, s);
             if (L.C.empty()) csr_identity(L.n, hC);
             else download_csr(L.C, hC, s);
-            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s);
+            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld);
         }
         if (c.rstat.n >= 2) ks.err = c.rstat.p + 1;
     }

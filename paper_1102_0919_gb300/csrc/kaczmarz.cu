@@ -946,7 +946,7 @@ namespace {
 // live, it is one band (every column resident in the window; no cross-band
 // requirement and no first touch written by another band).
 std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w,
-                            int resident_cap = 0) {
+                            int resident_cap = 0, int slot_cap = SLOT_CAP) {
     std::vector<int> bstart;
     int slots = 0;
     if (resident_cap > 0 && p.rows > 0) {
@@ -957,7 +957,7 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
         int R = std::min(256, p.rows - r0), good = 0;
         for (;;) {
             int nl = analyze_band(p, glv, r0, r0 + R, w, &slots);
-            if (slots > SLOT_CAP) {
+            if (slots > slot_cap) {
                 if (good) break;
                 R = std::max(1, R / 2);
                 if (R == 1) { good = 1; break; }
@@ -978,7 +978,8 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
 // of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
 // block Gauss-Seidel relaxations (b entries read the other unknown with
 // coefficient -s_j and are not updated; norms from a).
-void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0) {
+void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
+                int slot_cap = SLOT_CAP) {
     const int rows = p.rows, cols = p.cols;
     ks.rows = rows;
     ks.cols = cols;
@@ -987,7 +988,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
     BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
-    std::vector<int> bstart = form_bands(p, glv, w, resident_cap);
+    std::vector<int> bstart = form_bands(p, glv, w, resident_cap, slot_cap);
     const int nb = (int)bstart.size() - 1;
     int slots = 0;
     ks.nbands = nb;
@@ -1228,9 +1229,10 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0)
     ks.req = std::move(req);
 }
 
-void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s) {
+void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s,
+                        int slot_cap = SLOT_CAP) {
     HostSched h;
-    build_host(p, mode, h);
+    build_host(p, mode, h, 0, slot_cap);
     ks.rows = h.rows;
     ks.cols = h.cols;
     ks.shifted = h.shifted;
@@ -1269,6 +1271,44 @@ void append_row(Pattern &p, const HCsr &M, int i, int col_off, bool as_b) {
 
 }  // namespace
 
+namespace {
+
+// dynamic shared memory of one CTA: the window of `slots` rows (plus the
+// scratch slot 0) in the arithmetic type, then the staging buffers
+template <typename T, typename S, int LD, bool SHIFT>
+constexpr size_t smem_bytes(int slots) {
+    return ((size_t)(slots + 1) * LD * sizeof(T) + 127) / 128 * 128 +
+           (size_t)KZ_NBUF * Stage<T, S, LD, SHIFT>::stride;
+}
+template <int LD, bool SHIFT>
+int window_cap_ld() {
+    // the most window slots every storage type's launch can hold in 227 KB,
+    // less 2 KB for the kernel's static shared memory
+    constexpr size_t budget = 227u * 1024u - 2048u;
+    int cap = 4095;
+    auto fit = [&](size_t per_slot, size_t fixed) {
+        const long long n = ((long long)budget - (long long)fixed - 128) / (long long)per_slot - 1;
+        cap = std::min<long long>(cap, n);
+    };
+    fit((size_t)LD * sizeof(double), smem_bytes<double, double, LD, SHIFT>(0) - LD * sizeof(double));
+    fit((size_t)LD * sizeof(float), smem_bytes<float, float, LD, SHIFT>(0) - LD * sizeof(float));
+    fit((size_t)LD * sizeof(float), smem_bytes<float, bf16, LD, SHIFT>(0) - LD * sizeof(float));
+    return std::max(cap, SLOT_CAP);
+}
+
+}  // namespace
+
+int kz_window_cap(int ld, int mode) {
+    const bool shift = mode != 0;
+    switch (ld) {
+        case 4: return shift ? window_cap_ld<4, true>() : window_cap_ld<4, false>();
+        case 8: return shift ? window_cap_ld<8, true>() : window_cap_ld<8, false>();
+        case 12: return shift ? window_cap_ld<12, true>() : window_cap_ld<12, false>();
+        case 16: return shift ? window_cap_ld<16, true>() : window_cap_ld<16, false>();
+        default: return SLOT_CAP;
+    }
+}
+
 void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     build_from_pattern(merge_pattern(A, B), B ? 1 : 0, ks, s);
 }
@@ -1298,8 +1338,9 @@ Pattern stacked_pattern(const HCsr &A, const HCsr &B, int count) {
 
 }  // namespace
 
-void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s) {
-    build_from_pattern(stacked_pattern(A, B, count), 1, ks, s);
+void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s,
+                             int ld) {
+    build_from_pattern(stacked_pattern(A, B, count), 1, ks, s, kz_window_cap(ld, 1));
 }
 
 namespace {
@@ -1364,8 +1405,8 @@ HCsr transpose_csr(const HCsr &A) {
 }  // namespace
 
 void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
-                           KSched &ks, cudaStream_t s) {
-    build_from_pattern(fused_pattern(A, At, B, C, count), 2, ks, s);
+                           KSched &ks, cudaStream_t s, int ld) {
+    build_from_pattern(fused_pattern(A, At, B, C, count), 2, ks, s, kz_window_cap(ld, 2));
 }
 
 namespace {

@@ -96,7 +96,8 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s);
 
 // count sweeps over the rows of A - s B in sequence (SPD kind): one program,
 // so a sweep's rows start as soon as the rows they depend on are done.
-void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s);
+void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s,
+                             int ld = 0);
 
 // count block Gauss-Seidel relaxations of the minimal SVD kind as one
 // program over the unknown [v; u] (n + m rows of ld values): per relaxation
@@ -105,7 +106,12 @@ void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks
 // right-hand side block is [kappa; tau] (m + n rows).  The order of every
 // row's updates is that of the sequential relaxations.
 void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
-                           KSched &ks, cudaStream_t s);
+                           KSched &ks, cudaStream_t s, int ld = 0);
+
+// The largest window (live columns per band) whose launch fits a CTA's
+// shared memory at block width ld for every storage type (at least 512);
+// the smoothing phases' programs are banded with it.
+int kz_window_cap(int ld, int mode);
 
 // One sweep: x (cols x ld) updated in place; rhs (rows x ld) or null for 0;
 // shift: ld device values (shifted form).  Returns after queuing the kernel.
