@@ -311,6 +311,12 @@ class Solver:
         generalized-eigen variant."""
         self._check(samg_set_coarse_pinv(self._ctx, int(form)))
 
+    def residuals(self):
+        """rho_j of the current triplets (n_b values; no vector copies)."""
+        r = np.zeros(self.nb)
+        self._check(samg_get_triplets(self._ctx, None, None, None, _ptr(r)))
+        return r
+
     def set_relax_order(self, order):
         """"natural" (0, the paper's) or "coloured" (1, the variant)."""
         self._check(samg_set_relax_order(self._ctx, {"natural": 0, "coloured": 1}.get(order, order)))
