@@ -122,12 +122,25 @@ typedef struct {
                                the iteration, so its cycle convergence
                                factor differs from form 0's.
                              The setup phase always sweeps in natural order. */
+    int32_t square_form;  /* square SVD kind (m = n; Sec. 5.1):
+                             0 = as any SVD kind (rows and columns coarsened
+                               on A A^t and A^t A, or row_form 0's rows from
+                               A for the minimal target);
+                             1 = the C/F splitting and the sparsity patterns
+                               of both P and Q from the strength graph of A
+                               itself, every level square (the setting of the
+                               paper's square nonsymmetric example), P fitted
+                               to the u vectors and Q to the v vectors;
+                             2 = as 1 with one operator P = Q fitted to both
+                               sets of vectors, so that B_c = C_c.
+                             The Ritz step is two-sided in forms 1 and 2.
+                             Ignored by non-square or SPD problems. */
 } samg_params;
 
 /* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
  * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
  * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0, row_form 0,
- * relax_order 0. */
+ * relax_order 0, square_form 0. */
 void samg_default_params(samg_params *p);
 
 /* ---------------------------------------------------------------- setup --

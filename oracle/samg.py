@@ -57,6 +57,13 @@ silent the readings below are used (numbers as in the design notes):
   components of u in null(A^t) -- left there by rounding -- are invisible to
   every relaxation and correction and to the two-sided projection, and would
   otherwise stall the residual at the rounding level of the cycle.
+* R23 square SVD kind (Sec. 5.1): params["square_form"] = "from_A" takes the
+  C/F splitting and the sparsity patterns of both P and Q from the strength
+  graph of A itself (Eq. strength on N = A), as in the paper's square
+  nonsymmetric example (Sec. 6.1), so every level stays square; P is fitted
+  to the u vectors and Q to the v vectors.  "shared" fits one operator to
+  both sets (weights repeated) and takes Q = P, so that B_c = C_c.  The
+  Ritz step is two-sided.  The default "normal" keeps Sec. 3.7 (or R21).
 * R22 redo-P (Sec. 6.3): a triplet counts as converged once rho_j <=
   redo_tol; each time that count grows (some still above), one downward
   sweep of the multiplicative phase runs on copies of the boot triplets with
@@ -79,7 +86,8 @@ _LIB = None
 
 DEFAULTS = dict(n_t=8, theta=0.06, mu_t=8, mu_b=4, mu_tJ=1, mu_bJ=1, omega_J=0.7,
                 n_mult=10, coarsest_max=100, max_levels=30, seed=20110204, coarse_drop=1,
-                coarse_pinv="svd", row_form="induced", relax_order="natural")
+                coarse_pinv="svd", row_form="induced", relax_order="natural",
+                square_form="normal")
 
 
 def _lib():
@@ -608,6 +616,18 @@ def _jacobi_on_N(L: Level, spd: bool, side: str, Y: np.ndarray, omega: float) ->
     return Y - (omega * 2.0 / g) * (N @ Y) / d[:, None]
 
 
+def _square(p: dict, spd: bool, shape) -> str | None:
+    """The square form (R23) in use, or None."""
+    f = p.get("square_form", "normal")
+    return f if (f != "normal" and not spd and shape[0] == shape[1]) else None
+
+
+def _ritz_form(p: dict, spd: bool, shape) -> str:
+    """R21's one-sided Ritz step, or the two-sided one (the paper's row form
+    and the square forms)."""
+    return "paper" if _square(p, spd, shape) else p.get("row_form", "induced")
+
+
 def _induced(spd: bool, target: str, shape, row_form: str = "induced") -> bool:
     """R21: the minimal SVD kind with m >= n takes its row (u) interpolation
     from the column interpolation, P_0 = A Q_0 on the finest level and
@@ -630,7 +650,8 @@ def _down_sweep(A, spd: bool, target: str, nb: int, p: dict, Ut, Vt, sigma, ub, 
     coarsest level."""
     m, n = A.shape
     om = p["omega_J"]
-    induced = _induced(spd, target, A.shape, p.get("row_form", "induced"))
+    square = _square(p, spd, A.shape)
+    induced = (not square) and _induced(spd, target, A.shape, p.get("row_form", "induced"))
     boot = ub is not None
     fine = Level(A, sp.identity(m, format="csr"),
                  None if spd else sp.identity(n, format="csr"))
@@ -643,11 +664,13 @@ def _down_sweep(A, spd: bool, target: str, nb: int, p: dict, Ut, Vt, sigma, ub, 
         if max(ml, nl) <= p["coarsest_max"] or len(levels) >= p["max_levels"]:
             break
         # coarsening (Sec. 3.7) depends on A_l only
-        if spd:
+        if spd or square:
             Su = strength(L.A, p["theta"])
             cfu = rs_coarsen(Su)
             mc = nc = int(cfu.sum())
-            total_f, total_c = ml, mc
+            total_f, total_c = (ml, mc) if spd else (ml + nl, 2 * mc)
+            if square:
+                Sv, cfv = Su, cfu
         elif induced:
             Sv = strength(L.At @ L.A if lvl == 0 else L.A, p["theta"])
             cfv = rs_coarsen(Sv)
@@ -686,9 +709,15 @@ def _down_sweep(A, spd: bool, target: str, nb: int, p: dict, Ut, Vt, sigma, ub, 
                 Yv = None if spd else _jacobi_on_N(L, spd, "v", Vf, om)
             else:
                 Yu, Yv = Uf, Vf
-            L.P = fit_interp(Su, cfu, Yu, Uf, w)
-            if not spd:
-                L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
+            if square == "shared":
+                # one operator for both sides: the u and v vectors fitted together
+                L.P = fit_interp(Su, cfu, np.hstack([Yu, Yv]), np.hstack([Uf, Vf]),
+                                 np.concatenate([w, w]))
+                L.Q = L.P
+            else:
+                L.P = fit_interp(Su, cfu, Yu, Uf, w)
+                if not spd:
+                    L.Q = fit_interp(Sv, cfv, Yv, Vf, w)
         levels.append(galerkin(L, spd))
         # injection to the coarse level
         if induced:
@@ -722,7 +751,8 @@ def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
     A = _csr(A)
     m, n = A.shape
     om = p["omega_J"]
-    induced = _induced(spd, target, A.shape, p.get("row_form", "induced"))
+    induced = (not _square(p, spd, A.shape)) and _induced(spd, target, A.shape,
+                                                            p.get("row_form", "induced"))
     Ut = random_block(p["seed"], m, p["n_t"])
     Vt = None if spd else random_block(p["seed"] ^ (1 << 63), n, p["n_t"])
     if induced:
@@ -740,7 +770,7 @@ def setup(A, nb: int, target: str, kind: str, params: dict | None = None):
             if not spd:
                 vb = np.ascontiguousarray(L.Q @ vb)
             sigma = relax_boot_rq(L, spd, target, sigma, ub, vb, p["mu_b"], om)
-        sigma, Ub, Vb = ritz(A, spd, target, ub, vb, p.get("row_form", "induced"))
+        sigma, Ub, Vb = ritz(A, spd, target, ub, vb, _ritz_form(p, spd, A.shape))
     H = Hierarchy(kind, target, levels, p, Ut, Vt)
     return H, sigma, Ub, Vb
 
@@ -807,7 +837,7 @@ def solve(H: Hierarchy, sigma, U, V, tol: float = 1e-8, max_outer: int = 100,
             break
         Z = np.zeros_like(U)
         vcycle(H, 0, sigma, U, V, Z, None if spd else np.zeros_like(V), XY)
-        sigma, U, V = ritz(A, spd, H.target, U, V, H.params.get("row_form", "induced"))
+        sigma, U, V = ritz(A, spd, H.target, U, V, _ritz_form(H.params, spd, A.shape))
         hist.append(residual_norms(A, spd, sigma, U, V))
         if redo_tol is not None:
             conv = hist[-1] <= redo_tol

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32),
                 ("coarse_pinv", ctypes.c_int32), ("row_form", ctypes.c_int32),
-                ("relax_order", ctypes.c_int32)]
+                ("relax_order", ctypes.c_int32), ("square_form", ctypes.c_int32)]
 
 
 class _Csr(ctypes.Structure):
@@ -178,6 +178,8 @@ def make_params(**kw) -> Params:
             v = {"induced": 0, "paper": 1}.get(v, v)
         elif k == "relax_order":
             v = {"natural": 0, "coloured": 1}.get(v, v)
+        elif k == "square_form":
+            v = {"normal": 0, "from_A": 1, "shared": 2}.get(v, v)
         setattr(p, k, v)
     return p
 

@@ -65,6 +65,8 @@ void check_common(int n_b, const samg_params *prm) {
                "row_form must be 0 (rows from A) or 1 (the paper's A A^t coarsening)");
     SAMG_CHECK(prm->relax_order == 0 || prm->relax_order == 1, SAMG_E_INVALID,
                "relax_order must be 0 (natural, the paper's) or 1 (coloured variant)");
+    SAMG_CHECK(prm->square_form >= 0 && prm->square_form <= 2, SAMG_E_INVALID,
+               "square_form must be 0, 1 (splitting from A) or 2 (shared P = Q)");
 }
 
 template <typename T>
@@ -268,6 +270,7 @@ void samg_default_params(samg_params *p) {
     p->coarse_pinv = 0;
     p->row_form = 0;
     p->relax_order = 0;
+    p->square_form = 0;
 }
 
 const char *samg_last_error(const samg_ctx *ctx) {

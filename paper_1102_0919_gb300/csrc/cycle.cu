@@ -401,7 +401,9 @@ void ritz(samg_ctx &c, bool identity) {
     const int64_t n = L0.n;
     const int64_t mu = c.spd() ? L0.n : L0.m;
     Term<double> none{};
-    if (!identity && c.minimal() && !c.spd() && L0.m >= L0.n && c.prm.row_form == 0) {
+    const bool square_form = !c.spd() && L0.m == L0.n && c.prm.square_form != 0;
+    if (!identity && c.minimal() && !c.spd() && L0.m >= L0.n && c.prm.row_form == 0 &&
+        !square_form) {
         // left basis A V (Rayleigh-Ritz for A^t A on span V): excludes the
         // null(A^t) modes that no relaxation or correction can remove
         launch_combine<double, double>(L0.m, ld, nullptr, 0.0,

@@ -556,7 +556,10 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     SetupState st(c);
     st.nt = p.n_t;
     st.ldt = block_ld(p.n_t);
-    st.induced = !spd && c.minimal() && p.row_form == 0;
+    // square SVD kind, Sec. 5.1 (R23): splitting and patterns from A itself
+    // (1), or one operator P = Q for both sides (2)
+    const int sq = (!spd && Ah.m == Ah.n) ? p.square_form : 0;
+    st.induced = !spd && c.minimal() && p.row_form == 0 && sq == 0;
     const int m = Ah.m, n = Ah.n, ldt = st.ldt;
     st.ones.alloc(16);
     // random test vectors (Sec. 3.3)
@@ -598,7 +601,21 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                 Nu = st.N0u; Nv = st.N0v; Su = st.S0u; Sv = st.S0v; cfu = st.cf0u; cfv = st.cf0v;
             } else {
                 DCsr Nd;
-                if (spd || (st.induced && l > 0)) {
+                if (sq) {
+                    // one C/F splitting and one strength graph (of A) for u and v;
+                    // R14's Jacobi step (minimal) still needs A A^t and A^t A
+                    HCsr hA;
+                    download_csr(L.A, hA, s);
+                    strength_of(hA, p.theta, Su);
+                    Sv = Su;
+                    if (c.minimal()) {
+                        spgemm(L.A, L.At, Nd, s);
+                        download_csr(Nd, Nu, s);
+                        DCsr Nd2;
+                        spgemm(L.At, L.A, Nd2, s);
+                        download_csr(Nd2, Nv, s);
+                    }
+                } else if (spd || (st.induced && l > 0)) {
                     download_csr(L.A, Nv, s);
                 } else if (st.induced) {
                     spgemm(L.At, L.A, Nd, s);
@@ -626,7 +643,8 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                 }
                 if (spd || st.induced) strength_of(Nv, p.theta, Sv);
                 cfv = rs_split(Sv);
-                if (!spd && !st.induced) cfu = rs_split(Su);
+                if (sq) cfu = cfv;
+                else if (!spd && !st.induced) cfu = rs_split(Su);
                 if (l == 0) {
                     st.have0 = true;
                     st.N0u = Nu; st.N0v = Nv; st.S0u = Su; st.S0v = Sv; st.cf0u = cfu; st.cf0v = cfv;
@@ -682,7 +700,38 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                 }
             };
             HCsr hQ, hP;
-            if (spd) {
+            if (sq == 2) {
+                // P = Q fitted to the u and the v vectors together (weights
+                // repeated), so that B_c = C_c on every level
+                std::vector<double> Y((size_t)L.n * 2 * nf), w2(2 * nf);
+                fetch(s, ut, L.n, ldt, p.n_t, Y.data(), 2 * nf, 0);
+                if (cyc > 0) fetch(s, L.wd.u.p, L.n, c.ld, c.nb, Y.data(), 2 * nf, p.n_t);
+                fetch(s, vt, L.n, ldt, p.n_t, Y.data(), 2 * nf, nf);
+                if (cyc > 0) fetch(s, L.wd.v.p, L.n, c.ld, c.nb, Y.data(), 2 * nf, nf + p.n_t);
+                SAMG_CUDA(cudaStreamSynchronize(s));
+                for (int k = 0; k < nf; ++k) w2[k] = w2[nf + k] = w[k];
+                if (c.minimal()) {  // R14 on each side's F values with its own N
+                    std::vector<double> Yu((size_t)L.n * nf), Yv((size_t)L.n * nf), Fu, Fv;
+                    for (int i = 0; i < L.n; ++i)
+                        for (int k = 0; k < nf; ++k) {
+                            Yu[(size_t)i * nf + k] = Y[(size_t)i * 2 * nf + k];
+                            Yv[(size_t)i * nf + k] = Y[(size_t)i * 2 * nf + nf + k];
+                        }
+                    jacobi_host(Nu, Yu, nf, p.omega_J * 2.0 / gershgorin(Nu), Fu);
+                    jacobi_host(Nv, Yv, nf, p.omega_J * 2.0 / gershgorin(Nv), Fv);
+                    std::vector<double> YF(Y.size());
+                    for (int i = 0; i < L.n; ++i)
+                        for (int k = 0; k < nf; ++k) {
+                            YF[(size_t)i * 2 * nf + k] = Fu[(size_t)i * nf + k];
+                            YF[(size_t)i * 2 * nf + nf + k] = Fv[(size_t)i * nf + k];
+                        }
+                    ls_interp(Su, cfu, YF, Y, w2, 2 * nf, hP);
+                } else {
+                    ls_interp(Su, cfu, Y, Y, w2, 2 * nf, hP);
+                }
+                upload_csr(hP, L.P, s);
+                upload_csr(hP, L.Q, s);
+            } else if (spd) {
                 fit_side(Nv, Sv, cfv, L.n, ut, L.wd.u.p, hP);
                 upload_csr(hP, L.P, s);
             } else if (st.induced) {

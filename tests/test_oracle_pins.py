@@ -727,3 +727,32 @@ def test_coloured_order_pins():
     assert np.abs(X1 - X3).max() < 1e-12
     last = np.flatnonzero((col == col.max()) & (np.abs(D).sum(axis=1) > 0))
     assert last.size and np.abs(D[last] @ X1 - rhs[last]).max() < 1e-12
+
+
+def test_square_forms_keep_square_levels_and_reach_lapack():
+    """R23 (Sec. 5.1): with the C/F splitting and sparsity patterns of P and
+    Q taken from A, every level of a square nonsymmetric operator stays
+    square; with P = Q shared, B_c = C_c on every level.  The converged
+    triplets equal a dense LAPACK SVD (called) of the 20 x 20 upwind
+    convection-diffusion operator: its 4 largest (from A and shared) and its
+    4 smallest (shared) singular values."""
+    A = W.convdiff5(20, 8.0).to_scipy()
+    assert abs(A - A.T).max() > 0
+    sv = np.sort(np.linalg.svd(A.toarray(), compute_uv=False))
+    cases = [("dominant", "from_A", W.FD_PARAMS), ("dominant", "shared", W.FD_PARAMS),
+             ("minimal", "shared", W.GRAD_PARAMS)]
+    for target, form, base in cases:
+        prm = dict(base, seed=W.problem_seed(2), coarsest_max=40, n_mult=10, square_form=form)
+        H, s, U, V = oracle.setup(A, 4, target, "svd", prm)
+        for L in H.levels:
+            assert L.A.shape[0] == L.A.shape[1]
+        if form == "shared":
+            for l, L in enumerate(H.levels[:-1]):
+                assert L.Q is L.P
+                if l > 0:
+                    assert abs(L.B - L.C).max() == 0
+        s, U, V, hist = oracle.solve(H, s, U, V, tol=1e-10, max_outer=120)
+        ref = sv[::-1][:4] if target == "dominant" else sv[:4]
+        assert hist[-1].max() <= 1e-10, (target, form, hist[-1])
+        assert np.allclose(s, ref, rtol=1e-12), (target, form, s, ref)
+        assert np.allclose(A @ V, U * s, atol=1e-9 * sv[-1])

@@ -12,6 +12,9 @@ float64 values):
   y-neighbours -1/h^2, node (i, j) has index j*N + i.  eps = 1 is the FD
   Laplacian of the paper's Sec. 6.2 (Table "values", FD columns, scaled by
   1/h^2).
+* ``convdiff5(N, c)``  square nonsymmetric 5-point convection-diffusion
+  operator (upwind in x), standing in for the paper's nonsymmetric square
+  example.
 * ``gradient(N)``  forward-difference gradient on the same grid: one row per
   grid edge, values +-1/h, so that gradient(N)^t gradient(N) = laplacian5(N).
   x-edge rows r = j(N+1)+i (i in [0,N], j in [0,N)), then y-edge rows
@@ -89,6 +92,29 @@ def laplacian5(N: int, eps: float = 1.0) -> CSR:
     cols = [node]
     vals = [np.full(node.size, 2.0 * (eps + 1.0) * h2)]
     for di, dj, w in ((-1, 0, -eps * h2), (1, 0, -eps * h2), (0, -1, -h2), (0, 1, -h2)):
+        ii, jj = i + di, j + dj
+        ok = (ii >= 0) & (ii < N) & (jj >= 0) & (jj < N)
+        rows.append(node[ok])
+        cols.append((jj * N + ii)[ok])
+        vals.append(np.full(int(ok.sum()), w))
+    return _from_triplets(N * N, N * N, np.concatenate(rows), np.concatenate(cols),
+                          np.concatenate(vals))
+
+
+def convdiff5(N: int, c: float = 8.0) -> CSR:
+    """Square nonsymmetric 5-point operator: the Dirichlet Laplacian of
+    laplacian5(N) plus an upwind first difference c (u_i - u_{i-1}) / h in x
+    (h = 1/(N+1)), node (i, j) -> j*N + i.  A stand-in for the paper's
+    slightly nonsymmetric square test matrix (Sec. 6.1)."""
+    s = float(N + 1)
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="xy")
+    i = i.ravel()
+    j = j.ravel()
+    node = j * N + i
+    rows = [node]
+    cols = [node]
+    vals = [np.full(node.size, 4.0 * s * s + c * s)]
+    for di, dj, w in ((-1, 0, -s * s - c * s), (1, 0, -s * s), (0, -1, -s * s), (0, 1, -s * s)):
         ii, jj = i + di, j + dj
         ok = (ii >= 0) & (ii < N) & (jj >= 0) & (jj < N)
         rows.append(node[ok])
