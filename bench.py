@@ -300,6 +300,8 @@ def run_gpu(args):
     free_b, total_b = torch.cuda.mem_get_info(dev)
     log("setup %.1f s, levels %s, device memory in use %.2f GB" %
         (t_setup, levels, (total_b - free_b) / 1e9))
+    setup_stages = {k: round(v, 3) for k, v in s.setup_times().items()}
+    log("setup stages (s): %s" % setup_stages)
     sig0, U0, V0, res0 = s.triplets()
     # boot triplets resident in HBM (torch owns the memory)
     dsig = torch.tensor(sig0, device=dev, dtype=torch.float64)
@@ -500,7 +502,7 @@ def run_gpu(args):
                    if vec_bytes > 129e6 else
                    ("working set of about %.0f MB fits the 129 MB L2; no flush between "
                     "steps (latency-bound sweeps)" % (vec_bytes / 1e6)),
-                   "setup_s": round(t_setup, 3)},
+                   "setup_s": round(t_setup, 3), "setup_stages_s": setup_stages},
         "solve": {"outer_iterations": mixed["iterations"], "converged": mixed["converged"],
                   "resid": mixed["resid"], "sigma_relerr_max": mixed["sigma_relerr_max"],
                   "resid_after_2_steps": mixed["resid_after_2_steps"]},

@@ -279,6 +279,26 @@ uint64_t samg_launch_count(void);
 samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_t *launches,
                               double *total_ms, double *alg_bytes);
 
+/* Wall-clock seconds the last samg_setup spent in each stage of the
+ * multiplicative phase (Sec. 3), summed over its cycles and levels; the
+ * stream is synchronised at every stage boundary, so GPU work is charged to
+ * the stage that launched it.  Stages (index into seconds[]):
+ *   0 strength graphs and C/F splittings (Eq. strength, Alg. coarsening; host)
+ *   1 relaxation of the test vectors (Sec. 3.3)
+ *   2 relaxation of the boot vectors with Rayleigh-quotient updates, down and
+ *     up, and their interpolation (Sec. 3.4)
+ *   3 Rayleigh quotients and least-squares interpolation fits (Sec. 3.8; host)
+ *   4 Galerkin operators and transposes (Sec. 2)
+ *   5 level preparation: row norms, sweep schedules, precision copies
+ *   6 coarsest direct solve for the boot triplets (Sec. 3.6)
+ *   7 Ritz steps (Sec. 4.3)
+ *   8 completion of the solve-phase hierarchy
+ *   9 the rest (test-vector draw, injections, uploads)
+ * Writes min(count, SAMG_SETUP_STAGES) values.  SAMG_E_INVALID: ctx or
+ * seconds NULL, or count < 0. */
+#define SAMG_SETUP_STAGES 10
+samg_status samg_setup_times(const samg_ctx *ctx, double *seconds, int32_t count);
+
 /* Hierarchy description: levels, and per level m_l, n_l, nnz(A_l) (arrays of
  * n_levels entries; pass NULL to query n_levels only). */
 samg_status samg_get_hierarchy_info(const samg_ctx *ctx, int *n_levels, int32_t *m, int32_t *n,

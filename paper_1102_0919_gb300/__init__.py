@@ -116,6 +116,7 @@ samg_profile = _sig("samg_profile", _I, _CTX, _I)
 samg_launch_count = _sig("samg_launch_count", ctypes.c_uint64)
 samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+samg_setup_times = _sig("samg_setup_times", _I, _CTX, _P, ctypes.c_int32)
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
             "samg_solve", "samg_set_triplets", "samg_get_triplets", "samg_set_precision",
@@ -128,7 +129,8 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_host_strength_product", "samg_export", "samg_write_hierarchy",
             "samg_import_file", "samg_sweep_schedule", "samg_setup_batched",
             "samg_solve_batched", "samg_batch_problem", "samg_batch_size",
-            "samg_batch_last_error", "samg_batch_destroy", "samg_row_colours"]
+            "samg_batch_last_error", "samg_batch_destroy", "samg_row_colours",
+            "samg_setup_times"]
 
 
 def _arr(x, dtype):
@@ -350,6 +352,17 @@ class Solver:
                                              None if V_ptr is None else ctypes.c_void_p(V_ptr)))
 
     KERNELS = ("kaczmarz_sweep", "block_spmm", "jacobi", "coarsest_solve", "ritz")
+
+    SETUP_STAGES = ("strength_rs", "test_relax", "boot_relax", "ls_fit", "galerkin",
+                    "prepare_level", "coarsest", "ritz", "finalize", "other")
+
+    def setup_times(self):
+        """Wall seconds of the last setup's stages (strength and splitting,
+        test and boot relaxation, LS fits, Galerkin, level preparation,
+        coarsest solve, Ritz, completion, the rest)."""
+        t = np.zeros(len(self.SETUP_STAGES))
+        self._check(samg_setup_times(self._ctx, _ptr(t), len(t)))
+        return dict(zip(self.SETUP_STAGES, (float(x) for x in t)))
 
     def profile(self, on=True):
         self._check(samg_profile(self._ctx, 1 if on else 0))

@@ -536,6 +536,12 @@ samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_
     });
 }
 
+samg_status samg_setup_times(const samg_ctx *ctx, double *seconds, int32_t count) {
+    if (!ctx || !seconds || count < 0) return SAMG_E_INVALID;
+    for (int k = 0; k < count && k < SAMG_SETUP_STAGES; ++k) seconds[k] = ctx->setup_s[k];
+    return SAMG_OK;
+}
+
 samg_status samg_set_precision(samg_ctx *ctx, samg_precision prec) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {

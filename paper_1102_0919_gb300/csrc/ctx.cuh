@@ -127,6 +127,8 @@ struct samg_ctx {
     samg::DBuf<double> AV, AtU, Un, Vn, GU, GV, H, TU, TV, gwork, partu, partv;
     samg::DBuf<int> rstat;
     samg::Profiler prof;
+    // wall seconds of the setup phase's stages (samg_setup_times)
+    double setup_s[SAMG_SETUP_STAGES] = {};
     std::string err;
     bool poisoned = false;
     bool spd() const { return kind == SAMG_SPD_EIG; }

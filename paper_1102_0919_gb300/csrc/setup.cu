@@ -539,12 +539,29 @@ void coarsest_boot(SetupState &st) {
 
 }  // namespace
 
+// Charges the wall time since the previous mark to one setup stage, after
+// the stream has drained (samg_setup_times).
+struct StageClock {
+    samg_ctx &c;
+    std::chrono::steady_clock::time_point t;
+    explicit StageClock(samg_ctx &cx) : c(cx), t(std::chrono::steady_clock::now()) {
+        for (double &x : c.setup_s) x = 0.0;
+    }
+    void mark(int stage) {
+        SAMG_CUDA(cudaStreamSynchronize(c.stream));
+        const auto now = std::chrono::steady_clock::now();
+        c.setup_s[stage] += std::chrono::duration<double>(now - t).count();
+        t = now;
+    }
+};
+
 void host_setup(samg_ctx &c, const samg_csr &Ah) {
     cudaStream_t s = c.stream;
     const samg_params &p = c.prm;
     const bool spd = c.spd();
     SAMG_CHECK(spd || !c.minimal() || Ah.m >= Ah.n, SAMG_E_INVALID,
                "minimal SVD kind needs m >= n (pass A^t for wide matrices)");
+    StageClock clk(c);
     c.L.clear();
     c.L.reserve(p.max_levels + 2);
     c.L.emplace_back();
@@ -552,7 +569,9 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     c.L[0].m = Ah.m;
     c.L[0].n = Ah.n;
     alloc_finest_state(c);
+    clk.mark(9);
     prepare_level(c, 0);
+    clk.mark(5);
     SetupState st(c);
     st.nt = p.n_t;
     st.ldt = block_ld(p.n_t);
@@ -579,6 +598,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     }
     SAMG_CUDA(cudaGetLastError());
     // the fine-level test vectors need schedules of width ldt (same schedules)
+    clk.mark(9);
     for (int cyc = 0; cyc < p.n_mult; ++cyc) {
         c.L.resize(1);
         int l = 0;
@@ -650,6 +670,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                     st.N0u = Nu; st.N0v = Nv; st.S0u = Su; st.S0v = Sv; st.cf0u = cfu; st.cf0v = cfv;
                 }
             }
+            clk.mark(0);
             int nc = 0, mc = 0;
             for (char x : cfv) nc += x;
             if (spd || st.induced) mc = nc;
@@ -659,6 +680,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
             if (tot_c > 0.9 * tot_f || std::min(mc, nc) < 2 * c.nb) break;
             // relaxation of the test and boot vectors
             relax_test(st, l, ut, vt);
+            clk.mark(1);
             if (st.induced) {
                 if (l == 0)
                     launch_combine<double, double>(L.m, ldt, nullptr, 0.0,
@@ -668,6 +690,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                     SAMG_CUDA(cudaMemcpyAsync(ut, vt, sizeof(double) * L.n * ldt, cudaMemcpyDeviceToDevice, s));
             }
             if (cyc > 0) relax_boot_rq(st, l);
+            clk.mark(2);
             // LS fit on [test, boot]
             const int nf = p.n_t + (cyc > 0 ? c.nb : 0);
             std::vector<double> w(nf);
@@ -748,6 +771,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                 upload_csr(hP, L.P, s);
                 upload_csr(hQ, L.Q, s);
             }
+            clk.mark(3);
             // Galerkin operators of level l+1
             c.L.emplace_back();
             {
@@ -772,7 +796,9 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                 Lc.m = Lc.A.m;
                 Lc.n = Lc.A.n;
             }
+            clk.mark(4);
             prepare_level(c, l + 1);
+            clk.mark(5);
             // injection of test and boot vectors to level l+1
             Level &Lf = c.L[l];
             Level &Lc = c.L[l + 1];
@@ -808,7 +834,9 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
         SAMG_CHECK(c.L.size() >= 2, SAMG_E_INVALID,
                    "setup produced a single level (problem already at the coarsest size)");
         // coarsest: new boot triplets by a direct solve
+        clk.mark(9);
         coarsest_boot(st);
+        clk.mark(6);
         // upward: interpolate (Eq. ranges) and relax with Rayleigh-quotient updates
         for (int k = (int)c.L.size() - 2; k >= 0; --k) {
             Level &L = c.L[k];
@@ -822,21 +850,25 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
                                                Term<double>{}, c.sigma.p, L.wd.v.p, s);
             relax_boot_rq(st, k);
         }
+        clk.mark(2);
         // Ritz step on the finest level
         Level &L0 = c.L[0];
         SAMG_CUDA(cudaMemcpyAsync(c.U.p, L0.wd.u.p, c.U.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         if (!spd)
             SAMG_CUDA(cudaMemcpyAsync(c.V.p, L0.wd.v.p, c.V.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         ritz(c, false);
+        clk.mark(7);
     }
     // hierarchy of the last cycle: the cycle's per-level data are in place
     finalize_hierarchy(c);
+    clk.mark(8);
     share_error_word(c);
     for (auto &L : c.L) {
         L.wd.u.zero(s);
         if (!spd) L.wd.v.zero(s);
     }
     ritz(c, true);
+    clk.mark(7);
     SAMG_CUDA(cudaStreamSynchronize(s));
 }
 
