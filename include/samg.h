@@ -135,12 +135,19 @@ typedef struct {
                                sets of vectors, so that B_c = C_c.
                              The Ritz step is two-sided in forms 1 and 2.
                              Ignored by non-square or SPD problems. */
+    double redo_tol;      /* Sec. 6.3 redo of the interpolation for lagging
+                             triplets: 0 = off; > 0: samg_solve redetermines
+                             P and Q (samg_redo_interpolation) each time the
+                             number of triplets with rho_j <= redo_tol grows
+                             while some are still above it.  Makes samg_setup
+                             keep its fine test vectors on the device
+                             ((m + n) x n_t doubles, padded). */
 } samg_params;
 
 /* Defaults: n_t 8, theta 0.06, mu_t 8, mu_b 4, mu_tJ = mu_bJ = 1,
  * omega_J 0.7, n_mult 10, coarsest_max 100, max_levels 30,
  * seed 20110204, prec SAMG_FP32, n_conv 0 (all), coarse_pinv 0, row_form 0,
- * relax_order 0, square_form 0. */
+ * relax_order 0, square_form 0, redo_tol 0. */
 void samg_default_params(samg_params *p);
 
 /* ---------------------------------------------------------------- setup --
@@ -238,6 +245,16 @@ const char *samg_last_error(const samg_ctx *ctx);
  * (sigma, U, V) stays on the device.  *outer_done = iterations run.
  * Returns SAMG_E_NOT_CONVERGED when max_outer is reached first. */
 samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done);
+
+/* Sec. 6.3: redetermines the interpolation operators by one downward sweep
+ * of the multiplicative phase from the setup's fine test vectors and copies
+ * of the current boot triplets, with the LS weights of the test vectors and
+ * of the triplets marked converged (converged[j] != 0, n_b host ints) divided
+ * by 1000; the coarse levels, their schedules and the coarsest
+ * pseudo-inverse are rebuilt, and (sigma, U, V) is unchanged.  SAMG_E_INVALID
+ * when the context kept no setup state (redo_tol was 0 at samg_setup, or an
+ * imported hierarchy) or converged is NULL. */
+samg_status samg_redo_interpolation(samg_ctx *ctx, const int32_t *converged);
 
 /* Replace / read the boot triplets (host buffers; V ignored for SPD_EIG).
  * resid (n_b values, may be NULL) receives rho_j of the current triplets. */

@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("coarsest_max", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int), ("n_conv", ctypes.c_int32),
                 ("coarse_pinv", ctypes.c_int32), ("row_form", ctypes.c_int32),
-                ("relax_order", ctypes.c_int32), ("square_form", ctypes.c_int32)]
+                ("relax_order", ctypes.c_int32), ("square_form", ctypes.c_int32),
+                ("redo_tol", ctypes.c_double)]
 
 
 class _Csr(ctypes.Structure):
@@ -116,6 +117,7 @@ samg_profile = _sig("samg_profile", _I, _CTX, _I)
 samg_launch_count = _sig("samg_launch_count", ctypes.c_uint64)
 samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+samg_redo_interpolation = _sig("samg_redo_interpolation", _I, _CTX, _P)
 samg_setup_times = _sig("samg_setup_times", _I, _CTX, _P, ctypes.c_int32)
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
@@ -130,7 +132,7 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_import_file", "samg_sweep_schedule", "samg_setup_batched",
             "samg_solve_batched", "samg_batch_problem", "samg_batch_size",
             "samg_batch_last_error", "samg_batch_destroy", "samg_row_colours",
-            "samg_setup_times"]
+            "samg_setup_times", "samg_redo_interpolation"]
 
 
 def _arr(x, dtype):
@@ -355,6 +357,13 @@ class Solver:
 
     SETUP_STAGES = ("strength_rs", "test_relax", "boot_relax", "ls_fit", "galerkin",
                     "prepare_level", "coarsest", "ritz", "finalize", "other")
+
+    def redo_interpolation(self, converged):
+        """Sec. 6.3: new P and Q by one downward sweep, the LS weights of the
+        test vectors and of the converged triplets divided by 1000."""
+        c = np.ascontiguousarray(np.asarray(converged, dtype=np.int32))
+        assert c.size == self.nb
+        self._check(samg_redo_interpolation(self._ctx, _ptr(c)))
 
     def setup_times(self):
         """Wall seconds of the last setup's stages (strength and splitting,

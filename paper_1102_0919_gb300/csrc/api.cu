@@ -67,6 +67,8 @@ void check_common(int n_b, const samg_params *prm) {
                "relax_order must be 0 (natural, the paper's) or 1 (coloured variant)");
     SAMG_CHECK(prm->square_form >= 0 && prm->square_form <= 2, SAMG_E_INVALID,
                "square_form must be 0, 1 (splitting from A) or 2 (shared P = Q)");
+    SAMG_CHECK(prm->redo_tol >= 0.0 && std::isfinite(prm->redo_tol), SAMG_E_INVALID,
+               "redo_tol must be finite and >= 0");
 }
 
 template <typename T>
@@ -271,6 +273,7 @@ void samg_default_params(samg_params *p) {
     p->row_form = 0;
     p->relax_order = 0;
     p->square_form = 0;
+    p->redo_tol = 0.0;
 }
 
 const char *samg_last_error(const samg_ctx *ctx) {
@@ -294,6 +297,9 @@ samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, cons
     samg_status st = guarded(c, [&] {
         // argument checks first: they need no device
         check_common(n_b, params);
+        SAMG_CHECK(!params || params->redo_tol == 0.0, SAMG_E_INVALID,
+                   "redo_tol needs the setup phase's test vectors, which an imported "
+                   "hierarchy does not have");
         SAMG_CHECK(A != nullptr && n_levels >= 2 && P != nullptr, SAMG_E_INVALID,
                    "import needs A, P and at least two levels");
         SAMG_CHECK(kind == SAMG_SPD_EIG || Q != nullptr, SAMG_E_INVALID, "import: Q is NULL");
@@ -600,6 +606,7 @@ samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done
         SAMG_CHECK(max_outer >= 0 && tol > 0.0, SAMG_E_INVALID, "bad tol or max_outer");
         const int nconv = c.prm.n_conv > 0 && c.prm.n_conv < c.nb ? c.prm.n_conv : c.nb;
         std::vector<double> rs(c.ld);
+        int nredo = 0;  // most triplets seen at rho_j <= redo_tol (Sec. 6.3)
         for (;;) {
             c.resid.download(rs.data(), c.ld, c.stream);
             SAMG_CUDA(cudaStreamSynchronize(c.stream));
@@ -611,6 +618,13 @@ samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done
             }
             if (!finite) check_kaczmarz(c);
             SAMG_CHECK(finite, SAMG_E_INVALID, "non-finite residual");
+            if (done > 0 && c.prm.redo_tol > 0.0) {
+                std::vector<char> conv(c.nb);
+                int k = 0;
+                for (int j = 0; j < c.nb; ++j) k += (conv[j] = rs[j] <= c.prm.redo_tol);
+                if (k > nredo && k < c.nb) redo_interpolation(c, conv);
+                nredo = std::max(nredo, k);
+            }
             if (mx <= tol) { converged = true; break; }
             if (done >= max_outer) break;
             by_prec(c, [&](auto tag) { outer_vcycle<decltype(tag)>(c); });
@@ -625,6 +639,16 @@ samg_status samg_solve(samg_ctx *ctx, double tol, int max_outer, int *outer_done
         return SAMG_E_NOT_CONVERGED;
     }
     return st;
+}
+
+samg_status samg_redo_interpolation(samg_ctx *ctx, const int32_t *converged) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(converged != nullptr, SAMG_E_INVALID, "converged is NULL");
+        std::vector<char> conv(ctx->nb);
+        for (int j = 0; j < ctx->nb; ++j) conv[j] = converged[j] != 0;
+        redo_interpolation(*ctx, conv);
+    });
 }
 
 samg_status samg_get_hierarchy_info(const samg_ctx *ctx, int *n_levels, int32_t *m, int32_t *n,

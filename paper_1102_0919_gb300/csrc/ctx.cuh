@@ -3,6 +3,7 @@
 // Ritz step (Sec. 4.3).
 #pragma once
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -129,6 +130,9 @@ struct samg_ctx {
     samg::Profiler prof;
     // wall seconds of the setup phase's stages (samg_setup_times)
     double setup_s[SAMG_SETUP_STAGES] = {};
+    // the setup phase's state (fine test vectors, finest coarsening), kept
+    // after samg_setup when redo_tol > 0 for the redo of Sec. 6.3
+    std::shared_ptr<void> setup_keep;
     std::string err;
     bool poisoned = false;
     bool spd() const { return kind == SAMG_SPD_EIG; }
@@ -165,6 +169,10 @@ template <typename T> void outer_vcycle(samg_ctx &c);   // defect form on (U, V)
 
 void ritz(samg_ctx &c, bool identity);  // identity: residuals of the current triplets only
 void host_setup(samg_ctx &c, const samg_csr &A);  // multiplicative phase (setup.cu)
+// Sec. 6.3: new interpolation operators by one downward sweep of the
+// multiplicative phase, LS weights of the test vectors and of the converged
+// boot vectors (conv[j] != 0) divided by 1000; the iterate is unchanged
+void redo_interpolation(samg_ctx &c, const std::vector<char> &conv);
 // The setup's host steps on their own (setup.cu): strength (Eq. strength) and
 // Ruge-Stueben coarsening of N; weighted LS interpolation (Eq. LS) from the
 // strong C-point influences, nf vectors per point (row-major yF, yC).

@@ -342,11 +342,29 @@ void fetch(cudaStream_t s, const double *d, int rows, int ld, int nvec, double *
                                 nvec * sizeof(double), rows, cudaMemcpyDeviceToHost, s));
 }
 
+// Charges the wall time since the previous mark to one setup stage, after
+// the stream has drained (samg_setup_times).
+struct StageClock {
+    samg_ctx &c;
+    std::chrono::steady_clock::time_point t;
+    explicit StageClock(samg_ctx &cx, bool reset = true) : c(cx), t(std::chrono::steady_clock::now()) {
+        if (reset)
+            for (double &x : c.setup_s) x = 0.0;
+    }
+    void mark(int stage) {
+        SAMG_CUDA(cudaStreamSynchronize(c.stream));
+        const auto now = std::chrono::steady_clock::now();
+        c.setup_s[stage] += std::chrono::duration<double>(now - t).count();
+        t = now;
+    }
+};
+
 struct SetupState {
     samg_ctx &c;
     cudaStream_t s;
     int nt, ldt;
     bool induced;
+    int sq = 0;                     // square form in use (R23), 0 if none
     DBuf<double> Ut, Vt;            // fine test vectors (relaxed in place)
     std::vector<DBuf<double>> ut, vt;  // per level (coarse copies)
     DBuf<double> ones, dots, sgn;
@@ -537,23 +555,257 @@ void coarsest_boot(SetupState &st) {
     SAMG_CUDA(cudaStreamSynchronize(st.s));
 }
 
-}  // namespace
+// One downward sweep of a multiplicative cycle (Sec. 3.3): on each level
+// coarsen, relax the test vectors (and, after the first cycle, copies of the
+// finest boot triplets with Rayleigh-quotient updates of sigma), fit P and Q
+// by weighted LS, form the Galerkin operators and inject the vectors.  The
+// levels below the finest are rebuilt.  wscale (one factor per fitted
+// vector, or null) multiplies the LS weights.
+void down_sweep(SetupState &st, int cyc, const std::vector<double> *wscale, StageClock &clk) {
+    samg_ctx &c = st.c;
+    cudaStream_t s = c.stream;
+    const samg_params &p = c.prm;
+    const bool spd = c.spd();
+    const int sq = st.sq;
+    const int ldt = st.ldt;
+    c.L.resize(1);
+    int l = 0;
+    double *ut = st.Ut.p, *vt = spd ? nullptr : st.Vt.p;
+    st.ut.clear();
+    st.vt.clear();
+    if (cyc > 0) {
+        Level &L0 = c.L[0];
+        SAMG_CUDA(cudaMemcpyAsync(L0.wd.u.p, c.U.p, c.U.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (!spd)
+            SAMG_CUDA(cudaMemcpyAsync(L0.wd.v.p, c.V.p, c.V.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    for (;;) {
+        Level &L = c.L[l];
+        if (std::max(L.m, L.n) <= p.coarsest_max || (int)c.L.size() >= p.max_levels) break;
+        // coarsening depends on A_l only (cached on the finest level)
+        HCsr Nu, Nv, Su, Sv;
+        std::vector<char> cfu, cfv;
+        if (l == 0 && st.have0) {
+            Nu = st.N0u; Nv = st.N0v; Su = st.S0u; Sv = st.S0v; cfu = st.cf0u; cfv = st.cf0v;
+        } else {
+            DCsr Nd;
+            if (sq) {
+                // one C/F splitting and one strength graph (of A) for u and v;
+                // R14's Jacobi step (minimal) still needs A A^t and A^t A
+                HCsr hA;
+                download_csr(L.A, hA, s);
+                strength_of(hA, p.theta, Su);
+                Sv = Su;
+                if (c.minimal()) {
+                    spgemm(L.A, L.At, Nd, s);
+                    download_csr(Nd, Nu, s);
+                    DCsr Nd2;
+                    spgemm(L.At, L.A, Nd2, s);
+                    download_csr(Nd2, Nv, s);
+                }
+            } else if (spd || (st.induced && l > 0)) {
+                download_csr(L.A, Nv, s);
+            } else if (st.induced) {
+                spgemm(L.At, L.A, Nd, s);
+                download_csr(Nd, Nv, s);
+            } else if (c.minimal()) {
+                // minimal SVD kind in the paper's form (Sec. 3.7): rows
+                // coarsened on N_u = A A^t, columns on N_v = A^t A; both
+                // products are formed, since R14's Jacobi step needs them
+                spgemm(L.A, L.At, Nd, s);
+                download_csr(Nd, Nu, s);
+                DCsr Nd2;
+                spgemm(L.At, L.A, Nd2, s);
+                download_csr(Nd2, Nv, s);
+                strength_of(Nu, p.theta, Su);
+                strength_of(Nv, p.theta, Sv);
+            } else {
+                // dominant SVD kind: the strength graphs of A A^t and
+                // A^t A come from A and A^t directly (the LS fits need
+                // no N here, R14 being a minimal-kind step)
+                HCsr hA, hAt;
+                download_csr(L.A, hA, s);
+                download_csr(L.At, hAt, s);
+                strength_product(hA, hAt, p.theta, Su);
+                strength_product(hAt, hA, p.theta, Sv);
+            }
+            if (spd || st.induced) strength_of(Nv, p.theta, Sv);
+            cfv = rs_split(Sv);
+            if (sq) cfu = cfv;
+            else if (!spd && !st.induced) cfu = rs_split(Su);
+            if (l == 0) {
+                st.have0 = true;
+                st.N0u = Nu; st.N0v = Nv; st.S0u = Su; st.S0v = Sv; st.cf0u = cfu; st.cf0v = cfv;
+            }
+        }
+        clk.mark(0);
+        int nc = 0, mc = 0;
+        for (char x : cfv) nc += x;
+        if (spd || st.induced) mc = nc;
+        else for (char x : cfu) mc += x;
+        const int64_t tot_f = spd ? L.n : (int64_t)L.m + L.n;
+        const int64_t tot_c = spd ? nc : (int64_t)mc + nc;
+        if (tot_c > 0.9 * tot_f || std::min(mc, nc) < 2 * c.nb) break;
+        // relaxation of the test and boot vectors
+        relax_test(st, l, ut, vt);
+        clk.mark(1);
+        if (st.induced) {
+            if (l == 0)
+                launch_combine<double, double>(L.m, ldt, nullptr, 0.0,
+                                               Term<double>{view<double>(L.A), vt, 1.0, false},
+                                               Term<double>{}, c.sigma.p, ut, s);
+            else
+                SAMG_CUDA(cudaMemcpyAsync(ut, vt, sizeof(double) * L.n * ldt, cudaMemcpyDeviceToDevice, s));
+        }
+        if (cyc > 0) relax_boot_rq(st, l);
+        clk.mark(2);
+        // LS fit on [test, boot]
+        const int nf = p.n_t + (cyc > 0 ? c.nb : 0);
+        std::vector<double> w(nf);
+        {
+            auto rq = rayleigh(st, l, p.n_t, ldt, ut, spd ? ut : vt);
+            for (int k = 0; k < p.n_t; ++k) w[k] = rq[k];
+            if (cyc > 0) {
+                std::vector<double> sg(c.ld);
+                c.sigma.download(sg.data(), c.ld, s);
+                SAMG_CUDA(cudaStreamSynchronize(s));
+                for (int j = 0; j < c.nb; ++j) w[p.n_t + j] = sg[j];
+            }
+            for (auto &x : w) {
+                double a = std::max(std::fabs(x), 1e-300);
+                x = c.minimal() ? 1.0 / a : a;
+            }
+            // the redo of Sec. 6.3 scales the weights of the test vectors and
+            // of the converged boot vectors
+            if (wscale)
+                for (int k = 0; k < nf; ++k) w[k] *= (*wscale)[k];
+        }
+        auto fit_side = [&](const HCsr &N, const HCsr &S, const std::vector<char> &cf, int rows,
+                            const double *test, const double *boot, HCsr &Pout) {
+            std::vector<double> Y((size_t)rows * nf);
+            fetch(s, test, rows, ldt, p.n_t, Y.data(), nf, 0);
+            if (cyc > 0) fetch(s, boot, rows, c.ld, c.nb, Y.data(), nf, p.n_t);
+            SAMG_CUDA(cudaStreamSynchronize(s));
+            if (c.minimal()) {  // extra Jacobi step on the F values (R14 weight)
+                std::vector<double> YF;
+                jacobi_host(N, Y, nf, p.omega_J * 2.0 / gershgorin(N), YF);
+                ls_interp(S, cf, YF, Y, w, nf, Pout);
+            } else {
+                ls_interp(S, cf, Y, Y, w, nf, Pout);
+            }
+        };
+        HCsr hQ, hP;
+        if (sq == 2) {
+            // P = Q fitted to the u and the v vectors together (weights
+            // repeated), so that B_c = C_c on every level
+            std::vector<double> Y((size_t)L.n * 2 * nf), w2(2 * nf);
+            fetch(s, ut, L.n, ldt, p.n_t, Y.data(), 2 * nf, 0);
+            if (cyc > 0) fetch(s, L.wd.u.p, L.n, c.ld, c.nb, Y.data(), 2 * nf, p.n_t);
+            fetch(s, vt, L.n, ldt, p.n_t, Y.data(), 2 * nf, nf);
+            if (cyc > 0) fetch(s, L.wd.v.p, L.n, c.ld, c.nb, Y.data(), 2 * nf, nf + p.n_t);
+            SAMG_CUDA(cudaStreamSynchronize(s));
+            for (int k = 0; k < nf; ++k) w2[k] = w2[nf + k] = w[k];
+            if (c.minimal()) {  // R14 on each side's F values with its own N
+                std::vector<double> Yu((size_t)L.n * nf), Yv((size_t)L.n * nf), Fu, Fv;
+                for (int i = 0; i < L.n; ++i)
+                    for (int k = 0; k < nf; ++k) {
+                        Yu[(size_t)i * nf + k] = Y[(size_t)i * 2 * nf + k];
+                        Yv[(size_t)i * nf + k] = Y[(size_t)i * 2 * nf + nf + k];
+                    }
+                jacobi_host(Nu, Yu, nf, p.omega_J * 2.0 / gershgorin(Nu), Fu);
+                jacobi_host(Nv, Yv, nf, p.omega_J * 2.0 / gershgorin(Nv), Fv);
+                std::vector<double> YF(Y.size());
+                for (int i = 0; i < L.n; ++i)
+                    for (int k = 0; k < nf; ++k) {
+                        YF[(size_t)i * 2 * nf + k] = Fu[(size_t)i * nf + k];
+                        YF[(size_t)i * 2 * nf + nf + k] = Fv[(size_t)i * nf + k];
+                    }
+                ls_interp(Su, cfu, YF, Y, w2, 2 * nf, hP);
+            } else {
+                ls_interp(Su, cfu, Y, Y, w2, 2 * nf, hP);
+            }
+            upload_csr(hP, L.P, s);
+            upload_csr(hP, L.Q, s);
+        } else if (spd) {
+            fit_side(Nv, Sv, cfv, L.n, ut, L.wd.u.p, hP);
+            upload_csr(hP, L.P, s);
+        } else if (st.induced) {
+            fit_side(Nv, Sv, cfv, L.n, vt, L.wd.v.p, hQ);
+            upload_csr(hQ, L.Q, s);
+            if (l == 0) {
+                spgemm(L.A, L.Q, L.P, s);
+            } else {
+                upload_csr(hQ, L.P, s);
+            }
+        } else {
+            fit_side(Nu, Su, cfu, L.m, ut, L.wd.u.p, hP);
+            fit_side(Nv, Sv, cfv, L.n, vt, L.wd.v.p, hQ);
+            upload_csr(hP, L.P, s);
+            upload_csr(hQ, L.Q, s);
+        }
+        clk.mark(3);
+        // Galerkin operators of level l+1
+        c.L.emplace_back();
+        {
+            Level &Lf = c.L[l];
+            Level &Lc = c.L[l + 1];
+            transpose(Lf.P, Lf.Pt, s);
+            DCsr t1, t2, t3;
+            if (spd) {
+                spgemm(Lf.A, Lf.P, t1, s);
+                spgemm(Lf.Pt, t1, Lc.A, s);
+                if (Lf.B.empty()) spgemm(Lf.Pt, Lf.P, Lc.B, s);
+                else { spgemm(Lf.B, Lf.P, t2, s); spgemm(Lf.Pt, t2, Lc.B, s); }
+            } else {
+                transpose(Lf.Q, Lf.Qt, s);
+                spgemm(Lf.A, Lf.Q, t1, s);
+                spgemm(Lf.Pt, t1, Lc.A, s);
+                if (Lf.B.empty()) spgemm(Lf.Pt, Lf.P, Lc.B, s);
+                else { spgemm(Lf.B, Lf.P, t2, s); spgemm(Lf.Pt, t2, Lc.B, s); }
+                if (Lf.C.empty()) spgemm(Lf.Qt, Lf.Q, Lc.C, s);
+                else { spgemm(Lf.C, Lf.Q, t3, s); spgemm(Lf.Qt, t3, Lc.C, s); }
+            }
+            Lc.m = Lc.A.m;
+            Lc.n = Lc.A.n;
+        }
+        clk.mark(4);
+        prepare_level(c, l + 1);
+        clk.mark(5);
+        // injection of test and boot vectors to level l+1
+        Level &Lf = c.L[l];
+        Level &Lc = c.L[l + 1];
+        st.ut.emplace_back((size_t)(spd ? Lc.n : Lc.m) * ldt);
+        double *utc = st.ut.back().p;
+        double *vtc = nullptr;
+        if (spd) {
+            gather(st, cfv, ldt, ut, utc, nullptr);
+            if (cyc > 0) gather(st, cfv, c.ld, Lf.wd.u.p, Lc.wd.u.p, nullptr);
+        } else {
+            st.vt.emplace_back((size_t)Lc.n * ldt);
+            vtc = st.vt.back().p;
+            gather(st, cfv, ldt, vt, vtc, nullptr);
+            if (st.induced) {
+                // row test vectors are recomputed from vtc on the next level
+                if (cyc > 0) {
+                    if (l == 0) gather(st, cfv, c.ld, Lf.wd.v.p, Lc.wd.u.p, c.sigma.p);
+                    else gather(st, cfv, c.ld, Lf.wd.u.p, Lc.wd.u.p, nullptr);
+                    gather(st, cfv, c.ld, Lf.wd.v.p, Lc.wd.v.p, nullptr);
+                }
+            } else {
+                gather(st, cfu, ldt, ut, utc, nullptr);
+                if (cyc > 0) {
+                    gather(st, cfu, c.ld, Lf.wd.u.p, Lc.wd.u.p, nullptr);
+                    gather(st, cfv, c.ld, Lf.wd.v.p, Lc.wd.v.p, nullptr);
+                }
+            }
+        }
+        ut = utc;
+        vt = vtc;
+        ++l;
+    }
+}
 
-// Charges the wall time since the previous mark to one setup stage, after
-// the stream has drained (samg_setup_times).
-struct StageClock {
-    samg_ctx &c;
-    std::chrono::steady_clock::time_point t;
-    explicit StageClock(samg_ctx &cx) : c(cx), t(std::chrono::steady_clock::now()) {
-        for (double &x : c.setup_s) x = 0.0;
-    }
-    void mark(int stage) {
-        SAMG_CUDA(cudaStreamSynchronize(c.stream));
-        const auto now = std::chrono::steady_clock::now();
-        c.setup_s[stage] += std::chrono::duration<double>(now - t).count();
-        t = now;
-    }
-};
+}  // namespace
 
 void host_setup(samg_ctx &c, const samg_csr &Ah) {
     cudaStream_t s = c.stream;
@@ -572,12 +824,14 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     clk.mark(9);
     prepare_level(c, 0);
     clk.mark(5);
-    SetupState st(c);
+    auto keep = std::make_shared<SetupState>(c);
+    SetupState &st = *keep;
     st.nt = p.n_t;
     st.ldt = block_ld(p.n_t);
     // square SVD kind, Sec. 5.1 (R23): splitting and patterns from A itself
     // (1), or one operator P = Q for both sides (2)
     const int sq = (!spd && Ah.m == Ah.n) ? p.square_form : 0;
+    st.sq = sq;
     st.induced = !spd && c.minimal() && p.row_form == 0 && sq == 0;
     const int m = Ah.m, n = Ah.n, ldt = st.ldt;
     st.ones.alloc(16);
@@ -600,237 +854,7 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     // the fine-level test vectors need schedules of width ldt (same schedules)
     clk.mark(9);
     for (int cyc = 0; cyc < p.n_mult; ++cyc) {
-        c.L.resize(1);
-        int l = 0;
-        double *ut = st.Ut.p, *vt = spd ? nullptr : st.Vt.p;
-        st.ut.clear();
-        st.vt.clear();
-        if (cyc > 0) {
-            Level &L0 = c.L[0];
-            SAMG_CUDA(cudaMemcpyAsync(L0.wd.u.p, c.U.p, c.U.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            if (!spd)
-                SAMG_CUDA(cudaMemcpyAsync(L0.wd.v.p, c.V.p, c.V.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        }
-        for (;;) {
-            Level &L = c.L[l];
-            if (std::max(L.m, L.n) <= p.coarsest_max || (int)c.L.size() >= p.max_levels) break;
-            // coarsening depends on A_l only (cached on the finest level)
-            HCsr Nu, Nv, Su, Sv;
-            std::vector<char> cfu, cfv;
-            if (l == 0 && st.have0) {
-                Nu = st.N0u; Nv = st.N0v; Su = st.S0u; Sv = st.S0v; cfu = st.cf0u; cfv = st.cf0v;
-            } else {
-                DCsr Nd;
-                if (sq) {
-                    // one C/F splitting and one strength graph (of A) for u and v;
-                    // R14's Jacobi step (minimal) still needs A A^t and A^t A
-                    HCsr hA;
-                    download_csr(L.A, hA, s);
-                    strength_of(hA, p.theta, Su);
-                    Sv = Su;
-                    if (c.minimal()) {
-                        spgemm(L.A, L.At, Nd, s);
-                        download_csr(Nd, Nu, s);
-                        DCsr Nd2;
-                        spgemm(L.At, L.A, Nd2, s);
-                        download_csr(Nd2, Nv, s);
-                    }
-                } else if (spd || (st.induced && l > 0)) {
-                    download_csr(L.A, Nv, s);
-                } else if (st.induced) {
-                    spgemm(L.At, L.A, Nd, s);
-                    download_csr(Nd, Nv, s);
-                } else if (c.minimal()) {
-                    // minimal SVD kind in the paper's form (Sec. 3.7): rows
-                    // coarsened on N_u = A A^t, columns on N_v = A^t A; both
-                    // products are formed, since R14's Jacobi step needs them
-                    spgemm(L.A, L.At, Nd, s);
-                    download_csr(Nd, Nu, s);
-                    DCsr Nd2;
-                    spgemm(L.At, L.A, Nd2, s);
-                    download_csr(Nd2, Nv, s);
-                    strength_of(Nu, p.theta, Su);
-                    strength_of(Nv, p.theta, Sv);
-                } else {
-                    // dominant SVD kind: the strength graphs of A A^t and
-                    // A^t A come from A and A^t directly (the LS fits need
-                    // no N here, R14 being a minimal-kind step)
-                    HCsr hA, hAt;
-                    download_csr(L.A, hA, s);
-                    download_csr(L.At, hAt, s);
-                    strength_product(hA, hAt, p.theta, Su);
-                    strength_product(hAt, hA, p.theta, Sv);
-                }
-                if (spd || st.induced) strength_of(Nv, p.theta, Sv);
-                cfv = rs_split(Sv);
-                if (sq) cfu = cfv;
-                else if (!spd && !st.induced) cfu = rs_split(Su);
-                if (l == 0) {
-                    st.have0 = true;
-                    st.N0u = Nu; st.N0v = Nv; st.S0u = Su; st.S0v = Sv; st.cf0u = cfu; st.cf0v = cfv;
-                }
-            }
-            clk.mark(0);
-            int nc = 0, mc = 0;
-            for (char x : cfv) nc += x;
-            if (spd || st.induced) mc = nc;
-            else for (char x : cfu) mc += x;
-            const int64_t tot_f = spd ? L.n : (int64_t)L.m + L.n;
-            const int64_t tot_c = spd ? nc : (int64_t)mc + nc;
-            if (tot_c > 0.9 * tot_f || std::min(mc, nc) < 2 * c.nb) break;
-            // relaxation of the test and boot vectors
-            relax_test(st, l, ut, vt);
-            clk.mark(1);
-            if (st.induced) {
-                if (l == 0)
-                    launch_combine<double, double>(L.m, ldt, nullptr, 0.0,
-                                                   Term<double>{view<double>(L.A), vt, 1.0, false},
-                                                   Term<double>{}, c.sigma.p, ut, s);
-                else
-                    SAMG_CUDA(cudaMemcpyAsync(ut, vt, sizeof(double) * L.n * ldt, cudaMemcpyDeviceToDevice, s));
-            }
-            if (cyc > 0) relax_boot_rq(st, l);
-            clk.mark(2);
-            // LS fit on [test, boot]
-            const int nf = p.n_t + (cyc > 0 ? c.nb : 0);
-            std::vector<double> w(nf);
-            {
-                auto rq = rayleigh(st, l, p.n_t, ldt, ut, spd ? ut : vt);
-                for (int k = 0; k < p.n_t; ++k) w[k] = rq[k];
-                if (cyc > 0) {
-                    std::vector<double> sg(c.ld);
-                    c.sigma.download(sg.data(), c.ld, s);
-                    SAMG_CUDA(cudaStreamSynchronize(s));
-                    for (int j = 0; j < c.nb; ++j) w[p.n_t + j] = sg[j];
-                }
-                for (auto &x : w) {
-                    double a = std::max(std::fabs(x), 1e-300);
-                    x = c.minimal() ? 1.0 / a : a;
-                }
-            }
-            auto fit_side = [&](const HCsr &N, const HCsr &S, const std::vector<char> &cf, int rows,
-                                const double *test, const double *boot, HCsr &Pout) {
-                std::vector<double> Y((size_t)rows * nf);
-                fetch(s, test, rows, ldt, p.n_t, Y.data(), nf, 0);
-                if (cyc > 0) fetch(s, boot, rows, c.ld, c.nb, Y.data(), nf, p.n_t);
-                SAMG_CUDA(cudaStreamSynchronize(s));
-                if (c.minimal()) {  // extra Jacobi step on the F values (R14 weight)
-                    std::vector<double> YF;
-                    jacobi_host(N, Y, nf, p.omega_J * 2.0 / gershgorin(N), YF);
-                    ls_interp(S, cf, YF, Y, w, nf, Pout);
-                } else {
-                    ls_interp(S, cf, Y, Y, w, nf, Pout);
-                }
-            };
-            HCsr hQ, hP;
-            if (sq == 2) {
-                // P = Q fitted to the u and the v vectors together (weights
-                // repeated), so that B_c = C_c on every level
-                std::vector<double> Y((size_t)L.n * 2 * nf), w2(2 * nf);
-                fetch(s, ut, L.n, ldt, p.n_t, Y.data(), 2 * nf, 0);
-                if (cyc > 0) fetch(s, L.wd.u.p, L.n, c.ld, c.nb, Y.data(), 2 * nf, p.n_t);
-                fetch(s, vt, L.n, ldt, p.n_t, Y.data(), 2 * nf, nf);
-                if (cyc > 0) fetch(s, L.wd.v.p, L.n, c.ld, c.nb, Y.data(), 2 * nf, nf + p.n_t);
-                SAMG_CUDA(cudaStreamSynchronize(s));
-                for (int k = 0; k < nf; ++k) w2[k] = w2[nf + k] = w[k];
-                if (c.minimal()) {  // R14 on each side's F values with its own N
-                    std::vector<double> Yu((size_t)L.n * nf), Yv((size_t)L.n * nf), Fu, Fv;
-                    for (int i = 0; i < L.n; ++i)
-                        for (int k = 0; k < nf; ++k) {
-                            Yu[(size_t)i * nf + k] = Y[(size_t)i * 2 * nf + k];
-                            Yv[(size_t)i * nf + k] = Y[(size_t)i * 2 * nf + nf + k];
-                        }
-                    jacobi_host(Nu, Yu, nf, p.omega_J * 2.0 / gershgorin(Nu), Fu);
-                    jacobi_host(Nv, Yv, nf, p.omega_J * 2.0 / gershgorin(Nv), Fv);
-                    std::vector<double> YF(Y.size());
-                    for (int i = 0; i < L.n; ++i)
-                        for (int k = 0; k < nf; ++k) {
-                            YF[(size_t)i * 2 * nf + k] = Fu[(size_t)i * nf + k];
-                            YF[(size_t)i * 2 * nf + nf + k] = Fv[(size_t)i * nf + k];
-                        }
-                    ls_interp(Su, cfu, YF, Y, w2, 2 * nf, hP);
-                } else {
-                    ls_interp(Su, cfu, Y, Y, w2, 2 * nf, hP);
-                }
-                upload_csr(hP, L.P, s);
-                upload_csr(hP, L.Q, s);
-            } else if (spd) {
-                fit_side(Nv, Sv, cfv, L.n, ut, L.wd.u.p, hP);
-                upload_csr(hP, L.P, s);
-            } else if (st.induced) {
-                fit_side(Nv, Sv, cfv, L.n, vt, L.wd.v.p, hQ);
-                upload_csr(hQ, L.Q, s);
-                if (l == 0) {
-                    spgemm(L.A, L.Q, L.P, s);
-                } else {
-                    upload_csr(hQ, L.P, s);
-                }
-            } else {
-                fit_side(Nu, Su, cfu, L.m, ut, L.wd.u.p, hP);
-                fit_side(Nv, Sv, cfv, L.n, vt, L.wd.v.p, hQ);
-                upload_csr(hP, L.P, s);
-                upload_csr(hQ, L.Q, s);
-            }
-            clk.mark(3);
-            // Galerkin operators of level l+1
-            c.L.emplace_back();
-            {
-                Level &Lf = c.L[l];
-                Level &Lc = c.L[l + 1];
-                transpose(Lf.P, Lf.Pt, s);
-                DCsr t1, t2, t3;
-                if (spd) {
-                    spgemm(Lf.A, Lf.P, t1, s);
-                    spgemm(Lf.Pt, t1, Lc.A, s);
-                    if (Lf.B.empty()) spgemm(Lf.Pt, Lf.P, Lc.B, s);
-                    else { spgemm(Lf.B, Lf.P, t2, s); spgemm(Lf.Pt, t2, Lc.B, s); }
-                } else {
-                    transpose(Lf.Q, Lf.Qt, s);
-                    spgemm(Lf.A, Lf.Q, t1, s);
-                    spgemm(Lf.Pt, t1, Lc.A, s);
-                    if (Lf.B.empty()) spgemm(Lf.Pt, Lf.P, Lc.B, s);
-                    else { spgemm(Lf.B, Lf.P, t2, s); spgemm(Lf.Pt, t2, Lc.B, s); }
-                    if (Lf.C.empty()) spgemm(Lf.Qt, Lf.Q, Lc.C, s);
-                    else { spgemm(Lf.C, Lf.Q, t3, s); spgemm(Lf.Qt, t3, Lc.C, s); }
-                }
-                Lc.m = Lc.A.m;
-                Lc.n = Lc.A.n;
-            }
-            clk.mark(4);
-            prepare_level(c, l + 1);
-            clk.mark(5);
-            // injection of test and boot vectors to level l+1
-            Level &Lf = c.L[l];
-            Level &Lc = c.L[l + 1];
-            st.ut.emplace_back((size_t)(spd ? Lc.n : Lc.m) * ldt);
-            double *utc = st.ut.back().p;
-            double *vtc = nullptr;
-            if (spd) {
-                gather(st, cfv, ldt, ut, utc, nullptr);
-                if (cyc > 0) gather(st, cfv, c.ld, Lf.wd.u.p, Lc.wd.u.p, nullptr);
-            } else {
-                st.vt.emplace_back((size_t)Lc.n * ldt);
-                vtc = st.vt.back().p;
-                gather(st, cfv, ldt, vt, vtc, nullptr);
-                if (st.induced) {
-                    // row test vectors are recomputed from vtc on the next level
-                    if (cyc > 0) {
-                        if (l == 0) gather(st, cfv, c.ld, Lf.wd.v.p, Lc.wd.u.p, c.sigma.p);
-                        else gather(st, cfv, c.ld, Lf.wd.u.p, Lc.wd.u.p, nullptr);
-                        gather(st, cfv, c.ld, Lf.wd.v.p, Lc.wd.v.p, nullptr);
-                    }
-                } else {
-                    gather(st, cfu, ldt, ut, utc, nullptr);
-                    if (cyc > 0) {
-                        gather(st, cfu, c.ld, Lf.wd.u.p, Lc.wd.u.p, nullptr);
-                        gather(st, cfv, c.ld, Lf.wd.v.p, Lc.wd.v.p, nullptr);
-                    }
-                }
-            }
-            ut = utc;
-            vt = vtc;
-            ++l;
-        }
+        down_sweep(st, cyc, nullptr, clk);
         SAMG_CHECK(c.L.size() >= 2, SAMG_E_INVALID,
                    "setup produced a single level (problem already at the coarsest size)");
         // coarsest: new boot triplets by a direct solve
@@ -869,6 +893,40 @@ void host_setup(samg_ctx &c, const samg_csr &Ah) {
     }
     ritz(c, true);
     clk.mark(7);
+    SAMG_CUDA(cudaStreamSynchronize(s));
+    st.ut.clear();
+    st.vt.clear();
+    if (p.redo_tol > 0.0) c.setup_keep = keep;
+}
+
+void redo_interpolation(samg_ctx &c, const std::vector<char> &conv) {
+    SAMG_CHECK(c.setup_keep != nullptr, SAMG_E_INVALID,
+               "redo needs the setup phase's state: set redo_tol > 0 before samg_setup "
+               "(an imported hierarchy has none)");
+    SetupState &st = *static_cast<SetupState *>(c.setup_keep.get());
+    cudaStream_t s = c.stream;
+    const int nt = c.prm.n_t;
+    std::vector<double> ws(nt + c.nb, 1.0);
+    for (int k = 0; k < nt; ++k) ws[k] = 1e-3;
+    for (int j = 0; j < c.nb; ++j)
+        if (conv[j]) ws[nt + j] = 1e-3;
+    // the sweep relaxes copies of the boot triplets and updates sigma: the
+    // additive iterate's sigma is restored afterwards
+    std::vector<double> sg(c.ld);
+    c.sigma.download(sg.data(), c.ld, s);
+    SAMG_CUDA(cudaStreamSynchronize(s));
+    StageClock clk(c, false);
+    down_sweep(st, 1, &ws, clk);
+    SAMG_CHECK(c.L.size() >= 2, SAMG_E_INVALID, "redo produced a single level");
+    c.sigma.upload(sg.data(), c.ld, s);
+    finalize_hierarchy(c);
+    share_error_word(c);
+    for (auto &L : c.L) {
+        L.wd.u.zero(s);
+        if (!c.spd()) L.wd.v.zero(s);
+    }
+    st.ut.clear();
+    st.vt.clear();
     SAMG_CUDA(cudaStreamSynchronize(s));
 }
 
