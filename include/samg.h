@@ -426,7 +426,10 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
  * resident_slots = 0 gives the solve's schedule.  resident_slots in
  * [1, 4095] builds, when the program keeps at most that many columns live,
  * one band with every column resident in the window (a mode the solve does
- * not use yet).  Call with buf = NULL (capacity 0) to get *size,
+ * not use yet).  max_bands > 0 widens the bands until there are at most that
+ * many, as far as the window allows (the solve passes its device's SM
+ * count); 0 keeps 32 rows per level.  slot_cap: live columns per band, at
+ * most 4095 (0: 512; the solve uses the largest window its launch holds).  Call with buf = NULL (capacity 0) to get *size,
  * then with a buffer of that many bytes.  Layout, little-endian:
  *   i32 rows, cols, nbands, nlevels, nchunks, max_slots, mode, shifted;
  *   i64 nreq, image_bytes;
@@ -448,7 +451,8 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
  * have completed} (2 x i32, nq of them).  Returns SAMG_E_INVALID for a
  * malformed CSR or a short buffer. */
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
-                                int fused_count, int spd, int resident_slots, unsigned char *buf,
+                                int fused_count, int spd, int resident_slots, int max_bands,
+                                int slot_cap, unsigned char *buf,
                                 int64_t capacity, int64_t *size);
 
 /* Test hook for the bounded device waits (the paper has no counterpart):

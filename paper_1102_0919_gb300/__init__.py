@@ -103,7 +103,7 @@ samg_write_hierarchy = _sig("samg_write_hierarchy", _I, ctypes.c_char_p, _P, _I,
                             _P, _P, _P)
 samg_import_file = _sig("samg_import_file", _I, ctypes.c_char_p, _P, ctypes.c_void_p,
                         ctypes.POINTER(_CTX))
-samg_sweep_schedule = _sig("samg_sweep_schedule", _I, _P, _P, _P, _I, _I, _I, _P, ctypes.c_int64,
+samg_sweep_schedule = _sig("samg_sweep_schedule", _I, _P, _P, _P, _I, _I, _I, _I, _I, _P, ctypes.c_int64,
                            ctypes.POINTER(ctypes.c_int64))
 samg_host_strength_product = _sig("samg_host_strength_product", _I, _P, ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_int64), _P, _P, _P)
@@ -471,15 +471,19 @@ def sweep_plan(A, fused_count=0):
     return lv[:rows], d.value, nb.value
 
 
-def sweep_schedule(A, fused_count=0, spd=False, B=None, C=None, resident_slots=0):
+def sweep_schedule(A, fused_count=0, spd=False, B=None, C=None, resident_slots=0, max_bands=0,
+                   slot_cap=0):
     """Host-only: the serialized sweep schedule (bytes) the kernels receive
     (B, C: the level's operators; None = identity; resident_slots > 0: one
-    resident band when the program keeps at most that many columns live)."""
+    resident band when the program keeps at most that many columns live;
+    max_bands > 0: bands widened to at most that many where the window
+    allows; slot_cap: live columns per band, 0 = 512)."""
     c = _csr(A)
     cb = None if B is None else _csr(B)
     cc = None if C is None else _csr(C)
     args = (ctypes.byref(c), None if cb is None else ctypes.byref(cb),
-            None if cc is None else ctypes.byref(cc), fused_count, int(spd), int(resident_slots))
+            None if cc is None else ctypes.byref(cc), fused_count, int(spd), int(resident_slots),
+            int(max_bands), int(slot_cap))
     size = ctypes.c_int64(0)
     st = samg_sweep_schedule(*args, None, 0, ctypes.byref(size))
     if st != OK:

@@ -521,13 +521,17 @@ samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_
                         ctx->L[l].kAt.nlevels, ctx->L[l].kAt.nchunks);
         if (std::getenv("SAMG_PROFILE_LEVELS") && kernel_class == 0)
             for (int l = 0; l < ctx->nlev(); ++l)
-                for (size_t k = 0; k < ctx->L[l].kF.size(); ++k) {
-                    const KSched &f = ctx->L[l].kF[k];
-                    if (f.rows)
-                        fprintf(stderr, "[samg] level %d fused program of %zu relaxations: rows %d"
-                                " bands %d levels %d chunks %d reqs %lld slots %d\n",
-                                l, k, f.rows, f.nbands, f.nlevels, f.nchunks, (long long)f.req.n,
-                                f.max_slots);
+                for (int wide = 1; wide >= 0; --wide) {
+                    const std::vector<KSched> &progs = wide ? ctx->L[l].kF : ctx->L[l].kF4;
+                    for (size_t k = 0; k < progs.size(); ++k) {
+                        const KSched &f = progs[k];
+                        if (f.rows)
+                            fprintf(stderr, "[samg] level %d fused program of %zu relaxations (%s"
+                                    " windows): rows %d bands %d levels %d chunks %d reqs %lld"
+                                    " slots %d\n",
+                                    l, k, wide ? "float64" : "float32", f.rows, f.nbands, f.nlevels,
+                                    f.nchunks, (long long)f.req.n, f.max_slots);
+                    }
                 }
         if (launches) *launches = ctx->prof.launches[kernel_class];
         if (total_ms) *total_ms = ctx->prof.ms[kernel_class];
@@ -1011,7 +1015,8 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
 }
 
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
-                                int fused_count, int spd, int resident_slots, unsigned char *buf,
+                                int fused_count, int spd, int resident_slots, int max_bands,
+                                int slot_cap, unsigned char *buf,
                                 int64_t capacity, int64_t *size) {
     try {
         SAMG_CHECK(fused_count >= 0 && size && (capacity == 0 || buf), SAMG_E_INVALID,
@@ -1028,7 +1033,7 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
         }
         HostSched hs;
         host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs,
-                      resident_slots);
+                      resident_slots, max_bands, slot_cap);
         std::vector<unsigned char> out;
         out.reserve(64 + 4 * hs.band_chunk.size() + 40 * hs.chunk.size() + 16 * hs.lvl.size() +
                     8 * hs.req.size() + hs.img_d.size());
@@ -1084,8 +1089,9 @@ samg_status samg_debug_mute_band(samg_ctx *ctx, int level, int which, int band) 
         if (which < 2) {
             kaczmarz_mute_band(which == 0 ? L.kA : L.kAt, band, ctx->stream);
         } else {
-            for (KSched &k : L.kF)
-                if (k.rows) kaczmarz_mute_band(k, band, ctx->stream);
+            for (auto *progs : {&L.kF, &L.kF4})
+                for (KSched &k : *progs)
+                    if (k.rows) kaczmarz_mute_band(k, band, ctx->stream);
         }
     });
 }

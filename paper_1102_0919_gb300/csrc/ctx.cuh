@@ -30,6 +30,7 @@ struct Level {
     DCsr P, Pt, Q, Qt;          // empty on the coarsest level
     KSched kA, kAt;             // Kaczmarz schedules (minimal target)
     std::vector<KSched> kF;     // fused programs of `count` relaxations, by count
+    std::vector<KSched> kF4;    // the same with float32-only windows (float32, bfloat16)
     std::vector<CSched> kC;     // their coloured-order variants, by count
     DBuf<double> dBd, dCd;      // diagonals of B, C (dominant target)
     DBuf<float> dBf, dCf;

@@ -171,21 +171,25 @@ void relax_phase(samg_ctx &c, int l, int count) {
         relax_phase_coloured<T>(c, l, count);
         return;
     }
-    if ((int)L.kF.size() <= count) L.kF.resize(count + 1);
-    KSched &ks = L.kF[count];
+    // float64 launches need float64 windows; float32 and bfloat16 storage
+    // arithmetic in float32, whose windows hold twice the columns
+    const bool wide = sizeof(typename Acc<T>::T) == 8;
+    std::vector<KSched> &progs = wide ? L.kF : L.kF4;
+    if ((int)progs.size() <= count) progs.resize(count + 1);
+    KSched &ks = progs[count];
     if (ks.rows == 0) {
         HCsr hA, hB;
         download_csr(L.A, hA, s);
         if (L.B.empty()) csr_identity(c.spd() ? L.n : L.m, hB);
         else download_csr(L.B, hB, s);
         if (c.spd()) {
-            build_kschedule_stacked(hA, hB, count, ks, s, ld);
+            build_kschedule_stacked(hA, hB, count, ks, s, ld, wide);
         } else {
             HCsr hAt, hC;
             download_csr(L.At, hAt, s);
             if (L.C.empty()) csr_identity(L.n, hC);
             else download_csr(L.C, hC, s);
-            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld);
+            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld, wide);
         }
         if (c.rstat.n >= 2) ks.err = c.rstat.p + 1;
     }

@@ -16,7 +16,7 @@ constexpr int KZ_THREADS = 512;
 constexpr int KZ_COMPUTE = 480;    // compute threads (15 warps); warp 15 stages, polls, publishes
 constexpr int KZ_NBUF = 3;          // staging buffers (the producer runs up to 2 chunks ahead)
 constexpr int TARGET_PAR = 32;       // wanted rows per level inside a band
-constexpr int MAX_BAND_ROWS = 1 << 17;
+constexpr int MAX_BAND_ROWS = 1 << 21;
 constexpr int SLOT_CAP = 512;        // window slots: 512 * 16 cols * 8 B = 64 KiB
 // staging chunk limits: levels, rows, entries, staged first values,
 // cross-band requirements carried in the image
@@ -940,19 +940,12 @@ int write_image(std::vector<unsigned char> &img, bool shifted, const std::vector
 namespace {
 
 // Contiguous bands of rows, each grown (doubling) until it has about
-// TARGET_PAR rows per level, at most MAX_BAND_ROWS rows, and at most SLOT_CAP
+// `target` rows per level, at most MAX_BAND_ROWS rows, and at most slot_cap
 // columns live at once.  Returns the first row of every band, then p.rows.
-// resident_cap > 0: when the whole program keeps at most that many columns
-// live, it is one band (every column resident in the window; no cross-band
-// requirement and no first touch written by another band).
-std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w,
-                            int resident_cap = 0, int slot_cap = SLOT_CAP) {
+std::vector<int> form_bands_at(const Pattern &p, const std::vector<int> &glv, BandWork &w,
+                               int slot_cap, int target) {
     std::vector<int> bstart;
     int slots = 0;
-    if (resident_cap > 0 && p.rows > 0) {
-        analyze_band(p, glv, 0, p.rows, w, &slots);
-        if (slots <= resident_cap) return {0, p.rows};
-    }
     for (int r0 = 0; r0 < p.rows;) {
         int R = std::min(256, p.rows - r0), good = 0;
         for (;;) {
@@ -964,7 +957,7 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
                 continue;
             }
             good = R;
-            if (r0 + R >= p.rows || R >= MAX_BAND_ROWS || (R / std::max(nl, 1)) >= TARGET_PAR) break;
+            if (r0 + R >= p.rows || R >= MAX_BAND_ROWS || (R / std::max(nl, 1)) >= target) break;
             R = std::min(2 * R, p.rows - r0);
         }
         bstart.push_back(r0);
@@ -974,12 +967,45 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
     return bstart;
 }
 
+// The bands of a program: TARGET_PAR rows per level, unless that gives more
+// bands than max_bands (> 0), the CTAs that run at once.  Every band of a
+// fused program is live over most of its depth (the relaxations follow one
+// another a few levels apart), so bands beyond the resident CTAs would wait
+// for whole bands to finish and repeat the program's depth.  The rows wanted
+// per level then rise, first to 1.25 x the program's mean rows per global
+// level over max_bands, then doubling, while that lowers the band count (a
+// band whose live columns fill the window cannot grow).
+// resident_cap > 0: when the whole program keeps at most that many columns
+// live, it is one band (every column resident in the window; no cross-band
+// requirement and no first touch written by another band).
+std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w,
+                            int resident_cap = 0, int slot_cap = SLOT_CAP, int max_bands = 0) {
+    int slots = 0;
+    if (resident_cap > 0 && p.rows > 0) {
+        analyze_band(p, glv, 0, p.rows, w, &slots);
+        if (slots <= resident_cap) return {0, p.rows};
+    }
+    std::vector<int> best = form_bands_at(p, glv, w, slot_cap, TARGET_PAR);
+    if (max_bands <= 0 || (int)best.size() - 1 <= max_bands || p.rows == 0) return best;
+    int depth = 1;
+    for (int v : glv) depth = std::max(depth, v + 1);
+    const double per_level = (double)p.rows / depth;
+    int t = std::max(2 * TARGET_PAR, (int)std::ceil(1.25 * per_level / max_bands));
+    for (int it = 0; it < 6 && (int)best.size() - 1 > max_bands; ++it) {
+        std::vector<int> b = form_bands_at(p, glv, w, slot_cap, t);
+        if (b.size() >= best.size()) break;
+        best.swap(b);
+        t *= 2;
+    }
+    return best;
+}
+
 // Schedule of one sweep program (rows in program order).  mode: 0 plain rows
 // of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
 // block Gauss-Seidel relaxations (b entries read the other unknown with
 // coefficient -s_j and are not updated; norms from a).
 void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
-                int slot_cap = SLOT_CAP) {
+                int slot_cap = SLOT_CAP, int max_bands = 0) {
     const int rows = p.rows, cols = p.cols;
     ks.rows = rows;
     ks.cols = cols;
@@ -988,7 +1014,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
     BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
-    std::vector<int> bstart = form_bands(p, glv, w, resident_cap, slot_cap);
+    std::vector<int> bstart = form_bands(p, glv, w, resident_cap, slot_cap, max_bands);
     const int nb = (int)bstart.size() - 1;
     int slots = 0;
     ks.nbands = nb;
@@ -1230,9 +1256,9 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
 }
 
 void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s,
-                        int slot_cap = SLOT_CAP) {
+                        int slot_cap = SLOT_CAP, int max_bands = 0) {
     HostSched h;
-    build_host(p, mode, h, 0, slot_cap);
+    build_host(p, mode, h, 0, slot_cap, max_bands);
     ks.rows = h.rows;
     ks.cols = h.cols;
     ks.shifted = h.shifted;
@@ -1281,16 +1307,19 @@ constexpr size_t smem_bytes(int slots) {
            (size_t)KZ_NBUF * Stage<T, S, LD, SHIFT>::stride;
 }
 template <int LD, bool SHIFT>
-int window_cap_ld() {
-    // the most window slots every storage type's launch can hold in 227 KB,
-    // less 2 KB for the kernel's static shared memory
+int window_cap_ld(bool wide) {
+    // the most window slots the launches of every storage type that uses the
+    // schedule can hold in 227 KB, less 2 KB for the kernel's static shared
+    // memory: float64 windows (wide), and float32 windows (float32 and
+    // bfloat16 storage)
     constexpr size_t budget = 227u * 1024u - 2048u;
     int cap = 4095;
     auto fit = [&](size_t per_slot, size_t fixed) {
         const long long n = ((long long)budget - (long long)fixed - 128) / (long long)per_slot - 1;
         cap = std::min<long long>(cap, n);
     };
-    fit((size_t)LD * sizeof(double), smem_bytes<double, double, LD, SHIFT>(0) - LD * sizeof(double));
+    if (wide)
+        fit((size_t)LD * sizeof(double), smem_bytes<double, double, LD, SHIFT>(0) - LD * sizeof(double));
     fit((size_t)LD * sizeof(float), smem_bytes<float, float, LD, SHIFT>(0) - LD * sizeof(float));
     fit((size_t)LD * sizeof(float), smem_bytes<float, bf16, LD, SHIFT>(0) - LD * sizeof(float));
     return std::max(cap, SLOT_CAP);
@@ -1298,15 +1327,22 @@ int window_cap_ld() {
 
 }  // namespace
 
-int kz_window_cap(int ld, int mode) {
+int kz_window_cap(int ld, int mode, bool wide) {
     const bool shift = mode != 0;
     switch (ld) {
-        case 4: return shift ? window_cap_ld<4, true>() : window_cap_ld<4, false>();
-        case 8: return shift ? window_cap_ld<8, true>() : window_cap_ld<8, false>();
-        case 12: return shift ? window_cap_ld<12, true>() : window_cap_ld<12, false>();
-        case 16: return shift ? window_cap_ld<16, true>() : window_cap_ld<16, false>();
+        case 4: return shift ? window_cap_ld<4, true>(wide) : window_cap_ld<4, false>(wide);
+        case 8: return shift ? window_cap_ld<8, true>(wide) : window_cap_ld<8, false>(wide);
+        case 12: return shift ? window_cap_ld<12, true>(wide) : window_cap_ld<12, false>(wide);
+        case 16: return shift ? window_cap_ld<16, true>(wide) : window_cap_ld<16, false>(wide);
         default: return SLOT_CAP;
     }
+}
+
+int kz_device_ctas() {
+    int dev = 0, nsm = 0;
+    SAMG_CUDA(cudaGetDevice(&dev));
+    SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    return std::max(nsm, 1);
 }
 
 void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
@@ -1339,8 +1375,9 @@ Pattern stacked_pattern(const HCsr &A, const HCsr &B, int count) {
 }  // namespace
 
 void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s,
-                             int ld) {
-    build_from_pattern(stacked_pattern(A, B, count), 1, ks, s, kz_window_cap(ld, 1));
+                             int ld, bool wide) {
+    build_from_pattern(stacked_pattern(A, B, count), 1, ks, s, kz_window_cap(ld, 1, wide),
+                       kz_device_ctas());
 }
 
 namespace {
@@ -1405,8 +1442,9 @@ HCsr transpose_csr(const HCsr &A) {
 }  // namespace
 
 void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
-                           KSched &ks, cudaStream_t s, int ld) {
-    build_from_pattern(fused_pattern(A, At, B, C, count), 2, ks, s, kz_window_cap(ld, 2));
+                           KSched &ks, cudaStream_t s, int ld, bool wide) {
+    build_from_pattern(fused_pattern(A, At, B, C, count), 2, ks, s, kz_window_cap(ld, 2, wide),
+                       kz_device_ctas());
 }
 
 namespace {
@@ -1422,18 +1460,22 @@ Pattern sweep_pattern(const HCsr &A, int fused_count) {
 }  // namespace
 
 void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
-                   HostSched &h, int resident_cap) {
+                   HostSched &h, int resident_cap, int max_bands, int slot_cap) {
     SAMG_CHECK(resident_cap >= 0 && resident_cap <= 4095, SAMG_E_INVALID,
                "kaczmarz: resident window larger than the slot field (4095)");
+    SAMG_CHECK(max_bands >= 0 && slot_cap >= 0 && slot_cap <= 4095, SAMG_E_INVALID,
+               "kaczmarz: max_bands < 0, or a window outside the slot field (0..4095)");
+    if (slot_cap == 0) slot_cap = SLOT_CAP;
     if (spd) {
         const HCsr I = B ? HCsr() : identity_csr(A.m);
-        build_host(stacked_pattern(A, B ? *B : I, std::max(1, fused_count)), 1, h, resident_cap);
+        build_host(stacked_pattern(A, B ? *B : I, std::max(1, fused_count)), 1, h, resident_cap,
+                   slot_cap, max_bands);
     } else if (fused_count <= 0) {
-        build_host(merge_pattern(A, nullptr), 0, h, resident_cap);
+        build_host(merge_pattern(A, nullptr), 0, h, resident_cap, slot_cap, max_bands);
     } else {
         const HCsr Im = B ? HCsr() : identity_csr(A.m), In = C ? HCsr() : identity_csr(A.n);
         build_host(fused_pattern(A, transpose_csr(A), B ? *B : Im, C ? *C : In, fused_count), 2, h,
-                   resident_cap);
+                   resident_cap, slot_cap, max_bands);
     }
 }
 

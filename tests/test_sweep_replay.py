@@ -164,6 +164,54 @@ def test_coarse_level_programs_with_galerkin_b_and_c(kind):
             assert rel(got, ref) < 1e-10, rel(got, ref)
 
 
+@pytest.mark.parametrize("max_bands,slot_cap", [(4, 0), (6, 2700), (2, 64)])
+def test_bands_widened_to_the_resident_ctas_replay_block_gauss_seidel(max_bands, slot_cap):
+    # the solve bands a smoothing program with at most as many bands as the
+    # device runs CTAs at once, where the window allows: wider bands (more
+    # rows per level, longer sub-level lists) replay the same relaxations;
+    # a small window (64 columns) keeps more bands than asked for
+    A = W.gradient(96).to_scipy()
+    m, n = A.shape
+    count = 4
+    plain = parse(samg.sweep_schedule(A, count))
+    S = parse(samg.sweep_schedule(A, count, max_bands=max_bands, slot_cap=slot_cap))
+    if slot_cap == 2700:
+        assert S["nbands"] <= max_bands < plain["nbands"], (S["nbands"], plain["nbands"])
+    elif slot_cap == 0:
+        # the 512-column window stops the widening early
+        assert max_bands < S["nbands"] < plain["nbands"], (S["nbands"], plain["nbands"])
+    else:
+        assert S["nbands"] > max_bands
+    rng = np.random.default_rng(max_bands)
+    sig = np.linspace(3.0, 9.0, 8)
+    U, V = rng.standard_normal((m, 8)), rng.standard_normal((n, 8))
+    K, T = rng.standard_normal((m, 8)), rng.standard_normal((n, 8))
+    z = replay(S, np.vstack([V, U]), np.vstack([K, T]), sig)
+    L0 = oracle.Level(A, sp.identity(m, format="csr"), sp.identity(n, format="csr"))
+    Ur, Vr = U.copy(), V.copy()
+    for _ in range(count):
+        oracle.relax_boot(L0, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+    assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10
+
+
+def test_widened_bands_on_a_galerkin_level():
+    A = W.gradient(40).to_scipy()
+    H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(W.GRAD_PARAMS, seed=4, n_mult=2))
+    L = H.levels[1]
+    m, n = L.A.shape
+    nb = len(s)
+    rng = np.random.default_rng(8)
+    sig = np.abs(s) * (1 + 0.01 * rng.standard_normal(nb))
+    S = parse(samg.sweep_schedule(L.A, 3, B=L.B, C=L.C, max_bands=2, slot_cap=2700))
+    Uc, Vc = rng.standard_normal((m, nb)), rng.standard_normal((n, nb))
+    K, T = rng.standard_normal((m, nb)), rng.standard_normal((n, nb))
+    z = replay(S, np.vstack([Vc, Uc]), np.vstack([K, T]), sig)
+    Ur, Vr = Uc.copy(), Vc.copy()
+    for _ in range(3):
+        oracle.relax_boot(L, False, "minimal", sig, Ur, Vr, K, T, 0.7)
+    assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10
+
+
 def test_empty_rows_and_a_single_row():
     # rows without entries leave x unchanged; a one-row program is one level
     A = sp.csr_matrix(np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 0.0], [0.0, 0.0, 0.0],
