@@ -282,6 +282,16 @@ samg_status samg_set_coarse_pinv(samg_ctx *ctx, int form);
  * unchanged; each order's sweep programs are built on first use. */
 samg_status samg_set_relax_order(samg_ctx *ctx, int order);
 
+/* Banding of the exact-order sweep programs of the smoothing phases (a
+ * tuning of the parallel schedule; the sweeps' results do not depend on it
+ * beyond rounding order inside a row): a band of rows grows until it has
+ * about band_rows rows per dependency level (1..4096; default 32) or its
+ * live columns fill the shared-memory window; float_windows = 1 (default)
+ * gives float32 and bfloat16 launches programs banded with float32-only
+ * windows, 0 shares the float64 programs.  The programs are rebuilt on
+ * first use.  SAMG_E_INVALID for values out of range. */
+samg_status samg_set_sweep_banding(samg_ctx *ctx, int band_rows, int float_windows);
+
 /* Kernel timing: with profiling on, every launch of the solve phase is
  * bracketed by CUDA events on the context's stream.  samg_profile_read
  * returns, for one kernel class (0 Kaczmarz sweep, 1 block SpMM pass
@@ -426,10 +436,9 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
  * resident_slots = 0 gives the solve's schedule.  resident_slots in
  * [1, 4095] builds, when the program keeps at most that many columns live,
  * one band with every column resident in the window (a mode the solve does
- * not use yet).  max_bands > 0 widens the bands until there are at most that
- * many, as far as the window allows (the solve passes its device's SM
- * count); 0 keeps 32 rows per level.  slot_cap: live columns per band, at
- * most 4095 (0: 512; the solve uses the largest window its launch holds).  Call with buf = NULL (capacity 0) to get *size,
+ * not use yet).  band_rows: rows per level a band grows to (0: 32, the
+ * solve's default).  slot_cap: live columns per band, at most 4095 (0: 512;
+ * the solve uses the largest window its launch holds).  Call with buf = NULL (capacity 0) to get *size,
  * then with a buffer of that many bytes.  Layout, little-endian:
  *   i32 rows, cols, nbands, nlevels, nchunks, max_slots, mode, shifted;
  *   i64 nreq, image_bytes;
@@ -451,7 +460,7 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
  * have completed} (2 x i32, nq of them).  Returns SAMG_E_INVALID for a
  * malformed CSR or a short buffer. */
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
-                                int fused_count, int spd, int resident_slots, int max_bands,
+                                int fused_count, int spd, int resident_slots, int band_rows,
                                 int slot_cap, unsigned char *buf,
                                 int64_t capacity, int64_t *size);
 

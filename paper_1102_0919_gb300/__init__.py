@@ -118,6 +118,7 @@ samg_launch_count = _sig("samg_launch_count", ctypes.c_uint64)
 samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
 samg_redo_interpolation = _sig("samg_redo_interpolation", _I, _CTX, _P)
+samg_set_sweep_banding = _sig("samg_set_sweep_banding", _I, _CTX, _I, _I)
 samg_setup_times = _sig("samg_setup_times", _I, _CTX, _P, ctypes.c_int32)
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
@@ -132,7 +133,7 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_import_file", "samg_sweep_schedule", "samg_setup_batched",
             "samg_solve_batched", "samg_batch_problem", "samg_batch_size",
             "samg_batch_last_error", "samg_batch_destroy", "samg_row_colours",
-            "samg_setup_times", "samg_redo_interpolation"]
+            "samg_setup_times", "samg_redo_interpolation", "samg_set_sweep_banding"]
 
 
 def _arr(x, dtype):
@@ -323,6 +324,11 @@ class Solver:
         self._check(samg_get_triplets(self._ctx, None, None, None, _ptr(r)))
         return r
 
+    def set_sweep_banding(self, band_rows=32, float_windows=True):
+        """Rows per dependency level a sweep band grows to, and whether
+        float32 launches use programs with float32-only windows."""
+        self._check(samg_set_sweep_banding(self._ctx, int(band_rows), int(bool(float_windows))))
+
     def set_relax_order(self, order):
         """"natural" (0, the paper's) or "coloured" (1, the variant)."""
         self._check(samg_set_relax_order(self._ctx, {"natural": 0, "coloured": 1}.get(order, order)))
@@ -471,19 +477,19 @@ def sweep_plan(A, fused_count=0):
     return lv[:rows], d.value, nb.value
 
 
-def sweep_schedule(A, fused_count=0, spd=False, B=None, C=None, resident_slots=0, max_bands=0,
+def sweep_schedule(A, fused_count=0, spd=False, B=None, C=None, resident_slots=0, band_rows=0,
                    slot_cap=0):
     """Host-only: the serialized sweep schedule (bytes) the kernels receive
     (B, C: the level's operators; None = identity; resident_slots > 0: one
     resident band when the program keeps at most that many columns live;
-    max_bands > 0: bands widened to at most that many where the window
-    allows; slot_cap: live columns per band, 0 = 512)."""
+    band_rows: rows per level a band grows to, 0 = 32; slot_cap: live
+    columns per band, 0 = 512)."""
     c = _csr(A)
     cb = None if B is None else _csr(B)
     cc = None if C is None else _csr(C)
     args = (ctypes.byref(c), None if cb is None else ctypes.byref(cb),
             None if cc is None else ctypes.byref(cc), fused_count, int(spd), int(resident_slots),
-            int(max_bands), int(slot_cap))
+            int(band_rows), int(slot_cap))
     size = ctypes.c_int64(0)
     st = samg_sweep_schedule(*args, None, 0, ctypes.byref(size))
     if st != OK:

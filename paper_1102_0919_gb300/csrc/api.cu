@@ -570,6 +570,20 @@ samg_status samg_set_relax_order(samg_ctx *ctx, int order) {
     });
 }
 
+samg_status samg_set_sweep_banding(samg_ctx *ctx, int band_rows, int float_windows) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(band_rows >= 1 && band_rows <= 4096 && (float_windows == 0 || float_windows == 1),
+                   SAMG_E_INVALID, "sweep banding: band_rows in 1..4096, float_windows 0 or 1");
+        ctx->band_rows = band_rows;
+        ctx->float_windows = float_windows != 0;
+        for (Level &L : ctx->L) {
+            L.kF.clear();
+            L.kF4.clear();
+        }
+    });
+}
+
 samg_status samg_set_coarse_pinv(samg_ctx *ctx, int form) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {
@@ -1015,7 +1029,7 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
 }
 
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
-                                int fused_count, int spd, int resident_slots, int max_bands,
+                                int fused_count, int spd, int resident_slots, int band_rows,
                                 int slot_cap, unsigned char *buf,
                                 int64_t capacity, int64_t *size) {
     try {
@@ -1033,7 +1047,7 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
         }
         HostSched hs;
         host_schedule(h, B ? &hb : nullptr, C ? &hc : nullptr, fused_count, spd != 0, hs,
-                      resident_slots, max_bands, slot_cap);
+                      resident_slots, band_rows, slot_cap);
         std::vector<unsigned char> out;
         out.reserve(64 + 4 * hs.band_chunk.size() + 40 * hs.chunk.size() + 16 * hs.lvl.size() +
                     8 * hs.req.size() + hs.img_d.size());

@@ -129,6 +129,11 @@ struct samg_ctx {
     samg::DBuf<double> AV, AtU, Un, Vn, GU, GV, H, TU, TV, gwork, partu, partv;
     samg::DBuf<int> rstat;
     samg::Profiler prof;
+    // banding of the smoothing phases' sweep programs (samg_set_sweep_banding):
+    // rows per level a band grows to, and whether float32 launches get
+    // programs with float32-only windows
+    int band_rows = 32;
+    bool float_windows = true;
     // wall seconds of the setup phase's stages (samg_setup_times)
     double setup_s[SAMG_SETUP_STAGES] = {};
     // the setup phase's state (fine test vectors, finest coarsening), kept

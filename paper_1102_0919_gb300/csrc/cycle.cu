@@ -173,7 +173,7 @@ void relax_phase(samg_ctx &c, int l, int count) {
     }
     // float64 launches need float64 windows; float32 and bfloat16 storage
     // arithmetic in float32, whose windows hold twice the columns
-    const bool wide = sizeof(typename Acc<T>::T) == 8;
+    const bool wide = sizeof(typename Acc<T>::T) == 8 || !c.float_windows;
     std::vector<KSched> &progs = wide ? L.kF : L.kF4;
     if ((int)progs.size() <= count) progs.resize(count + 1);
     KSched &ks = progs[count];
@@ -183,13 +183,13 @@ void relax_phase(samg_ctx &c, int l, int count) {
         if (L.B.empty()) csr_identity(c.spd() ? L.n : L.m, hB);
         else download_csr(L.B, hB, s);
         if (c.spd()) {
-            build_kschedule_stacked(hA, hB, count, ks, s, ld, wide);
+            build_kschedule_stacked(hA, hB, count, ks, s, ld, wide, c.band_rows);
         } else {
             HCsr hAt, hC;
             download_csr(L.At, hAt, s);
             if (L.C.empty()) csr_identity(L.n, hC);
             else download_csr(L.C, hC, s);
-            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld, wide);
+            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld, wide, c.band_rows);
         }
         if (c.rstat.n >= 2) ks.err = c.rstat.p + 1;
     }

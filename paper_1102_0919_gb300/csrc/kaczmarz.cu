@@ -967,37 +967,18 @@ std::vector<int> form_bands_at(const Pattern &p, const std::vector<int> &glv, Ba
     return bstart;
 }
 
-// The bands of a program: TARGET_PAR rows per level, unless that gives more
-// bands than max_bands (> 0), the CTAs that run at once.  Every band of a
-// fused program is live over most of its depth (the relaxations follow one
-// another a few levels apart), so bands beyond the resident CTAs would wait
-// for whole bands to finish and repeat the program's depth.  The rows wanted
-// per level then rise, first to 1.25 x the program's mean rows per global
-// level over max_bands, then doubling, while that lowers the band count (a
-// band whose live columns fill the window cannot grow).
 // resident_cap > 0: when the whole program keeps at most that many columns
 // live, it is one band (every column resident in the window; no cross-band
-// requirement and no first touch written by another band).
+// requirement and no first touch written by another band).  Otherwise bands
+// of about band_rows rows per level (0: TARGET_PAR).
 std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandWork &w,
-                            int resident_cap = 0, int slot_cap = SLOT_CAP, int max_bands = 0) {
+                            int resident_cap = 0, int slot_cap = SLOT_CAP, int band_rows = 0) {
     int slots = 0;
     if (resident_cap > 0 && p.rows > 0) {
         analyze_band(p, glv, 0, p.rows, w, &slots);
         if (slots <= resident_cap) return {0, p.rows};
     }
-    std::vector<int> best = form_bands_at(p, glv, w, slot_cap, TARGET_PAR);
-    if (max_bands <= 0 || (int)best.size() - 1 <= max_bands || p.rows == 0) return best;
-    int depth = 1;
-    for (int v : glv) depth = std::max(depth, v + 1);
-    const double per_level = (double)p.rows / depth;
-    int t = std::max(2 * TARGET_PAR, (int)std::ceil(1.25 * per_level / max_bands));
-    for (int it = 0; it < 6 && (int)best.size() - 1 > max_bands; ++it) {
-        std::vector<int> b = form_bands_at(p, glv, w, slot_cap, t);
-        if (b.size() >= best.size()) break;
-        best.swap(b);
-        t *= 2;
-    }
-    return best;
+    return form_bands_at(p, glv, w, slot_cap, band_rows > 0 ? band_rows : TARGET_PAR);
 }
 
 // Schedule of one sweep program (rows in program order).  mode: 0 plain rows
@@ -1005,7 +986,7 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
 // block Gauss-Seidel relaxations (b entries read the other unknown with
 // coefficient -s_j and are not updated; norms from a).
 void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
-                int slot_cap = SLOT_CAP, int max_bands = 0) {
+                int slot_cap = SLOT_CAP, int band_rows = 0) {
     const int rows = p.rows, cols = p.cols;
     ks.rows = rows;
     ks.cols = cols;
@@ -1014,7 +995,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
     BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
     // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
-    std::vector<int> bstart = form_bands(p, glv, w, resident_cap, slot_cap, max_bands);
+    std::vector<int> bstart = form_bands(p, glv, w, resident_cap, slot_cap, band_rows);
     const int nb = (int)bstart.size() - 1;
     int slots = 0;
     ks.nbands = nb;
@@ -1256,9 +1237,9 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
 }
 
 void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s,
-                        int slot_cap = SLOT_CAP, int max_bands = 0) {
+                        int slot_cap = SLOT_CAP, int band_rows = 0) {
     HostSched h;
-    build_host(p, mode, h, 0, slot_cap, max_bands);
+    build_host(p, mode, h, 0, slot_cap, band_rows);
     ks.rows = h.rows;
     ks.cols = h.cols;
     ks.shifted = h.shifted;
@@ -1338,12 +1319,6 @@ int kz_window_cap(int ld, int mode, bool wide) {
     }
 }
 
-int kz_device_ctas() {
-    int dev = 0, nsm = 0;
-    SAMG_CUDA(cudaGetDevice(&dev));
-    SAMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    return std::max(nsm, 1);
-}
 
 void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s) {
     build_from_pattern(merge_pattern(A, B), B ? 1 : 0, ks, s);
@@ -1375,9 +1350,9 @@ Pattern stacked_pattern(const HCsr &A, const HCsr &B, int count) {
 }  // namespace
 
 void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s,
-                             int ld, bool wide) {
+                             int ld, bool wide, int band_rows) {
     build_from_pattern(stacked_pattern(A, B, count), 1, ks, s, kz_window_cap(ld, 1, wide),
-                       kz_device_ctas());
+                       band_rows);
 }
 
 namespace {
@@ -1442,9 +1417,9 @@ HCsr transpose_csr(const HCsr &A) {
 }  // namespace
 
 void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
-                           KSched &ks, cudaStream_t s, int ld, bool wide) {
+                           KSched &ks, cudaStream_t s, int ld, bool wide, int band_rows) {
     build_from_pattern(fused_pattern(A, At, B, C, count), 2, ks, s, kz_window_cap(ld, 2, wide),
-                       kz_device_ctas());
+                       band_rows);
 }
 
 namespace {
@@ -1460,22 +1435,22 @@ Pattern sweep_pattern(const HCsr &A, int fused_count) {
 }  // namespace
 
 void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
-                   HostSched &h, int resident_cap, int max_bands, int slot_cap) {
+                   HostSched &h, int resident_cap, int band_rows, int slot_cap) {
     SAMG_CHECK(resident_cap >= 0 && resident_cap <= 4095, SAMG_E_INVALID,
                "kaczmarz: resident window larger than the slot field (4095)");
-    SAMG_CHECK(max_bands >= 0 && slot_cap >= 0 && slot_cap <= 4095, SAMG_E_INVALID,
-               "kaczmarz: max_bands < 0, or a window outside the slot field (0..4095)");
+    SAMG_CHECK(band_rows >= 0 && slot_cap >= 0 && slot_cap <= 4095, SAMG_E_INVALID,
+               "kaczmarz: band_rows < 0, or a window outside the slot field (0..4095)");
     if (slot_cap == 0) slot_cap = SLOT_CAP;
     if (spd) {
         const HCsr I = B ? HCsr() : identity_csr(A.m);
         build_host(stacked_pattern(A, B ? *B : I, std::max(1, fused_count)), 1, h, resident_cap,
-                   slot_cap, max_bands);
+                   slot_cap, band_rows);
     } else if (fused_count <= 0) {
-        build_host(merge_pattern(A, nullptr), 0, h, resident_cap, slot_cap, max_bands);
+        build_host(merge_pattern(A, nullptr), 0, h, resident_cap, slot_cap, band_rows);
     } else {
         const HCsr Im = B ? HCsr() : identity_csr(A.m), In = C ? HCsr() : identity_csr(A.n);
         build_host(fused_pattern(A, transpose_csr(A), B ? *B : Im, C ? *C : In, fused_count), 2, h,
-                   resident_cap, slot_cap, max_bands);
+                   resident_cap, slot_cap, band_rows);
     }
 }
 

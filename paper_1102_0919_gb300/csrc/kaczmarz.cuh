@@ -86,11 +86,10 @@ struct HostSched {
 // B, C null: identity.  The same pattern builders as the solve's.
 // resident_cap > 0 (at most 4095): a program that keeps at most that many
 // columns live is built as one band with every column resident (a mode the
-// solve does not use yet).  max_bands > 0: bands widened until at most that
-// many (as far as the window allows), as the solve does with its SM count.
-// slot_cap: live columns per band (0: 512).
+// solve does not use yet).  band_rows: rows per level a band grows to (0:
+// 32).  slot_cap: live columns per band (0: 512).
 void host_schedule(const HCsr &A, const HCsr *B, const HCsr *C, int fused_count, bool spd,
-                   HostSched &h, int resident_cap = 0, int max_bands = 0, int slot_cap = 0);
+                   HostSched &h, int resident_cap = 0, int band_rows = 0, int slot_cap = 0);
 
 // Build the schedule of the rows of A (shift form when B != nullptr: rows of
 // A - s B over the union pattern).  Host CSR inputs.
@@ -99,7 +98,7 @@ void build_kschedule(const HCsr &A, const HCsr *B, KSched &ks, cudaStream_t s);
 // count sweeps over the rows of A - s B in sequence (SPD kind): one program,
 // so a sweep's rows start as soon as the rows they depend on are done.
 void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks, cudaStream_t s,
-                             int ld = 0, bool wide = true);
+                             int ld = 0, bool wide = true, int band_rows = 0);
 
 // count block Gauss-Seidel relaxations of the minimal SVD kind as one
 // program over the unknown [v; u] (n + m rows of ld values): per relaxation
@@ -108,21 +107,18 @@ void build_kschedule_stacked(const HCsr &A, const HCsr &B, int count, KSched &ks
 // right-hand side block is [kappa; tau] (m + n rows).  The order of every
 // row's updates is that of the sequential relaxations.
 // Both builders band the program with kz_window_cap(ld, mode, wide) live
-// columns and at most as many bands as the device has SMs, where the window
-// allows.  wide: the schedule serves float64 launches too; otherwise only
-// float32 windows (float32 and bfloat16 storage), which hold twice the
-// columns.
+// columns and about band_rows rows per level (0: 32).  wide: the schedule
+// serves float64 launches too; otherwise only float32 windows (float32 and
+// bfloat16 storage), which hold more columns.
 void build_kschedule_fused(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &C, int count,
-                           KSched &ks, cudaStream_t s, int ld = 0, bool wide = true);
+                           KSched &ks, cudaStream_t s, int ld = 0, bool wide = true,
+                           int band_rows = 0);
 
 // The largest window (live columns per band) whose launch fits a CTA's
 // shared memory at block width ld (at least 512): for float64 and float32
 // windows (wide), or float32 windows only.
 int kz_window_cap(int ld, int mode, bool wide = true);
 
-// CTAs of the sweep kernel that run at once on the current device (one per
-// SM).
-int kz_device_ctas();
 
 // One sweep: x (cols x ld) updated in place; rhs (rows x ld) or null for 0;
 // shift: ld device values (shifted form).  Returns after queuing the kernel.

@@ -164,25 +164,25 @@ def test_coarse_level_programs_with_galerkin_b_and_c(kind):
             assert rel(got, ref) < 1e-10, rel(got, ref)
 
 
-@pytest.mark.parametrize("max_bands,slot_cap", [(4, 0), (6, 2700), (2, 64)])
-def test_bands_widened_to_the_resident_ctas_replay_block_gauss_seidel(max_bands, slot_cap):
-    # the solve bands a smoothing program with at most as many bands as the
-    # device runs CTAs at once, where the window allows: wider bands (more
-    # rows per level, longer sub-level lists) replay the same relaxations;
-    # a small window (64 columns) keeps more bands than asked for
+@pytest.mark.parametrize("band_rows,slot_cap", [(8, 0), (128, 0), (128, 2700), (512, 64)])
+def test_bands_of_other_widths_replay_block_gauss_seidel(band_rows, slot_cap):
+    # the bands' rows per level (samg_set_sweep_banding) and window size
+    # change the schedule only: narrower bands (8 rows per level), wider ones
+    # (more rows per level, longer sub-level lists, more live columns) and a
+    # small window (64 columns, which stops a band's growth early) replay the
+    # same relaxations
     A = W.gradient(96).to_scipy()
     m, n = A.shape
     count = 4
     plain = parse(samg.sweep_schedule(A, count))
-    S = parse(samg.sweep_schedule(A, count, max_bands=max_bands, slot_cap=slot_cap))
-    if slot_cap == 2700:
-        assert S["nbands"] <= max_bands < plain["nbands"], (S["nbands"], plain["nbands"])
-    elif slot_cap == 0:
-        # the 512-column window stops the widening early
-        assert max_bands < S["nbands"] < plain["nbands"], (S["nbands"], plain["nbands"])
+    S = parse(samg.sweep_schedule(A, count, band_rows=band_rows, slot_cap=slot_cap))
+    if band_rows < 32:
+        assert S["nbands"] > plain["nbands"], (S["nbands"], plain["nbands"])
+    elif slot_cap != 64:
+        assert S["nbands"] < plain["nbands"], (S["nbands"], plain["nbands"])
     else:
-        assert S["nbands"] > max_bands
-    rng = np.random.default_rng(max_bands)
+        assert S["nbands"] > plain["nbands"], (S["nbands"], plain["nbands"])
+    rng = np.random.default_rng(band_rows + slot_cap)
     sig = np.linspace(3.0, 9.0, 8)
     U, V = rng.standard_normal((m, 8)), rng.standard_normal((n, 8))
     K, T = rng.standard_normal((m, 8)), rng.standard_normal((n, 8))
@@ -202,7 +202,7 @@ def test_widened_bands_on_a_galerkin_level():
     nb = len(s)
     rng = np.random.default_rng(8)
     sig = np.abs(s) * (1 + 0.01 * rng.standard_normal(nb))
-    S = parse(samg.sweep_schedule(L.A, 3, B=L.B, C=L.C, max_bands=2, slot_cap=2700))
+    S = parse(samg.sweep_schedule(L.A, 3, B=L.B, C=L.C, band_rows=512, slot_cap=2700))
     Uc, Vc = rng.standard_normal((m, nb)), rng.standard_normal((n, nb))
     K, T = rng.standard_normal((m, nb)), rng.standard_normal((n, nb))
     z = replay(S, np.vstack([Vc, Uc]), np.vstack([K, T]), sig)
