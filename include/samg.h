@@ -286,9 +286,9 @@ samg_status samg_set_relax_order(samg_ctx *ctx, int order);
  * tuning of the parallel schedule; the sweeps' results do not depend on it
  * beyond rounding order inside a row): a band of rows grows until it has
  * about band_rows rows per dependency level (1..4096; default 32) or its
- * live columns fill the shared-memory window; float_windows = 1 (default)
- * gives float32 and bfloat16 launches programs banded with float32-only
- * windows, 0 shares the float64 programs.  The programs are rebuilt on
+ * live columns fill the shared-memory window; float_windows = 1 gives
+ * float32 and bfloat16 launches programs banded with float32-only windows,
+ * 0 (default) shares the float64 programs.  The programs are rebuilt on
  * first use.  SAMG_E_INVALID for values out of range. */
 samg_status samg_set_sweep_banding(samg_ctx *ctx, int band_rows, int float_windows);
 

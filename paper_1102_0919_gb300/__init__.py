@@ -324,7 +324,7 @@ class Solver:
         self._check(samg_get_triplets(self._ctx, None, None, None, _ptr(r)))
         return r
 
-    def set_sweep_banding(self, band_rows=32, float_windows=True):
+    def set_sweep_banding(self, band_rows=32, float_windows=False):
         """Rows per dependency level a sweep band grows to, and whether
         float32 launches use programs with float32-only windows."""
         self._check(samg_set_sweep_banding(self._ctx, int(band_rows), int(bool(float_windows))))

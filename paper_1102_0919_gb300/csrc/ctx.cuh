@@ -133,7 +133,7 @@ struct samg_ctx {
     // rows per level a band grows to, and whether float32 launches get
     // programs with float32-only windows
     int band_rows = 32;
-    bool float_windows = true;
+    bool float_windows = false;
     // wall seconds of the setup phase's stages (samg_setup_times)
     double setup_s[SAMG_SETUP_STAGES] = {};
     // the setup phase's state (fine test vectors, finest coarsening), kept

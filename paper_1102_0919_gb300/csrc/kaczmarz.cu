@@ -191,13 +191,27 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned b
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
                  "r"(bytes) : "memory");
 }
+// L2 policy for data read once per launch (chunk images, right-hand sides):
+// evicted first, so that it does not displace the iterate's recently
+// written rows, which other bands read next
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 // bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
-                                         unsigned long long *b) {
+                                         unsigned long long *b, unsigned long long pol) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(b)), "l"(pol) : "memory");
+}
+// asynchronous 16-byte global -> shared copy with an L2 policy
+__device__ __forceinline__ void cp_async16_hint(void *dst, const void *src, unsigned long long pol) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "l"(pol) : "memory");
 }
 __device__ __forceinline__ void cp_async_arrive(unsigned long long *b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
@@ -488,6 +502,7 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
         if (comm) {
             // ------------------------------------------------------ producer warp
             const int lane = threadIdx.x & 31;
+            const unsigned long long once = l2_evict_first();
             int sn = cb, vn = cb;
             bool aborted = false;
             unsigned long long t0 = gtimer();  // re-armed whenever something advances
@@ -535,7 +550,8 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                             // the asynchronous overwrite
                             fence_proxy_async();
                             mbar_expect_tx(&mb_sched[bi], bytes);
-                            bulk_g2s(bufs + (size_t)bi * SG::stride, kv.img + off, bytes, &mb_sched[bi]);
+                            bulk_g2s(bufs + (size_t)bi * SG::stride, kv.img + off, bytes, &mb_sched[bi],
+                                     once);
                         }
                         __syncwarp();
                         ++sn;
@@ -564,8 +580,11 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
                         if (rhs)
                             for (int q = lane; q < ck.nr * P; q += 32) {
                                 const int r = q / P, p = q % P;
-                                piece(B + SG::o_rhs + (size_t)SG::VB * r + PB * p,
-                                      reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + PB * p);
+                                unsigned char *d = B + SG::o_rhs + (size_t)SG::VB * r + PB * p;
+                                const unsigned char *g =
+                                    reinterpret_cast<const unsigned char *>(rhs + (size_t)ri[r].x * LD) + PB * p;
+                                if constexpr (PB == 16) cp_async16_hint(d, g, once);
+                                else piece(d, g);
                             }
                         for (int q = lane; q < ck.nx * P; q += 32) {
                             const int r = q / P, p = q % P;
