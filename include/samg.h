@@ -446,7 +446,9 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
  *   per chunk: i32 L0, nl, nr, ne, nx, nq, bytes, 0; i64 offset;
  *   per level: i32 first requirement, requirement count, publish, 0;
  *   per requirement: i32 band, levels that band must have completed;
- *   the chunk images (float64 coefficients).
+ *   the chunk images (float64 coefficients);
+ *   i32 order[nbands]: the band each ticket claims (every band's required
+ *   bands at earlier tickets).
  * A chunk image holds, at 16-byte aligned offsets: per level {first row,
  * rows, lanes log2, flags: 1 has requirements | 2 publish after it}
  * (4 x i32); per level {first requirement in the image's list, count}

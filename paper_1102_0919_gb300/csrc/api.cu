@@ -1076,6 +1076,7 @@ samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg
             put32(r.y);
         }
         out.insert(out.end(), hs.img_d.begin(), hs.img_d.end());
+        for (int v : hs.order) put32(v);
         *size = (int64_t)out.size();
         if (buf) {
             SAMG_CHECK(capacity >= (int64_t)out.size(), SAMG_E_INVALID,

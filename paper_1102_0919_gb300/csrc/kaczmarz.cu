@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <queue>
 #include <type_traits>
 
 #include "kaczmarz.cuh"
@@ -60,6 +61,8 @@ struct Pattern {                      // rows of a sweep program: a (and b) coef
     std::vector<int> ci;
     std::vector<double> a, b;
     std::vector<int> rhs;             // right-hand-side row of each row (empty: its own)
+    std::vector<int> seg;             // first rows of the program's sweeps after the first:
+                                      // no band crosses one
 };
 
 Pattern merge_pattern(const HCsr &A, const HCsr *B) {
@@ -419,6 +422,7 @@ struct KView {
     const int4 *lvl;           // per level: {first req, requirement count, publish, 0}
     const unsigned char *img;  // chunk images with coefficients of the launch's precision
     const int2 *req;           // {band, levels that band must have completed}
+    const int *order;          // ticket -> band (every band's requirements earlier)
     unsigned long long *progress;
     KCtl *ctl;
 };
@@ -487,7 +491,8 @@ __global__ void __launch_bounds__(KZ_THREADS, 1)
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_band = (int)atomicAdd(&kv.ctl->ticket, 1u);
+            const unsigned t = atomicAdd(&kv.ctl->ticket, 1u);
+            s_band = t < (unsigned)kv.nbands ? kv.order[t] : kv.nbands;
             s_done = 0;
             for (int q = 0; q < KZ_NBUF; ++q) {  // no chunk of this band staged yet
                 s_cl0[q] = -(1 << 30);
@@ -914,7 +919,7 @@ void launch_one(const KSched &ks, const S *rhs, S *x, const double *shift, cudaS
     }
     const unsigned char *img = sizeof(T) == 4 ? ks.img_f.p : ks.img_d.p;
     KView kv{ks.err ? ks.err : &ks.ctl.p->err, ks.nbands, ks.band_chunk.p, ks.chunk.p, ks.lvl.p,
-             img, ks.req.p, ks.progress.p, ks.ctl.p};
+             img, ks.req.p, ks.order.p, ks.progress.p, ks.ctl.p};
     SAMG_COUNT_LAUNCH();
     kern<<<grid, KZ_THREADS, smem, s>>>(kv, rhs, x, shift, slots);
     SAMG_CUDA(cudaGetLastError());
@@ -965,8 +970,11 @@ std::vector<int> form_bands_at(const Pattern &p, const std::vector<int> &glv, Ba
                                int slot_cap, int target) {
     std::vector<int> bstart;
     int slots = 0;
+    size_t si = 0;
     for (int r0 = 0; r0 < p.rows;) {
-        int R = std::min(256, p.rows - r0), good = 0;
+        while (si < p.seg.size() && p.seg[si] <= r0) ++si;
+        const int r_end = si < p.seg.size() ? p.seg[si] : p.rows;  // this sweep's end
+        int R = std::min(256, r_end - r0), good = 0;
         for (;;) {
             int nl = analyze_band(p, glv, r0, r0 + R, w, &slots);
             if (slots > slot_cap) {
@@ -976,14 +984,68 @@ std::vector<int> form_bands_at(const Pattern &p, const std::vector<int> &glv, Ba
                 continue;
             }
             good = R;
-            if (r0 + R >= p.rows || R >= MAX_BAND_ROWS || (R / std::max(nl, 1)) >= target) break;
-            R = std::min(2 * R, p.rows - r0);
+            if (r0 + R >= r_end || R >= MAX_BAND_ROWS || (R / std::max(nl, 1)) >= target) break;
+            R = std::min(2 * R, r_end - r0);
         }
         bstart.push_back(r0);
         r0 += good;
     }
     bstart.push_back(p.rows);
     return bstart;
+}
+
+// The order in which the CTAs claim bands (ticket -> band).  Any order in
+// which every band's required bands come earlier is free of deadlock: the
+// unfinished band with the smallest ticket has all its required bands
+// finished, so it always advances.  Program order is one such order, but
+// a CTA that claims a band whose rows the wavefront reaches late holds its
+// SM idle meanwhile, and with more bands than SMs the later sweeps of a
+// fused program then start late.  Among the bands whose required bands are
+// all placed, this takes the one that could start earliest: the start of
+// its first level in a model with a CTA per band, levels of one unit and
+// cross-band handoffs of two.
+std::vector<int> claim_order(int nb, const std::vector<int> &band_lvl0,
+                             const std::vector<int4> &lvl, const std::vector<int2> &req) {
+    constexpr double HANDOFF = 2.0;
+    std::vector<double> fin(lvl.size(), 0.0), est(nb, 0.0);
+    std::vector<std::vector<int>> deps(nb);
+    for (int b = 0; b < nb; ++b) {  // program order: required bands come first
+        double t = 0.0;
+        for (int L = band_lvl0[b]; L < band_lvl0[b + 1]; ++L) {
+            for (int q = lvl[L].x; q < lvl[L].x + lvl[L].y; ++q) {
+                const int bb = req[q].x;
+                t = std::max(t, fin[band_lvl0[bb] + req[q].y - 1] + HANDOFF);
+                deps[b].push_back(bb);
+            }
+            if (L == band_lvl0[b]) est[b] = t;
+            t += 1.0;
+            fin[L] = t;
+        }
+        std::sort(deps[b].begin(), deps[b].end());
+        deps[b].erase(std::unique(deps[b].begin(), deps[b].end()), deps[b].end());
+    }
+    std::vector<std::vector<int>> users(nb);
+    std::vector<int> left(nb);
+    for (int b = 0; b < nb; ++b) {
+        left[b] = (int)deps[b].size();
+        for (int bb : deps[b]) users[bb].push_back(b);
+    }
+    using Item = std::pair<double, int>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> ready;
+    for (int b = 0; b < nb; ++b)
+        if (!left[b]) ready.push({est[b], b});
+    std::vector<int> order;
+    order.reserve(nb);
+    while (!ready.empty()) {
+        const int b = ready.top().second;
+        ready.pop();
+        order.push_back(b);
+        for (int u : users[b])
+            if (--left[u] == 0) ready.push({est[u], u});
+    }
+    SAMG_CHECK((int)order.size() == nb, SAMG_E_INVALID,
+               "kaczmarz: band requirements are not acyclic");
+    return order;
 }
 
 // resident_cap > 0: when the whole program keeps at most that many columns
@@ -1246,6 +1308,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
     ks.max_slots = max_slots;
     ks.nent = nent;
     ks.nchunks = (int)chunk.size();
+    ks.order = claim_order(nb, band_lvl0, lvl, req);
     if (req.empty()) req.push_back(make_int2(0, 0));
     ks.band_chunk = std::move(band_chunk);
     ks.chunk = std::move(chunk);
@@ -1276,6 +1339,7 @@ void build_from_pattern(const Pattern &p, int mode, KSched &ks, cudaStream_t s,
     ks.img_f.upload(h.img_f.data(), h.img_f.size(), s);
     ks.img_d.upload(h.img_d.data(), h.img_d.size(), s);
     ks.req.upload(h.req.data(), h.req.size(), s);
+    ks.order.upload(h.order.data(), h.order.size(), s);
     ks.progress.alloc(std::max(nb, 1));
     ks.progress.zero(s);
     ks.ctl.alloc(1);
@@ -1353,6 +1417,7 @@ Pattern stacked_pattern(const HCsr &A, const HCsr &B, int count) {
     p.cols = one.cols;
     p.rp.assign(1, 0);
     for (int k = 0; k < count; ++k) {
+        if (k > 0) p.seg.push_back(k * one.rows);
         for (int i = 0; i < one.rows; ++i) {
             for (int64_t e = one.rp[i]; e < one.rp[i + 1]; ++e) {
                 p.ci.push_back(one.ci[e]);
@@ -1385,6 +1450,8 @@ Pattern fused_pattern(const HCsr &A, const HCsr &At, const HCsr &B, const HCsr &
     p.cols = n + m;  // unknown [v; u]
     p.rp.assign(1, 0);
     for (int k = 0; k < count; ++k) {
+        if (k > 0) p.seg.push_back(k * (m + n));
+        p.seg.push_back(k * (m + n) + m);
         // rows of A for v: a_i . v - s_j (B u)_i = kappa_i (v columns, then u)
         for (int i = 0; i < m; ++i) {
             append_row(p, A, i, 0, false);

@@ -59,6 +59,7 @@ struct KSched {
     DBuf<int4> lvl;            // per level: {first req, requirement count, publish, 0}
     DBuf<unsigned char> img_f, img_d;  // chunk images, float / double coefficients
     DBuf<int2> req;            // {band, level that band must have completed}
+    DBuf<int> order;           // nbands: the band each ticket claims
     DBuf<unsigned long long> progress;  // nbands
     DBuf<KCtl> ctl;
     mutable int grid_cache[256] = {};  // resident CTAs per kernel instance
@@ -77,6 +78,7 @@ struct HostSched {
     std::vector<int4> lvl;
     std::vector<unsigned char> img_f, img_d;
     std::vector<int2> req;
+    std::vector<int> order;    // ticket -> band
 };
 
 // Host-only: the schedule, as the kernels receive it, of one sweep over the

@@ -33,10 +33,54 @@ def parse(blob):
     req = np.frombuffer(b[at:at + 8 * nreq], "<i4").reshape(nreq, 2)
     at += 8 * nreq
     img = b[at:at + imgb]
-    assert at + imgb == len(blob)
+    at += imgb
+    order = np.frombuffer(b[at:at + 4 * nbands], "<i4")
+    assert at + 4 * nbands == len(blob)
     return dict(rows=int(rows), cols=int(cols), nbands=int(nbands), max_slots=int(max_slots),
                 mode=int(mode), shifted=bool(shifted), band_chunk=band_chunk, chunks=chunks,
-                lvl=lvl, req=req, img=img)
+                lvl=lvl, req=req, img=img, order=order)
+
+
+def check_claim_order(S, ctas):
+    """The tickets' band order: a permutation in which every band's required
+    bands come earlier, and a claim-by-ticket run on `ctas` CTAs (a band
+    holds its CTA from its claim to its last level) that finishes: at every
+    step some claimed band can run its next level."""
+    nb = S["nbands"]
+    order = [int(v) for v in S["order"]]
+    assert sorted(order) == list(range(nb)), "order is not a permutation of the bands"
+    pos = {b: t for t, b in enumerate(order)}
+    bc, lvl, req = S["band_chunk"], S["lvl"], S["req"]
+    need = []
+    for b in range(nb):
+        if bc[b] == bc[b + 1]:
+            need.append([])
+            continue
+        L0 = S["chunks"][bc[b]]["L0"]
+        last = S["chunks"][bc[b + 1] - 1]
+        per = []
+        for L in range(L0, last["L0"] + last["nl"]):
+            rq = req[lvl[L, 0]:lvl[L, 0] + lvl[L, 1]]
+            for bb, _ in rq:
+                assert pos[int(bb)] < pos[b], "a band's required band has a later ticket"
+            per.append(rq)
+        need.append(per)
+    done = [0] * nb
+    nxt_ticket = 0
+    running = []
+    while nxt_ticket < nb or running:
+        while len(running) < ctas and nxt_ticket < nb:
+            running.append(order[nxt_ticket])
+            nxt_ticket += 1
+        moved = False
+        for b in list(running):
+            while done[b] < len(need[b]) and all(done[int(bb)] >= int(k) for bb, k in need[b][done[b]]):
+                done[b] += 1
+                moved = True
+            if done[b] == len(need[b]):
+                running.remove(b)
+                moved = True
+        assert moved, "claim-by-ticket run stalls"
 
 
 def _image(S, c):

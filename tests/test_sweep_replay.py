@@ -10,7 +10,7 @@ import scipy.sparse as sp
 
 import oracle
 import workloads as W
-from sweep_replay import parse, replay
+from sweep_replay import check_claim_order, parse, replay
 
 samg = pytest.importorskip("paper_1102_0919_gb300")
 
@@ -210,6 +210,39 @@ def test_widened_bands_on_a_galerkin_level():
     for _ in range(3):
         oracle.relax_boot(L, False, "minimal", sig, Ur, Vr, K, T, 0.7)
     assert rel(z[:n], Vr) < 1e-10 and rel(z[n:], Ur) < 1e-10
+
+
+def _nine_point(N):
+    I = sp.identity(N, format="csr")
+    T = sp.diags([np.full(N - 1, -1.0), np.full(N, 4.0), np.full(N - 1, -1.0)], [-1, 0, 1])
+    E = sp.diags([np.ones(N - 1), np.ones(N), np.ones(N - 1)], [-1, 0, 1])
+    return sp.csr_matrix(sp.kron(I, T) - 0.5 * sp.kron(sp.diags([np.ones(N - 1), np.ones(N - 1)],
+                                                                [-1, 1]), E))
+
+
+@pytest.mark.parametrize("name", ["gradient96", "nine_point80", "random", "galerkin"])
+def test_claim_order_is_safe_for_any_cta_count(name):
+    # the CTAs claim bands in the schedule's ticket order; every band's
+    # required bands must hold earlier tickets, so that a run on any number
+    # of CTAs finishes (a later band never holds the last free CTA while an
+    # earlier one it waits for is unclaimed)
+    if name == "gradient96":
+        S = parse(samg.sweep_schedule(W.gradient(96).to_scipy(), 4, band_rows=8))
+    elif name == "nine_point80":
+        S = parse(samg.sweep_schedule(_nine_point(80), 4, band_rows=8))
+        # a 2-D stencil: the rows of later lines start late, so the order
+        # moves the next relaxation's first bands ahead of them
+        assert list(S["order"]) != list(range(S["nbands"]))
+    elif name == "random":
+        S = parse(samg.sweep_schedule(_rand_rect(1500, 700, 9, dens=0.01), 2))
+    else:
+        A = W.gradient(40).to_scipy()
+        H, s, U, V = oracle.setup(A, 8, "minimal", "svd", dict(W.GRAD_PARAMS, seed=4, n_mult=2))
+        L = H.levels[1]
+        S = parse(samg.sweep_schedule(L.A, 3, B=L.B, C=L.C, band_rows=8))
+    assert S["nbands"] >= 4
+    for ctas in (1, 2, 5, S["nbands"]):
+        check_claim_order(S, ctas)
 
 
 def test_empty_rows_and_a_single_row():
