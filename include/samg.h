@@ -285,12 +285,18 @@ samg_status samg_set_relax_order(samg_ctx *ctx, int order);
 /* Banding of the exact-order sweep programs of the smoothing phases (a
  * tuning of the parallel schedule; the sweeps' results do not depend on it
  * beyond rounding order inside a row): a band of rows grows until it has
- * about band_rows rows per dependency level (1..4096; default 32) or its
- * live columns fill the shared-memory window; float_windows = 1 gives
- * float32 and bfloat16 launches programs banded with float32-only windows,
- * 0 (default) shares the float64 programs.  The programs are rebuilt on
- * first use.  SAMG_E_INVALID for values out of range. */
+ * about band_rows rows per dependency level (1..4096 on every level; 0, the
+ * default, takes 32 on the finest level and, on a coarser level of m x n,
+ * max(m, n) / 65536 rounded to a power of two within [2, 32], the
+ * fastest measured) or its live columns fill the shared-memory window;
+ * per-level settings are cleared.  float_windows = 1 gives float32 and
+ * bfloat16 launches programs banded with float32-only windows, 0 (default)
+ * shares the float64 programs.  The programs are rebuilt on first use.
+ * SAMG_E_INVALID for values out of range. */
 samg_status samg_set_sweep_banding(samg_ctx *ctx, int band_rows, int float_windows);
+
+/* The same for one level (band_rows 0: back to the context's setting). */
+samg_status samg_set_sweep_banding_level(samg_ctx *ctx, int level, int band_rows);
 
 /* Kernel timing: with profiling on, every launch of the solve phase is
  * bracketed by CUDA events on the context's stream.  samg_profile_read

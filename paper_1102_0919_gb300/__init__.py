@@ -119,6 +119,7 @@ samg_profile_read = _sig("samg_profile_read", _I, _CTX, _I, _I, ctypes.POINTER(c
                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
 samg_redo_interpolation = _sig("samg_redo_interpolation", _I, _CTX, _P)
 samg_set_sweep_banding = _sig("samg_set_sweep_banding", _I, _CTX, _I, _I)
+samg_set_sweep_banding_level = _sig("samg_set_sweep_banding_level", _I, _CTX, _I, _I)
 samg_setup_times = _sig("samg_setup_times", _I, _CTX, _P, ctypes.c_int32)
 
 EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", "samg_last_error",
@@ -133,7 +134,8 @@ EXPORTED = ["samg_default_params", "samg_setup", "samg_import", "samg_destroy", 
             "samg_import_file", "samg_sweep_schedule", "samg_setup_batched",
             "samg_solve_batched", "samg_batch_problem", "samg_batch_size",
             "samg_batch_last_error", "samg_batch_destroy", "samg_row_colours",
-            "samg_setup_times", "samg_redo_interpolation", "samg_set_sweep_banding"]
+            "samg_setup_times", "samg_redo_interpolation", "samg_set_sweep_banding",
+            "samg_set_sweep_banding_level"]
 
 
 def _arr(x, dtype):
@@ -324,10 +326,14 @@ class Solver:
         self._check(samg_get_triplets(self._ctx, None, None, None, _ptr(r)))
         return r
 
-    def set_sweep_banding(self, band_rows=32, float_windows=False):
-        """Rows per dependency level a sweep band grows to, and whether
-        float32 launches use programs with float32-only windows."""
-        self._check(samg_set_sweep_banding(self._ctx, int(band_rows), int(bool(float_windows))))
+    def set_sweep_banding(self, band_rows=0, float_windows=False, level=None):
+        """Rows per dependency level a sweep band grows to (0: the default
+        per level), and whether float32 launches use programs with
+        float32-only windows; with level, that level only."""
+        if level is not None:
+            self._check(samg_set_sweep_banding_level(self._ctx, int(level), int(band_rows)))
+        else:
+            self._check(samg_set_sweep_banding(self._ctx, int(band_rows), int(bool(float_windows))))
 
     def set_relax_order(self, order):
         """"natural" (0, the paper's) or "coloured" (1, the variant)."""

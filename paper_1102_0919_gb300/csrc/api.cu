@@ -573,14 +573,27 @@ samg_status samg_set_relax_order(samg_ctx *ctx, int order) {
 samg_status samg_set_sweep_banding(samg_ctx *ctx, int band_rows, int float_windows) {
     if (!ctx) return SAMG_E_INVALID;
     return guarded(ctx, [&] {
-        SAMG_CHECK(band_rows >= 1 && band_rows <= 4096 && (float_windows == 0 || float_windows == 1),
-                   SAMG_E_INVALID, "sweep banding: band_rows in 1..4096, float_windows 0 or 1");
+        SAMG_CHECK(band_rows >= 0 && band_rows <= 4096 && (float_windows == 0 || float_windows == 1),
+                   SAMG_E_INVALID, "sweep banding: band_rows in 0..4096, float_windows 0 or 1");
         ctx->band_rows = band_rows;
+        ctx->band_rows_level.clear();
         ctx->float_windows = float_windows != 0;
         for (Level &L : ctx->L) {
             L.kF.clear();
             L.kF4.clear();
         }
+    });
+}
+
+samg_status samg_set_sweep_banding_level(samg_ctx *ctx, int level, int band_rows) {
+    if (!ctx) return SAMG_E_INVALID;
+    return guarded(ctx, [&] {
+        SAMG_CHECK(level >= 0 && level < ctx->nlev() && band_rows >= 0 && band_rows <= 4096,
+                   SAMG_E_INVALID, "sweep banding: level out of range or band_rows not in 0..4096");
+        if ((int)ctx->band_rows_level.size() <= level) ctx->band_rows_level.resize(level + 1, 0);
+        ctx->band_rows_level[level] = band_rows;
+        ctx->L[level].kF.clear();
+        ctx->L[level].kF4.clear();
     });
 }
 

@@ -130,9 +130,11 @@ struct samg_ctx {
     samg::DBuf<int> rstat;
     samg::Profiler prof;
     // banding of the smoothing phases' sweep programs (samg_set_sweep_banding):
-    // rows per level a band grows to, and whether float32 launches get
-    // programs with float32-only windows
-    int band_rows = 32;
+    // rows per level a band grows to (0: the per-level default), per-level
+    // overrides, and whether float32 launches get programs with float32-only
+    // windows
+    int band_rows = 0;
+    std::vector<int> band_rows_level;
     bool float_windows = false;
     // wall seconds of the setup phase's stages (samg_setup_times)
     double setup_s[SAMG_SETUP_STAGES] = {};

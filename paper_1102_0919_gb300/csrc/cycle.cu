@@ -156,6 +156,24 @@ static void relax_phase_coloured(samg_ctx &c, int l, int count) {
 // schedule is built on first use for each count); other kinds relax one at a
 // time.  The result is that of count calls of relax() up to the rounding
 // order inside each row.
+// Rows per dependency level a band of level l's smoothing programs grows to:
+// a per-level override, else the context's setting, else the default.  The
+// default follows measurements (mixed precision, the 1024^2 gradient's 13
+// levels, every level timed at 1 to 32 rows per level, bands claimed in
+// claim order): the finest level runs fastest at 32; on the Galerkin levels
+// the best width falls with the level's size, about max(m, n) / 65536
+// rows (8 at 524,288 unknowns, 4 at 262,143, 2 from about 65,000 down),
+// narrower bands keeping more sweeps' wavefronts resident at once.
+static int band_rows_for(const samg_ctx &c, int l) {
+    if (l < (int)c.band_rows_level.size() && c.band_rows_level[l] > 0) return c.band_rows_level[l];
+    if (c.band_rows > 0) return c.band_rows;
+    if (l == 0) return 32;
+    const int64_t size = std::max(c.L[l].m, c.L[l].n);
+    int t = 2;  // max(m, n) / 65536 rounded to a power of two, within [2, 32]
+    while (t < 32 && 2 * size >= (int64_t)3 * t * 65536) t *= 2;
+    return t;
+}
+
 template <typename T>
 void relax_phase(samg_ctx &c, int l, int count) {
     if (!c.minimal() || count <= 0) {
@@ -183,13 +201,13 @@ void relax_phase(samg_ctx &c, int l, int count) {
         if (L.B.empty()) csr_identity(c.spd() ? L.n : L.m, hB);
         else download_csr(L.B, hB, s);
         if (c.spd()) {
-            build_kschedule_stacked(hA, hB, count, ks, s, ld, wide, c.band_rows);
+            build_kschedule_stacked(hA, hB, count, ks, s, ld, wide, band_rows_for(c, l));
         } else {
             HCsr hAt, hC;
             download_csr(L.At, hAt, s);
             if (L.C.empty()) csr_identity(L.n, hC);
             else download_csr(L.C, hC, s);
-            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld, wide, c.band_rows);
+            build_kschedule_fused(hA, hAt, hB, hC, count, ks, s, ld, wide, band_rows_for(c, l));
         }
         if (c.rstat.n >= 2) ks.err = c.rstat.p + 1;
     }
