@@ -162,10 +162,12 @@ def traffic_record():
 
 # --------------------------------------------------------------- CPU oracle
 def _oracle_params(prm, n_conv):
-    keys = ("mu_b", "omega_J", "coarse_drop", "coarse_pinv", "row_form", "relax_order")
+    keys = ("mu_b", "omega_J", "coarse_drop", "coarse_pinv", "row_form", "relax_order",
+            "square_form")
     p = {k: prm[k] for k in keys if k in prm}
     for k, names in (("coarse_pinv", ("svd", "geneig")), ("row_form", ("induced", "paper")),
-                     ("relax_order", ("natural", "coloured"))):
+                     ("relax_order", ("natural", "coloured")),
+                     ("square_form", ("normal", "from_A", "shared"))):
         if isinstance(p.get(k), int):
             p[k] = names[p[k]]
     return p
