@@ -119,6 +119,34 @@ def test_relaxation_each_level(case, prec, tol):
     g.set_precision("fp64")
 
 
+@pytest.mark.parametrize("band_rows,float_windows", [(1, False), (2, True), (8, False), (64, True)])
+def test_relaxation_under_other_sweep_bandings(case, band_rows, float_windows):
+    """The sweep programs' banding (samg_set_sweep_banding: rows per level a
+    band grows to, float32-only windows) and the claim order change the
+    parallel schedule only: every level's smoothing phase still equals the
+    oracle's sequential block Gauss-Seidel relaxations, in float64 and
+    float32."""
+    H, g = case["H"], case["g"]
+    spd = case["kind"] == "spd"
+    try:
+        g.set_sweep_banding(band_rows, float_windows)
+        for prec, tol in (("fp64", TOL64), ("fp32", TOL32)):
+            g.set_precision(prec)
+            for l in range(len(H.levels) - 1):
+                sig, U, V, K, T = _vecs(case, l, 170 + l)
+                Ug, Vg = g.relax(l, sig, U, V, K, T, count=3)
+                Ur, Vr = U.copy(), None if spd else V.copy()
+                for _ in range(3):
+                    oracle.relax_boot(H.levels[l], spd, H.target, sig, Ur, Vr, K, T,
+                                      H.params["omega_J"])
+                assert rel(Ug, Ur) < tol, (prec, l, rel(Ug, Ur))
+                if not spd:
+                    assert rel(Vg, Vr) < tol, (prec, l, rel(Vg, Vr))
+    finally:
+        g.set_sweep_banding()
+        g.set_precision("fp64")
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32), ("bf16", TOLB16)])
 def test_relaxation_coloured_each_level(case, prec, tol):
     """relax_order = 1 (the coloured variant): every level's smoothing phase
