@@ -5,6 +5,8 @@ itself is not compared with the oracle's: from the second coarsening down
 it depends on rounding (the oracle's own level sizes change with the number
 of BLAS threads), so the two setups build different, equally valid
 hierarchies."""
+import time
+
 import numpy as np
 import pytest
 
@@ -20,8 +22,15 @@ samg = pytest.importorskip("paper_1102_0919_gb300")
 def test_laplacian_workload_minimal_eigenpairs(prec):
     wl = W.workload(1)
     A = wl.build().to_scipy()
+    t0 = time.perf_counter()
     s = samg.Solver.setup(A, wl.nb, wl.target, wl.kind, prec=prec,
                           **dict(wl.params, seed=W.problem_seed(1)))
+    wall = time.perf_counter() - t0
+    # the setup's stage clock: every stage accounted, none above the wall time
+    st = s.setup_times()
+    assert set(st) == set(samg.Solver.SETUP_STAGES)
+    assert all(v >= 0.0 for v in st.values()) and 0.0 < sum(st.values()) <= wall
+    assert st["test_relax"] > 0.0 and st["strength_rs"] > 0.0 and st["ls_fit"] > 0.0
     levels = s.levels()
     ok, it = s.solve(1e-10, 60)
     sig, U, _, res = s.triplets()
