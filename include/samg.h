@@ -182,19 +182,26 @@ samg_status samg_import(const samg_csr *A, int n_levels, const samg_csr *P, cons
 
 /* Many independent problems with the same n_b, target, kind and parameters
  * (the batched workload of uneven sizes; the paper treats one problem at a
- * time).  Each problem gets its own hierarchy and context on the given
- * stream; samg_solve_batched solves them one after another.  Fusing
- * problems into shared launches or one captured graph is not built.
+ * time).  Each problem gets its own hierarchy, context and CUDA stream.
+ * Fusing problems into shared launches or one captured graph is not built.
  *  - samg_setup_batched: every problem's arguments are checked before any
  *    device call (SAMG_E_INVALID names the problem); then the setups run in
- *    order, and a failure destroys the contexts made so far.
- *  - samg_solve_batched: outer_done (count entries, may be NULL) receives
- *    each problem's iterations.  It returns SAMG_E_NOT_CONVERGED when some
- *    problem reached max_outer (the others are still solved), or the first
- *    other error, which stops the loop.
+ *    order on the given stream, and a failure destroys the contexts made so
+ *    far.  After its setup each context moves to a non-blocking stream the
+ *    batch creates and owns (destroyed by samg_batch_destroy).
+ *  - samg_solve_batched: rounds of one outer iteration per unconverged
+ *    problem, each on its problem's stream, so that the problems overlap on
+ *    the device; between rounds the host reads every problem's residuals
+ *    and Ritz status (pinned copies).  It starts after the work queued on
+ *    the setup's stream and queues that stream behind the problems' work.
+ *    With redo_tol > 0 the problems are solved one after another instead.
+ *    outer_done (count entries, may be NULL) receives each problem's
+ *    iterations.  It returns SAMG_E_NOT_CONVERGED when some problem reached
+ *    max_outer (the others are still solved), or the first other error,
+ *    which stops every problem.
  *  - samg_batch_problem: the problem's context, owned by the batch (valid
  *    until samg_batch_destroy), for samg_get_triplets and the other
- *    per-context calls.
+ *    per-context calls, which run on the problem's stream.
  *  - samg_batch_last_error(NULL) reports a failed samg_setup_batched. */
 typedef struct samg_batch samg_batch;
 samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, samg_target target,

@@ -383,12 +383,15 @@ samg_status samg_setup(const samg_csr *A, int n_b, samg_target target, samg_kind
 
 struct samg_batch {
     std::vector<samg_ctx *> ctx;
+    std::vector<cudaStream_t> streams;  // one per problem, owned by the batch
+    cudaStream_t caller = nullptr;      // the stream given at setup
     std::string err;
 };
 
 void samg_batch_destroy(samg_batch *b) {
     if (!b) return;
     for (samg_ctx *c : b->ctx) samg_destroy(c);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     delete b;
 }
 
@@ -426,6 +429,7 @@ samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, sam
     if (!b) return SAMG_E_NOMEM;
     try {
         b->ctx.reserve(count);  // push_back below cannot throw after this
+        b->streams.reserve(count);
         for (int p = 0; p < count; ++p) {
             samg_ctx *c = nullptr;
             const samg_status st = samg_setup(A[p], n_b, target, kind, params, cuda_stream, &c);
@@ -436,7 +440,20 @@ samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, sam
                 return st;
             }
             b->ctx.push_back(c);
+            // the problem's solve runs on a stream of its own, so that the
+            // batch's problems overlap on the device
+            cudaStream_t ps = nullptr;
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                samg_batch_destroy(b);
+                g_create_error = std::string("setup_batched: stream: ") + cudaGetErrorString(e);
+                return SAMG_E_CUDA;
+            }
+            b->streams.push_back(ps);
+            c->stream = ps;
         }
+        b->caller = (cudaStream_t)cuda_stream;
     } catch (const std::bad_alloc &) {
         samg_batch_destroy(b);
         g_create_error = "setup_batched: host allocation failed";
@@ -448,23 +465,127 @@ samg_status samg_setup_batched(const samg_csr *const *A, int count, int n_b, sam
 
 samg_status samg_solve_batched(samg_batch *b, double tol, int max_outer, int *outer_done) {
     if (!b) return SAMG_E_INVALID;
-    samg_status worst = SAMG_OK;
     b->err.clear();
-    for (size_t p = 0; p < b->ctx.size(); ++p) {
-        int done = 0;
-        const samg_status st = samg_solve(b->ctx[p], tol, max_outer, &done);
-        if (outer_done) outer_done[p] = done;
-        if (st == SAMG_E_NOT_CONVERGED) {
-            worst = SAMG_E_NOT_CONVERGED;
-            b->err = "problem " + std::to_string(p) + " reached max_outer before the tolerance";
-            continue;
+    const int np = (int)b->ctx.size();
+    bool redo = false;
+    for (samg_ctx *c : b->ctx) redo = redo || c->prm.redo_tol > 0.0;
+    if (redo || max_outer < 0 || !(tol > 0.0)) {
+        // one problem after another (the redo of Sec. 6.3 rebuilds a
+        // problem's hierarchy between its iterations)
+        samg_status worst = SAMG_OK;
+        for (int p = 0; p < np; ++p) {
+            int done = 0;
+            const samg_status st = samg_solve(b->ctx[p], tol, max_outer, &done);
+            if (outer_done) outer_done[p] = done;
+            if (st == SAMG_E_NOT_CONVERGED) {
+                worst = SAMG_E_NOT_CONVERGED;
+                b->err = "problem " + std::to_string(p) + " reached max_outer before the tolerance";
+                continue;
+            }
+            if (st != SAMG_OK) {
+                b->err = "problem " + std::to_string(p) + ": " + samg_last_error(b->ctx[p]);
+                return st;
+            }
         }
-        if (st != SAMG_OK) {
-            b->err = "problem " + std::to_string(p) + ": " + samg_last_error(b->ctx[p]);
-            return st;
-        }
+        return worst;
     }
-    return worst;
+    // Every problem advances one outer iteration per round on its own
+    // stream; the host then reads all the rounds' residuals and Ritz
+    // statuses (pinned copies) and drops the problems that converged.
+    const int ld = b->ctx[0]->ld;
+    const size_t per = (size_t)ld * sizeof(double) + 2 * sizeof(int);
+    unsigned char *host = nullptr;
+    if (cudaMallocHost(&host, per * np) != cudaSuccess) {
+        b->err = "solve_batched: pinned host memory";
+        return SAMG_E_NOMEM;
+    }
+    std::vector<int> done(np, 0);
+    std::vector<char> state(np, 0);  // 0 running, 1 converged, 2 out of iterations, 3 failed
+    samg_status fail = SAMG_OK;
+    int failed_p = -1;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, b->caller);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(b->ctx[p]->stream, ev, 0);
+    if (e != cudaSuccess) {
+        fail = SAMG_E_CUDA;
+        b->err = std::string("solve_batched: ") + cudaGetErrorString(e);
+    }
+    auto run = [&](int p, auto &&f) {
+        const samg_status st = guarded(b->ctx[p], f);
+        if (st != SAMG_OK && fail == SAMG_OK) {
+            state[p] = 3;
+            fail = st;
+            failed_p = p;
+        }
+    };
+    while (fail == SAMG_OK) {
+        for (int p = 0; p < np; ++p)
+            if (!state[p])
+                run(p, [&] {
+                    samg_ctx &c = *b->ctx[p];
+                    unsigned char *h = host + per * p;
+                    SAMG_CUDA(cudaMemcpyAsync(h, c.resid.p, (size_t)ld * sizeof(double),
+                                              cudaMemcpyDeviceToHost, c.stream));
+                    SAMG_CUDA(cudaMemcpyAsync(h + (size_t)ld * sizeof(double), c.rstat.p,
+                                              2 * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+                });
+        bool any = false;
+        for (int p = 0; p < np && fail == SAMG_OK; ++p) {
+            if (state[p]) continue;
+            run(p, [&] {
+                samg_ctx &c = *b->ctx[p];
+                SAMG_CUDA(cudaStreamSynchronize(c.stream));
+                const unsigned char *h = host + per * p;
+                const double *rs = reinterpret_cast<const double *>(h);
+                int st2[2];
+                std::memcpy(st2, h + (size_t)ld * sizeof(double), sizeof(st2));
+                SAMG_CHECK(st2[1] == 0, SAMG_E_TIMEOUT, "Kaczmarz sweep: a cross-band wait timed out");
+                SAMG_CHECK(done[p] == 0 || st2[0] != 1, SAMG_E_INVALID,
+                           "ritz: boot vectors are linearly dependent");
+                const int nconv = c.prm.n_conv > 0 && c.prm.n_conv < c.nb ? c.prm.n_conv : c.nb;
+                double mx = 0.0;
+                bool finite = true;
+                for (int j = 0; j < c.nb; ++j) {
+                    finite = finite && std::isfinite(rs[j]);
+                    if (j < nconv) mx = std::max(mx, rs[j]);
+                }
+                SAMG_CHECK(finite, SAMG_E_INVALID, "non-finite residual");
+                if (mx <= tol) { state[p] = 1; return; }
+                if (done[p] >= max_outer) { state[p] = 2; return; }
+                by_prec(c, [&](auto tag) { outer_vcycle<decltype(tag)>(c); });
+                ritz(c, false, false);
+                ++done[p];
+                any = true;
+            });
+        }
+        if (!any) break;
+    }
+    // the caller's stream continues after every problem's work
+    for (int p = 0; p < np; ++p) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev, b->ctx[p]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->caller, ev, 0);
+    }
+    if (ev) cudaEventDestroy(ev);
+    cudaFreeHost(host);
+    if (outer_done)
+        for (int p = 0; p < np; ++p) outer_done[p] = done[p];
+    if (fail != SAMG_OK) {
+        b->err = failed_p >= 0 ? "problem " + std::to_string(failed_p) + ": " +
+                                     samg_last_error(b->ctx[failed_p])
+                               : b->err;
+        return fail;
+    }
+    if (e != cudaSuccess) {
+        b->err = std::string("solve_batched: ") + cudaGetErrorString(e);
+        return SAMG_E_CUDA;
+    }
+    for (int p = 0; p < np; ++p)
+        if (state[p] == 2) {
+            b->err = "problem " + std::to_string(p) + " reached max_outer before the tolerance";
+            return SAMG_E_NOT_CONVERGED;
+        }
+    return SAMG_OK;
 }
 
 samg_status samg_batch_problem(samg_batch *b, int problem, samg_ctx **ctx) {

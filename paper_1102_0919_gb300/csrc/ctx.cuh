@@ -175,7 +175,10 @@ template <typename T> void coarse_solve(samg_ctx &c);
 template <typename T> void vcycle(samg_ctx &c, int l);
 template <typename T> void outer_vcycle(samg_ctx &c);   // defect form on (U, V)
 
-void ritz(samg_ctx &c, bool identity);  // identity: residuals of the current triplets only
+// identity: residuals of the current triplets only; check: wait for the
+// step's status and raise on linearly dependent boot vectors (false: the
+// caller reads rstat[0] later)
+void ritz(samg_ctx &c, bool identity, bool check = true);
 void host_setup(samg_ctx &c, const samg_csr &A);  // multiplicative phase (setup.cu)
 // Sec. 6.3: new interpolation operators by one downward sweep of the
 // multiplicative phase, LS weights of the test vectors and of the converged

@@ -413,7 +413,7 @@ __global__ void k_identity(int ld, double *T) {
     if (q < ld * ld) T[q] = (q / ld == q % ld) ? 1.0 : 0.0;
 }
 
-void ritz(samg_ctx &c, bool identity) {
+void ritz(samg_ctx &c, bool identity, bool check) {
     Level &L0 = c.L[0];
     const int ld = c.ld, nb = c.nb;
     cudaStream_t s = c.stream;
@@ -465,7 +465,7 @@ void ritz(samg_ctx &c, bool identity) {
                       c.resid.p, s);
     std::swap(c.U, c.Un);
     if (!c.spd()) std::swap(c.V, c.Vn);
-    if (!identity) {
+    if (!identity && check) {
         int st = 0;
         SAMG_CUDA(cudaMemcpyAsync(&st, c.rstat.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SAMG_CUDA(cudaStreamSynchronize(s));

@@ -56,3 +56,29 @@ def test_batched_small_gap_with_guard_pairs():
             assert np.allclose(lam[:4], laplacian5_eigs(N, e)[:4], rtol=1e-9)
     finally:
         b.close()
+
+
+def test_concurrent_rounds_match_solving_each_problem_alone():
+    # samg_solve_batched runs the problems in rounds on their own streams;
+    # each problem's iterations and triplets equal those of its own context
+    # solved alone (same setup, same arithmetic, float64)
+    ids = [0, 5, 9, 10]
+    probs = _problems(ids)
+    As = [W.laplacian5(N, e).to_scipy() for N, e in probs]
+    prm = dict(W.FD_PARAMS, seed=W.problem_seed(5))
+    b = samg.Batch.setup(As, 4, "minimal", "spd", prec="fp64", **prm)
+    try:
+        ok, done = b.solve(1e-10, 200)
+        assert ok, done
+        for k, A in enumerate(As):
+            s = samg.Solver.setup(A, 4, "minimal", "spd", prec="fp64", **prm)
+            try:
+                ok1, it1 = s.solve(1e-10, 200)
+                assert ok1 and it1 == done[k], (ids[k], it1, done[k])
+                lam1 = s.triplets()[0]
+                lam = b.problem(k).triplets()[0]
+                assert np.allclose(lam, lam1, rtol=1e-13), (ids[k], lam, lam1)
+            finally:
+                s.close()
+    finally:
+        b.close()
