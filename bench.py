@@ -586,7 +586,8 @@ def batched_workload(dev, stream, ids=(0, 2, 5, 6, 9, 10)):
                 "unknowns": int(sum(N * N for N, _ in probs)), "setup_s": round(t_setup, 2),
                 "value": ev0.elapsed_time(ev1) / 1e3, "unit": "s", "converged": bool(ok),
                 "outer_iterations": [int(x) for x in done], "lambda_relerr_max": err,
-                "note": "problems solved one after another on one stream (no fused kernels)"}
+                "note": "samg_solve_batched: rounds of one outer iteration per unconverged problem, "
+                        "each problem on its own stream (no fused cross-problem kernels)"}
     except Exception as e:  # noqa: BLE001 -- the main line must still print
         return {"error": "%s: %s" % (type(e).__name__, e)}
 
