@@ -334,8 +334,10 @@ samg_status samg_profile_read(samg_ctx *ctx, int kernel_class, int reset, int64_
  *   7 Ritz steps (Sec. 4.3)
  *   8 completion of the solve-phase hierarchy
  *   9 the rest (test-vector draw, injections, uploads)
- * Writes min(count, SAMG_SETUP_STAGES) values.  SAMG_E_INVALID: ctx or
- * seconds NULL, or count < 0. */
+ * A samg_redo_interpolation (or a redo inside samg_solve) adds its
+ * downward sweep's time to the same stages.  Writes min(count,
+ * SAMG_SETUP_STAGES) values.  SAMG_E_INVALID: ctx or seconds NULL, or
+ * count < 0. */
 #define SAMG_SETUP_STAGES 10
 samg_status samg_setup_times(const samg_ctx *ctx, double *seconds, int32_t count);
 
