@@ -216,3 +216,31 @@ def replay(S, x, rhs=None, shift=None):
         if publish:
             progress[b] = nxt[b]
     return x
+
+
+def claim_model(S, ctas, order=None, handoff=2.0):
+    """Completion time of a schedule in a model of the device: `ctas` CTAs
+    claim bands in ticket order (`order`, default the schedule's own); a
+    band holds its CTA from its claim to its last level; a level takes one
+    unit and starts after the band's previous level and, for each
+    requirement, `handoff` units after the required level ended."""
+    import heapq
+    nb = S["nbands"]
+    order = [int(v) for v in (S["order"] if order is None else order)]
+    bc, lvl, req = S["band_chunk"], S["lvl"], S["req"]
+    fin = [None] * nb
+    free = [0.0] * ctas
+    for b in order:
+        t = heapq.heappop(free)
+        f = []
+        if bc[b] < bc[b + 1]:
+            L0 = S["chunks"][bc[b]]["L0"]
+            last = S["chunks"][bc[b + 1] - 1]
+            for L in range(L0, last["L0"] + last["nl"]):
+                for bb, need in req[lvl[L, 0]:lvl[L, 0] + lvl[L, 1]]:
+                    t = max(t, fin[int(bb)][int(need) - 1] + handoff)
+                t += 1.0
+                f.append(t)
+        fin[b] = f
+        heapq.heappush(free, t)
+    return max(f[-1] for f in fin if f)

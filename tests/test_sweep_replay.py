@@ -10,7 +10,7 @@ import scipy.sparse as sp
 
 import oracle
 import workloads as W
-from sweep_replay import check_claim_order, parse, replay
+from sweep_replay import check_claim_order, claim_model, parse, replay
 
 samg = pytest.importorskip("paper_1102_0919_gb300")
 
@@ -243,6 +243,25 @@ def test_claim_order_is_safe_for_any_cta_count(name):
     assert S["nbands"] >= 4
     for ctas in (1, 2, 5, S["nbands"]):
         check_claim_order(S, ctas)
+
+
+def test_claim_order_keeps_the_relaxations_wavefronts_resident():
+    # with more bands than CTAs (here 3 per CTA, as on the coarse levels of
+    # the 1024^2 gradient: about 500 bands on 152 SMs), program order makes
+    # CTAs hold the bands of a sweep's last lines, which the wavefront
+    # reaches late, while the next relaxation's first bands wait; in a model
+    # of the claims (unit levels, handoffs of two) the schedule's own order
+    # finishes at least a quarter sooner, and with a CTA per band both equal
+    # the unlimited time
+    S = parse(samg.sweep_schedule(_nine_point(120), 4, band_rows=4))
+    nb = S["nbands"]
+    assert nb >= 60
+    ctas = nb // 3
+    prog = claim_model(S, ctas, order=range(nb))
+    mine = claim_model(S, ctas)
+    free = claim_model(S, nb)
+    assert mine <= 0.75 * prog, (mine, prog, free)
+    assert claim_model(S, nb, order=range(nb)) == free <= mine
 
 
 def test_empty_rows_and_a_single_row():
