@@ -264,6 +264,41 @@ def test_claim_order_keeps_the_relaxations_wavefronts_resident():
     assert claim_model(S, nb, order=range(nb)) == free <= mine
 
 
+@pytest.mark.parametrize("spd", [False, True])
+def test_no_band_crosses_a_sweep_of_a_fused_program(spd):
+    # the next relaxation's first bands must depend only on the first bands
+    # of the one before (the claim order relies on it): every band's rows
+    # lie inside one sweep of the program (rows of A or of A^t of one
+    # relaxation; one stacked sweep of the SPD kind)
+    if spd:
+        A = W.laplacian5(60, 0.3).to_scipy()
+        count = 3
+        S = parse(samg.sweep_schedule(A, count, spd=True, band_rows=8))
+        seg = [k * A.shape[0] for k in range(1, count)]
+    else:
+        A = W.gradient(64).to_scipy()
+        m, n = A.shape
+        count = 3
+        S = parse(samg.sweep_schedule(A, count, band_rows=8))
+        seg = sorted({k * (m + n) for k in range(1, count)} | {k * (m + n) + m for k in range(count)})
+    assert S["nbands"] > count
+    # program rows of each band, from the images' row records: right-hand
+    # side rows repeat per relaxation, so rebuild program rows from the
+    # band's position in program order (bands are contiguous row ranges)
+    starts = []
+    row = 0
+    bc = S["band_chunk"]
+    for b in range(S["nbands"]):
+        starts.append(row)
+        for c in range(bc[b], bc[b + 1]):
+            row += S["chunks"][c]["nr"]
+    starts.append(row)
+    assert row == S["rows"]
+    for b in range(S["nbands"]):
+        lo, hi = starts[b], starts[b + 1]
+        assert not any(lo < x < hi for x in seg), (b, lo, hi)
+
+
 def test_empty_rows_and_a_single_row():
     # rows without entries leave x unchanged; a one-row program is one level
     A = sp.csr_matrix(np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 0.0], [0.0, 0.0, 0.0],
