@@ -14,7 +14,10 @@ Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``):
   * a hand-computed Ruge-Stueben coarsening, exact LS recovery of a known
     interpolation, Galerkin matvec identities, Kaczmarz projection
     identities, Ritz exactness on exact subspaces, and the additive =
-    multiplicative identity of Eq. e.
+    multiplicative identity of Eq. e;
+  * the square SVD forms of Sec. 5.1 (R23) against LAPACK on an upwind
+    convection-diffusion operator, and the Sec. 6.3 redo (R22): iterate
+    kept, weighted misfit of the favoured vectors not raised.
 
 Parity unpinned: the per-cycle convergence rates of the figures (the
 figures are not in the available text) and the setup constants the paper
@@ -24,5 +27,6 @@ from .samg import (DEFAULTS, Hierarchy, Level, coarse_geneig, coarsest_pinv_appl
                    coarsest_triplets,
                    dense_XY, fit_interp, galerkin, hierarchy_from_interp, interp_sets, kaczmarz_sweep,
                    kaczmarz_sweep_coloured, colour_order, row_colours,
-                   level_residual, random_block, rayleigh, relax_boot, relax_test, residual_norms,
+                   level_residual, random_block, rayleigh, redo_interpolation, relax_boot,
+                   relax_test, residual_norms,
                    ritz, rs_coarsen, setup, solve, strength, vcycle)
