@@ -475,7 +475,10 @@ samg_status samg_row_colours(const samg_csr *A, int32_t *colour, int32_t *ncolou
  * entry a (f64); per entry b (f64, shifted programs only); per staged value
  * its column (i32); per carried requirement {band, levels that band must
  * have completed} (2 x i32, nq of them).  Returns SAMG_E_INVALID for a
- * malformed CSR or a short buffer. */
+ * malformed CSR or a short buffer.  The schedule is built on up
+ * to SAMG_HOST_THREADS host threads (environment variable; default: the
+ * hardware's, at most 16), as every schedule the library builds, and does
+ * not depend on their number. */
 samg_status samg_sweep_schedule(const samg_csr *A, const samg_csr *B, const samg_csr *C,
                                 int fused_count, int spd, int resident_slots, int band_rows,
                                 int slot_cap, unsigned char *buf,

@@ -2,9 +2,13 @@
 // exact-order Kaczmarz relaxation of Sec. 5.3 (see kaczmarz.cuh).
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <memory>
 #include <mutex>
 #include <queue>
+#include <thread>
 #include <type_traits>
 
 #include "kaczmarz.cuh"
@@ -963,17 +967,62 @@ int write_image(std::vector<unsigned char> &img, bool shifted, const std::vector
 
 namespace {
 
+// Runs fn(worker, b) for b in [0, n) on up to `threads` host threads (band
+// b taken from a shared counter); the first exception is rethrown.
+template <typename F>
+void for_bands(int n, int threads, F &&fn) {
+    threads = std::max(1, std::min(threads, n));
+    std::atomic<int> next{0};
+    std::exception_ptr err;
+    std::mutex mu;
+    auto work = [&](int t) {
+        for (;;) {
+            const int b = next.fetch_add(1);
+            if (b >= n) return;
+            try {
+                fn(t, b);
+            } catch (...) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (!err) err = std::current_exception();
+                next.store(n);
+                return;
+            }
+        }
+    };
+    if (threads == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (std::thread &th : pool) th.join();
+    }
+    if (err) std::rethrow_exception(err);
+}
+
+// Host threads of the schedule builder: SAMG_HOST_THREADS when set (>= 1),
+// else the hardware's, at most 16 (each holds five arrays over the columns).
+int builder_threads() {
+    if (const char *e = std::getenv("SAMG_HOST_THREADS")) {
+        const int v = std::atoi(e);
+        if (v >= 1) return std::min(v, 64);
+    }
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(h ? h : 1u, 16u));
+}
+
 // Contiguous bands of rows, each grown (doubling) until it has about
 // `target` rows per level, at most MAX_BAND_ROWS rows, and at most slot_cap
 // columns live at once.  Returns the first row of every band, then p.rows.
 std::vector<int> form_bands_at(const Pattern &p, const std::vector<int> &glv, BandWork &w,
-                               int slot_cap, int target) {
+                               int slot_cap, int target, int from = 0, int to = -1) {
     std::vector<int> bstart;
     int slots = 0;
     size_t si = 0;
-    for (int r0 = 0; r0 < p.rows;) {
+    if (to < 0) to = p.rows;
+    for (int r0 = from; r0 < to;) {
         while (si < p.seg.size() && p.seg[si] <= r0) ++si;
-        const int r_end = si < p.seg.size() ? p.seg[si] : p.rows;  // this sweep's end
+        const int r_end = std::min(to, si < p.seg.size() ? p.seg[si] : p.rows);  // this sweep's end
         int R = std::min(256, r_end - r0), good = 0;
         for (;;) {
             int nl = analyze_band(p, glv, r0, r0 + R, w, &slots);
@@ -990,7 +1039,7 @@ std::vector<int> form_bands_at(const Pattern &p, const std::vector<int> &glv, Ba
         bstart.push_back(r0);
         r0 += good;
     }
-    bstart.push_back(p.rows);
+    bstart.push_back(to);
     return bstart;
 }
 
@@ -1059,13 +1108,35 @@ std::vector<int> form_bands(const Pattern &p, const std::vector<int> &glv, BandW
         analyze_band(p, glv, 0, p.rows, w, &slots);
         if (slots <= resident_cap) return {0, p.rows};
     }
-    return form_bands_at(p, glv, w, slot_cap, band_rows > 0 ? band_rows : TARGET_PAR);
+    const int target = band_rows > 0 ? band_rows : TARGET_PAR;
+    if (p.seg.empty() || p.rows == 0) return form_bands_at(p, glv, w, slot_cap, target);
+    // no band crosses a sweep: the sweeps are banded independently, each from
+    // its first row, on several host threads
+    std::vector<int> cut{0};
+    for (int x : p.seg)
+        if (x > cut.back() && x < p.rows) cut.push_back(x);
+    cut.push_back(p.rows);
+    const int nseg = (int)cut.size() - 1;
+    std::vector<std::vector<int>> part(nseg);
+    const int nthr = std::min(builder_threads(), nseg);
+    std::vector<std::unique_ptr<BandWork>> works(nthr);
+    for (auto &wp : works) wp.reset(new BandWork(p.cols));
+    for_bands(nseg, nthr, [&](int t, int k) {
+        part[k] = form_bands_at(p, glv, *works[t], slot_cap, target, cut[k], cut[k + 1]);
+    });
+    std::vector<int> bstart;
+    for (int k = 0; k < nseg; ++k) bstart.insert(bstart.end(), part[k].begin(), part[k].end() - 1);
+    bstart.push_back(p.rows);
+    return bstart;
 }
 
 // Schedule of one sweep program (rows in program order).  mode: 0 plain rows
-// of A; 1 rows of A - s_j B (norms formed per column); 2 a fused program of
+// of A; 1 rows of A - s B (norms formed per column); 2 a fused program of
 // block Gauss-Seidel relaxations (b entries read the other unknown with
-// coefficient -s_j and are not updated; norms from a).
+// coefficient -s_j and are not updated; norms from a).  The bands are
+// analysed, given their requirements and written out on several host
+// threads; every step that orders or numbers things across bands is a
+// sequential pass, so the schedule does not depend on the thread count.
 void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
                 int slot_cap = SLOT_CAP, int band_rows = 0) {
     const int rows = p.rows, cols = p.cols;
@@ -1073,32 +1144,60 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
     ks.cols = cols;
     ks.shifted = mode != 0;
     ks.mode = mode;
-    BandWork w(cols);
     const std::vector<int> glv = global_levels(p);
-    // 1. bands: contiguous rows, grown until about TARGET_PAR rows per level
-    std::vector<int> bstart = form_bands(p, glv, w, resident_cap, slot_cap, band_rows);
+    // 1. bands: contiguous rows, grown until about band_rows rows per level
+    std::vector<int> bstart;
+    {
+        BandWork w(cols);
+        bstart = form_bands(p, glv, w, resident_cap, slot_cap, band_rows);
+    }
     const int nb = (int)bstart.size() - 1;
-    int slots = 0;
     ks.nbands = nb;
-    // 2. per band: levels, window slots, sub-levels (<= chunk limits), chunks
-    std::vector<int> band_chunk(nb + 1, 0);
-    std::vector<int4> lvl;  // per level: {first req, requirement count, publish, 0}
-    std::vector<KChunk> chunk;
-    std::vector<unsigned char> img_f, img_d;
-    std::vector<int2> req;
-    std::vector<int> g_band(cols, -1), g_sub(cols, 0), slot(cols, 0), last_sub(cols, 0);
-    std::vector<int> waited(nb, 0), waited_stamp(nb, -1);
-    int64_t nent = 0;
-    int max_slots = 0;
-    std::vector<std::vector<int>> pub(nb);  // per band: band-local sub-levels to publish
-    std::vector<int> band_lvl0(nb + 1, 0);
-    std::vector<int> lvl_chunk;  // per (global) level: its chunk
-    struct PendReq { int sub, band, need; };
+    // per row its band; per entry the previous row touching the column (-1:
+    // none); per column its first row
+    std::vector<int> band_of(rows, 0), prev(p.ci.size(), -1), first_row(cols, -1);
+    for (int b = 0; b < nb; ++b)
+        for (int r = bstart[b]; r < bstart[b + 1]; ++r) band_of[r] = b;
+    {
+        std::vector<int> last(cols, -1);
+        for (int r = 0; r < rows; ++r)
+            for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
+                const int c = p.ci[e];
+                prev[e] = last[c];
+                last[c] = r;
+                if (first_row[c] < 0) first_row[c] = r;
+            }
+    }
+    // a first touch in band b of a column no earlier band touched: its value
+    // is final when the band starts (staged)
+    auto fresh = [&](int c, int b) { return band_of[first_row[c]] == b; };
+    const int nthr = builder_threads();
+    std::vector<std::unique_ptr<BandWork>> works(std::min(nthr, std::max(nb, 1)));
+    for (auto &wp : works) wp.reset(new BandWork(cols));
     struct RowRec { int row, sub; };
-    for (int b = 0; b < nb; ++b) {
+    struct Band {
+        int nl = 0, slots = 0, nsub = 0;
+        std::vector<RowRec> rr;                          // rows in sub-level order
+        std::vector<int> sub_rows, sub_ents, sub_xs, sub_maxe;
+        std::vector<int2> req;                           // requirements, sub-level order
+        std::vector<int> sub_req0, sub_nreq;             // per sub-level: first, count
+        std::vector<int2> pub;                           // {band, sub-level} to publish
+        std::vector<KChunk> chunk;                       // offsets local to the band
+        std::vector<int> lvl_chunk;                      // per sub-level: local chunk
+        std::vector<unsigned char> img_f, img_d;
+        int64_t nent = 0;
+    };
+    std::vector<Band> B(nb);
+    std::vector<int> row_sub(rows, 0);
+    // per worker: window slots by column
+    std::vector<std::vector<int>> slot_of(works.size());
+    // 2a. per band: levels, rows by level, sub-levels (<= chunk limits)
+    for_bands(nb, (int)works.size(), [&](int t, int b) {
+        BandWork &w = *works[t];
+        Band &bd = B[b];
         const int r0 = bstart[b], r1 = bstart[b + 1];
-        int nl = analyze_band(p, glv, r0, r1, w, &slots);
-        max_slots = std::max(max_slots, slots);
+        const int nl = analyze_band(p, glv, r0, r1, w, &bd.slots);
+        bd.nl = nl;
         // rows grouped by level (ascending row order inside a level)
         std::vector<int> lcount(nl + 1, 0);
         for (int r = r0; r < r1; ++r) lcount[w.rowlv[r - r0] + 1]++;
@@ -1108,6 +1207,108 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
             std::vector<int> fillp(lcount.begin(), lcount.end() - 1);
             for (int r = r0; r < r1; ++r) order[fillp[w.rowlv[r - r0]]++] = r;
         }
+        // sub-levels: a level's independent rows split so that each piece
+        // fits one staging chunk
+        for (int l = 0; l < nl; ++l) {
+            int cr = 0, ce = 0, cx = 0;
+            bool open = false;
+            for (int k = lcount[l]; k < lcount[l + 1]; ++k) {
+                const int r = order[k];
+                const int ne = (int)(p.rp[r + 1] - p.rp[r]);
+                int nx = 0;
+                for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
+                    const int c = p.ci[e];
+                    if (w.firstlv[c] == l && fresh(c, b)) ++nx;
+                }
+                if (!open || cr + 1 > KZ_CHR || ce + ne > KZ_CHE || cx + nx > KZ_CHX) {
+                    bd.sub_rows.push_back(0); bd.sub_ents.push_back(0); bd.sub_xs.push_back(0);
+                    bd.sub_maxe.push_back(0);
+                    cr = ce = cx = 0;
+                    open = true;
+                }
+                SAMG_CHECK(ne <= KZ_CHE && nx <= KZ_CHX, SAMG_E_INVALID,
+                           "kaczmarz: a row has more entries than a staging chunk holds");
+                cr += 1; ce += ne; cx += nx;
+                bd.sub_rows.back() = cr; bd.sub_ents.back() = ce; bd.sub_xs.back() = cx;
+                bd.sub_maxe.back() = std::max(bd.sub_maxe.back(), ne);
+                const int sub = (int)bd.sub_rows.size() - 1;
+                bd.rr.push_back({r, sub});
+                row_sub[r] = sub;
+            }
+        }
+        bd.nsub = (int)bd.sub_rows.size();
+    });
+    // 2b. per band: requirements.  A first touch of a column an earlier band
+    // touched needs that band to have completed the sub-level of its last
+    // touch, which is the previous touch of the column in program order.
+    std::vector<std::vector<int>> waited(works.size()), waited_stamp(works.size());
+    for (size_t t = 0; t < works.size(); ++t) {
+        waited[t].assign(nb, 0);
+        waited_stamp[t].assign(nb, -1);
+    }
+    for_bands(nb, (int)works.size(), [&](int t, int b) {
+        BandWork &w = *works[t];
+        Band &bd = B[b];
+        const int r0 = bstart[b], r1 = bstart[b + 1];
+        int slots = 0;
+        analyze_band(p, glv, r0, r1, w, &slots);
+        struct PendReq { int sub, band, need; };
+        std::vector<PendReq> pend;
+        for (const RowRec &x : bd.rr) {
+            const int lv = w.rowlv[x.row - r0];
+            for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e) {
+                const int c = p.ci[e];
+                if (w.firstlv[c] == lv && prev[e] >= 0 && prev[e] < r0)
+                    pend.push_back({x.sub, band_of[prev[e]], row_sub[prev[e]] + 1});
+            }
+        }
+        // per sub-level: max need per band, dropping needs already waited for
+        std::sort(pend.begin(), pend.end(), [](const PendReq &a, const PendReq &b2) {
+            return a.sub != b2.sub ? a.sub < b2.sub : (a.band != b2.band ? a.band < b2.band : a.need > b2.need);
+        });
+        std::vector<int> &wt = waited[t], &ws = waited_stamp[t];
+        bd.sub_req0.assign(bd.nsub, 0);
+        bd.sub_nreq.assign(bd.nsub, 0);
+        size_t q = 0;
+        for (int l = 0; l < bd.nsub; ++l) {
+            bd.sub_req0[l] = (int)bd.req.size();
+            while (q < pend.size() && pend[q].sub == l) {
+                const PendReq &pr = pend[q];
+                if (ws[pr.band] != b || wt[pr.band] < pr.need) {
+                    ws[pr.band] = b;
+                    wt[pr.band] = pr.need;
+                    bd.req.push_back(make_int2(pr.band, pr.need));
+                    bd.pub.push_back(make_int2(pr.band, pr.need - 1));
+                }
+                const int bb = pr.band;
+                while (q < pend.size() && pend[q].sub == l && pend[q].band == bb) ++q;
+            }
+            bd.sub_nreq[l] = (int)bd.req.size() - bd.sub_req0[l];
+        }
+    });
+    // 2c. global level records and requirement list, in band order
+    std::vector<int> band_lvl0(nb + 1, 0);
+    std::vector<int4> lvl;  // per level: {first req, requirement count, publish, 0}
+    std::vector<int2> req;
+    int max_slots = 0;
+    for (int b = 0; b < nb; ++b) {
+        Band &bd = B[b];
+        band_lvl0[b] = (int)lvl.size();
+        const int base = (int)req.size();
+        for (int l = 0; l < bd.nsub; ++l) lvl.push_back(make_int4(base + bd.sub_req0[l], bd.sub_nreq[l], 0, 0));
+        req.insert(req.end(), bd.req.begin(), bd.req.end());
+        max_slots = std::max(max_slots, bd.slots);
+    }
+    band_lvl0[nb] = (int)lvl.size();
+    // 2d. per band: window slots, chunks and their images
+    for (size_t t = 0; t < works.size(); ++t) slot_of[t].assign(cols, 0);
+    for_bands(nb, (int)works.size(), [&](int t, int b) {
+        BandWork &w = *works[t];
+        std::vector<int> &slot = slot_of[t];
+        Band &bd = B[b];
+        const int r0 = bstart[b], r1 = bstart[b + 1];
+        int slots = 0;
+        const int nl = analyze_band(p, glv, r0, r1, w, &slots);
         // window slots by interval colouring over levels
         std::vector<std::vector<int>> starts(nl), ends(nl);
         for (int c : w.touched)
@@ -1126,73 +1327,8 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
                 for (int c : ends[l]) freel.push_back(slot[c]);
             }
         }
-        // sub-levels: a level's independent rows split so that each piece fits
-        // one staging chunk
-        std::vector<RowRec> rr;
-        std::vector<int> sub_rows, sub_ents, sub_xs, sub_maxe;  // per sub-level counts
-        for (int l = 0; l < nl; ++l) {
-            int cr = 0, ce = 0, cx = 0;
-            bool open = false;
-            for (int k = lcount[l]; k < lcount[l + 1]; ++k) {
-                const int r = order[k];
-                const int ne = (int)(p.rp[r + 1] - p.rp[r]);
-                int nx = 0;
-                for (int64_t e = p.rp[r]; e < p.rp[r + 1]; ++e) {
-                    const int c = p.ci[e];
-                    if (w.firstlv[c] == l && g_band[c] < 0) ++nx;
-                }
-                if (!open || cr + 1 > KZ_CHR || ce + ne > KZ_CHE || cx + nx > KZ_CHX) {
-                    sub_rows.push_back(0); sub_ents.push_back(0); sub_xs.push_back(0);
-                    sub_maxe.push_back(0);
-                    cr = ce = cx = 0;
-                    open = true;
-                }
-                SAMG_CHECK(ne <= KZ_CHE && nx <= KZ_CHX, SAMG_E_INVALID,
-                           "kaczmarz: a row has more entries than a staging chunk holds");
-                cr += 1; ce += ne; cx += nx;
-                sub_rows.back() = cr; sub_ents.back() = ce; sub_xs.back() = cx;
-                sub_maxe.back() = std::max(sub_maxe.back(), ne);
-                rr.push_back({r, (int)sub_rows.size() - 1});
-            }
-        }
-        const int nsub = (int)sub_rows.size();
-        for (const RowRec &x : rr)
-            for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e)
-                if (w.lastlv[p.ci[e]] == w.rowlv[x.row - r0]) last_sub[p.ci[e]] = x.sub;
-        // requirements: a first touch of a column last written by an earlier
-        // band needs that band to have completed the sub-level of its last touch
-        const int L0 = (int)lvl.size();
-        band_lvl0[b] = L0;
-        band_chunk[b] = (int)chunk.size();
-        std::vector<PendReq> pend;
-        for (const RowRec &x : rr) {
-            const int lv = w.rowlv[x.row - r0];
-            for (int64_t e = p.rp[x.row]; e < p.rp[x.row + 1]; ++e) {
-                const int c = p.ci[e];
-                if (w.firstlv[c] == lv && g_band[c] >= 0) pend.push_back({x.sub, g_band[c], g_sub[c] + 1});
-            }
-        }
-        // per sub-level: max need per band, dropping needs already waited for
-        std::sort(pend.begin(), pend.end(), [](const PendReq &a, const PendReq &b2) {
-            return a.sub != b2.sub ? a.sub < b2.sub : (a.band != b2.band ? a.band < b2.band : a.need > b2.need);
-        });
-        lvl.resize(L0 + nsub, int4{0, 0, 0, 0});
-        size_t q = 0;
-        for (int l = 0; l < nsub; ++l) {
-            lvl[L0 + l].x = (int)req.size();
-            while (q < pend.size() && pend[q].sub == l) {
-                const PendReq &pr = pend[q];
-                if (waited_stamp[pr.band] != b || waited[pr.band] < pr.need) {
-                    waited_stamp[pr.band] = b;
-                    waited[pr.band] = pr.need;
-                    req.push_back(make_int2(pr.band, pr.need));
-                    pub[pr.band].push_back(pr.need - 1);
-                }
-                const int bb = pr.band;
-                while (q < pend.size() && pend[q].sub == l && pend[q].band == bb) ++q;
-            }
-            lvl[L0 + l].y = (int)req.size() - lvl[L0 + l].x;
-        }
+        const int L0 = band_lvl0[b];
+        const int nsub = bd.nsub;
         // chunks of consecutive sub-levels; a sub-level's requirements travel
         // in its chunk's image unless they alone exceed KZ_CHQ (then the
         // kernel reads them from the global list)
@@ -1201,13 +1337,13 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
         {
             int cl = 0, cr = 0, ce = 0, cx = 0, cq = 0;
             for (int q = 0; q < nsub; ++q) {
-                if (q == 0 || cl + 1 > KZ_CHL || cr + sub_rows[q] > KZ_CHR ||
-                    ce + sub_ents[q] > KZ_CHE || cx + sub_xs[q] > KZ_CHX ||
+                if (q == 0 || cl + 1 > KZ_CHL || cr + bd.sub_rows[q] > KZ_CHR ||
+                    ce + bd.sub_ents[q] > KZ_CHE || cx + bd.sub_xs[q] > KZ_CHX ||
                     cq + img_reqs(q) > KZ_CHQ) {
                     chunk_first_sub.push_back(q);
                     cl = cr = ce = cx = cq = 0;
                 }
-                cl += 1; cr += sub_rows[q]; ce += sub_ents[q]; cx += sub_xs[q]; cq += img_reqs(q);
+                cl += 1; cr += bd.sub_rows[q]; ce += bd.sub_ents[q]; cx += bd.sub_xs[q]; cq += img_reqs(q);
             }
         }
         // one image per chunk (chunk-local row and entry numbers)
@@ -1218,7 +1354,8 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
         std::vector<double> rinv, ca, cbv;
         std::vector<int> xc;
         for (int ch = 0; ch < nch; ++ch) {
-            const int q0 = chunk_first_sub[ch], q1 = ch + 1 < nch ? chunk_first_sub[ch + 1] : nsub;
+            const int q0 = chunk_first_sub[ch];
+            const int q1 = ch + 1 < nch ? chunk_first_sub[ch + 1] : nsub;
             lrec.clear(); qrec.clear(); rrec.clear(); erec.clear(); rinv.clear(); ca.clear();
             cbv.clear(); xc.clear(); rqrec.clear();
             for (int qq = q0; qq < q1; ++qq) {
@@ -1226,10 +1363,10 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
                 // (at most 32; 6 marks rows of more than 32 entries, whose lanes
                 // take two or more entries)
                 int lg = 0;
-                while (lg < 6 && (1 << lg) < sub_maxe[qq]) ++lg;
+                while (lg < 6 && (1 << lg) < bd.sub_maxe[qq]) ++lg;
                 const int row0 = (int)rrec.size();
-                for (; ri < rr.size() && rr[ri].sub == qq; ++ri) {
-                    const int r = rr[ri].row;
+                for (; ri < bd.rr.size() && bd.rr[ri].sub == qq; ++ri) {
+                    const int r = bd.rr[ri].row;
                     const int lv = w.rowlv[r - r0];
                     const int e0 = (int)erec.size();
                     double n2 = 0.0;
@@ -1239,7 +1376,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
                         // window slot + 1; slot 0 is scratch for columns touched once
                         const int sl = (w.cnt[c] >= 2) ? slot[c] + 1 : 0;
                         int staged = 0, xi = 0;
-                        if (first && g_band[c] < 0) {
+                        if (first && fresh(c, b)) {
                             staged = 1;
                             xi = (int)xc.size();
                             xc.push_back(c);
@@ -1262,7 +1399,7 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
                 } else {
                     qrec.push_back(make_int2(g.x, -g.y - 1));
                 }
-                lvl_chunk.push_back((int)chunk.size());
+                bd.lvl_chunk.push_back((int)bd.chunk.size());
             }
             KChunk ck{};
             ck.L0 = L0 + q0;
@@ -1271,17 +1408,43 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
             ck.ne = (int)erec.size();
             ck.nx = (int)xc.size();
             ck.nq = (int)rqrec.size();
-            ck.off_f = (long long)img_f.size();
-            ck.off_d = (long long)img_d.size();
-            ck.bytes_f = write_image<float>(img_f, ks.shifted, lrec, qrec, rrec, rinv, erec, ca, cbv, xc, rqrec);
-            ck.bytes_d = write_image<double>(img_d, ks.shifted, lrec, qrec, rrec, rinv, erec, ca, cbv, xc, rqrec);
+            ck.off_f = (long long)bd.img_f.size();
+            ck.off_d = (long long)bd.img_d.size();
+            ck.bytes_f = write_image<float>(bd.img_f, ks.shifted, lrec, qrec, rrec, rinv, erec, ca, cbv, xc, rqrec);
+            ck.bytes_d = write_image<double>(bd.img_d, ks.shifted, lrec, qrec, rrec, rinv, erec, ca, cbv, xc, rqrec);
+            bd.chunk.push_back(ck);
+            bd.nent += ck.ne;
+        }
+        bd.rr.clear();
+        bd.rr.shrink_to_fit();
+    });
+    // 2e. concatenation in band order
+    std::vector<int> band_chunk(nb + 1, 0);
+    std::vector<KChunk> chunk;
+    std::vector<int> lvl_chunk;  // per (global) level: its chunk
+    std::vector<unsigned char> img_f, img_d;
+    int64_t nent = 0;
+    {
+        size_t tf = 0, td = 0;
+        for (const Band &bd : B) { tf += bd.img_f.size(); td += bd.img_d.size(); }
+        img_f.reserve(tf);
+        img_d.reserve(td);
+    }
+    for (int b = 0; b < nb; ++b) {
+        Band &bd = B[b];
+        band_chunk[b] = (int)chunk.size();
+        const long long of = (long long)img_f.size(), od = (long long)img_d.size();
+        for (KChunk ck : bd.chunk) {
+            ck.off_f += of;
+            ck.off_d += od;
             chunk.push_back(ck);
-            nent += ck.ne;
         }
-        for (int c : w.touched) {
-            g_band[c] = b;
-            g_sub[c] = last_sub[c];
-        }
+        for (int lc : bd.lvl_chunk) lvl_chunk.push_back(band_chunk[b] + lc);
+        img_f.insert(img_f.end(), bd.img_f.begin(), bd.img_f.end());
+        img_d.insert(img_d.end(), bd.img_d.begin(), bd.img_d.end());
+        std::vector<unsigned char>().swap(bd.img_f);
+        std::vector<unsigned char>().swap(bd.img_d);
+        nent += bd.nent;
     }
     band_chunk[nb] = (int)chunk.size();
     // publish flags: levels a later band waits for, and every band's last
@@ -1299,9 +1462,8 @@ void build_host(const Pattern &p, int mode, HostSched &ks, int resident_cap = 0,
         f |= 2;
         std::memcpy(img_d.data() + ck.off_d + at, &f, 4);
     };
-    band_lvl0[nb] = (int)lvl.size();
     for (int b = 0; b < nb; ++b) {
-        for (int l : pub[b]) set_publish(band_lvl0[b] + l);
+        for (const int2 &pb : B[b].pub) set_publish(band_lvl0[pb.x] + pb.y);
         set_publish(band_lvl0[b + 1] - 1);
     }
     ks.nlevels = (int)lvl.size();

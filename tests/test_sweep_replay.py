@@ -299,6 +299,21 @@ def test_no_band_crosses_a_sweep_of_a_fused_program(spd):
         assert not any(lo < x < hi for x in seg), (b, lo, hi)
 
 
+def test_schedules_do_not_depend_on_the_host_thread_count(monkeypatch):
+    # the builder analyses and writes bands on several host threads; every
+    # ordering step is sequential, so one thread and several give the same
+    # bytes (fused program with Galerkin-like 2-D rows, single sweep, SPD)
+    import hashlib
+    cases = [(_nine_point(70), 4, {}), (W.gradient(80).to_scipy(), 0, {}),
+             (oracle.samg._csr(W.laplacian5(30, 0.3).to_scipy()), 2, {"spd": True})]
+    for A, count, kw in cases:
+        digests = []
+        for threads in ("1", "3", "8"):
+            monkeypatch.setenv("SAMG_HOST_THREADS", threads)
+            digests.append(hashlib.sha256(samg.sweep_schedule(A, count, band_rows=8, **kw)).hexdigest())
+        assert len(set(digests)) == 1, digests
+
+
 def test_empty_rows_and_a_single_row():
     # rows without entries leave x unchanged; a one-row program is one level
     A = sp.csr_matrix(np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 0.0], [0.0, 0.0, 0.0],
